@@ -53,7 +53,7 @@ class Params(C.Structure):
 def params(**kw) -> Params:
     """Defaults: tolerance 5e-7 and h0 = 10 (Sec. II); the rest are our readings."""
     d = dict(rtol=5e-7, atol=5e-7, h0=10.0, safety=0.9, fac_min=0.2, fac_max=10.0, h_min=1e-10,
-             land_tol=1e-7, max_steps=10_000_000, land_max_iter=8, stop_mode=0, term_mask=T_ALL,
+             land_tol=1e-7, max_steps=1_000_000, land_max_iter=8, stop_mode=0, term_mask=T_ALL,
              theta_mode=0, fixed_step=0, pad_=0)
     d.update(kw)
     return Params(**d)

@@ -406,7 +406,7 @@ int32_t validate(const OBinary& b) {
 bool params_ok(const OParams& p) {
   return p.rtol >= 0.0 && p.atol >= 0.0 && (p.rtol > 0.0 || p.atol > 0.0) && p.h0 > 0.0 &&
          p.safety > 0.0 && p.fac_min > 0.0 && p.fac_max >= 1.0 && p.fac_min <= 1.0 && p.h_min >= 0.0 &&
-         p.land_tol > 0.0 && p.max_steps > 0 && p.land_max_iter >= 0;
+         p.land_tol > 0.0 && p.max_steps > 0 && p.land_max_iter >= 1;
 }
 
 // Root in (0, 1] of the cubic Hermite interpolant of omega over one step:
@@ -426,9 +426,20 @@ double hermite_root(double w0, double d0, double w1, double d1, double wf) {
   return s;
 }
 
-// Adaptive integration of one binary.  If hs != nullptr the accepted step
-// sizes (including the final landing step) are appended to it; if tr != nullptr
-// the state after every accepted step is appended (t, y[10]).
+// Adaptive integration of one binary, one DP5 attempt per loop iteration.
+// Mode STEP: ordinary steps under error control.  An accepted attempt whose
+// omega reaches omega_f either ends the run (STOP_FIRST_CROSS), lands at once
+// if it is already within land_tol, or switches to mode LAND, which retakes
+// the step from its start (t, y) with Newton-updated sizes until omega is
+// within land_tol of omega_f, then moves the state along f onto omega_f.
+// A run ends with PN status codes:
+//   MAX_STEPS    max_steps attempts made without finishing (the state is the
+//                last committed one; if it happens during LAND, the last retake),
+//   H_UNDERFLOW  a rejection pushed h below h_min,
+//   NONFINITE    an attempt produced a non-finite state or error norm,
+//   LAND_MAXIT   land_max_iter retakes did not reach land_tol (last retake kept).
+// If hs != nullptr the accepted step sizes (the landing step last) are appended;
+// if tr != nullptr the state after every accepted step is appended (t, y[10]).
 OResult integrate_one(const OBinary& b, const OParams& p, std::vector<double>* hs,
                       std::vector<double>* tr) {
   OResult r;
@@ -447,81 +458,71 @@ OResult integrate_one(const OBinary& b, const OParams& p, std::vector<double>* h
   double k[7][10], y5[10];
   rhs(ms, p, y, k[0]);
   bool last_rejected = false;
+  bool landing = false;
+  double h_lo = 0.0, h_hi = 0.0;
+  int land_it = 0;
   int64_t attempts = 0;
   if (tr) { tr->push_back(t); for (int i = 0; i < 10; i++) tr->push_back(y[i]); }
 
+  auto commit = [&](double hc) {
+    t = t + hc;
+    for (int i = 0; i < 10; i++) y[i] = y5[i];
+    r.n_acc++;
+    if (hs) hs->push_back(hc);
+    if (tr) { tr->push_back(t); for (int i = 0; i < 10; i++) tr->push_back(y[i]); }
+  };
+  auto land = [&](double g) {  // first-order move of the retaken state onto omega_f
+    const double dh = -g / k[6][0];
+    for (int i = 0; i < 10; i++) y5[i] = y5[i] + dh * k[6][i];
+    commit(h + dh);
+  };
+
   for (;;) {
-    if (attempts >= p.max_steps) { r.status = ST_MAX_STEPS; break; }
-    attempts++;
     dp5_attempt(ms, p, y, h, k, y5);
-    double err = p.fixed_step ? 0.0 : err_norm(p, y, y5, h, k);
+    attempts++;
+    const double err = p.fixed_step ? 0.0 : err_norm(p, y, y5, h, k);
     if (!all_finite(y5, 10) || !std::isfinite(err)) { r.status = ST_NONFINITE; break; }
-    if (err <= 1.0) {
-      if (y5[0] >= b.omega_f) {
-        if (p.stop_mode == 1) {  // first crossing: keep the overshooting state
-          t = t + h;
-          for (int i = 0; i < 10; i++) y[i] = y5[i];
-          r.n_acc++;
-          if (hs) hs->push_back(h);
-          if (tr) { tr->push_back(t); for (int i = 0; i < 10; i++) tr->push_back(y[i]); }
-          r.status = ST_OK;
-          break;
-        }
-        // Land on omega_f.  Start from the root of the cubic Hermite
-        // interpolant of omega over the overshooting step, then retake the
-        // step from (t, y) with Newton updates on g(h) = omega5(h) - omega_f,
-        // slope = omega-rate of the last stage, kept inside the bracket
-        // (h_lo, h_hi) in which g changes sign, until |g| <= land_tol omega_f.
-        // The converged retake is finally moved along f by dh = -g / domega/dt,
-        // which puts omega on omega_f up to O(dh^2).
-        double h_lo = 0.0, h_hi = h;
-        double hstar = h;
-        double g = y5[0] - b.omega_f;
-        bool done = std::fabs(g) <= p.land_tol * b.omega_f;
-        double hn = h * hermite_root(y[0], h * k[0][0], y5[0], h * k[6][0], b.omega_f);
-        int it = 0;
-        while (!done && it < p.land_max_iter) {
-          it++;
-          if (!(hn > h_lo && hn < h_hi)) hn = 0.5 * (h_lo + h_hi);
-          if (attempts >= p.max_steps) break;
-          attempts++;
-          r.n_land++;
-          dp5_attempt(ms, p, y, hn, k, y5);
-          if (!all_finite(y5, 10)) break;
-          g = y5[0] - b.omega_f;
-          hstar = hn;
-          if (std::fabs(g) <= p.land_tol * b.omega_f) { done = true; break; }
-          if (g > 0.0) h_hi = hn; else h_lo = hn;
-          hn = hn - g / k[6][0];
-        }
-        if (!all_finite(y5, 10)) { r.status = ST_NONFINITE; break; }
-        double dh = 0.0;
-        if (done) {
-          dh = -g / k[6][0];
-          for (int i = 0; i < 10; i++) y5[i] = y5[i] + dh * k[6][i];
-        }
-        t = t + (hstar + dh);
-        for (int i = 0; i < 10; i++) y[i] = y5[i];
-        r.n_acc++;
-        if (hs) hs->push_back(hstar + dh);
-        if (tr) { tr->push_back(t); for (int i = 0; i < 10; i++) tr->push_back(y[i]); }
-        r.status = done ? ST_OK : (attempts >= p.max_steps ? ST_MAX_STEPS : ST_LAND_MAXIT);
+
+    if (landing) {
+      r.n_land++;
+      land_it++;
+      const double g = y5[0] - b.omega_f;
+      if (std::fabs(g) <= p.land_tol * b.omega_f) { land(g); r.status = ST_OK; break; }
+      if (land_it >= p.land_max_iter || attempts >= p.max_steps) {
+        commit(h);
+        r.status = attempts >= p.max_steps ? ST_MAX_STEPS : ST_LAND_MAXIT;
         break;
       }
-      // Accept.
-      t = t + h;
-      for (int i = 0; i < 10; i++) { y[i] = y5[i]; k[0][i] = k[6][i]; }
-      r.n_acc++;
-      if (hs) hs->push_back(h);
-      if (tr) { tr->push_back(t); for (int i = 0; i < 10; i++) tr->push_back(y[i]); }
-      if (!p.fixed_step) {
-        double fac = (err == 0.0) ? p.fac_max : p.safety * std::pow(err, -0.2);
-        const double fmax = last_rejected ? 1.0 : p.fac_max;
-        if (fac > fmax) fac = fmax;
-        if (fac < p.fac_min) fac = p.fac_min;
-        h = h * fac;
+      if (g > 0.0) h_hi = h; else h_lo = h;
+      h = h - g / k[6][0];
+      if (!(h > h_lo && h < h_hi)) h = 0.5 * (h_lo + h_hi);
+      continue;
+    }
+
+    if (err <= 1.0) {
+      if (y5[0] >= b.omega_f) {
+        const double g = y5[0] - b.omega_f;
+        if (p.stop_mode == 1) { commit(h); r.status = ST_OK; break; }
+        if (std::fabs(g) <= p.land_tol * b.omega_f) { land(g); r.status = ST_OK; break; }
+        // Seed the retakes from the root of the step's cubic Hermite interpolant.
+        landing = true;
+        land_it = 0;
+        h_lo = 0.0;
+        h_hi = h;
+        const double hn = h * hermite_root(y[0], h * k[0][0], y5[0], h * k[6][0], b.omega_f);
+        h = (hn > h_lo && hn < h_hi) ? hn : 0.5 * (h_lo + h_hi);
+      } else {
+        commit(h);
+        for (int i = 0; i < 10; i++) k[0][i] = k[6][i];  // first same as last
+        if (!p.fixed_step) {
+          double fac = (err == 0.0) ? p.fac_max : p.safety * std::pow(err, -0.2);
+          const double fmax = last_rejected ? 1.0 : p.fac_max;
+          if (fac > fmax) fac = fmax;
+          if (fac < p.fac_min) fac = p.fac_min;
+          h = h * fac;
+        }
+        last_rejected = false;
       }
-      last_rejected = false;
     } else {
       r.n_rej++;
       double fac = p.safety * std::pow(err, -0.2);
@@ -531,6 +532,7 @@ OResult integrate_one(const OBinary& b, const OParams& p, std::vector<double>* h
       last_rejected = true;
       if (h < p.h_min) { r.status = ST_H_UNDERFLOW; break; }
     }
+    if (attempts >= p.max_steps) { r.status = ST_MAX_STEPS; break; }
   }
   for (int i = 0; i < 10; i++) r.y[i] = y[i];
   r.t = t;
