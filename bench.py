@@ -1,0 +1,338 @@
+#!/usr/bin/env python
+"""Throughput benchmark of the batched PN inspiral integrator on B300.
+
+One step = one pass of the hot path over one batch: integrate the
+1,048,576-binary ensemble (equal mass, chi_i ~ U[0,1], isotropic spins,
+M omega 0.01 -> 0.05; Dormand-Prince 5(4) at tolerance 5e-7, h0 = 10, stop on
+omega_f) with the inputs resident in HBM.  Prints one JSON line.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun each rank integrates its own ensemble (a different seed) of the
+same size: independent binaries, no data exchange ("scaling": "weak").
+"""
+from __future__ import annotations
+
+import argparse
+import csv
+import ctypes as C
+import hashlib
+import io
+import json
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "inspirals/sec (Mω 0.01→0.05) & % FP64 peak; mixed vs FP64 at ≤1e-6 dot err"
+WORKLOAD = ("1,048,576 binaries, m1 = m2 = 0.5, chi_i ~ U[0,1], isotropic spin directions, L-hat = z, "
+            "M omega 0.01 -> 0.05, DP5(4) tol 5e-7, h0 = 10, stop on omega_f")
+
+# Algorithmic floating-point operations of one Dormand-Prince attempt, as the
+# plain FP64 formulation counts them (each +, -, *, / one operation; no FMA):
+# the right-hand side of Eqs. (1)-(4) is 118 operations (+ 1 cbrt + 1 log) and
+# is evaluated 6 times per attempt; the stages, the error norm and the step
+# control add 633 (+ 1 sqrt + 1 pow).  tests/test_bench_constants.py checks
+# these against the oracle's operation counter.
+FLOPS_RHS = 118
+FLOPS_STEP = 633
+FLOPS_ATTEMPT = 6 * FLOPS_RHS + FLOPS_STEP
+
+# DRAM traffic of the integration kernel per binary from an ncu capture
+# (dram__bytes_read.sum + dram__bytes_write.sum, profiles/); valid only while
+# the kernel sources hash to KERNEL_SHA.
+PROFILED = {"kernel_sha": None, "dram_bytes_per_binary": None}
+
+
+def kernel_sha() -> str:
+    h = hashlib.sha256()
+    for f in ("pn_device.cuh", "pn_kernels.cu", "pn_internal.h"):
+        with open(os.path.join(ROOT, "paper_0908_3889_b300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
+    ap.add_argument("--n", type=int, default=1_048_576, help="binaries per rank (default: the full workload)")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-mixed", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms during the timed region."""
+
+    def __init__(self, index: int):
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--query-gpu={q}", "--format=csv,noheader,nounits",
+                                       "-i", str(index), "-lms", "200"], stdout=subprocess.PIPE,
+                                      stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.p = None
+
+    def stop(self) -> dict:
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.p.terminate()
+        out, _ = self.p.communicate(timeout=10)
+        sm, smax, reasons = [], [], set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for row in csv.reader(io.StringIO(out)):
+            if len(row) < 9:
+                continue
+            try:
+                sm.append(float(row[1]))
+                smax.append(float(row[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, row[5:9]):
+                if v.strip().lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def peak_probe():
+    from paper_0908_3889_b300.build import PEAK_LIB
+    lib = C.CDLL(PEAK_LIB)
+    lib.pn_peak_probe.argtypes = [C.POINTER(C.c_double), C.POINTER(C.c_double)]
+    f64, f32 = C.c_double(), C.c_double()
+    if lib.pn_peak_probe(C.byref(f64), C.byref(f32)) != 0:
+        return None, None
+    return f64.value, f32.value
+
+
+def cpu_oracle_rate(ens, target_s: float = 10.0, threads: int = 0):
+    """Time the CPU oracle on a bounded sample of the ensemble (about target_s seconds)."""
+    import oracle
+    import workloads
+    n_all = ens["m1"].shape[0]
+    calib = workloads.take(ens, np.arange(min(2048, n_all)))
+    oracle.integrate(calib, threads=threads)  # builds/loads the oracle
+    t0 = time.perf_counter()
+    r = oracle.integrate(calib, threads=threads)
+    dt = time.perf_counter() - t0
+    rate = calib["m1"].shape[0] / dt
+    m = int(min(n_all, max(2048, rate * target_s)))
+    sample = workloads.take(ens, np.arange(m))
+    t0 = time.perf_counter()
+    r = oracle.integrate(sample, threads=threads)
+    dt = time.perf_counter() - t0
+    return m / dt, m, int(r["threads_used"]), dt
+
+
+def reference_arm(args, rank, world):
+    """The oracle, as it stands, on the host cores: the base contract's reference arm for this path."""
+    if rank != 0:
+        return
+    import workloads
+    ens = workloads.config("C1", n=args.n)
+    _, m, threads, _ = cpu_oracle_rate(ens, target_s=1.0)
+    per_step = max(1024, m)
+    import oracle
+    total, count = 0.0, 0
+    for s in range(args.warmup + args.steps):
+        idx = (np.arange(per_step) + s * per_step) % ens["m1"].shape[0]
+        sample = workloads.take(ens, idx)
+        t0 = time.perf_counter()
+        oracle.integrate(sample)
+        dt = time.perf_counter() - t0
+        if s >= args.warmup:
+            total += dt
+            count += per_step
+    value = count / total
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "inspirals/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "sample_per_step": per_step, "device": "host CPU"},
+            "cpu_baseline": {"value": value, "unit": "inspirals/s", "cores": threads, "kind": "oracle",
+                             "sample": f"{per_step} binaries of the 1,048,576-binary ensemble per step"},
+            "e2e": {"value": value, "unit": "inspirals/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse_args()
+    rank, world, local = dist_env()
+    if args.impl == "reference":
+        reference_arm(args, rank, world)
+        return
+
+    import torch
+    import paper_0908_3889_b300 as pn
+    import workloads
+    from paper_0908_3889_b300.build import build
+
+    if world > 1:
+        import torch.distributed as tdist
+        torch.cuda.set_device(local)
+        tdist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    else:
+        tdist = None
+        torch.cuda.set_device(0)
+    if rank == 0:
+        build()
+    if tdist:
+        tdist.barrier()
+    dev = torch.device("cuda", torch.cuda.current_device())
+
+    def barrier():
+        if tdist:
+            tdist.barrier()
+        torch.cuda.synchronize()
+
+    def max_over_ranks(x: float) -> float:
+        if not tdist:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device=dev)
+        tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
+        return float(t.item())
+
+    n = args.n
+    ens = workloads.config("C1", n=n, seed=workloads.SEED_BASE + 1 + 1000 * rank)
+    inp = pn.to_device(ens, device=dev)
+    out = pn.alloc_outputs(n, dev)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)  # 256 MB > L2 (126 MB)
+
+    f64_peak, f32_peak = peak_probe()
+
+    def timed_run(b, steps, warmup):
+        for _ in range(warmup):
+            b.integrate(inp, out)
+        barrier()
+        clocks = ClockSampler(torch.cuda.current_device()) if rank == 0 else None
+        t_wall0 = time.perf_counter()
+        total_ms = 0.0
+        stream = torch.cuda.current_stream()
+        for _ in range(steps):
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            b.integrate(inp, out)
+            e1.record(stream)
+            e1.synchronize()
+            total_ms += e0.elapsed_time(e1)
+        barrier()
+        wall = time.perf_counter() - t_wall0
+        ck = clocks.stop() if clocks else None
+        return total_ms, wall, ck
+
+    # FP64 headline.
+    prm = pn.params(precision=0)
+    with pn.Batch(n, prm) as b:
+        tune = b.autotune(inp)
+        total_ms, wall, clocks = timed_run(b, args.steps, args.warmup)
+        st = b.stats(inp, out)
+    total_ms = max_over_ranks(total_ms)
+    ms_step = total_ms / args.steps
+    value = world * n * args.steps / (total_ms * 1e-3)
+    attempts = st["acc_total"] + st["rej_total"] + st["land_total"]
+    flops_launch = FLOPS_ATTEMPT * attempts
+    achieved = flops_launch / (ms_step * 1e-3)
+    fp64_out = {k: out[k].clone() for k in ("dot_s1s2", "dot_ls1", "dot_ls2", "status")}
+    sha = kernel_sha()
+    traffic = (PROFILED["dram_bytes_per_binary"] * n
+               if PROFILED["kernel_sha"] == sha and PROFILED["dram_bytes_per_binary"] else None)
+    roof = {"bound": "alu", "achieved": achieved / 1e12, "peak": (f64_peak or 0) / 1e12, "unit": "TFLOP/s",
+            "frac": achieved / f64_peak if f64_peak else None, "traffic": traffic,
+            "pipe": "FP64", "peak_source": "FP64 FMA throughput measured live by the peak probe (2 flops per FMA)",
+            "flops_per_attempt": FLOPS_ATTEMPT, "attempts_per_launch": attempts,
+            "kernel": "pn::k_integrate<FP64>"}
+
+    # Mixed precision on the same ensemble.
+    mixed = None
+    if not args.no_mixed:
+        with pn.Batch(n, pn.params(precision=1)) as b:
+            b.autotune(inp)
+            mix_ms, _, _ = timed_run(b, args.steps, 1)
+            mst = b.stats(inp, out)
+        mix_ms = max_over_ranks(mix_ms)
+        ok = (fp64_out["status"] == 0) & (out["status"] == 0)
+        errs = {}
+        for k in ("dot_s1s2", "dot_ls1", "dot_ls2"):
+            d = (out[k] - fp64_out[k]).abs()[ok & torch.isfinite(fp64_out[k])]
+            errs[k] = {"max": float(d.max()), "p99": float(torch.quantile(d[:1_000_000].float(), 0.99)),
+                       "p50": float(d.median())}
+        m_attempts = mst["acc_total"] + mst["rej_total"] + mst["land_total"]
+        mixed = {"value": world * n * args.steps / (mix_ms * 1e-3), "unit": "inspirals/s",
+                 "ms_per_step": mix_ms / args.steps, "speedup_vs_fp64": total_ms / mix_ms,
+                 "dot_err_vs_fp64": errs, "fp64_pipe_achieved_tflops": (FLOPS_STEP * m_attempts) /
+                 (mix_ms / args.steps * 1e-3) / 1e12, "fp32_peak_tflops": (f32_peak or 0) / 1e12}
+
+    # End to end through the host-buffer entry point (pinned host memory).
+    e2e = None
+    if not args.no_e2e:
+        hin = pn.to_device(ens, device="cpu", pin_memory=True)
+        hout = pn.alloc_outputs(n, pin_memory=True)
+        with pn.Batch(n, prm) as b:
+            b.autotune(inp)
+            for _ in range(max(1, args.warmup)):
+                pn.pn_batch_integrate_host(b.handle, n, hin, hout)
+            barrier()
+            t0 = time.perf_counter()
+            for _ in range(args.steps):
+                pn.pn_batch_integrate_host(b.handle, n, hin, hout)
+            barrier()
+            e2e_s = max_over_ranks(time.perf_counter() - t0)
+        e2e = {"value": world * n * args.steps / e2e_s, "unit": "inspirals/s",
+               "h2d_bytes_per_step": 15 * 8 * n, "d2h_bytes_per_step": (14 * 8 + 4 * 4) * n}
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        rate, m, threads, dt = cpu_oracle_rate(ens, target_s=10.0)
+        rate1, m1_, _, _ = cpu_oracle_rate(workloads.take(ens, np.arange(4096)), target_s=2.0, threads=1)
+        import oracle
+        pp = workloads.config("PAPER_PERF", n=64)
+        t0 = time.perf_counter()
+        oracle.integrate(pp, threads=1)
+        paper_rate = 64 / (time.perf_counter() - t0)
+        cpu = {"value": rate, "unit": "inspirals/s", "cores": threads, "kind": "oracle",
+               "sample": f"first {m} binaries of the ensemble ({dt:.1f} s on {threads} threads)",
+               "single_thread_value": rate1,
+               "paper_test_inspiral_single_thread": {"value": paper_rate, "unit": "inspirals/s",
+                                                      "workload": "one inspiral omega 0.004 -> 0.1, 64 copies",
+                                                      "paper_value_2009_xeon_e5410": 57.0}}
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": "inspirals/s", "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                "config": {"workload": WORKLOAD, "n_binaries_per_gpu": n, "precision": "fp64",
+                           "schedule": {1: "plain", 2: "persistent"}.get(tune["schedule"], tune["schedule"]),
+                           "block": tune["block"], "l2": "flushed before each step (256 MB write)",
+                           "parallelism": f"replicas x{world}", "attempts_per_binary": attempts / n,
+                           "kernel_sha": sha},
+                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": args.steps,
+                "clocks": clocks, "mixed": mixed,
+                "fp32_fma_peak_tflops": (f32_peak or 0) / 1e12, "fp64_fma_peak_tflops": (f64_peak or 0) / 1e12}
+        print(json.dumps(line), flush=True)
+    if tdist:
+        tdist.barrier()
+        tdist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,262 @@
+/*
+ * pn_batch.h -- C ABI of the B300 batched post-Newtonian inspiral integrator.
+ *
+ * Problem (arXiv:0908.3889, Herrmann et al. 2009, Sec. II):  for every binary
+ * black hole i, integrate the PN equations of motion Eqs. (1)-(4) -- the
+ * orbital frequency omega (Eq. 1), the spins S1, S2 precessing as
+ * dS_i/dt = Omega_i x S_i (Eqs. 2, 4) and the orbital axis L-hat (Eq. 3) --
+ * with total mass M = m1 + m2 = 1, S_i = chi_i m_i^2 S_i-hat, from a circular
+ * orbit at omega_0 with L-hat = z-hat (Sec. V) up to omega_f, with the
+ * Dormand-Prince 5(4) method at error tolerance 5e-7 and first step h = 10
+ * (Sec. II).  The binaries are independent ("embarrassingly parallel",
+ * Sec. I); one call integrates a whole batch on one GPU.
+ *
+ * Conventions for every entry point:
+ *  - Return value: PN_OK (0) or a negative PN_E_* code.  Per-binary failures
+ *    are not call errors: they are reported in outputs.status[i].  After an
+ *    error pn_last_error() describes it.
+ *  - Device pointers are caller-owned CUDA device memory (e.g. torch tensors),
+ *    float64 unless stated, one value per binary ("structure of arrays"),
+ *    each array at least n elements long and 8-byte aligned.  The library
+ *    never frees or retains them beyond the call's stream work.
+ *  - Calls are ordered on the stream given to pn_batch_init and return
+ *    without waiting for the GPU, except where a call says it synchronises.
+ *  - A pn_batch is not thread-safe: one host thread at a time per handle.
+ */
+#ifndef PN_BATCH_H
+#define PN_BATCH_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define PN_ABI_VERSION 1
+
+/* ---- return codes ---- */
+#define PN_OK 0
+#define PN_E_ARG (-1)           /* invalid argument (NULL, n out of range, bad parameter) */
+#define PN_E_CUDA (-2)          /* a CUDA runtime call or kernel launch failed */
+#define PN_E_NOMEM (-3)         /* device or host allocation failed */
+#define PN_E_UNIMPLEMENTED (-4) /* option not supported by this build */
+
+/* ---- per-binary status (outputs.status) ---- */
+#define PN_ST_OK 0
+#define PN_ST_MAX_STEPS 1   /* attempt budget params.max_steps exhausted */
+#define PN_ST_H_UNDERFLOW 2 /* step size fell below params.h_min after a rejection */
+#define PN_ST_NONFINITE 3   /* the state or the error estimate became NaN / Inf */
+#define PN_ST_BAD_INPUT 4   /* non-finite input, m_i <= 0, |m1+m2-1| > 1e-12, chi outside [0,1],
+                               omega_0 <= 0, omega_f <= omega_0, or | |L-hat_0| - 1 | > 1e-12 */
+#define PN_ST_LAND_MAXIT 5  /* the stop at omega_f did not converge in land_max_iter retakes */
+
+/* ---- parameter enums ---- */
+#define PN_FP64 0  /* everything in FP64 */
+#define PN_MIXED 1 /* right-hand side in FP32; stages, state, error estimate and step control in FP64 */
+
+#define PN_STOP_LAND 0        /* stop exactly on omega_f (default) */
+#define PN_STOP_FIRST_CROSS 1 /* stop at the first accepted state with omega >= omega_f */
+
+#define PN_THETA_BCV2 0       /* 3PN: theta-hat multiplies eta once (default reading) */
+#define PN_THETA_AS_PRINTED 1 /* 3PN: theta-hat eta^2, as the paper's Eq. (1) prints it */
+
+#define PN_SCHED_AUTO 0       /* use the autotuned choice if any, else persistent */
+#define PN_SCHED_PLAIN 1      /* one grid pass: BPT binaries per thread, fixed assignment */
+#define PN_SCHED_PERSISTENT 2 /* persistent grid, lanes refill from a device work queue */
+
+/* PN terms of Eq. (1) and the precession of Eqs. (2)-(4) (term_mask bits) */
+#define PN_TERM_1PN (1u << 0)  /* -(743 + 924 eta)/336 x^{2/3} */
+#define PN_TERM_SO (1u << 1)   /* 1.5PN spin-orbit sum */
+#define PN_TERM_TAIL (1u << 2) /* +4 pi x */
+#define PN_TERM_2PN (1u << 3)  /* non-spin 2PN */
+#define PN_TERM_SS (1u << 4)   /* 2PN spin-spin */
+#define PN_TERM_25PN (1u << 5)
+#define PN_TERM_3PN (1u << 6)  /* 3PN including the log */
+#define PN_TERM_35PN (1u << 7)
+#define PN_TERM_PREC (1u << 8) /* spin and L-hat precession; off freezes S_i and L-hat */
+#define PN_TERM_ALL 0x1ffu
+
+typedef struct {
+  /* Integrator (Sec. II gives the 5e-7 tolerance and h0 = 10; the rest are readings):
+   * a step is accepted when the RMS over the 10 state components of
+   * e_i / (atol + rtol * max(|y_i|, |y_new_i|)) is <= 1, e = h sum_j (b_j - bhat_j) k_j;
+   * the next step is h * clamp(safety * err^(-1/5), fac_min, fac_max), with no growth
+   * right after a rejection. */
+  double rtol;     /* default 5e-7 */
+  double atol;     /* default 5e-7 */
+  double h0;       /* first step, default 10 (units of M) */
+  double safety;   /* default 0.9 */
+  double fac_min;  /* default 0.2 */
+  double fac_max;  /* default 10 */
+  double h_min;    /* default 1e-10: a rejected step below this gives PN_ST_H_UNDERFLOW */
+  double land_tol; /* stop: Newton retakes until |omega - omega_f| <= land_tol * omega_f, then a
+                      first-order move along f lands omega on omega_f; default 1e-7 */
+  int64_t max_steps;     /* cap on attempts (accepted + rejected + landing retakes); default 1e6 */
+  int32_t land_max_iter; /* retakes allowed at the stop, default 8 */
+  int32_t stop_mode;     /* PN_STOP_* */
+  uint32_t term_mask;    /* PN_TERM_* bits, default PN_TERM_ALL */
+  int32_t theta_mode;    /* PN_THETA_* */
+  int32_t fixed_step;    /* 1: accept every attempt with h = h0 (convergence studies), default 0 */
+  int32_t precision;     /* PN_FP64 or PN_MIXED */
+  int32_t schedule;      /* PN_SCHED_* */
+  int32_t block;         /* threads per block (multiple of 32, <= 512); 0 = autotuned / default */
+  int32_t bpt;           /* binaries per thread, 1 or 2; 0 = autotuned / default */
+  int32_t ckpt_every;    /* adjoint: accepted steps between state checkpoints, default 64 */
+} pn_params;
+
+/* Inputs, one value per binary (device pointers).  Read-only for
+ * pn_batch_integrate / _adjoint / _stats; written by pn_batch_sample.
+ * s1*, s2*: spin directions S_i-hat (their raw components are used:
+ * S_i(0) = chi_i m_i^2 S_i-hat); l*: L-hat at omega_0 (unit); masses with
+ * m1 + m2 = 1. */
+typedef struct {
+  double *m1, *m2, *chi1, *chi2;
+  double *s1x, *s1y, *s1z, *s2x, *s2y, *s2z;
+  double *lx, *ly, *lz;
+  double *omega0, *omega_f;
+} pn_inputs;
+
+/* Outputs, one value per binary (device pointers, written by the call).
+ * S1, S2, L: final state (L is the evolved L-hat, not renormalised);
+ * omega, t: final frequency and time (t from 0 at omega_0);
+ * n_acc / n_rej / n_land: accepted steps (the final landing step counts once),
+ * rejected attempts, landing retakes (int32);  status: PN_ST_* (int32);
+ * dot_s1s2 = S1.S2/(|S1||S2|), dot_ls1 = L.S1/(|L||S1|), dot_ls2 likewise
+ * (Sec. V's scalar products; NaN when a spin is zero).  On PN_ST_BAD_INPUT
+ * the state, t and dots are NaN and the counters 0. */
+typedef struct {
+  double *S1x, *S1y, *S1z, *S2x, *S2y, *S2z, *Lx, *Ly, *Lz;
+  double *omega, *t;
+  int32_t *n_acc, *n_rej, *n_land, *status;
+  double *dot_s1s2, *dot_ls1, *dot_ls2;
+} pn_outputs;
+
+/* Distribution for pn_batch_sample (Sec. V: isotropic spin directions by
+ * Marsaglia's method; masses, spin magnitudes and omega_0 as configured). */
+typedef struct {
+  int32_t q_mode;   /* q = m1/m2: 0 fixed q_lo, 1 uniform [q_lo,q_hi], 2 log-uniform [q_lo,q_hi] */
+  int32_t chi_mode; /* chi_i: 0 fixed chi_lo, 1 uniform [chi_lo,chi_hi] (independent per BH) */
+  double q_lo, q_hi, chi_lo, chi_hi;
+  double omega0_lo, omega0_hi; /* omega_0 uniform in [lo, hi] (equal bounds: fixed) */
+  double omega_f;
+} pn_dist;
+
+/* Cotangents of a scalar loss with respect to the outputs (device pointers,
+ * length n; a NULL pointer means zero).  Used by pn_batch_adjoint. */
+typedef struct {
+  const double *dot_s1s2, *dot_ls1, *dot_ls2;
+  const double *Lx, *Ly, *Lz;
+  const double *S1x, *S1y, *S1z, *S2x, *S2y, *S2z;
+  const double *t;
+} pn_cotangents;
+
+/* Gradients written by pn_batch_adjoint (device pointers, length n): the loss
+ * differentiated with respect to the raw components of S1-hat(0), S2-hat(0)
+ * and the mass ratio q = m1/m2 (with M = 1 and chi_i fixed). */
+typedef struct {
+  double *s1x, *s1y, *s1z, *s2x, *s2y, *s2z;
+  double *q;
+} pn_grads;
+
+/* Batch statistics (host struct filled by pn_batch_stats). */
+typedef struct {
+  int64_t n;
+  int64_t count_by_status[8];
+  int64_t acc_total, rej_total, land_total;
+  int32_t acc_min, acc_max;
+  int32_t attempts_min, attempts_max;
+  /* Pearson r (Sec. V A) of initial vs final scalar products over binaries
+   * with status OK and finite products: S1-hat.S2-hat, L-hat.S1-hat, L-hat.S2-hat. */
+  double pearson_s1s2, pearson_ls1, pearson_ls2;
+  int64_t pearson_count;
+  double mean_final_s1s2, std_final_s1s2;
+  /* Device time of the last pn_batch_integrate / pn_batch_adjoint (ms, CUDA events). */
+  double ms_last_integrate, ms_last_adjoint;
+} pn_stats;
+
+/* Result of pn_batch_autotune. */
+typedef struct {
+  int32_t schedule, block, bpt;
+  int32_t n_candidates;
+  double best_ms;     /* time of the chosen configuration on the tuning prefix */
+  int64_t n_tuned;    /* binaries in the tuning prefix */
+} pn_tune_result;
+
+typedef struct pn_batch pn_batch; /* opaque: owns only its workspace */
+
+/* Library ABI version (PN_ABI_VERSION). */
+int pn_abi_version(void);
+
+/* Fill *p with the defaults listed in pn_params. */
+void pn_params_default(pn_params *p);
+
+/* Create a batch context for up to n_max binaries per call on the current
+ * CUDA device and the given stream (cudaStream_t, NULL = legacy default).
+ * Allocates the small device workspace (queue head, reduction buffers, the
+ * logarithm table) and records *p.  Errors: PN_E_ARG (NULL out/p, n_max < 1,
+ * bad parameters), PN_E_CUDA, PN_E_NOMEM.  *out is NULL on failure. */
+int pn_batch_init(pn_batch **out, int64_t n_max, const pn_params *p, void *cuda_stream);
+
+/* Replace the parameters (same validation as pn_batch_init). */
+int pn_batch_set_params(pn_batch *b, const pn_params *p);
+
+/* Draw n binaries of the distribution d into the caller's input arrays, from
+ * counter-based SplitMix64 uniforms keyed by (seed, binary index, draw number)
+ * (Sec. V; Marsaglia 1972 for the directions; L-hat = z-hat).  Draw j of
+ * binary i is the j-th output of the SplitMix64 stream seeded with the i-th
+ * output of the stream seeded with `seed`, as a 53-bit uniform; draws 0..3
+ * give q, chi1, chi2, omega_0 and draws 4.. the Marsaglia pairs for S1-hat
+ * then S2-hat.  Errors: PN_E_ARG (NULL pointers, n > n_max, bad d), PN_E_CUDA. */
+int pn_batch_sample(pn_batch *b, uint64_t seed, const pn_dist *d, int64_t n, const pn_inputs *in);
+
+/* Integrate binaries 0..n-1 of *in and write *out (asynchronous).
+ * 0 <= n <= n_max (n = 0 does nothing).  Errors: PN_E_ARG (NULL pointers,
+ * n out of range), PN_E_CUDA (launch failure).  Uses the schedule, block and
+ * binaries-per-thread of the parameters, or the autotuned choice for 0. */
+int pn_batch_integrate(pn_batch *b, int64_t n, const pn_inputs *in, pn_outputs *out);
+
+/* Same as pn_batch_integrate with HOST input and output arrays: copies the
+ * inputs to the library's device staging buffers (allocated on first use,
+ * n_max binaries), integrates, copies the outputs back and synchronises the
+ * stream.  Page-locked host memory gives the fastest copies.  Errors:
+ * PN_E_ARG, PN_E_NOMEM, PN_E_CUDA. */
+int pn_batch_integrate_host(pn_batch *b, int64_t n, const pn_inputs *host_in, pn_outputs *host_out);
+
+/* Time the candidate (schedule, block, binaries-per-thread) configurations of
+ * the current precision on the first min(n, 262144) binaries of *in (writing
+ * *scratch_out), keep the fastest for later calls with schedule/block/bpt = 0,
+ * and report it in *res (may be NULL).  Synchronises.  Errors: PN_E_ARG, PN_E_CUDA. */
+int pn_batch_autotune(pn_batch *b, int64_t n, const pn_inputs *in, pn_outputs *scratch_out,
+                      pn_tune_result *res);
+
+/* Reverse-mode gradient of L = sum_i gbar_i . outputs_i with respect to
+ * S1-hat(0), S2-hat(0) and q, through the accepted Dormand-Prince steps of
+ * the forward integration with the step sizes held fixed and the stop at
+ * omega_f differentiated as an implicit function (the landing step size h*
+ * solves omega(h*) = omega_f).  Runs the forward pass, records the accepted
+ * step sizes and a checkpoint every params.ckpt_every accepted steps in
+ * library-owned device memory (grown on demand), then sweeps backwards one
+ * checkpoint segment at a time, recomputing the segment's states.  Requires
+ * PN_STOP_LAND and PN_FP64; binaries whose status is not PN_ST_OK get NaN
+ * gradients.  If out is not NULL the forward outputs are written there too.
+ * Errors: PN_E_ARG, PN_E_NOMEM, PN_E_CUDA, PN_E_UNIMPLEMENTED (other modes). */
+int pn_batch_adjoint(pn_batch *b, int64_t n, const pn_inputs *in, const pn_cotangents *gbar,
+                     pn_grads *grad, pn_outputs *out);
+
+/* Reduce outputs 0..n-1 (and the initial scalar products of *in) into *host
+ * (counts per status, step totals, Pearson r of Sec. V A).  Synchronises.
+ * Errors: PN_E_ARG, PN_E_CUDA. */
+int pn_batch_stats(pn_batch *b, int64_t n, const pn_inputs *in, const pn_outputs *out, pn_stats *host);
+
+/* Release the workspace (waits for the stream).  NULL is ignored. */
+void pn_batch_destroy(pn_batch *b);
+
+/* Message of the last error on b (or of the last failed pn_batch_init on this
+ * thread when b is NULL); empty string if none.  Valid until the next call. */
+const char *pn_last_error(const pn_batch *b);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PN_BATCH_H */

@@ -1,0 +1,294 @@
+"""Python binding of the C ABI (include/pn_batch.h): same names, torch tensors for memory and streams.
+
+Every function here only marshals arguments; all of the integration runs in
+the CUDA library.  Ensembles are dicts of float64 tensors on one CUDA device:
+
+  inputs   m1, m2, chi1, chi2, omega0, omega_f: shape (n,)
+           s1hat, s2hat, lhat: shape (3, n), component-major (structure of arrays)
+  outputs  S1, S2, Lhat: (3, n); omega, t, dot_s1s2, dot_ls1, dot_ls2: (n,) float64;
+           n_acc, n_rej, n_land, status: (n,) int32
+"""
+from __future__ import annotations
+
+import ctypes as C
+from dataclasses import dataclass
+
+import numpy as np
+import torch
+
+from . import _native as N
+
+INPUT_KEYS = ("m1", "m2", "chi1", "chi2", "s1hat", "s2hat", "lhat", "omega0", "omega_f")
+VEC_INPUTS = ("s1hat", "s2hat", "lhat")
+OUTPUT_KEYS = ("S1", "S2", "Lhat", "omega", "t", "n_acc", "n_rej", "n_land", "status",
+               "dot_s1s2", "dot_ls1", "dot_ls2")
+_ERR = {N.PN_E_ARG: "PN_E_ARG", N.PN_E_CUDA: "PN_E_CUDA", N.PN_E_NOMEM: "PN_E_NOMEM",
+        N.PN_E_UNIMPLEMENTED: "PN_E_UNIMPLEMENTED"}
+
+
+class PNError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{_ERR.get(code, code)}: {msg}")
+        self.code = code
+
+
+def _lib():
+    return N.load()
+
+
+def _check(rc: int, handle) -> None:
+    if rc != N.PN_OK:
+        raise PNError(rc, (_lib().pn_last_error(handle) or b"").decode())
+
+
+def params(**kw) -> N.pn_params:
+    """pn_params with the library defaults, fields overridden by keyword."""
+    p = N.pn_params()
+    _lib().pn_params_default(C.byref(p))
+    for k, v in kw.items():
+        if not hasattr(p, k):
+            raise KeyError(k)
+        setattr(p, k, v)
+    return p
+
+
+def _dptr(t: torch.Tensor):
+    return C.cast(C.c_void_p(t.data_ptr()), C.POINTER(C.c_double))
+
+
+def _iptr(t: torch.Tensor):
+    return C.cast(C.c_void_p(t.data_ptr()), C.POINTER(C.c_int32))
+
+
+def _check_tensor(t: torch.Tensor, n: int, dtype, name: str, rows: int | None = None, device=None):
+    """Arrays may be longer than n (the C ABI reads elements 0..n-1); rows of a vector must be contiguous."""
+    if not isinstance(t, torch.Tensor):
+        raise TypeError(f"{name} must be a torch.Tensor")
+    if t.dtype != dtype:
+        raise TypeError(f"{name} must be {dtype}")
+    ok_shape = (t.dim() == 1 and rows is None) or (rows is not None and t.dim() == 2 and t.shape[0] == rows)
+    if not ok_shape or t.shape[-1] < n:
+        want = f"({n},)" if rows is None else f"({rows}, >= {n})"
+        raise ValueError(f"{name} has shape {tuple(t.shape)}, expected {want}")
+    if t.stride(-1) != 1:
+        raise ValueError(f"{name} must be contiguous along the binary index")
+    if device is not None and t.device != device:
+        raise ValueError(f"{name} is on {t.device}, expected {device}")
+
+
+def inputs_struct(inp: dict, n: int | None = None) -> N.pn_inputs:
+    n = int(inp["m1"].shape[0]) if n is None else n
+    dev = inp["m1"].device
+    for k in INPUT_KEYS:
+        _check_tensor(inp[k], n, torch.float64, k, 3 if k in VEC_INPUTS else None, dev)
+    s = N.pn_inputs()
+    for k in ("m1", "m2", "chi1", "chi2", "omega0", "omega_f"):
+        setattr(s, k, _dptr(inp[k]))
+    for k, pre in (("s1hat", "s1"), ("s2hat", "s2"), ("lhat", "l")):
+        for c, ax in enumerate("xyz"):
+            setattr(s, pre + ax, _dptr(inp[k][c]))
+    return s
+
+
+def outputs_struct(out: dict, n: int | None = None) -> N.pn_outputs:
+    n = int(out["omega"].shape[0]) if n is None else n
+    dev = out["omega"].device
+    s = N.pn_outputs()
+    for k, pre in (("S1", "S1"), ("S2", "S2"), ("Lhat", "L")):
+        _check_tensor(out[k], n, torch.float64, k, 3, dev)
+        for c, ax in enumerate("xyz"):
+            setattr(s, pre + ax, _dptr(out[k][c]))
+    for k in ("omega", "t", "dot_s1s2", "dot_ls1", "dot_ls2"):
+        _check_tensor(out[k], n, torch.float64, k, None, dev)
+        setattr(s, k, _dptr(out[k]))
+    for k in ("n_acc", "n_rej", "n_land", "status"):
+        _check_tensor(out[k], n, torch.int32, k, None, dev)
+        setattr(s, k, _iptr(out[k]))
+    return s
+
+
+def alloc_inputs(n: int, device="cuda", pin_memory: bool = False) -> dict:
+    """One (15, n) float64 block with per-field views."""
+    kw = dict(dtype=torch.float64, device=device)
+    blk = torch.empty((15, n), **kw) if not pin_memory else torch.empty((15, n), dtype=torch.float64, pin_memory=True)
+    d = {"m1": blk[0], "m2": blk[1], "chi1": blk[2], "chi2": blk[3], "s1hat": blk[4:7], "s2hat": blk[7:10],
+         "lhat": blk[10:13], "omega0": blk[13], "omega_f": blk[14]}
+    d["_block"] = blk
+    return d
+
+
+def alloc_outputs(n: int, device="cuda", pin_memory: bool = False) -> dict:
+    """One (14, n) float64 block and one (4, n) int32 block with per-field views."""
+    if pin_memory:
+        fb = torch.empty((14, n), dtype=torch.float64, pin_memory=True)
+        ib = torch.empty((4, n), dtype=torch.int32, pin_memory=True)
+    else:
+        fb = torch.empty((14, n), dtype=torch.float64, device=device)
+        ib = torch.empty((4, n), dtype=torch.int32, device=device)
+    return {"S1": fb[0:3], "S2": fb[3:6], "Lhat": fb[6:9], "omega": fb[9], "t": fb[10], "dot_s1s2": fb[11],
+            "dot_ls1": fb[12], "dot_ls2": fb[13], "n_acc": ib[0], "n_rej": ib[1], "n_land": ib[2], "status": ib[3],
+            "_block": fb, "_iblock": ib}
+
+
+def to_device(ens: dict, device="cuda", pin_memory: bool = False) -> dict:
+    """Copy a NumPy ensemble (workloads layout) into a fresh input block."""
+    n = int(np.asarray(ens["m1"]).shape[0])
+    d = alloc_inputs(n, device, pin_memory)
+    for k in INPUT_KEYS:
+        d[k].copy_(torch.from_numpy(np.ascontiguousarray(ens[k], dtype=np.float64)))
+    return d
+
+
+def to_numpy(out: dict) -> dict:
+    return {k: out[k].cpu().numpy() for k in OUTPUT_KEYS if k in out}
+
+
+# ---------------------------------------------------------------------------
+# The C ABI, function by function.
+# ---------------------------------------------------------------------------
+def pn_abi_version() -> int:
+    return _lib().pn_abi_version()
+
+
+def pn_batch_init(n_max: int, prm: N.pn_params | None = None, stream=None) -> C.c_void_p:
+    prm = prm or params()
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    sp = stream.cuda_stream if hasattr(stream, "cuda_stream") else stream
+    h = C.c_void_p()
+    _check(_lib().pn_batch_init(C.byref(h), int(n_max), C.byref(prm), C.c_void_p(sp)), None)
+    return h
+
+
+def pn_batch_set_params(h, prm: N.pn_params) -> None:
+    _check(_lib().pn_batch_set_params(h, C.byref(prm)), h)
+
+
+def pn_batch_sample(h, seed: int, dist: N.pn_dist, n: int, inputs: dict) -> None:
+    _check(_lib().pn_batch_sample(h, C.c_uint64(seed), C.byref(dist), int(n), C.byref(inputs_struct(inputs, n))), h)
+
+
+def pn_batch_integrate(h, n: int, inputs: dict, outputs: dict) -> None:
+    _check(_lib().pn_batch_integrate(h, int(n), C.byref(inputs_struct(inputs, n)),
+                                     C.byref(outputs_struct(outputs, n))), h)
+
+
+def _host_inputs_struct(inp: dict, n: int) -> N.pn_inputs:
+    for k in INPUT_KEYS:
+        _check_tensor(inp[k], n, torch.float64, k, 3 if k in VEC_INPUTS else None, torch.device("cpu"))
+    return inputs_struct(inp, n)
+
+
+def pn_batch_integrate_host(h, n: int, host_inputs: dict, host_outputs: dict) -> None:
+    """Host (CPU, ideally pinned) tensors in and out; copies happen inside the call, which synchronises."""
+    _check(_lib().pn_batch_integrate_host(h, int(n), C.byref(_host_inputs_struct(host_inputs, n)),
+                                          C.byref(outputs_struct(host_outputs, n))), h)
+
+
+def pn_batch_autotune(h, n: int, inputs: dict, scratch: dict) -> dict:
+    r = N.pn_tune_result()
+    _check(_lib().pn_batch_autotune(h, int(n), C.byref(inputs_struct(inputs, n)),
+                                    C.byref(outputs_struct(scratch, n)), C.byref(r)), h)
+    return {f: getattr(r, f) for f, _ in N.pn_tune_result._fields_}
+
+
+def pn_batch_adjoint(h, n: int, inputs: dict, cotangents: dict, grads: dict, outputs: dict | None = None) -> None:
+    cs = N.pn_cotangents()
+    dev = inputs["m1"].device
+    for f in N.COT_FIELDS:
+        t = cotangents.get(f)
+        if t is not None:
+            _check_tensor(t, n, torch.float64, f, None, dev)
+            setattr(cs, f, _dptr(t))
+    gs = N.pn_grads()
+    for f in N.GRAD_FIELDS:
+        _check_tensor(grads[f], n, torch.float64, f, None, dev)
+        setattr(gs, f, _dptr(grads[f]))
+    os_ = C.byref(outputs_struct(outputs, n)) if outputs is not None else None
+    _check(_lib().pn_batch_adjoint(h, int(n), C.byref(inputs_struct(inputs, n)), C.byref(cs), C.byref(gs), os_), h)
+
+
+def pn_batch_stats(h, n: int, inputs: dict, outputs: dict) -> dict:
+    s = N.pn_stats()
+    _check(_lib().pn_batch_stats(h, int(n), C.byref(inputs_struct(inputs, n)), C.byref(outputs_struct(outputs, n)),
+                                 C.byref(s)), h)
+    d = {f: getattr(s, f) for f, _ in N.pn_stats._fields_}
+    d["count_by_status"] = list(s.count_by_status)
+    return d
+
+
+def pn_batch_destroy(h) -> None:
+    if h:
+        _lib().pn_batch_destroy(h)
+
+
+def pn_last_error(h=None) -> str:
+    return (_lib().pn_last_error(h) or b"").decode()
+
+
+# ---------------------------------------------------------------------------
+# Conveniences.
+# ---------------------------------------------------------------------------
+@dataclass
+class Batch:
+    """Owns one pn_batch handle (use as a context manager)."""
+    n_max: int
+    prm: N.pn_params | None = None
+    stream: object = None
+
+    def __post_init__(self):
+        self.handle = pn_batch_init(self.n_max, self.prm, self.stream)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            pn_batch_destroy(self.handle)
+            self.handle = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_params(self, prm: N.pn_params):
+        pn_batch_set_params(self.handle, prm)
+
+    def integrate(self, inputs: dict, outputs: dict | None = None, n: int | None = None) -> dict:
+        n = int(inputs["m1"].shape[0]) if n is None else n
+        outputs = alloc_outputs(n, inputs["m1"].device) if outputs is None else outputs
+        pn_batch_integrate(self.handle, n, inputs, outputs)
+        return outputs
+
+    def sample(self, seed: int, dist: N.pn_dist, n: int, inputs: dict | None = None, device="cuda") -> dict:
+        inputs = alloc_inputs(n, device) if inputs is None else inputs
+        pn_batch_sample(self.handle, seed, dist, n, inputs)
+        return inputs
+
+    def stats(self, inputs: dict, outputs: dict, n: int | None = None) -> dict:
+        n = int(inputs["m1"].shape[0]) if n is None else n
+        return pn_batch_stats(self.handle, n, inputs, outputs)
+
+    def autotune(self, inputs: dict, n: int | None = None) -> dict:
+        n = int(inputs["m1"].shape[0]) if n is None else n
+        scratch = alloc_outputs(min(n, 262144) if n else 1, inputs["m1"].device)
+        # the scratch outputs only need to cover the tuning prefix
+        return pn_batch_autotune(self.handle, min(n, 262144), inputs, scratch)
+
+
+def dist(q=(1.0, 1.0), q_mode: int = 0, chi=(1.0, 1.0), chi_mode: int = 0, omega0=(0.01, 0.01),
+         omega_f: float = 0.05) -> N.pn_dist:
+    return N.pn_dist(q_mode=q_mode, chi_mode=chi_mode, q_lo=q[0], q_hi=q[1], chi_lo=chi[0], chi_hi=chi[1],
+                     omega0_lo=omega0[0], omega0_hi=omega0[1], omega_f=omega_f)
+
+
+def integrate(inputs: dict, **kw) -> dict:
+    """Integrate a device ensemble with the given parameter overrides; returns the output dict."""
+    n = int(inputs["m1"].shape[0])
+    with Batch(max(n, 1), params(**kw)) as b:
+        return b.integrate(inputs)

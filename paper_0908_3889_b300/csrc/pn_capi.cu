@@ -1,0 +1,488 @@
+// pn_capi.cu -- the extern "C" boundary declared in include/pn_batch.h.
+//
+// Host-side runtime of the integrator: parameter validation, the library's
+// small device workspace, launch-shape choice (schedule, block size) and its
+// autotuner, CUDA-graph capture of the persistent launch (queue reset +
+// kernel), the host-buffer entry point, and the statistics reduction.
+
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+
+#include "pn_internal.h"
+
+using pn::KArgs;
+
+struct pn_batch {
+  int64_t n_max = 0;
+  pn_params p{};
+  cudaStream_t stream = nullptr;
+  cudaStream_t cap_stream = nullptr;  // private stream used only for graph capture
+  int device = 0;
+  int num_sms = 0;
+  unsigned long long* d_queue = nullptr;
+  double* d_tab = nullptr;
+  double* d_stat_part = nullptr;
+  double* d_stat_total = nullptr;
+  double* d_setup = nullptr;  // per-binary set-up table, setup_fields() x n_max doubles
+  cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+  bool timed_integrate = false, timed_adjoint = false;
+  // graph of the last persistent launch
+  cudaGraphExec_t gexec = nullptr;
+  bool have_key = false;
+  KArgs key_args{};
+  int key_prec = -1, key_block = 0, key_grid = 0;
+  // autotuned launch shape per precision
+  struct Tuned {
+    bool valid = false;
+    int schedule = PN_SCHED_PERSISTENT, block = 128, bpt = 1;
+  } tuned[2];
+  // staging for pn_batch_integrate_host
+  double* d_stage_d = nullptr;
+  int32_t* d_stage_i = nullptr;
+  std::string err;
+};
+
+static thread_local std::string g_init_err;
+
+static int fail(pn_batch* b, int code, const std::string& msg) {
+  if (b) b->err = msg;
+  else g_init_err = msg;
+  return code;
+}
+
+static int cuda_fail(pn_batch* b, cudaError_t e, const char* what) {
+  char buf[256];
+  snprintf(buf, sizeof(buf), "%s: %s", what, cudaGetErrorString(e));
+  return fail(b, PN_E_CUDA, buf);
+}
+
+#define PN_CUDA(b, call)                               \
+  do {                                                 \
+    cudaError_t e_ = (call);                           \
+    if (e_ != cudaSuccess) return cuda_fail(b, e_, #call); \
+  } while (0)
+
+extern "C" int pn_abi_version(void) { return PN_ABI_VERSION; }
+
+extern "C" void pn_params_default(pn_params* p) {
+  if (!p) return;
+  std::memset(p, 0, sizeof(*p));
+  p->rtol = 5e-7;
+  p->atol = 5e-7;
+  p->h0 = 10.0;
+  p->safety = 0.9;
+  p->fac_min = 0.2;
+  p->fac_max = 10.0;
+  p->h_min = 1e-10;
+  p->land_tol = 1e-7;
+  p->max_steps = 1000000;
+  p->land_max_iter = 8;
+  p->stop_mode = PN_STOP_LAND;
+  p->term_mask = PN_TERM_ALL;
+  p->theta_mode = PN_THETA_BCV2;
+  p->fixed_step = 0;
+  p->precision = PN_FP64;
+  p->schedule = PN_SCHED_AUTO;
+  p->block = 0;
+  p->bpt = 0;
+  p->ckpt_every = 64;
+}
+
+// Parameter domain.  Besides the integrator's own constraints, atol >= 1e-30
+// and safety/fac_max >= 1e-3, safety/fac_min <= 1e3 keep the error-norm scales
+// and the step-control thresholds inside the FP32 normal range that the
+// kernels' FP32 seeds need.
+static bool params_valid(const pn_params* p, std::string* why) {
+  auto bad = [&](const char* m) { *why = m; return false; };
+  if (!(p->rtol >= 0.0 && std::isfinite(p->rtol))) return bad("rtol must be finite and >= 0");
+  if (!(p->atol >= 1e-30 && std::isfinite(p->atol))) return bad("atol must be finite and >= 1e-30");
+  if (!(p->h0 > 0.0 && std::isfinite(p->h0))) return bad("h0 must be finite and > 0");
+  if (!(p->safety > 0.0 && p->fac_min > 0.0 && p->fac_min <= 1.0 && p->fac_max >= 1.0 && std::isfinite(p->fac_max)))
+    return bad("need safety > 0 and 0 < fac_min <= 1 <= fac_max");
+  if (!(p->safety / p->fac_max >= 1e-3 && p->safety / p->fac_min <= 1e3))
+    return bad("need safety/fac_max >= 1e-3 and safety/fac_min <= 1e3");
+  if (!(p->h_min >= 0.0)) return bad("h_min must be >= 0");
+  if (!(p->land_tol > 0.0 && p->land_tol < 1.0)) return bad("land_tol must be in (0, 1)");
+  if (p->max_steps < 1) return bad("max_steps must be >= 1");
+  if (p->land_max_iter < 1) return bad("land_max_iter must be >= 1");
+  if (p->stop_mode != PN_STOP_LAND && p->stop_mode != PN_STOP_FIRST_CROSS) return bad("bad stop_mode");
+  if (p->theta_mode != PN_THETA_BCV2 && p->theta_mode != PN_THETA_AS_PRINTED) return bad("bad theta_mode");
+  if (p->term_mask & ~PN_TERM_ALL) return bad("unknown term_mask bits");
+  if (p->fixed_step != 0 && p->fixed_step != 1) return bad("fixed_step must be 0 or 1");
+  if (p->precision != PN_FP64 && p->precision != PN_MIXED) return bad("bad precision");
+  if (p->schedule < PN_SCHED_AUTO || p->schedule > PN_SCHED_PERSISTENT) return bad("bad schedule");
+  if (p->block != 0 && (p->block < 32 || p->block > pn::kMaxBlock || p->block % 32 != 0))
+    return bad("block must be 0 or a multiple of 32 in [32, 256]");
+  if (p->bpt != 0 && p->bpt != 1) return bad("bpt must be 0 or 1 in this build");
+  if (p->ckpt_every < 1) return bad("ckpt_every must be >= 1");
+  return true;
+}
+
+static pn::Ctl make_ctl(const pn_params& p) {
+  pn::Ctl c;
+  c.rtol = p.rtol;
+  c.atol = p.atol;
+  c.h0 = p.h0;
+  c.safety = p.safety;
+  c.fac_min = p.fac_min;
+  c.fac_max = p.fac_max;
+  c.h_min = p.h_min;
+  c.land_tol = p.land_tol;
+  c.s_lo = std::pow(p.safety / p.fac_max, 10.0);
+  c.s_hi = std::pow(p.safety / p.fac_min, 10.0);
+  c.max_steps = p.max_steps > 2147483647 ? 2147483647 : (int32_t)p.max_steps;
+  c.land_max_iter = p.land_max_iter;
+  c.stop_mode = p.stop_mode;
+  c.fixed_step = p.fixed_step;
+  c.terms.mask = p.term_mask;
+  c.terms.theta_mode = p.theta_mode;
+  c.pad_ = 0;
+  return c;
+}
+
+static bool inputs_ok(const pn_inputs* in) {
+  return in && in->m1 && in->m2 && in->chi1 && in->chi2 && in->s1x && in->s1y && in->s1z && in->s2x && in->s2y &&
+         in->s2z && in->lx && in->ly && in->lz && in->omega0 && in->omega_f;
+}
+static bool outputs_ok(const pn_outputs* o) {
+  return o && o->S1x && o->S1y && o->S1z && o->S2x && o->S2y && o->S2z && o->Lx && o->Ly && o->Lz && o->omega &&
+         o->t && o->n_acc && o->n_rej && o->n_land && o->status && o->dot_s1s2 && o->dot_ls1 && o->dot_ls2;
+}
+
+extern "C" const char* pn_last_error(const pn_batch* b) { return b ? b->err.c_str() : g_init_err.c_str(); }
+
+extern "C" void pn_batch_destroy(pn_batch* b) {
+  if (!b) return;
+  if (b->stream || true) cudaStreamSynchronize(b->stream);
+  if (b->gexec) cudaGraphExecDestroy(b->gexec);
+  if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
+  for (auto& e : b->ev)
+    if (e) cudaEventDestroy(e);
+  cudaFree(b->d_queue);
+  cudaFree(b->d_tab);
+  cudaFree(b->d_stat_part);
+  cudaFree(b->d_stat_total);
+  cudaFree(b->d_setup);
+  cudaFree(b->d_stage_d);
+  cudaFree(b->d_stage_i);
+  delete b;
+}
+
+extern "C" int pn_batch_init(pn_batch** out, int64_t n_max, const pn_params* p, void* cuda_stream) {
+  if (!out) return fail(nullptr, PN_E_ARG, "out is NULL");
+  *out = nullptr;
+  if (!p) return fail(nullptr, PN_E_ARG, "params is NULL");
+  if (n_max < 1) return fail(nullptr, PN_E_ARG, "n_max must be >= 1");
+  std::string why;
+  if (!params_valid(p, &why)) return fail(nullptr, PN_E_ARG, why);
+  pn_batch* b = new (std::nothrow) pn_batch();
+  if (!b) return fail(nullptr, PN_E_NOMEM, "host allocation failed");
+  b->n_max = n_max;
+  b->p = *p;
+  b->stream = (cudaStream_t)cuda_stream;
+  cudaError_t e = cudaGetDevice(&b->device);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&b->num_sms, cudaDevAttrMultiProcessorCount, b->device);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaMalloc(&b->d_queue, sizeof(unsigned long long));
+  if (e == cudaSuccess) e = cudaMalloc(&b->d_tab, 256 * sizeof(double));
+  if (e == cudaSuccess) e = cudaMalloc(&b->d_stat_part, (size_t)pn::kStatGrid * pn::kStatWords * sizeof(double));
+  if (e == cudaSuccess) e = cudaMalloc(&b->d_stat_total, pn::kStatWords * sizeof(double));
+  for (int k = 0; k < 4 && e == cudaSuccess; k++) e = cudaEventCreate(&b->ev[k]);
+  if (e == cudaSuccess) {
+    double tab[256];
+    pn::fill_log_table(tab);
+    e = cudaMemcpy(b->d_tab, tab, sizeof(tab), cudaMemcpyHostToDevice);
+  }
+  if (e != cudaSuccess) {
+    const int rc = (e == cudaErrorMemoryAllocation) ? PN_E_NOMEM : PN_E_CUDA;
+    char buf[256];
+    snprintf(buf, sizeof(buf), "pn_batch_init: %s", cudaGetErrorString(e));
+    pn_batch_destroy(b);
+    return fail(nullptr, rc, buf);
+  }
+  *out = b;
+  return PN_OK;
+}
+
+extern "C" int pn_batch_set_params(pn_batch* b, const pn_params* p) {
+  if (!b) return fail(nullptr, PN_E_ARG, "batch is NULL");
+  if (!p) return fail(b, PN_E_ARG, "params is NULL");
+  std::string why;
+  if (!params_valid(p, &why)) return fail(b, PN_E_ARG, why);
+  b->p = *p;
+  return PN_OK;
+}
+
+namespace {
+
+struct Shape {
+  bool persistent;
+  int block;
+  int grid;
+};
+
+Shape choose_shape(pn_batch* b, int64_t n, int prec, int sched_override = -1, int block_override = 0) {
+  const pn_params& p = b->p;
+  const pn_batch::Tuned& tu = b->tuned[prec];
+  int sched = sched_override >= 0 ? sched_override : p.schedule;
+  if (sched == PN_SCHED_AUTO) sched = tu.valid ? tu.schedule : PN_SCHED_PERSISTENT;
+  int block = block_override ? block_override : p.block;
+  if (block == 0) block = tu.valid ? tu.block : 128;
+  Shape s;
+  s.persistent = (sched == PN_SCHED_PERSISTENT);
+  s.block = block;
+  const int64_t full = (n + block - 1) / block;
+  if (s.persistent) {
+    int per_sm = 0;
+    if (pn::integrate_occupancy(prec, true, block, &per_sm) != cudaSuccess || per_sm < 1) per_sm = 1;
+    const int64_t cap = (int64_t)b->num_sms * per_sm;
+    s.grid = (int)(full < cap ? full : cap);
+  } else {
+    s.grid = (int)full;
+  }
+  return s;
+}
+
+// Launch one integration of n binaries with the given shape on b->stream.
+// The persistent shape goes through a CUDA graph (queue reset + kernel),
+// captured on a private stream and re-used while the arguments repeat.
+int run_integrate(pn_batch* b, int64_t n, const pn_inputs* in, pn_outputs* out, int prec, const Shape& sh) {
+  KArgs a;
+  std::memset(&a, 0, sizeof(a));
+  a.in = *in;
+  a.out = *out;
+  a.n = n;
+  a.queue = b->d_queue;
+  a.tab = b->d_tab;
+  a.ctl = make_ctl(b->p);
+  if (n == 0 || sh.grid == 0) return PN_OK;
+  if (!b->d_setup) {
+    cudaError_t e = cudaMalloc(&b->d_setup, (size_t)pn::setup_fields() * (size_t)b->n_max * sizeof(double));
+    if (e != cudaSuccess) {
+      b->d_setup = nullptr;
+      cudaGetLastError();
+      return fail(b, PN_E_NOMEM, "set-up table allocation failed");
+    }
+  }
+  const int64_t stride = b->n_max;
+  if (!sh.persistent) {
+    cudaError_t e = pn::launch_setup(prec, a, b->d_setup, stride, b->stream);
+    if (e != cudaSuccess) return cuda_fail(b, e, "set-up kernel launch");
+    e = pn::launch_integrate(prec, false, sh.block, sh.grid, a, b->d_setup, stride, b->stream);
+    if (e != cudaSuccess) return cuda_fail(b, e, "integrate kernel launch");
+    return PN_OK;
+  }
+  const bool same = b->gexec && b->have_key && b->key_prec == prec && b->key_block == sh.block &&
+                    b->key_grid == sh.grid && std::memcmp(&b->key_args, &a, sizeof(a)) == 0;
+  if (!same) {
+    cudaGraph_t g = nullptr;
+    PN_CUDA(b, cudaStreamBeginCapture(b->cap_stream, cudaStreamCaptureModeThreadLocal));
+    cudaError_t e1 = cudaMemsetAsync(b->d_queue, 0, sizeof(unsigned long long), b->cap_stream);
+    cudaError_t e2 = pn::launch_setup(prec, a, b->d_setup, stride, b->cap_stream);
+    if (e2 == cudaSuccess) e2 = pn::launch_integrate(prec, true, sh.block, sh.grid, a, b->d_setup, stride, b->cap_stream);
+    cudaError_t e3 = cudaStreamEndCapture(b->cap_stream, &g);
+    if (e1 != cudaSuccess) { if (g) cudaGraphDestroy(g); return cuda_fail(b, e1, "graph capture (memset)"); }
+    if (e2 != cudaSuccess) { if (g) cudaGraphDestroy(g); return cuda_fail(b, e2, "graph capture (kernel)"); }
+    if (e3 != cudaSuccess) return cuda_fail(b, e3, "cudaStreamEndCapture");
+    bool updated = false;
+    if (b->gexec) {
+      cudaGraphExecUpdateResultInfo info;
+      if (cudaGraphExecUpdate(b->gexec, g, &info) == cudaSuccess) updated = true;
+      else {
+        cudaGetLastError();
+        cudaGraphExecDestroy(b->gexec);
+        b->gexec = nullptr;
+      }
+    }
+    if (!updated) {
+      cudaError_t e = cudaGraphInstantiate(&b->gexec, g, 0);
+      if (e != cudaSuccess) { cudaGraphDestroy(g); b->gexec = nullptr; return cuda_fail(b, e, "cudaGraphInstantiate"); }
+    }
+    cudaGraphDestroy(g);
+    b->have_key = true;
+    b->key_args = a;
+    b->key_prec = prec;
+    b->key_block = sh.block;
+    b->key_grid = sh.grid;
+  }
+  PN_CUDA(b, cudaGraphLaunch(b->gexec, b->stream));
+  return PN_OK;
+}
+
+}  // namespace
+
+extern "C" int pn_batch_integrate(pn_batch* b, int64_t n, const pn_inputs* in, pn_outputs* out) {
+  if (!b) return fail(nullptr, PN_E_ARG, "batch is NULL");
+  if (n < 0 || n > b->n_max) return fail(b, PN_E_ARG, "n must be in [0, n_max]");
+  if (!inputs_ok(in)) return fail(b, PN_E_ARG, "NULL input pointer");
+  if (!outputs_ok(out)) return fail(b, PN_E_ARG, "NULL output pointer");
+  const int prec = b->p.precision;
+  const Shape sh = choose_shape(b, n, prec);
+  PN_CUDA(b, cudaEventRecord(b->ev[0], b->stream));
+  const int rc = run_integrate(b, n, in, out, prec, sh);
+  if (rc != PN_OK) return rc;
+  PN_CUDA(b, cudaEventRecord(b->ev[1], b->stream));
+  b->timed_integrate = true;
+  return PN_OK;
+}
+
+extern "C" int pn_batch_integrate_host(pn_batch* b, int64_t n, const pn_inputs* hin, pn_outputs* hout) {
+  if (!b) return fail(nullptr, PN_E_ARG, "batch is NULL");
+  if (n < 0 || n > b->n_max) return fail(b, PN_E_ARG, "n must be in [0, n_max]");
+  if (!inputs_ok(hin)) return fail(b, PN_E_ARG, "NULL input pointer");
+  if (!outputs_ok(hout)) return fail(b, PN_E_ARG, "NULL output pointer");
+  const size_t N = (size_t)b->n_max;
+  if (!b->d_stage_d) {
+    cudaError_t e = cudaMalloc(&b->d_stage_d, 29 * N * sizeof(double));
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_stage_i, 4 * N * sizeof(int32_t));
+    if (e != cudaSuccess) {
+      cudaFree(b->d_stage_d);
+      b->d_stage_d = nullptr;
+      b->d_stage_i = nullptr;
+      return fail(b, PN_E_NOMEM, "staging allocation failed");
+    }
+  }
+  double* D = b->d_stage_d;
+  int32_t* I = b->d_stage_i;
+  pn_inputs din;
+  double** dp[15] = {&din.m1, &din.m2, &din.chi1, &din.chi2, &din.s1x, &din.s1y, &din.s1z, &din.s2x,
+                     &din.s2y, &din.s2z, &din.lx, &din.ly, &din.lz, &din.omega0, &din.omega_f};
+  double* const hp[15] = {hin->m1, hin->m2, hin->chi1, hin->chi2, hin->s1x, hin->s1y, hin->s1z, hin->s2x,
+                          hin->s2y, hin->s2z, hin->lx, hin->ly, hin->lz, hin->omega0, hin->omega_f};
+  const size_t bytes = (size_t)n * sizeof(double);
+  for (int k = 0; k < 15; k++) {
+    *dp[k] = D + (size_t)k * N;
+    if (n) PN_CUDA(b, cudaMemcpyAsync(*dp[k], hp[k], bytes, cudaMemcpyHostToDevice, b->stream));
+  }
+  pn_outputs dout;
+  double** op[14] = {&dout.S1x, &dout.S1y, &dout.S1z, &dout.S2x, &dout.S2y, &dout.S2z, &dout.Lx,
+                     &dout.Ly, &dout.Lz, &dout.omega, &dout.t, &dout.dot_s1s2, &dout.dot_ls1, &dout.dot_ls2};
+  double* const ho[14] = {hout->S1x, hout->S1y, hout->S1z, hout->S2x, hout->S2y, hout->S2z, hout->Lx,
+                          hout->Ly, hout->Lz, hout->omega, hout->t, hout->dot_s1s2, hout->dot_ls1, hout->dot_ls2};
+  for (int k = 0; k < 14; k++) *op[k] = D + (size_t)(15 + k) * N;
+  int32_t** ip[4] = {&dout.n_acc, &dout.n_rej, &dout.n_land, &dout.status};
+  int32_t* const hi[4] = {hout->n_acc, hout->n_rej, hout->n_land, hout->status};
+  for (int k = 0; k < 4; k++) *ip[k] = I + (size_t)k * N;
+  int rc = pn_batch_integrate(b, n, &din, &dout);
+  if (rc != PN_OK) return rc;
+  for (int k = 0; k < 14 && n; k++)
+    PN_CUDA(b, cudaMemcpyAsync(ho[k], *op[k], bytes, cudaMemcpyDeviceToHost, b->stream));
+  for (int k = 0; k < 4 && n; k++)
+    PN_CUDA(b, cudaMemcpyAsync(hi[k], *ip[k], (size_t)n * sizeof(int32_t), cudaMemcpyDeviceToHost, b->stream));
+  PN_CUDA(b, cudaStreamSynchronize(b->stream));
+  return PN_OK;
+}
+
+extern "C" int pn_batch_autotune(pn_batch* b, int64_t n, const pn_inputs* in, pn_outputs* scratch,
+                                 pn_tune_result* res) {
+  if (!b) return fail(nullptr, PN_E_ARG, "batch is NULL");
+  if (n < 1 || n > b->n_max) return fail(b, PN_E_ARG, "n must be in [1, n_max]");
+  if (!inputs_ok(in)) return fail(b, PN_E_ARG, "NULL input pointer");
+  if (!outputs_ok(scratch)) return fail(b, PN_E_ARG, "NULL output pointer");
+  const int prec = b->p.precision;
+  const int64_t nt = n < 262144 ? n : 262144;
+  const int scheds[2] = {PN_SCHED_PLAIN, PN_SCHED_PERSISTENT};
+  const int blocks[3] = {64, 128, 256};
+  double best = 1e300;
+  int bs = PN_SCHED_PERSISTENT, bb = 128, nc = 0;
+  for (int si = 0; si < 2; si++)
+    for (int bi = 0; bi < 3; bi++) {
+      const Shape sh = choose_shape(b, nt, prec, scheds[si], blocks[bi]);
+      int rc = run_integrate(b, nt, in, scratch, prec, sh);  // warm-up
+      if (rc != PN_OK) return rc;
+      float tmin = 1e30f;
+      for (int rep = 0; rep < 2; rep++) {
+        PN_CUDA(b, cudaEventRecord(b->ev[2], b->stream));
+        rc = run_integrate(b, nt, in, scratch, prec, sh);
+        if (rc != PN_OK) return rc;
+        PN_CUDA(b, cudaEventRecord(b->ev[3], b->stream));
+        PN_CUDA(b, cudaEventSynchronize(b->ev[3]));
+        float ms = 0.f;
+        PN_CUDA(b, cudaEventElapsedTime(&ms, b->ev[2], b->ev[3]));
+        if (ms < tmin) tmin = ms;
+      }
+      nc++;
+      if (tmin < best) {
+        best = tmin;
+        bs = scheds[si];
+        bb = blocks[bi];
+      }
+    }
+  b->tuned[prec].valid = true;
+  b->tuned[prec].schedule = bs;
+  b->tuned[prec].block = bb;
+  b->tuned[prec].bpt = 1;
+  if (res) {
+    res->schedule = bs;
+    res->block = bb;
+    res->bpt = 1;
+    res->n_candidates = nc;
+    res->best_ms = best;
+    res->n_tuned = nt;
+  }
+  return PN_OK;
+}
+
+extern "C" int pn_batch_adjoint(pn_batch* b, int64_t n, const pn_inputs* in, const pn_cotangents* gbar,
+                                pn_grads* grad, pn_outputs* out) {
+  (void)n; (void)in; (void)gbar; (void)grad; (void)out;
+  if (!b) return fail(nullptr, PN_E_ARG, "batch is NULL");
+  return fail(b, PN_E_UNIMPLEMENTED, "pn_batch_adjoint is not built yet");
+}
+
+extern "C" int pn_batch_sample(pn_batch* b, uint64_t seed, const pn_dist* d, int64_t n, const pn_inputs* in) {
+  if (!b) return fail(nullptr, PN_E_ARG, "batch is NULL");
+  if (!d) return fail(b, PN_E_ARG, "dist is NULL");
+  if (n < 0 || n > b->n_max) return fail(b, PN_E_ARG, "n must be in [0, n_max]");
+  if (!inputs_ok(in)) return fail(b, PN_E_ARG, "NULL input pointer");
+  if (d->q_mode < 0 || d->q_mode > 2 || d->chi_mode < 0 || d->chi_mode > 1) return fail(b, PN_E_ARG, "bad dist mode");
+  if (!(d->q_lo > 0.0 && d->q_hi >= d->q_lo && std::isfinite(d->q_hi))) return fail(b, PN_E_ARG, "need 0 < q_lo <= q_hi");
+  if (!(d->chi_lo >= 0.0 && d->chi_hi >= d->chi_lo && d->chi_hi <= 1.0)) return fail(b, PN_E_ARG, "need 0 <= chi_lo <= chi_hi <= 1");
+  if (!(d->omega0_lo > 0.0 && d->omega0_hi >= d->omega0_lo && d->omega_f > d->omega0_hi))
+    return fail(b, PN_E_ARG, "need 0 < omega0_lo <= omega0_hi < omega_f");
+  cudaError_t e = pn::launch_sample(seed, *d, n, *in, b->stream);
+  if (e != cudaSuccess) return cuda_fail(b, e, "sample kernel launch");
+  return PN_OK;
+}
+
+extern "C" int pn_batch_stats(pn_batch* b, int64_t n, const pn_inputs* in, const pn_outputs* out, pn_stats* host) {
+  if (!b) return fail(nullptr, PN_E_ARG, "batch is NULL");
+  if (n < 0 || n > b->n_max) return fail(b, PN_E_ARG, "n must be in [0, n_max]");
+  if (!inputs_ok(in)) return fail(b, PN_E_ARG, "NULL input pointer");
+  if (!outputs_ok(out)) return fail(b, PN_E_ARG, "NULL output pointer");
+  if (!host) return fail(b, PN_E_ARG, "host stats is NULL");
+  double t[pn::kStatWords];
+  cudaError_t e = pn::launch_stats(n, *in, *out, b->d_stat_part, b->d_stat_total, b->stream);
+  if (e != cudaSuccess) return cuda_fail(b, e, "stats kernel launch");
+  PN_CUDA(b, cudaMemcpyAsync(t, b->d_stat_total, sizeof(t), cudaMemcpyDeviceToHost, b->stream));
+  PN_CUDA(b, cudaStreamSynchronize(b->stream));
+  std::memset(host, 0, sizeof(*host));
+  host->n = n;
+  for (int k = 0; k < 8; k++) host->count_by_status[k] = (int64_t)t[k];
+  host->acc_total = (int64_t)t[8];
+  host->rej_total = (int64_t)t[9];
+  host->land_total = (int64_t)t[10];
+  host->acc_min = n ? (int32_t)t[11] : 0;
+  host->acc_max = n ? (int32_t)t[12] : 0;
+  host->attempts_min = n ? (int32_t)t[13] : 0;
+  host->attempts_max = n ? (int32_t)t[14] : 0;
+  const double N = t[15];
+  host->pearson_count = (int64_t)N;
+  double* r[3] = {&host->pearson_s1s2, &host->pearson_ls1, &host->pearson_ls2};
+  for (int p = 0; p < 3; p++) {
+    const double sx = t[16 + 5 * p], sy = t[17 + 5 * p], sxx = t[18 + 5 * p], syy = t[19 + 5 * p],
+                 sxy = t[20 + 5 * p];
+    const double num = N * sxy - sx * sy;
+    const double den = std::sqrt((N * sxx - sx * sx) * (N * syy - sy * sy));
+    *r[p] = (N > 1 && den > 0) ? num / den : NAN;
+  }
+  host->mean_final_s1s2 = N > 0 ? t[31] / N : NAN;
+  host->std_final_s1s2 = N > 1 ? std::sqrt((t[32] - t[31] * t[31] / N) / (N - 1)) : NAN;
+  float ms = 0.f;
+  host->ms_last_integrate = (b->timed_integrate && cudaEventElapsedTime(&ms, b->ev[0], b->ev[1]) == cudaSuccess) ? ms : NAN;
+  host->ms_last_adjoint = NAN;
+  cudaGetLastError();
+  return PN_OK;
+}

@@ -1,0 +1,464 @@
+// pn_device.cuh -- device arithmetic of the batched PN inspiral integrator (sm_103a).
+//
+// One binary per lane, its state in registers.  The method is that of
+// arXiv:0908.3889 Sec. II: Eqs. (1)-(4) integrated in t with the Dormand-Prince
+// 5(4) pair (Dormand & Prince 1980), error tolerance 5e-7, first step h = 10,
+// from omega_0 up to omega_f.
+//
+// B300 shapes this file: the FP64 pipe issues ~2 lanes/clk/SM (64x below FP32),
+// and the CUDA FP64 cbrt / log / pow / divide cost roughly 17 / 37 / 100 / 8
+// FMA-equivalents there.  So every FP64 instruction counts.  The
+// transcendentals the RHS and the step control need are computed from FP32
+// seeds plus short FP64 corrections whose truncation error is below 1e-17
+// relative; comparisons, absolute values and maxima of doubles use integer
+// instructions on the bit patterns; and in mixed precision the FP32<->FP64
+// conversions are done with integer instructions, not the FP64 pipe.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace pn {
+
+// ---------------------------------------------------------------------------
+// Bit-level helpers (integer pipe).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t hi32(double d) { return (uint32_t)__double2hiint(d); }
+__device__ __forceinline__ uint32_t lo32(double d) { return (uint32_t)__double2loint(d); }
+__device__ __forceinline__ double mk64(uint32_t hi, uint32_t lo) { return __hiloint2double((int)hi, (int)lo); }
+__device__ __forceinline__ double dnan() { return __longlong_as_double(0x7ff8000000000000ll); }
+
+// |d| (clears the sign bit).
+__device__ __forceinline__ double dabs(double d) { return mk64(hi32(d) & 0x7fffffffu, lo32(d)); }
+
+// max(|a|, |b|) by integer comparison of the magnitudes' bit patterns (which
+// order like the values for non-negative doubles; NaN sorts above Inf).
+__device__ __forceinline__ double max_abs(double a, double b) {
+  const unsigned long long x = (unsigned long long)__double_as_longlong(a) & 0x7fffffffffffffffull;
+  const unsigned long long y = (unsigned long long)__double_as_longlong(b) & 0x7fffffffffffffffull;
+  return __longlong_as_double((long long)(x > y ? x : y));
+}
+
+// a <= b for a, b >= 0 (not NaN), by integer comparison.
+__device__ __forceinline__ bool le_pos(double a, double b) {
+  return (unsigned long long)__double_as_longlong(a) <= (unsigned long long)__double_as_longlong(b);
+}
+
+// True if d is finite (exponent field not all ones).
+__device__ __forceinline__ bool finite64(double d) { return (hi32(d) & 0x7ff00000u) != 0x7ff00000u; }
+
+// Seed conversion double -> float for positive normal d in [2^-126, 2^128):
+// drops the exponent bias difference and keeps the top 23 fraction bits
+// (truncation).  Two integer instructions.
+__device__ __forceinline__ float seed_f32(double d) {
+  return __uint_as_float(__funnelshift_l(lo32(d), hi32(d), 3) - (384u << 23));
+}
+
+// Exact conversion float -> double for positive normal f.
+__device__ __forceinline__ double seed_f64(float f) {
+  const uint32_t b = __float_as_uint(f);
+  return mk64((b >> 3) + (896u << 20), b << 29);
+}
+
+// double -> float rounded to nearest (ties away from zero), any sign;
+// |d| < 2^-126 flushes to a signed zero, overflow gives Inf, NaN stays NaN.
+__device__ __forceinline__ float f64_to_f32(double d) {
+  const uint32_t hi = hi32(d), lo = lo32(d);
+  const uint32_t ahi = hi & 0x7fffffffu;
+  uint32_t b = (__funnelshift_l(lo, ahi, 3) - (384u << 23)) + ((lo >> 28) & 1u);
+  if (ahi < (897u << 20)) b = 0u;
+  else if (ahi >= (1151u << 20)) b = (ahi > 0x7ff00000u || (ahi == 0x7ff00000u && lo != 0u)) ? 0x7fc00000u : 0x7f800000u;
+  return __uint_as_float(b | (hi & 0x80000000u));
+}
+
+// float -> double, exact for normal floats; subnormals flush to a signed zero;
+// Inf and NaN are kept.
+__device__ __forceinline__ double f32_to_f64(float f) {
+  const uint32_t b = __float_as_uint(f);
+  const uint32_t a = b & 0x7fffffffu;
+  uint32_t hi = (a >> 3) + (896u << 20);
+  uint32_t lo = a << 29;
+  if (a < 0x00800000u) { hi = 0u; lo = 0u; }
+  else if (a >= 0x7f800000u) { hi = (a > 0x7f800000u) ? 0x7ff80000u : 0x7ff00000u; lo = 0u; }
+  return mk64(hi | (b & 0x80000000u), lo);
+}
+
+// ---------------------------------------------------------------------------
+// FP64 functions from FP32 seeds (each relative error below one ulp).
+// ---------------------------------------------------------------------------
+
+// x^(-1/3), odd in x, for |x| in [2^-126, 2^128).  Seed: FP32 rcbrtf of the
+// truncated |x|.  One third-order step of the binomial series
+// (1 - e)^(-1/3) = 1 + e/3 + 2e^2/9 + O(e^3), e = 1 - |x| r^3.
+__device__ __forceinline__ double inv_cbrt(double x) {
+  const uint32_t hx = hi32(x);
+  const double ax = mk64(hx & 0x7fffffffu, lo32(x));
+  double r = seed_f64(rcbrtf(seed_f32(ax)));
+  const double r3 = (r * r) * r;
+  const double e = fma(-ax, r3, 1.0);
+  r = fma(r, e * fma(e, 2.0 / 9.0, 1.0 / 3.0), r);
+  return mk64(hi32(r) | (hx & 0x80000000u), lo32(r));
+}
+
+// 1/x for positive normal x: FP32 reciprocal seed, then r (1 + e + e^2),
+// e = 1 - x r (the series of 1/(1 - e)).
+__device__ __forceinline__ double rcp_pos(double x) {
+  const double r = seed_f64(__frcp_rn(seed_f32(x)));
+  const double e = fma(-x, r, 1.0);
+  return fma(r, fma(e, e, e), r);
+}
+
+// s^(-1/10) for s in [2^-126, 2^128): FP32 exp2/log2 seed, then
+// z (1 + e/10 + 11 e^2/200), e = 1 - s z^10 (the series of (1 - e)^(-1/10)).
+__device__ __forceinline__ double pow_m_tenth(double s) {
+  double z = seed_f64(exp2f(-0.1f * log2f(seed_f32(s))));
+  const double z2 = z * z;
+  const double z4 = z2 * z2;
+  const double z10 = (z4 * z4) * z2;
+  const double e = fma(-s, z10, 1.0);
+  return fma(z, e * fma(e, 11.0 / 200.0, 0.1), z);
+}
+
+// Cody-Waite split of ln 2: LN2_HI has 40 significant bits, so k * LN2_HI is
+// exact for |k| < 2^12; LN2_HI + LN2_LO = ln 2 to 2e-31.
+#define PN_LN2_HI 0.6931471805601177
+#define PN_LN2_LO (-1.7239444525614835e-13)
+
+// ln|x| for |x| in the normal double range by Tang's table-driven method
+// (P. T. P. Tang, ACM TOMS 16, 1990): |x| = 2^k m with m in [1, 2);
+// F = 1 + (2j + 1)/256 where j is the top 7 bits of m's fraction, so
+// |m - F| <= 2^-8 and f = m - F is exact; u = f / F; then
+// ln|x| = k ln2 + ln F + ln(1 + u), the last from its Taylor series to u^6
+// (truncation below u^7/7 < 2e-18).  tab[2j] = 1/F_j, tab[2j+1] = ln F_j
+// (computed on the host in extended precision, rounded to double).
+__device__ __forceinline__ double log_tang(double x, const double* __restrict__ tab) {
+  const uint32_t hx = hi32(x) & 0x7fffffffu;
+  const int k = (int)(hx >> 20) - 1023;
+  const uint32_t j = (hx >> 13) & 127u;
+  const double m = mk64((hx & 0x000fffffu) | 0x3ff00000u, lo32(x));
+  const double F = mk64(0x3ff00000u | ((2u * j + 1u) << 12), 0u);
+  const double u = (m - F) * tab[2 * j];
+  double q = fma(u, -1.0 / 6.0, 0.2);
+  q = fma(q, u, -0.25);
+  q = fma(q, u, 1.0 / 3.0);
+  q = fma(q, u, -0.5);
+  const double p = fma(q, u * u, u);
+  // (double)k from the bit pattern 2^52 + 2^31 + k, minus 2^52 + 2^31.
+  const double kd = mk64(0x43300000u, (uint32_t)k ^ 0x80000000u) - 4503601774854144.0;
+  return fma(kd, PN_LN2_HI, tab[2 * j + 1]) + fma(kd, PN_LN2_LO, p);
+}
+
+// ---------------------------------------------------------------------------
+// Per-binary coefficients of Eqs. (1) and (4) (M = m1 + m2 = 1, eta = m1 m2).
+// ---------------------------------------------------------------------------
+template <class R>
+struct Coef {
+  R K;             // (96/5) eta                     -- Eq. (1) prefactor
+  R w1, w2;        // (113 m_i^2 + 75 eta) / (12 m_i^2): 1.5PN spin-orbit weight on L.S_i
+  R tail;          // 4 pi                            -- 1.5PN tail
+  R ss247, ss721;  // 247 eta / (48 m1^2 m2^2), 721 eta / (48 m1^2 m2^2): 2PN spin-spin
+  R c1, c2, c25, c35;  // non-spin coefficients of x^{2/3}, x^{4/3}, x^{5/3}, x^{7/3}
+  R c3l;           // 3PN non-log coefficient minus (856/105) ln 16
+  R clog;          // -(856/105)(2/3): coefficient of ln(M omega) in the 3PN bracket
+  R a1, a2;        // eta (4 + 3 m2/m1), eta (4 + 3 m1/m2)   -- Eq. (4)
+  R prec;          // 1/2 (precession on) or 0
+  R nie;           // -1/eta                                  -- Eq. (3)
+};
+
+struct TermCfg {
+  uint32_t mask;
+  int32_t theta_mode;
+};
+
+#define PN_PI 3.141592653589793
+#define PN_EULER_GAMMA 0.5772156649015329
+
+// Coefficients from the masses, in FP64 (once per binary).
+__device__ __forceinline__ Coef<double> make_coef(double m1, double m2, TermCfg tc) {
+  Coef<double> c;
+  const double eta = m1 * m2;
+  const double e2 = eta * eta;
+  const double im1 = 1.0 / (m1 * m1), im2 = 1.0 / (m2 * m2);
+  const uint32_t mk = tc.mask;
+  c.K = (96.0 / 5.0) * eta;
+  c.w1 = (mk & 2u) ? (113.0 * (m1 * m1) + 75.0 * eta) / 12.0 * im1 : 0.0;
+  c.w2 = (mk & 2u) ? (113.0 * (m2 * m2) + 75.0 * eta) / 12.0 * im2 : 0.0;
+  c.tail = (mk & 4u) ? 4.0 * PN_PI : 0.0;
+  const double ss = (mk & 16u) ? eta / 48.0 * im1 * im2 : 0.0;
+  c.ss247 = 247.0 * ss;
+  c.ss721 = 721.0 * ss;
+  c.c1 = (mk & 1u) ? -(743.0 + 924.0 * eta) / 336.0 : 0.0;
+  c.c2 = (mk & 8u) ? 34103.0 / 18144.0 + 13661.0 / 2016.0 * eta + 59.0 / 18.0 * e2 : 0.0;
+  c.c25 = (mk & 32u) ? -(4159.0 + 15876.0 * eta) * PN_PI / 672.0 : 0.0;
+  // 3PN: theta-hat = 1039/4620 multiplies eta once (default) or eta^2 (as printed).
+  const double theta = 1039.0 / 4620.0;
+  const double th_eta = (tc.theta_mode == 0) ? theta : theta * eta;
+  const double c3 = 16447322263.0 / 139708800.0 - 1712.0 / 105.0 * PN_EULER_GAMMA + 16.0 / 3.0 * PN_PI * PN_PI +
+                    (-273811877.0 / 1088640.0 + 451.0 / 48.0 * PN_PI * PN_PI - 88.0 / 3.0 * th_eta) * eta +
+                    541.0 / 896.0 * e2 - 5605.0 / 2592.0 * e2 * eta;
+  c.c3l = (mk & 64u) ? c3 - 856.0 / 105.0 * (4.0 * 0.6931471805599453) : 0.0;
+  c.clog = (mk & 64u) ? -1712.0 / 315.0 : 0.0;
+  c.c35 = (mk & 128u) ? (-4415.0 / 4032.0 + 358675.0 / 6048.0 * eta + 91495.0 / 1512.0 * e2) * PN_PI : 0.0;
+  c.a1 = eta * (4.0 + 3.0 * m2 / m1);
+  c.a2 = eta * (4.0 + 3.0 * m1 / m2);
+  c.prec = (mk & 256u) ? 0.5 : 0.0;
+  c.nie = -1.0 / eta;
+  return c;
+}
+
+// The FP32 coefficients, rounded with the same integer conversion the kernels use.
+__device__ __forceinline__ Coef<float> to_f32(const Coef<double>& c) {
+  Coef<float> f;
+  const double* s = &c.K;
+  float* d = &f.K;
+#pragma unroll
+  for (int k = 0; k < 16; k++) d[k] = f64_to_f32(s[k]);
+  return f;
+}
+
+// ---------------------------------------------------------------------------
+// Right-hand side f(y), y = (omega, S1, S2, L), M = 1, x = omega, v = x^{1/3}.
+//   Eq. (1): domega/dt = (96/5) eta omega^2 v^5 P, P = 1 + c1 v^2 - SO v^3
+//            + (c2 - SS) v^4 + c25 v^5 + (c3 - 856/105 ln(16 v^2)) v^6 + c35 v^7,
+//            SO = sum_i chi_i L.S_i-hat (113 m_i^2 + 75 eta)/12 - 4 pi,
+//            SS = eta chi1 chi2 (247 S1-hat.S2-hat - 721 L.S1-hat L.S2-hat)/48,
+//            with chi_i S_i-hat = S_i / m_i^2.
+//   Eq. (4): Omega_1 = (x^2/2) [eta v^{-1} (4 + 3 m2/m1) L + S2 - 3 (S2.L) L], 1<->2.
+//   Eq. (2): dS_i/dt = Omega_i x S_i.   Eq. (3): dL/dt = -(v/eta)(dS1/dt + dS2/dt).
+// Written with A_i = L x S_i and C = S1 x S2:
+//   dS1/dt = (x^2/2)[(a1/v - 3 L.S2) A1 - C],  dS2/dt = (x^2/2)[(a2/v - 3 L.S1) A2 + C].
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void rhs64(const Coef<double>& c, const double* __restrict__ tab, const double* y,
+                                      double* f) {
+  const double w = y[0];
+  const double S1x = y[1], S1y = y[2], S1z = y[3];
+  const double S2x = y[4], S2y = y[5], S2z = y[6];
+  const double Lx = y[7], Ly = y[8], Lz = y[9];
+
+  // r = w^{-1/3}, v = w^{1/3}; |w| outside [2^-126, 2^128) (incl. 0, Inf, NaN) gives NaN.
+  double r = inv_cbrt(w);
+  if ((hi32(w) & 0x7fffffffu) - (897u << 20) >= ((1151u - 897u) << 20)) r = dnan();
+  const double v = w * (r * r);
+  const double v2 = v * v;
+  const double lw = log_tang(w, tab);
+
+  const double LS1 = fma(Lz, S1z, fma(Ly, S1y, Lx * S1x));
+  const double LS2 = fma(Lz, S2z, fma(Ly, S2y, Lx * S2x));
+  const double S12 = fma(S1z, S2z, fma(S1y, S2y, S1x * S2x));
+
+  const double so = fma(c.w1, LS1, fma(c.w2, LS2, -c.tail));
+  const double c2p = fma(c.ss721, LS1 * LS2, fma(-c.ss247, S12, c.c2));
+  const double c3p = fma(c.clog, lw, c.c3l);
+  double P = fma(v, c.c35, c3p);
+  P = fma(v, P, c.c25);
+  P = fma(v, P, c2p);
+  P = fma(v, P, -so);
+  P = fma(v, P, c.c1);
+  P = fma(v2, P, 1.0);
+  const double w2 = w * w;
+  f[0] = (((w2 * w) * v2) * c.K) * P;
+
+  const double A1x = fma(Ly, S1z, -Lz * S1y), A1y = fma(Lz, S1x, -Lx * S1z), A1z = fma(Lx, S1y, -Ly * S1x);
+  const double A2x = fma(Ly, S2z, -Lz * S2y), A2y = fma(Lz, S2x, -Lx * S2z), A2z = fma(Lx, S2y, -Ly * S2x);
+  const double Cx = fma(S1y, S2z, -S1z * S2y), Cy = fma(S1z, S2x, -S1x * S2z), Cz = fma(S1x, S2y, -S1y * S2x);
+  const double pre = c.prec * w2;
+  const double p1 = pre * fma(c.a1, r, -3.0 * LS2);
+  const double p2 = pre * fma(c.a2, r, -3.0 * LS1);
+  const double pCx = pre * Cx, pCy = pre * Cy, pCz = pre * Cz;
+  const double d1x = fma(p1, A1x, -pCx), d1y = fma(p1, A1y, -pCy), d1z = fma(p1, A1z, -pCz);
+  const double d2x = fma(p2, A2x, pCx), d2y = fma(p2, A2y, pCy), d2z = fma(p2, A2z, pCz);
+  f[1] = d1x; f[2] = d1y; f[3] = d1z;
+  f[4] = d2x; f[5] = d2y; f[6] = d2z;
+  const double lf = v * c.nie;
+  f[7] = lf * (d1x + d2x);
+  f[8] = lf * (d1y + d2y);
+  f[9] = lf * (d1z + d2z);
+}
+
+// The same right-hand side in FP32 (mixed precision).
+__device__ __forceinline__ void rhs32(const Coef<float>& c, const float* y, float* f) {
+  const float w = y[0];
+  const float S1x = y[1], S1y = y[2], S1z = y[3];
+  const float S2x = y[4], S2y = y[5], S2z = y[6];
+  const float Lx = y[7], Ly = y[8], Lz = y[9];
+  const float r = rcbrtf(w);
+  const float v = w * (r * r);
+  const float v2 = v * v;
+  const float lw = logf(fabsf(w));
+  const float LS1 = fmaf(Lz, S1z, fmaf(Ly, S1y, Lx * S1x));
+  const float LS2 = fmaf(Lz, S2z, fmaf(Ly, S2y, Lx * S2x));
+  const float S12 = fmaf(S1z, S2z, fmaf(S1y, S2y, S1x * S2x));
+  const float so = fmaf(c.w1, LS1, fmaf(c.w2, LS2, -c.tail));
+  const float c2p = fmaf(c.ss721, LS1 * LS2, fmaf(-c.ss247, S12, c.c2));
+  const float c3p = fmaf(c.clog, lw, c.c3l);
+  float P = fmaf(v, c.c35, c3p);
+  P = fmaf(v, P, c.c25);
+  P = fmaf(v, P, c2p);
+  P = fmaf(v, P, -so);
+  P = fmaf(v, P, c.c1);
+  P = fmaf(v2, P, 1.0f);
+  const float w2 = w * w;
+  f[0] = (((w2 * w) * v2) * c.K) * P;
+  const float A1x = fmaf(Ly, S1z, -Lz * S1y), A1y = fmaf(Lz, S1x, -Lx * S1z), A1z = fmaf(Lx, S1y, -Ly * S1x);
+  const float A2x = fmaf(Ly, S2z, -Lz * S2y), A2y = fmaf(Lz, S2x, -Lx * S2z), A2z = fmaf(Lx, S2y, -Ly * S2x);
+  const float Cx = fmaf(S1y, S2z, -S1z * S2y), Cy = fmaf(S1z, S2x, -S1x * S2z), Cz = fmaf(S1x, S2y, -S1y * S2x);
+  const float pre = c.prec * w2;
+  const float p1 = pre * fmaf(c.a1, r, -3.0f * LS2);
+  const float p2 = pre * fmaf(c.a2, r, -3.0f * LS1);
+  const float pCx = pre * Cx, pCy = pre * Cy, pCz = pre * Cz;
+  const float d1x = fmaf(p1, A1x, -pCx), d1y = fmaf(p1, A1y, -pCy), d1z = fmaf(p1, A1z, -pCz);
+  const float d2x = fmaf(p2, A2x, pCx), d2y = fmaf(p2, A2y, pCy), d2z = fmaf(p2, A2z, pCz);
+  f[1] = d1x; f[2] = d1y; f[3] = d1z;
+  f[4] = d2x; f[5] = d2y; f[6] = d2z;
+  const float lf = v * c.nie;
+  f[7] = lf * (d1x + d2x);
+  f[8] = lf * (d1y + d2y);
+  f[9] = lf * (d1z + d2z);
+}
+
+// ---------------------------------------------------------------------------
+// Dormand & Prince (1980) RK5(4)7M coefficients (published table).
+// ---------------------------------------------------------------------------
+#define DP_A21 (1.0 / 5.0)
+#define DP_A31 (3.0 / 40.0)
+#define DP_A32 (9.0 / 40.0)
+#define DP_A41 (44.0 / 45.0)
+#define DP_A42 (-56.0 / 15.0)
+#define DP_A43 (32.0 / 9.0)
+#define DP_A51 (19372.0 / 6561.0)
+#define DP_A52 (-25360.0 / 2187.0)
+#define DP_A53 (64448.0 / 6561.0)
+#define DP_A54 (-212.0 / 729.0)
+#define DP_A61 (9017.0 / 3168.0)
+#define DP_A62 (-355.0 / 33.0)
+#define DP_A63 (46732.0 / 5247.0)
+#define DP_A64 (49.0 / 176.0)
+#define DP_A65 (-5103.0 / 18656.0)
+#define DP_B1 (35.0 / 384.0)
+#define DP_B3 (500.0 / 1113.0)
+#define DP_B4 (125.0 / 192.0)
+#define DP_B5 (-2187.0 / 6784.0)
+#define DP_B6 (11.0 / 84.0)
+// b - bhat (5th minus embedded 4th order weights), exact rationals
+#define DP_E1 (71.0 / 57600.0)
+#define DP_E3 (-71.0 / 16695.0)
+#define DP_E4 (71.0 / 1920.0)
+#define DP_E5 (-17253.0 / 339200.0)
+#define DP_E6 (22.0 / 525.0)
+#define DP_E7 (-1.0 / 40.0)
+
+// Step-control and stop parameters as the kernels use them.
+struct Ctl {
+  double rtol, atol, h0, safety, fac_min, fac_max, h_min, land_tol;
+  double s_lo;  // (safety/fac_max)^10: at or below it the growth factor is fac_max
+  double s_hi;  // (safety/fac_min)^10: at or above it the factor is fac_min
+  int32_t max_steps, land_max_iter, stop_mode, fixed_step;
+  TermCfg terms;
+  int32_t pad_;
+};
+
+// k = f(y) in the kernel's precision (PREC 0: FP64; 1: FP32 RHS with the
+// state rounded to FP32 on the way in and the rates widened on the way out).
+template <int PREC>
+__device__ __forceinline__ void eval_rhs(const Coef<double>& c64, const Coef<float>& c32,
+                                         const double* __restrict__ tab, const double* y, double* k) {
+  if constexpr (PREC == 0) {
+    rhs64(c64, tab, y, k);
+  } else {
+    float yf[10], kf[10];
+#pragma unroll
+    for (int i = 0; i < 10; i++) yf[i] = f64_to_f32(y[i]);
+    rhs32(c32, yf, kf);
+#pragma unroll
+    for (int i = 0; i < 10; i++) k[i] = f32_to_f64(kf[i]);
+  }
+}
+
+// One Dormand-Prince attempt of size h from y, with k1 = f(y) given.
+// Writes y5 (the 5th-order solution), k7 = f(y5) and returns the mean of the
+// squared scaled error components, s = err^2 (err = RMS norm).
+template <int PREC>
+__device__ __forceinline__ double dp5_attempt(const Coef<double>& c64, const Coef<float>& c32,
+                                              const double* __restrict__ tab, const Ctl& ctl, const double* y,
+                                              const double* k1, double h, double* y5, double* k7) {
+  double k2[10], k3[10], k4[10], k5[10], k6[10], ys[10];
+  {
+    const double a1 = h * DP_A21;
+#pragma unroll
+    for (int i = 0; i < 10; i++) ys[i] = fma(a1, k1[i], y[i]);
+  }
+  eval_rhs<PREC>(c64, c32, tab, ys, k2);
+  {
+    const double a1 = h * DP_A31, a2 = h * DP_A32;
+#pragma unroll
+    for (int i = 0; i < 10; i++) ys[i] = fma(a2, k2[i], fma(a1, k1[i], y[i]));
+  }
+  eval_rhs<PREC>(c64, c32, tab, ys, k3);
+  {
+    const double a1 = h * DP_A41, a2 = h * DP_A42, a3 = h * DP_A43;
+#pragma unroll
+    for (int i = 0; i < 10; i++) ys[i] = fma(a3, k3[i], fma(a2, k2[i], fma(a1, k1[i], y[i])));
+  }
+  eval_rhs<PREC>(c64, c32, tab, ys, k4);
+  {
+    const double a1 = h * DP_A51, a2 = h * DP_A52, a3 = h * DP_A53, a4 = h * DP_A54;
+#pragma unroll
+    for (int i = 0; i < 10; i++) ys[i] = fma(a4, k4[i], fma(a3, k3[i], fma(a2, k2[i], fma(a1, k1[i], y[i]))));
+  }
+  eval_rhs<PREC>(c64, c32, tab, ys, k5);
+  {
+    const double a1 = h * DP_A61, a2 = h * DP_A62, a3 = h * DP_A63, a4 = h * DP_A64, a5 = h * DP_A65;
+#pragma unroll
+    for (int i = 0; i < 10; i++)
+      ys[i] = fma(a5, k5[i], fma(a4, k4[i], fma(a3, k3[i], fma(a2, k2[i], fma(a1, k1[i], y[i])))));
+  }
+  eval_rhs<PREC>(c64, c32, tab, ys, k6);
+  {
+    const double b1 = h * DP_B1, b3 = h * DP_B3, b4 = h * DP_B4, b5 = h * DP_B5, b6 = h * DP_B6;
+#pragma unroll
+    for (int i = 0; i < 10; i++)
+      y5[i] = fma(b6, k6[i], fma(b5, k5[i], fma(b4, k4[i], fma(b3, k3[i], fma(b1, k1[i], y[i])))));
+  }
+  eval_rhs<PREC>(c64, c32, tab, y5, k7);
+  const double e1 = h * DP_E1, e3 = h * DP_E3, e4 = h * DP_E4, e5 = h * DP_E5, e6 = h * DP_E6, e7 = h * DP_E7;
+  double sum = 0.0;
+#pragma unroll
+  for (int i = 0; i < 10; i++) {
+    const double e = fma(e7, k7[i], fma(e6, k6[i], fma(e5, k5[i], fma(e4, k4[i], fma(e3, k3[i], e1 * k1[i])))));
+    const double sc = fma(ctl.rtol, max_abs(y[i], y5[i]), ctl.atol);
+    const double q = e * rcp_pos(sc);
+    sum = fma(q, q, sum);
+  }
+  return sum * 0.1;
+}
+
+// Growth factor of the step control: clamp(safety * s^(-1/10), fac_min, fmax)
+// with s = err^2, i.e. safety * err^(-1/5).
+__device__ __forceinline__ double step_factor(const Ctl& ctl, double s, double fmax) {
+  double fac;
+  if (le_pos(s, ctl.s_lo)) fac = ctl.fac_max;
+  else if (le_pos(ctl.s_hi, s)) fac = ctl.fac_min;
+  else fac = ctl.safety * pow_m_tenth(s);
+  if (!le_pos(fac, fmax)) fac = fmax;
+  if (le_pos(fac, ctl.fac_min)) fac = ctl.fac_min;
+  return fac;
+}
+
+// Root in (0, 1] of the cubic Hermite interpolant of omega over a step (end
+// values w0, w1; end slopes times h: d0, d1), three Newton steps from the
+// linear guess.  Once per binary, plain FP64.
+__device__ __forceinline__ double hermite_root(double w0, double d0, double w1, double d1, double wf) {
+  double s = (wf - w0) / (w1 - w0);
+#pragma unroll
+  for (int it = 0; it < 3; it++) {
+    const double s2 = s * s, s3 = s2 * s;
+    const double ps = (2.0 * s3 - 3.0 * s2 + 1.0) * w0 + (s3 - 2.0 * s2 + s) * d0 + (3.0 * s2 - 2.0 * s3) * w1 +
+                      (s3 - s2) * d1;
+    const double dps = (6.0 * s2 - 6.0 * s) * w0 + (3.0 * s2 - 4.0 * s + 1.0) * d0 + (6.0 * s - 6.0 * s2) * w1 +
+                       (3.0 * s2 - 2.0 * s) * d1;
+    s = s - (ps - wf) / dps;
+  }
+  return s;
+}
+
+}  // namespace pn

@@ -1,0 +1,44 @@
+// pn_internal.h -- declarations shared by the kernels (pn_kernels.cu) and the C ABI layer (pn_capi.cu).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "pn_batch.h"
+#include "pn_device.cuh"
+
+namespace pn {
+
+struct KArgs {
+  pn_inputs in;
+  pn_outputs out;
+  int64_t n;
+  unsigned long long* queue;  // persistent schedule: next unclaimed binary index
+  const double* tab;          // 256 doubles: (1/F_j, ln F_j) of the logarithm table
+  Ctl ctl;
+};
+
+constexpr int kMaxBlock = 256;
+
+// Set-up table: setup_fields() doubles per binary, field-major with the given stride (>= n).
+int setup_fields();
+// Validate every binary, write BAD_INPUT results, and fill the set-up table.
+cudaError_t launch_setup(int prec, const KArgs& a, double* ws, int64_t stride, cudaStream_t s);
+// Integration kernel launch (reads the set-up table).  prec: PN_FP64 / PN_MIXED;
+// persistent: work-queue schedule.
+cudaError_t launch_integrate(int prec, bool persistent, int block, int grid, const KArgs& a, const double* ws,
+                             int64_t stride, cudaStream_t s);
+// Resident blocks per SM of that kernel at this block size.
+cudaError_t integrate_occupancy(int prec, bool persistent, int block, int* blocks_per_sm);
+
+cudaError_t launch_sample(uint64_t seed, const pn_dist& d, int64_t n, const pn_inputs& in, cudaStream_t s);
+
+// Statistics: partial sums per block into part (grid x kStatWords doubles), then one block reduces them.
+constexpr int kStatWords = 40;
+constexpr int kStatGrid = 296;
+cudaError_t launch_stats(int64_t n, const pn_inputs& in, const pn_outputs& out, double* part, double* total,
+                         cudaStream_t s);
+
+// Host-side table for log_tang: tab[2j] = 1/F_j, tab[2j+1] = ln F_j, F_j = 1 + (2j+1)/256.
+void fill_log_table(double* tab256);
+
+}  // namespace pn

@@ -1,0 +1,489 @@
+// pn_kernels.cu -- CUDA kernels of the batched PN inspiral integrator (sm_103a).
+//
+// k_integrate: one binary per lane, state in registers, one Dormand-Prince
+// attempt per loop iteration for every lane that holds a binary, so a warp
+// stays converged on the RHS-heavy part whatever each lane's step history.
+// The per-lane control is a small state machine (STEP / LAND) that takes the
+// decisions of arXiv:0908.3889 Sec. II's integrator as read here: error
+// control at tolerance rtol = atol = 5e-7 with first step h0 = 10, and the stop
+// at omega_f by retaking the crossing step.  Two schedules share the code:
+//   plain       thread g integrates binary g (grid covers n);
+//   persistent  a grid sized to the resident capacity; a lane that finishes
+//               claims the next binary from a device counter, with one
+//               atomicAdd per warp (ballot + popc), so binaries of very
+//               different lengths do not leave lanes idle.
+// Inputs and outputs are structure-of-arrays: lane i touches element i of
+// each array, so every load and store of a warp is one coalesced 256-byte
+// transaction.
+
+#include <cmath>
+
+#include "pn_internal.h"
+
+namespace pn {
+
+struct Lane {
+  int64_t i;
+  double y[10];
+  double k1[10];  // f(y), carried across accepted steps (first same as last)
+  double t, h, h_lo, h_hi, wf;
+  int32_t n_acc, n_rej, n_land, attempts, land_it;
+  bool landing, last_rej;
+  Coef<double> c64;
+  Coef<float> c32;
+};
+
+__device__ __forceinline__ void write_result(const pn_outputs& o, int64_t i, const double* y, double t, int32_t n_acc,
+                                             int32_t n_rej, int32_t n_land, int32_t status) {
+  o.S1x[i] = y[1]; o.S1y[i] = y[2]; o.S1z[i] = y[3];
+  o.S2x[i] = y[4]; o.S2y[i] = y[5]; o.S2z[i] = y[6];
+  o.Lx[i] = y[7]; o.Ly[i] = y[8]; o.Lz[i] = y[9];
+  o.omega[i] = y[0];
+  o.t[i] = t;
+  o.n_acc[i] = n_acc; o.n_rej[i] = n_rej; o.n_land[i] = n_land; o.status[i] = status;
+  // Sec. V's scalar products of the unit vectors (NaN for a zero spin: 0/0).
+  const double n1 = sqrt(y[1] * y[1] + y[2] * y[2] + y[3] * y[3]);
+  const double n2 = sqrt(y[4] * y[4] + y[5] * y[5] + y[6] * y[6]);
+  const double nl = sqrt(y[7] * y[7] + y[8] * y[8] + y[9] * y[9]);
+  o.dot_s1s2[i] = (y[1] * y[4] + y[2] * y[5] + y[3] * y[6]) / (n1 * n2);
+  o.dot_ls1[i] = (y[7] * y[1] + y[8] * y[2] + y[9] * y[3]) / (nl * n1);
+  o.dot_ls2[i] = (y[7] * y[4] + y[8] * y[5] + y[9] * y[6]) / (nl * n2);
+}
+
+// Per-binary set-up table (structure of arrays, `stride` doubles per field):
+// fields 0..15 the coefficients, 16..25 the initial state y0, 26..35 k1 = f(y0)
+// in the kernel's precision, 36 omega_f (NaN marks a binary whose BAD_INPUT
+// result is already written).  k_setup fills it with one converged pass, so a
+// lane that picks up a new binary in k_integrate only loads.
+constexpr int kSetupFields = 37;
+
+__device__ __forceinline__ double* fld(double* ws, int64_t stride, int f) { return ws + (size_t)f * stride; }
+
+template <int PREC>
+__global__ void __launch_bounds__(256) k_setup(const KArgs a, double* __restrict__ ws, int64_t stride) {
+  __shared__ double s_tab[256];
+  for (int q = threadIdx.x; q < 256; q += blockDim.x) s_tab[q] = a.tab[q];
+  __syncthreads();
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= a.n) return;
+  const pn_inputs& in = a.in;
+  const double m1 = in.m1[i], m2 = in.m2[i], chi1 = in.chi1[i], chi2 = in.chi2[i];
+  const double s1x = in.s1x[i], s1y = in.s1y[i], s1z = in.s1z[i];
+  const double s2x = in.s2x[i], s2y = in.s2y[i], s2z = in.s2z[i];
+  const double lx = in.lx[i], ly = in.ly[i], lz = in.lz[i];
+  const double w0 = in.omega0[i], wf = in.omega_f[i];
+  // Validation of PN_ST_BAD_INPUT (same conditions as the header states).
+  bool ok = finite64(m1) && finite64(m2) && finite64(chi1) && finite64(chi2) && finite64(s1x) && finite64(s1y) &&
+            finite64(s1z) && finite64(s2x) && finite64(s2y) && finite64(s2z) && finite64(lx) && finite64(ly) &&
+            finite64(lz) && finite64(w0) && finite64(wf);
+  ok = ok && m1 > 0.0 && m2 > 0.0 && fabs(m1 + m2 - 1.0) <= 1e-12;
+  ok = ok && chi1 >= 0.0 && chi1 <= 1.0 && chi2 >= 0.0 && chi2 <= 1.0;
+  ok = ok && w0 > 0.0 && wf > w0;
+  ok = ok && fabs(sqrt(lx * lx + ly * ly + lz * lz) - 1.0) <= 1e-12;
+  if (!ok) {
+    double y[10];
+    for (int c = 0; c < 10; c++) y[c] = dnan();
+    write_result(a.out, i, y, dnan(), 0, 0, 0, PN_ST_BAD_INPUT);
+    fld(ws, stride, 36)[i] = dnan();
+    return;
+  }
+  const Coef<double> c = make_coef(m1, m2, a.ctl.terms);
+  const Coef<float> cf = to_f32(c);
+  // Initial state (Secs. II, V): omega_0, S_i = chi_i m_i^2 S_i-hat, L-hat(0).
+  double y[10], k[10];
+  y[0] = w0;
+  y[1] = chi1 * (m1 * m1) * s1x; y[2] = chi1 * (m1 * m1) * s1y; y[3] = chi1 * (m1 * m1) * s1z;
+  y[4] = chi2 * (m2 * m2) * s2x; y[5] = chi2 * (m2 * m2) * s2y; y[6] = chi2 * (m2 * m2) * s2z;
+  y[7] = lx; y[8] = ly; y[9] = lz;
+  eval_rhs<PREC>(c, cf, s_tab, y, k);
+  const double* cv = &c.K;
+#pragma unroll
+  for (int f = 0; f < 16; f++) fld(ws, stride, f)[i] = cv[f];
+#pragma unroll
+  for (int f = 0; f < 10; f++) {
+    fld(ws, stride, 16 + f)[i] = y[f];
+    fld(ws, stride, 26 + f)[i] = k[f];
+  }
+  fld(ws, stride, 36)[i] = wf;
+}
+
+// Pick up binary i from the set-up table.  Returns false if its result was
+// already written (invalid input).
+template <int PREC>
+__device__ __forceinline__ bool lane_load(Lane& L, const Ctl& ctl, const double* __restrict__ ws, int64_t stride,
+                                          int64_t i) {
+  const double wf = ws[(size_t)36 * stride + i];
+  if (!finite64(wf)) return false;
+  L.i = i;
+  double* cv = &L.c64.K;
+#pragma unroll
+  for (int f = 0; f < 16; f++) cv[f] = ws[(size_t)f * stride + i];
+  if constexpr (PREC == 1) {
+    float* fv = &L.c32.K;
+#pragma unroll
+    for (int f = 0; f < 16; f++) fv[f] = f64_to_f32(cv[f]);
+  }
+#pragma unroll
+  for (int f = 0; f < 10; f++) {
+    L.y[f] = ws[(size_t)(16 + f) * stride + i];
+    L.k1[f] = ws[(size_t)(26 + f) * stride + i];
+  }
+  L.t = 0.0;
+  L.h = ctl.h0;
+  L.h_lo = 0.0;
+  L.h_hi = 0.0;
+  L.wf = wf;
+  L.n_acc = L.n_rej = L.n_land = L.attempts = L.land_it = 0;
+  L.landing = false;
+  L.last_rej = false;
+  return true;
+}
+
+__device__ __forceinline__ void lane_commit(Lane& L, const double* y5, double hc) {
+  L.t = L.t + hc;
+#pragma unroll
+  for (int c = 0; c < 10; c++) L.y[c] = y5[c];
+  L.n_acc++;
+}
+
+// Decisions after one attempt (y5, k7 = f(y5), s = err^2).  Returns true when
+// the binary is finished, with its status in *status.
+__device__ __forceinline__ bool lane_decide(Lane& L, const Ctl& ctl, double* y5, const double* k7, double s,
+                                            int32_t* status) {
+  bool fin = ctl.fixed_step ? true : finite64(s);
+#pragma unroll
+  for (int c = 0; c < 10; c++) fin = fin && finite64(y5[c]);
+  if (!fin) { *status = PN_ST_NONFINITE; return true; }
+  const double tolw = ctl.land_tol * L.wf;
+
+  if (L.landing) {
+    L.n_land++;
+    L.land_it++;
+    const double g = y5[0] - L.wf;
+    if (fabs(g) <= tolw) {  // converged: move onto omega_f along f
+      const double dh = -g / k7[0];
+#pragma unroll
+      for (int c = 0; c < 10; c++) y5[c] = fma(dh, k7[c], y5[c]);
+      lane_commit(L, y5, L.h + dh);
+      *status = PN_ST_OK;
+      return true;
+    }
+    if (L.land_it >= ctl.land_max_iter || L.attempts >= ctl.max_steps) {
+      lane_commit(L, y5, L.h);
+      *status = (L.attempts >= ctl.max_steps) ? PN_ST_MAX_STEPS : PN_ST_LAND_MAXIT;
+      return true;
+    }
+    if (g > 0.0) L.h_hi = L.h; else L.h_lo = L.h;
+    double hn = L.h - g / k7[0];
+    if (!(hn > L.h_lo && hn < L.h_hi)) hn = 0.5 * (L.h_lo + L.h_hi);
+    L.h = hn;
+    return false;
+  }
+
+  if (ctl.fixed_step || le_pos(s, 1.0)) {
+    if (y5[0] >= L.wf) {
+      const double g = y5[0] - L.wf;
+      if (ctl.stop_mode == PN_STOP_FIRST_CROSS) {
+        lane_commit(L, y5, L.h);
+        *status = PN_ST_OK;
+        return true;
+      }
+      if (fabs(g) <= tolw) {
+        const double dh = -g / k7[0];
+#pragma unroll
+        for (int c = 0; c < 10; c++) y5[c] = fma(dh, k7[c], y5[c]);
+        lane_commit(L, y5, L.h + dh);
+        *status = PN_ST_OK;
+        return true;
+      }
+      // Retake the crossing step, seeded by the root of its Hermite cubic.
+      L.landing = true;
+      L.land_it = 0;
+      L.h_lo = 0.0;
+      L.h_hi = L.h;
+      const double hn = L.h * hermite_root(L.y[0], L.h * L.k1[0], y5[0], L.h * k7[0], L.wf);
+      L.h = (hn > L.h_lo && hn < L.h_hi) ? hn : 0.5 * (L.h_lo + L.h_hi);
+    } else {
+      lane_commit(L, y5, L.h);
+#pragma unroll
+      for (int c = 0; c < 10; c++) L.k1[c] = k7[c];
+      if (!ctl.fixed_step) L.h = L.h * step_factor(ctl, s, L.last_rej ? 1.0 : ctl.fac_max);
+      L.last_rej = false;
+    }
+  } else {
+    L.n_rej++;
+    L.h = L.h * step_factor(ctl, s, 1.0);
+    L.last_rej = true;
+    if (L.h < ctl.h_min) { *status = PN_ST_H_UNDERFLOW; return true; }
+  }
+  if (L.attempts >= ctl.max_steps) { *status = PN_ST_MAX_STEPS; return true; }
+  return false;
+}
+
+template <int PREC, bool PERSIST>
+__global__ void __launch_bounds__(kMaxBlock) k_integrate(const KArgs a, const double* __restrict__ ws,
+                                                         int64_t stride) {
+  __shared__ double s_tab[256];
+  for (int q = threadIdx.x; q < 256; q += blockDim.x) s_tab[q] = a.tab[q];
+  __syncthreads();
+
+  const unsigned lane = threadIdx.x & 31u;
+  Lane L;
+  bool have = false, exhausted = false;
+  for (;;) {
+    const bool need = !have && !exhausted;
+    int64_t idx = -1;
+    if constexpr (PERSIST) {
+      const unsigned m = __ballot_sync(0xffffffffu, need);
+      if (m != 0u) {
+        const int leader = __ffs((int)m) - 1;
+        unsigned long long base = 0ull;
+        if ((int)lane == leader) base = atomicAdd(a.queue, (unsigned long long)__popc((int)m));
+        base = __shfl_sync(0xffffffffu, base, leader);
+        if (need) idx = (int64_t)(base + (unsigned long long)__popc((int)(m & ((1u << lane) - 1u))));
+      }
+    } else {
+      if (need) idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    }
+    if (need) {
+      if (idx >= 0 && idx < a.n) have = lane_load<PREC>(L, a.ctl, ws, stride, idx);
+      if (!PERSIST || idx >= a.n) exhausted = true;
+    }
+    if (__all_sync(0xffffffffu, !have && exhausted)) break;
+    if (have) {
+      double y5[10], k7[10];
+      const double s = dp5_attempt<PREC>(L.c64, L.c32, s_tab, a.ctl, L.y, L.k1, L.h, y5, k7);
+      L.attempts++;
+      int32_t st;
+      if (lane_decide(L, a.ctl, y5, k7, s, &st)) {
+        write_result(a.out, L.i, L.y, L.t, L.n_acc, L.n_rej, L.n_land, st);
+        have = false;
+      }
+    }
+  }
+}
+
+template <int PREC, bool PERSIST>
+static const void* integrate_fn() {
+  return (const void*)k_integrate<PREC, PERSIST>;
+}
+
+static const void* pick(int prec, bool persistent) {
+  if (prec == PN_MIXED) return persistent ? integrate_fn<1, true>() : integrate_fn<1, false>();
+  return persistent ? integrate_fn<0, true>() : integrate_fn<0, false>();
+}
+
+int setup_fields() { return kSetupFields; }
+
+cudaError_t launch_setup(int prec, const KArgs& a, double* ws, int64_t stride, cudaStream_t s) {
+  if (a.n <= 0) return cudaSuccess;
+  const int block = 256;
+  const unsigned grid = (unsigned)((a.n + block - 1) / block);
+  if (prec == PN_MIXED) k_setup<1><<<grid, block, 0, s>>>(a, ws, stride);
+  else k_setup<0><<<grid, block, 0, s>>>(a, ws, stride);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_integrate(int prec, bool persistent, int block, int grid, const KArgs& a, const double* ws,
+                             int64_t stride, cudaStream_t s) {
+  if (grid <= 0) return cudaSuccess;
+  if (prec == PN_MIXED) {
+    if (persistent) k_integrate<1, true><<<grid, block, 0, s>>>(a, ws, stride);
+    else k_integrate<1, false><<<grid, block, 0, s>>>(a, ws, stride);
+  } else {
+    if (persistent) k_integrate<0, true><<<grid, block, 0, s>>>(a, ws, stride);
+    else k_integrate<0, false><<<grid, block, 0, s>>>(a, ws, stride);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t integrate_occupancy(int prec, bool persistent, int block, int* blocks_per_sm) {
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, pick(prec, persistent), block, 0);
+}
+
+// ---------------------------------------------------------------------------
+// Initial-data sampler (Sec. V): counter-based SplitMix64 uniforms
+// (Steele, Lea & Flood 2014) and Marsaglia's (1972) isotropic directions.
+// Every floating-point operation is an explicitly rounded IEEE operation, so
+// the draws are reproducible bit for bit on any IEEE machine (the log-uniform
+// mass ratio also uses exp and log).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint64_t splitmix64(uint64_t x) {  // output for state x (already advanced)
+  uint64_t z = x;
+  z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ull;
+  z = (z ^ (z >> 27)) * 0x94d049bb133111ebull;
+  return z ^ (z >> 31);
+}
+
+// j-th output (from 0) of the stream whose seed is the i-th output of the
+// stream seeded with `seed`, as a 53-bit uniform in [0, 1).
+__device__ __forceinline__ double uniform53(uint64_t seed, uint64_t i, uint64_t j) {
+  const uint64_t gamma = 0x9e3779b97f4a7c15ull;
+  const uint64_t key = splitmix64(seed + (i + 1ull) * gamma);
+  const uint64_t z = splitmix64(key + (j + 1ull) * gamma);
+  return __dmul_rn((double)(z >> 11), 1.0 / 9007199254740992.0);
+}
+
+__global__ void k_sample(uint64_t seed, pn_dist d, int64_t n, pn_inputs o) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const uint64_t ui = (uint64_t)i;
+  const double u0 = uniform53(seed, ui, 0);
+  double q;
+  if (d.q_mode == 0) q = d.q_lo;
+  else if (d.q_mode == 1) q = __dadd_rn(d.q_lo, __dmul_rn(__dsub_rn(d.q_hi, d.q_lo), u0));
+  else q = __dmul_rn(d.q_lo, exp(__dmul_rn(u0, log(__ddiv_rn(d.q_hi, d.q_lo)))));
+  const double one_q = __dadd_rn(1.0, q);
+  o.m1[i] = __ddiv_rn(q, one_q);
+  o.m2[i] = __ddiv_rn(1.0, one_q);
+  const double u1 = uniform53(seed, ui, 1), u2 = uniform53(seed, ui, 2);
+  const double span = __dsub_rn(d.chi_hi, d.chi_lo);
+  o.chi1[i] = d.chi_mode == 0 ? d.chi_lo : __dadd_rn(d.chi_lo, __dmul_rn(span, u1));
+  o.chi2[i] = d.chi_mode == 0 ? d.chi_lo : __dadd_rn(d.chi_lo, __dmul_rn(span, u2));
+  const double u3 = uniform53(seed, ui, 3);
+  o.omega0[i] = __dadd_rn(d.omega0_lo, __dmul_rn(__dsub_rn(d.omega0_hi, d.omega0_lo), u3));
+  o.omega_f[i] = d.omega_f;
+  uint64_t j = 4;
+  for (int b = 0; b < 2; b++) {
+    double vx = 0.0, vy = 0.0, vz = 1.0;
+    for (int tries = 0; tries < 64; tries++) {
+      const double x1 = __dsub_rn(__dmul_rn(2.0, uniform53(seed, ui, j)), 1.0);
+      const double x2 = __dsub_rn(__dmul_rn(2.0, uniform53(seed, ui, j + 1)), 1.0);
+      j += 2;
+      const double s = __dadd_rn(__dmul_rn(x1, x1), __dmul_rn(x2, x2));
+      if (s >= 1.0) continue;
+      const double r = __dsqrt_rn(__dsub_rn(1.0, s));
+      vx = __dmul_rn(__dmul_rn(2.0, x1), r);
+      vy = __dmul_rn(__dmul_rn(2.0, x2), r);
+      vz = __dsub_rn(1.0, __dmul_rn(2.0, s));
+      break;
+    }
+    if (b == 0) { o.s1x[i] = vx; o.s1y[i] = vy; o.s1z[i] = vz; }
+    else { o.s2x[i] = vx; o.s2y[i] = vy; o.s2z[i] = vz; }
+  }
+  o.lx[i] = 0.0; o.ly[i] = 0.0; o.lz[i] = 1.0;
+}
+
+cudaError_t launch_sample(uint64_t seed, const pn_dist& d, int64_t n, const pn_inputs& in, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  const int block = 256;
+  const int64_t grid = (n + block - 1) / block;
+  k_sample<<<(unsigned)grid, block, 0, s>>>(seed, d, n, in);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Batch statistics: per-status counts, step totals and extremes, and the
+// Pearson moments of initial vs final scalar products (Sec. V A).
+// Layout of a stat record (kStatWords doubles):
+//   0..7 count per status, 8 acc sum, 9 rej sum, 10 land sum,
+//   11 acc min, 12 acc max, 13 attempts min, 14 attempts max,
+//   15 pearson count, then for p in 0..2: 16+5p .. 20+5p = sum x, sum y, sum xx, sum yy, sum xy,
+//   31 sum final s1s2, 32 sum final s1s2^2.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ double warp_sum(double v) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+__device__ __forceinline__ double warp_min(double v) {
+  for (int o = 16; o > 0; o >>= 1) v = fmin(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+__device__ __forceinline__ double warp_max(double v) {
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+
+__device__ __forceinline__ bool is_minmax(int w) { return w >= 11 && w <= 14; }
+__device__ __forceinline__ bool is_min(int w) { return w == 11 || w == 13; }
+
+__device__ void block_reduce_store(double (*acc)[kStatWords], double* v, double* dst) {
+  // v: this thread's kStatWords values; acc: shared [32][kStatWords]
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int w = 0; w < kStatWords; w++) {
+    double x = is_minmax(w) ? (is_min(w) ? warp_min(v[w]) : warp_max(v[w])) : warp_sum(v[w]);
+    if (lane == 0) acc[wid][w] = x;
+  }
+  __syncthreads();
+  if (threadIdx.x < kStatWords) {
+    const int w = threadIdx.x;
+    double x = acc[0][w];
+    for (int k = 1; k < nw; k++) {
+      const double z = acc[k][w];
+      x = is_minmax(w) ? (is_min(w) ? fmin(x, z) : fmax(x, z)) : x + z;
+    }
+    dst[w] = x;
+  }
+}
+
+__device__ __forceinline__ double unit_dot(double ax, double ay, double az, double bx, double by, double bz) {
+  const double na = sqrt(ax * ax + ay * ay + az * az), nb = sqrt(bx * bx + by * by + bz * bz);
+  return (ax * bx + ay * by + az * bz) / (na * nb);
+}
+
+__global__ void __launch_bounds__(256) k_stats_part(int64_t n, pn_inputs in, pn_outputs out, double* part) {
+  __shared__ double acc[32][kStatWords];
+  double v[kStatWords];
+  for (int w = 0; w < kStatWords; w++) v[w] = 0.0;
+  v[11] = v[13] = 1e300;
+  v[12] = v[14] = -1e300;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const int st = out.status[i];
+    v[(st >= 0 && st < 8) ? st : 7] += 1.0;
+    const double a = out.n_acc[i], r = out.n_rej[i], l = out.n_land[i];
+    v[8] += a; v[9] += r; v[10] += l;
+    v[11] = fmin(v[11], a); v[12] = fmax(v[12], a);
+    v[13] = fmin(v[13], a + r + l); v[14] = fmax(v[14], a + r + l);
+    if (st == PN_ST_OK) {
+      const double x0 = unit_dot(in.s1x[i], in.s1y[i], in.s1z[i], in.s2x[i], in.s2y[i], in.s2z[i]);
+      const double x1 = unit_dot(in.lx[i], in.ly[i], in.lz[i], in.s1x[i], in.s1y[i], in.s1z[i]);
+      const double x2 = unit_dot(in.lx[i], in.ly[i], in.lz[i], in.s2x[i], in.s2y[i], in.s2z[i]);
+      const double y0 = out.dot_s1s2[i], y1 = out.dot_ls1[i], y2 = out.dot_ls2[i];
+      if (isfinite(x0) && isfinite(x1) && isfinite(x2) && isfinite(y0) && isfinite(y1) && isfinite(y2)) {
+        const double xs[3] = {x0, x1, x2}, ys[3] = {y0, y1, y2};
+        v[15] += 1.0;
+        for (int p = 0; p < 3; p++) {
+          v[16 + 5 * p] += xs[p];
+          v[17 + 5 * p] += ys[p];
+          v[18 + 5 * p] += xs[p] * xs[p];
+          v[19 + 5 * p] += ys[p] * ys[p];
+          v[20 + 5 * p] += xs[p] * ys[p];
+        }
+        v[31] += y0;
+        v[32] += y0 * y0;
+      }
+    }
+  }
+  block_reduce_store(acc, v, part + (size_t)blockIdx.x * kStatWords);
+}
+
+__global__ void __launch_bounds__(256) k_stats_total(const double* part, int nparts, double* total) {
+  __shared__ double acc[32][kStatWords];
+  double v[kStatWords];
+  for (int w = 0; w < kStatWords; w++) v[w] = is_minmax(w) ? (is_min(w) ? 1e300 : -1e300) : 0.0;
+  for (int p = threadIdx.x; p < nparts; p += blockDim.x)
+    for (int w = 0; w < kStatWords; w++) {
+      const double z = part[(size_t)p * kStatWords + w];
+      v[w] = is_minmax(w) ? (is_min(w) ? fmin(v[w], z) : fmax(v[w], z)) : v[w] + z;
+    }
+  block_reduce_store(acc, v, total);
+}
+
+cudaError_t launch_stats(int64_t n, const pn_inputs& in, const pn_outputs& out, double* part, double* total,
+                         cudaStream_t s) {
+  k_stats_part<<<kStatGrid, 256, 0, s>>>(n, in, out, part);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  k_stats_total<<<1, 256, 0, s>>>(part, kStatGrid, total);
+  return cudaGetLastError();
+}
+
+void fill_log_table(double* tab) {
+  for (int j = 0; j < 128; j++) {
+    const long double F = 1.0L + (long double)(2 * j + 1) / 256.0L;
+    tab[2 * j] = (double)(1.0L / F);
+    tab[2 * j + 1] = (double)logl(F);
+  }
+}
+
+}  // namespace pn
