@@ -251,8 +251,26 @@ int pn_batch_stats(pn_batch *b, int64_t n, const pn_inputs *in, const pn_outputs
 /* Release the workspace (waits for the stream).  NULL is ignored. */
 void pn_batch_destroy(pn_batch *b);
 
-/* Message of the last error on b (or of the last failed pn_batch_init on this
- * thread when b is NULL); empty string if none.  Valid until the next call. */
+/* Integrate binaries 0..n-1 like pn_batch_integrate (persistent schedule, 128
+ * threads per block) without allocating any device memory, for callers that
+ * must not allocate: hosts that give all device memory to their own pool or
+ * budget and cannot have a library call cudaMalloc behind their back.  The
+ * paper has no counterpart; it is a deployment variant of the same kernels.
+ * Scratch (work-queue counter, logarithm table, per-binary set-up table) lives
+ * in one fixed area of about 4.6 MiB inside the library's device image, held
+ * on every GPU that loads the library until exit, so n <= 16384 per call
+ * (larger n: PN_E_ARG).  No pn_batch is needed: *p, *in and *out are as for
+ * pn_batch_init / pn_batch_integrate, and the work is queued on cuda_stream
+ * (cudaStream_t, NULL = legacy default) without waiting.  All calls share the
+ * area (each call resets what it reads), so calls whose GPU work overlaps race.
+ * The first call on a device looks up the area's address and uploads the
+ * logarithm table with a synchronous copy; make that first call before any
+ * stream capture.  Errors: PN_E_ARG, PN_E_CUDA; message via pn_last_error(NULL). */
+int pn_integrate_noalloc(int64_t n, const pn_params *p, const pn_inputs *in, pn_outputs *out, void *cuda_stream);
+
+/* Message of the last error on b (or, when b is NULL, of the last failed
+ * pn_batch_init or pn_integrate_noalloc on this thread); empty string if none.
+ * Valid until the next call. */
 const char *pn_last_error(const pn_batch *b);
 
 #ifdef __cplusplus

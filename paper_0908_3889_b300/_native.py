@@ -95,6 +95,8 @@ SIGNATURES = {
     "pn_batch_stats": (C.c_int, [C.c_void_p, C.c_int64, C.POINTER(pn_inputs), C.POINTER(pn_outputs),
                                  C.POINTER(pn_stats)]),
     "pn_batch_destroy": (None, [C.c_void_p]),
+    "pn_integrate_noalloc": (C.c_int, [C.c_int64, C.POINTER(pn_params), C.POINTER(pn_inputs), C.POINTER(pn_outputs),
+                                       C.c_void_p]),
     "pn_last_error": (C.c_char_p, [C.c_void_p]),
 }
 

@@ -66,6 +66,19 @@ static int cuda_fail(pn_batch* b, cudaError_t e, const char* what) {
 
 extern "C" int pn_abi_version(void) { return PN_ABI_VERSION; }
 
+static bool params_valid(const pn_params* p, std::string* why);
+static pn::Ctl make_ctl(const pn_params& p);
+static bool inputs_ok(const pn_inputs* in);
+static bool outputs_ok(const pn_outputs* o);
+
+// Helpers for entry points that run without a pn_batch (pn_noalloc.cu).
+namespace pn {
+int set_thread_error(int code, const std::string& msg) { return fail(nullptr, code, msg); }
+bool check_params(const pn_params* p, std::string* why) { return params_valid(p, why); }
+bool check_io(const pn_inputs* in, const pn_outputs* out) { return inputs_ok(in) && outputs_ok(out); }
+Ctl ctl_from(const pn_params& p) { return make_ctl(p); }
+}  // namespace pn
+
 extern "C" void pn_params_default(pn_params* p) {
   if (!p) return;
   std::memset(p, 0, sizeof(*p));

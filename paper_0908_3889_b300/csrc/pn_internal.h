@@ -3,6 +3,8 @@
 
 #include <cuda_runtime.h>
 
+#include <string>
+
 #include "pn_batch.h"
 #include "pn_device.cuh"
 
@@ -37,6 +39,13 @@ constexpr int kStatWords = 40;
 constexpr int kStatGrid = 296;
 cudaError_t launch_stats(int64_t n, const pn_inputs& in, const pn_outputs& out, double* part, double* total,
                          cudaStream_t s);
+
+// Parameter and pointer checks shared by the C entry points (pn_capi.cu), and
+// the thread-local error message that pn_last_error(NULL) returns.
+int set_thread_error(int code, const std::string& msg);
+bool check_params(const pn_params* p, std::string* why);
+bool check_io(const pn_inputs* in, const pn_outputs* out);
+Ctl ctl_from(const pn_params& p);
 
 // Host-side table for log_tang: tab[2j] = 1/F_j, tab[2j+1] = ln F_j, F_j = 1 + (2j+1)/256.
 void fill_log_table(double* tab256);
