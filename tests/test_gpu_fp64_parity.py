@@ -113,11 +113,23 @@ def test_bad_inputs_and_limits(pn, orc):
 def test_first_cross_mode_within_its_conditioning(pn, orc):
     """Stopping at the first crossing returns the overshooting state, which depends directly on the last
     step size; the error controller fixes step sizes only to ~1e-9 under roundoff (the oracle itself moves
-    that much when h0 changes by one ulp).  The GPU must agree within 10x the oracle's own sensitivity."""
+    that much when h0 or an input changes by one ulp).  The GPU must agree within 10x the largest of the
+    oracle's own responses to one-ulp perturbations."""
     ens = workloads.config("C4", n=300)
     o = orc.integrate(ens, orc.params(stop_mode=1))
-    o_ulp = orc.integrate(ens, orc.params(stop_mode=1, h0=10.0 * (1 + 2.0**-52)))
-    sens = parity_errors(o_ulp, o)
+    sens = {}
+    variants = []
+    for kw in (dict(h0=10.0 * (1 + 2.0**-52)), dict(h0=10.0 * (1 - 2.0**-53))):
+        variants.append((ens, kw))
+    for key in ("omega0", "s1hat", "m1"):
+        e2 = {k: v.copy() for k, v in ens.items()}
+        e2[key] = e2[key] * (1 + 2.0**-52)
+        if key == "m1":
+            e2["m2"] = 1 - e2["m1"]
+        variants.append((e2, {}))
+    for e2, kw in variants:  # the oracle's own response to one-ulp perturbations
+        e_ulp = parity_errors(orc.integrate(e2, orc.params(stop_mode=1, **kw)), o)
+        sens = {k: max(sens.get(k, 0.0), v) for k, v in e_ulp.items()}
     g = run_gpu(pn, ens, stop_mode=1)
     assert np.array_equal(g["status"], o["status"]) and np.all(decided_alike(g, o))
     e = parity_errors(g, o)
