@@ -262,11 +262,11 @@ def main():
             "flops_per_attempt": FLOPS_ATTEMPT, "attempts_per_launch": attempts,
             "kernel": "pn::k_integrate<FP64>"}
 
-    # Mixed precision on the same ensemble.
-    mixed = None
-    if not args.no_mixed:
-        with pn.Batch(n, pn.params(precision=1)) as b:
-            b.autotune(inp)
+    # Mixed precision on the same ensemble: FP32 right-hand side (PN_MIXED) and
+    # double-single right-hand side on the FP32 pipe (PN_MIXED_DS).
+    def mixed_run(prec):
+        with pn.Batch(n, pn.params(precision=prec)) as b:
+            tn = b.autotune(inp)
             mix_ms, _, _ = timed_run(b, args.steps, 1)
             mst = b.stats(inp, out)
         mix_ms = max_over_ranks(mix_ms)
@@ -277,10 +277,18 @@ def main():
             errs[k] = {"max": float(d.max()), "p99": float(torch.quantile(d[:1_000_000].float(), 0.99)),
                        "p50": float(d.median())}
         m_attempts = mst["acc_total"] + mst["rej_total"] + mst["land_total"]
-        mixed = {"value": world * n * args.steps / (mix_ms * 1e-3), "unit": "inspirals/s",
-                 "ms_per_step": mix_ms / args.steps, "speedup_vs_fp64": total_ms / mix_ms,
-                 "dot_err_vs_fp64": errs, "fp64_pipe_achieved_tflops": (FLOPS_STEP * m_attempts) /
-                 (mix_ms / args.steps * 1e-3) / 1e12, "fp32_peak_tflops": (f32_peak or 0) / 1e12}
+        return {"value": world * n * args.steps / (mix_ms * 1e-3), "unit": "inspirals/s",
+                "ms_per_step": mix_ms / args.steps, "speedup_vs_fp64": total_ms / mix_ms,
+                "dot_err_vs_fp64": errs, "schedule": {1: "plain", 2: "persistent"}.get(tn["schedule"]),
+                "block": tn["block"], "fp64_pipe_achieved_tflops": (FLOPS_STEP * m_attempts) /
+                (mix_ms / args.steps * 1e-3) / 1e12}
+
+    mixed = mixed_ds = None
+    if not args.no_mixed:
+        mixed = mixed_run(1)
+        mixed["rhs"] = "FP32"
+        mixed_ds = mixed_run(2)
+        mixed_ds["rhs"] = "double-single (pairs of FP32) on the FP32 pipe"
 
     # End to end through the host-buffer entry point (pinned host memory).
     e2e = None
@@ -326,7 +334,7 @@ def main():
                            "parallelism": f"replicas x{world}", "attempts_per_binary": attempts / n,
                            "kernel_sha": sha},
                 "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": args.steps,
-                "clocks": clocks, "mixed": mixed,
+                "clocks": clocks, "mixed": mixed, "mixed_ds": mixed_ds,
                 "fp32_fma_peak_tflops": (f32_peak or 0) / 1e12, "fp64_fma_peak_tflops": (f64_peak or 0) / 1e12}
         print(json.dumps(line), flush=True)
     if tdist:

@@ -53,6 +53,8 @@ extern "C" {
 /* ---- parameter enums ---- */
 #define PN_FP64 0  /* everything in FP64 */
 #define PN_MIXED 1 /* right-hand side in FP32; stages, state, error estimate and step control in FP64 */
+#define PN_MIXED_DS 2 /* right-hand side in double-single (pairs of FP32, ~48-bit significand) on the FP32
+                         pipe; stages, state, error estimate and step control in FP64 */
 
 #define PN_STOP_LAND 0        /* stop exactly on omega_f (default) */
 #define PN_STOP_FIRST_CROSS 1 /* stop at the first accepted state with omega >= omega_f */
@@ -97,7 +99,7 @@ typedef struct {
   uint32_t term_mask;    /* PN_TERM_* bits, default PN_TERM_ALL */
   int32_t theta_mode;    /* PN_THETA_* */
   int32_t fixed_step;    /* 1: accept every attempt with h = h0 (convergence studies), default 0 */
-  int32_t precision;     /* PN_FP64 or PN_MIXED */
+  int32_t precision;     /* PN_FP64, PN_MIXED or PN_MIXED_DS */
   int32_t schedule;      /* PN_SCHED_* */
   int32_t block;         /* threads per block (multiple of 32, <= 512); 0 = autotuned / default */
   int32_t bpt;           /* binaries per thread, 1 or 2; 0 = autotuned / default */

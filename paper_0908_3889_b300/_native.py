@@ -13,7 +13,7 @@ LIB_PATH = os.path.join(HERE, "libpn_b300.so")
 
 PN_OK, PN_E_ARG, PN_E_CUDA, PN_E_NOMEM, PN_E_UNIMPLEMENTED = 0, -1, -2, -3, -4
 PN_ST_OK, PN_ST_MAX_STEPS, PN_ST_H_UNDERFLOW, PN_ST_NONFINITE, PN_ST_BAD_INPUT, PN_ST_LAND_MAXIT = range(6)
-PN_FP64, PN_MIXED = 0, 1
+PN_FP64, PN_MIXED, PN_MIXED_DS = 0, 1, 2
 PN_STOP_LAND, PN_STOP_FIRST_CROSS = 0, 1
 PN_THETA_BCV2, PN_THETA_AS_PRINTED = 0, 1
 PN_SCHED_AUTO, PN_SCHED_PLAIN, PN_SCHED_PERSISTENT = 0, 1, 2

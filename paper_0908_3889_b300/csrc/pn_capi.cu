@@ -37,7 +37,7 @@ struct pn_batch {
   struct Tuned {
     bool valid = false;
     int schedule = PN_SCHED_PERSISTENT, block = 128, bpt = 1;
-  } tuned[2];
+  } tuned[3];
   // staging for pn_batch_integrate_host
   double* d_stage_d = nullptr;
   int32_t* d_stage_i = nullptr;
@@ -124,7 +124,7 @@ static bool params_valid(const pn_params* p, std::string* why) {
   if (p->theta_mode != PN_THETA_BCV2 && p->theta_mode != PN_THETA_AS_PRINTED) return bad("bad theta_mode");
   if (p->term_mask & ~PN_TERM_ALL) return bad("unknown term_mask bits");
   if (p->fixed_step != 0 && p->fixed_step != 1) return bad("fixed_step must be 0 or 1");
-  if (p->precision != PN_FP64 && p->precision != PN_MIXED) return bad("bad precision");
+  if (p->precision != PN_FP64 && p->precision != PN_MIXED && p->precision != PN_MIXED_DS) return bad("bad precision");
   if (p->schedule < PN_SCHED_AUTO || p->schedule > PN_SCHED_PERSISTENT) return bad("bad schedule");
   if (p->block != 0 && (p->block < 32 || p->block > pn::kMaxBlock || p->block % 32 != 0))
     return bad("block must be 0 or a multiple of 32 in [32, 256]");
@@ -199,12 +199,12 @@ extern "C" int pn_batch_init(pn_batch** out, int64_t n_max, const pn_params* p, 
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&b->num_sms, cudaDevAttrMultiProcessorCount, b->device);
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking);
   if (e == cudaSuccess) e = cudaMalloc(&b->d_queue, sizeof(unsigned long long));
-  if (e == cudaSuccess) e = cudaMalloc(&b->d_tab, 256 * sizeof(double));
+  if (e == cudaSuccess) e = cudaMalloc(&b->d_tab, pn::kLogTabBytes);
   if (e == cudaSuccess) e = cudaMalloc(&b->d_stat_part, (size_t)pn::kStatGrid * pn::kStatWords * sizeof(double));
   if (e == cudaSuccess) e = cudaMalloc(&b->d_stat_total, pn::kStatWords * sizeof(double));
   for (int k = 0; k < 4 && e == cudaSuccess; k++) e = cudaEventCreate(&b->ev[k]);
   if (e == cudaSuccess) {
-    double tab[256];
+    double tab[pn::kLogTabBytes / sizeof(double)];
     pn::fill_log_table(tab);
     e = cudaMemcpy(b->d_tab, tab, sizeof(tab), cudaMemcpyHostToDevice);
   }

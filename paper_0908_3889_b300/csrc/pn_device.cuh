@@ -317,6 +317,189 @@ __device__ __forceinline__ void rhs32(const Coef<float>& c, const float* y, floa
 }
 
 // ---------------------------------------------------------------------------
+// Double-single ("pair of FP32") arithmetic for the PN_MIXED_DS right-hand
+// side: a value is hi + lo with |lo| <= ulp(hi)/2, about 48 significand bits.
+// Error-free transformations: Knuth's two-sum and Dekker's fast two-sum for
+// addition, the FMA-based exact product for multiplication; the
+// double-single add and multiply follow the usual pair-arithmetic recipes
+// (Dekker 1971; Bailey's DSFUN).  Every operation is an explicitly rounded
+// FP32 instruction (no reassociation or contraction) on the FP32 pipe, which
+// on B300 has 64x the FP64 pipe's throughput.
+// ---------------------------------------------------------------------------
+struct ds {
+  float hi, lo;
+};
+
+__device__ __forceinline__ ds ds_of(float h) { return ds{h, 0.0f}; }
+// s + e = a + b exactly, given |a| >= |b| or a == 0.
+__device__ __forceinline__ ds fast_two_sum(float a, float b) {
+  const float s = __fadd_rn(a, b);
+  return ds{s, __fsub_rn(b, __fsub_rn(s, a))};
+}
+// s + e = a + b exactly.
+__device__ __forceinline__ ds two_sum(float a, float b) {
+  const float s = __fadd_rn(a, b);
+  const float v = __fsub_rn(s, a);
+  return ds{s, __fadd_rn(__fsub_rn(a, __fsub_rn(s, v)), __fsub_rn(b, v))};
+}
+// p + e = a * b exactly.
+__device__ __forceinline__ ds two_prod(float a, float b) {
+  const float p = __fmul_rn(a, b);
+  return ds{p, __fmaf_rn(a, b, -p)};
+}
+__device__ __forceinline__ ds ds_add(ds a, ds b) {
+  const ds s = two_sum(a.hi, b.hi);
+  return fast_two_sum(s.hi, __fadd_rn(s.lo, __fadd_rn(a.lo, b.lo)));
+}
+__device__ __forceinline__ ds ds_neg(ds a) { return ds{-a.hi, -a.lo}; }
+__device__ __forceinline__ ds ds_sub(ds a, ds b) { return ds_add(a, ds_neg(b)); }
+__device__ __forceinline__ ds ds_mul(ds a, ds b) {
+  const float p = __fmul_rn(a.hi, b.hi);
+  float e = __fmaf_rn(a.hi, b.hi, -p);
+  e = __fmaf_rn(a.hi, b.lo, e);
+  e = __fmaf_rn(a.lo, b.hi, e);
+  return fast_two_sum(p, e);
+}
+__device__ __forceinline__ ds ds_mul_f(ds a, float b) {
+  const float p = __fmul_rn(a.hi, b);
+  float e = __fmaf_rn(a.hi, b, -p);
+  e = __fmaf_rn(a.lo, b, e);
+  return fast_two_sum(p, e);
+}
+__device__ __forceinline__ ds ds_fma(ds a, ds b, ds c) { return ds_add(ds_mul(a, b), c); }  // a b + c
+// Exact scaling by a power of two given as a float.
+__device__ __forceinline__ ds ds_scale(ds a, float p2) { return ds{a.hi * p2, a.lo * p2}; }
+
+// double -> double-single: hi is d rounded to FP32 (f64_to_f32); the residual
+// d - hi is the low 29 significand bits of d (minus 2^29 when hi was rounded
+// up), an integer R with |R| <= 2^28, so lo = R * 2^(E - 1075) rounded to FP32.
+// Integer and FP32 instructions only.  For |d| outside [2^-74, 2^180) lo is 0.
+__device__ __forceinline__ ds split64(double d) {
+  const float hi = f64_to_f32(d);
+  const uint32_t lw = lo32(d), hw = hi32(d);
+  const uint32_t E = (hw >> 20) & 0x7ffu;
+  const int32_t R = ((int32_t)(lw << 3)) >> 3;
+  float lo = __fmul_rn(__int2float_rn(R), __uint_as_float((E - 948u) << 23));
+  lo = __uint_as_float(__float_as_uint(lo) ^ (hw & 0x80000000u));
+  if (E - 949u > 253u) lo = 0.0f;
+  return ds{hi, lo};
+}
+
+// double-single -> double (exact sum of the two parts).
+__device__ __forceinline__ double ds_to_f64(ds a) { return f32_to_f64(a.hi) + f32_to_f64(a.lo); }
+
+// x^(-1/3) in double-single: FP32 seed r0 = rcbrtf(hi), then
+// r0 (1 + e/3 + 2e^2/9) with e = 1 - x r0^3 formed in double-single.
+__device__ __forceinline__ ds ds_inv_cbrt(ds x) {
+  const float r0 = rcbrtf(x.hi);
+  const ds r3 = ds_mul_f(two_prod(r0, r0), r0);
+  const ds e = ds_sub(ds_of(1.0f), ds_mul(x, r3));
+  const float t = __fmul_rn(e.hi, __fmaf_rn(e.hi, 2.0f / 9.0f, 1.0f / 3.0f));
+  return two_sum(r0, __fmul_rn(r0, t));
+}
+
+// ln(2) = PN_LN2F_1 + PN_LN2F_2 + PN_LN2F_3 (16, 24, 24 significant bits), so
+// k * PN_LN2F_1 is exact in FP32 for |k| < 256.
+#define PN_LN2F_1 0.693145751953125f
+#define PN_LN2F_2 1.428606765330187e-06f
+#define PN_LN2F_3 5.497923148104107e-14f
+
+// ln|x| in double-single by Tang's table method on the FP32 high part:
+// |x| = 2^k m, F = 1 + (2j+1)/256 with j the top 7 fraction bits of m,
+// u = (m - F + lo/2^k) / F (|u| < 2^-8), ln(1 + u) = u - u^2/2 (double-single)
+// + u^3 (1/3 - u/4 + u^2/5 - u^3/6) (FP32), and ln|x| = k ln2 + ln F + ln(1 + u).
+// tabf[4j..4j+3] = 1/F_j (hi, lo), ln F_j (hi, lo).  |x| must be a normal FP32 value.
+__device__ __forceinline__ ds ds_log(ds x, const float* __restrict__ tabf) {
+  const bool neg = x.hi < 0.0f;
+  const float h = neg ? -x.hi : x.hi, l = neg ? -x.lo : x.lo;
+  const uint32_t hb = __float_as_uint(h);
+  const int k = (int)(hb >> 23) - 127;
+  const uint32_t j = (hb >> 16) & 127u;
+  const float m = __uint_as_float((hb & 0x007fffffu) | 0x3f800000u);
+  const float F = __uint_as_float(0x3f800000u | ((2u * j + 1u) << 15));
+  const float l_scaled = __fmul_rn(l, __uint_as_float((uint32_t)(127 - k) << 23));
+  const ds f = two_sum(__fsub_rn(m, F), l_scaled);
+  const ds u = ds_mul(f, ds{tabf[4 * j], tabf[4 * j + 1]});
+  const ds u2h = ds_scale(ds_mul(u, u), -0.5f);
+  const float uh = u.hi;
+  float q = __fmaf_rn(uh, -1.0f / 6.0f, 0.2f);
+  q = __fmaf_rn(q, uh, -0.25f);
+  q = __fmaf_rn(q, uh, 1.0f / 3.0f);
+  const float tail = __fmul_rn(__fmul_rn(__fmul_rn(uh, uh), uh), q);
+  const ds ln1pu = ds_add(ds_add(u, u2h), ds_of(tail));
+  const float kf = (float)k;
+  ds kl = ds_add(ds_of(__fmul_rn(kf, PN_LN2F_1)), two_prod(kf, PN_LN2F_2));
+  kl = ds_add(kl, ds_of(__fmul_rn(kf, PN_LN2F_3)));
+  return ds_add(ds_add(kl, ds{tabf[4 * j + 2], tabf[4 * j + 3]}), ln1pu);
+}
+
+// The right-hand side of Eqs. (1)-(4) in double-single arithmetic, the same
+// formulation as rhs64.  |omega| outside the FP32 normal range gives NaN.
+__device__ __forceinline__ void rhs_ds(const Coef<ds>& c, const float* __restrict__ tabf, const ds* y, ds* f) {
+  const ds w = y[0];
+  const ds S1x = y[1], S1y = y[2], S1z = y[3];
+  const ds S2x = y[4], S2y = y[5], S2z = y[6];
+  const ds Lx = y[7], Ly = y[8], Lz = y[9];
+  ds r = ds_inv_cbrt(w);
+  if ((__float_as_uint(w.hi) & 0x7fffffffu) - 0x00800000u >= 0x7f000000u) r = ds{__int_as_float(0x7fc00000), 0.0f};
+  const ds v = ds_mul(w, ds_mul(r, r));
+  const ds v2 = ds_mul(v, v);
+  const ds lw = ds_log(w, tabf);
+  const ds LS1 = ds_fma(Lz, S1z, ds_fma(Ly, S1y, ds_mul(Lx, S1x)));
+  const ds LS2 = ds_fma(Lz, S2z, ds_fma(Ly, S2y, ds_mul(Lx, S2x)));
+  const ds S12 = ds_fma(S1z, S2z, ds_fma(S1y, S2y, ds_mul(S1x, S2x)));
+  const ds so = ds_fma(c.w1, LS1, ds_fma(c.w2, LS2, ds_neg(c.tail)));
+  const ds c2p = ds_fma(c.ss721, ds_mul(LS1, LS2), ds_fma(ds_neg(c.ss247), S12, c.c2));
+  const ds c3p = ds_fma(c.clog, lw, c.c3l);
+  ds P = ds_fma(v, c.c35, c3p);
+  P = ds_fma(v, P, c.c25);
+  P = ds_fma(v, P, c2p);
+  P = ds_fma(v, P, ds_neg(so));
+  P = ds_fma(v, P, c.c1);
+  P = ds_fma(v2, P, ds_of(1.0f));
+  const ds w2 = ds_mul(w, w);
+  f[0] = ds_mul(ds_mul(ds_mul(ds_mul(w2, w), v2), c.K), P);
+  const ds A1x = ds_sub(ds_mul(Ly, S1z), ds_mul(Lz, S1y)), A1y = ds_sub(ds_mul(Lz, S1x), ds_mul(Lx, S1z)),
+           A1z = ds_sub(ds_mul(Lx, S1y), ds_mul(Ly, S1x));
+  const ds A2x = ds_sub(ds_mul(Ly, S2z), ds_mul(Lz, S2y)), A2y = ds_sub(ds_mul(Lz, S2x), ds_mul(Lx, S2z)),
+           A2z = ds_sub(ds_mul(Lx, S2y), ds_mul(Ly, S2x));
+  const ds Cx = ds_sub(ds_mul(S1y, S2z), ds_mul(S1z, S2y)), Cy = ds_sub(ds_mul(S1z, S2x), ds_mul(S1x, S2z)),
+           Cz = ds_sub(ds_mul(S1x, S2y), ds_mul(S1y, S2x));
+  const ds pre = ds_mul(c.prec, w2);
+  const ds p1 = ds_mul(pre, ds_fma(c.a1, r, ds_mul_f(LS2, -3.0f)));
+  const ds p2 = ds_mul(pre, ds_fma(c.a2, r, ds_mul_f(LS1, -3.0f)));
+  const ds pCx = ds_mul(pre, Cx), pCy = ds_mul(pre, Cy), pCz = ds_mul(pre, Cz);
+  const ds d1x = ds_sub(ds_mul(p1, A1x), pCx), d1y = ds_sub(ds_mul(p1, A1y), pCy), d1z = ds_sub(ds_mul(p1, A1z), pCz);
+  const ds d2x = ds_fma(p2, A2x, pCx), d2y = ds_fma(p2, A2y, pCy), d2z = ds_fma(p2, A2z, pCz);
+  f[1] = d1x; f[2] = d1y; f[3] = d1z;
+  f[4] = d2x; f[5] = d2y; f[6] = d2z;
+  const ds lf = ds_mul(v, c.nie);
+  f[7] = ds_mul(lf, ds_add(d1x, d2x));
+  f[8] = ds_mul(lf, ds_add(d1y, d2y));
+  f[9] = ds_mul(lf, ds_add(d1z, d2z));
+}
+
+__device__ __forceinline__ Coef<ds> to_ds(const Coef<double>& c) {
+  Coef<ds> r;
+  const double* s = &c.K;
+  ds* d = &r.K;
+#pragma unroll
+  for (int k = 0; k < 16; k++) d[k] = split64(s[k]);
+  return r;
+}
+
+// Coefficients in the precisions the kernels use, and the two logarithm tables.
+struct Coefs {
+  Coef<double> c64;
+  Coef<float> c32;
+  Coef<ds> cds;
+};
+struct Tabs {
+  const double* d;  // 256 doubles for log_tang
+  const float* f;   // 512 floats for ds_log
+};
+
+// ---------------------------------------------------------------------------
 // Dormand & Prince (1980) RK5(4)7M coefficients (published table).
 // ---------------------------------------------------------------------------
 #define DP_A21 (1.0 / 5.0)
@@ -357,20 +540,27 @@ struct Ctl {
   int32_t pad_;
 };
 
-// k = f(y) in the kernel's precision (PREC 0: FP64; 1: FP32 RHS with the
-// state rounded to FP32 on the way in and the rates widened on the way out).
+// k = f(y) in the kernel's precision: PREC 0 FP64; 1 FP32 (state rounded to
+// FP32 on the way in, rates widened on the way out); 2 double-single (state
+// split into FP32 pairs, rates summed back to FP64).
 template <int PREC>
-__device__ __forceinline__ void eval_rhs(const Coef<double>& c64, const Coef<float>& c32,
-                                         const double* __restrict__ tab, const double* y, double* k) {
+__device__ __forceinline__ void eval_rhs(const Coefs& cf, const Tabs& tb, const double* y, double* k) {
   if constexpr (PREC == 0) {
-    rhs64(c64, tab, y, k);
-  } else {
+    rhs64(cf.c64, tb.d, y, k);
+  } else if constexpr (PREC == 1) {
     float yf[10], kf[10];
 #pragma unroll
     for (int i = 0; i < 10; i++) yf[i] = f64_to_f32(y[i]);
-    rhs32(c32, yf, kf);
+    rhs32(cf.c32, yf, kf);
 #pragma unroll
     for (int i = 0; i < 10; i++) k[i] = f32_to_f64(kf[i]);
+  } else {
+    ds yd[10], kd[10];
+#pragma unroll
+    for (int i = 0; i < 10; i++) yd[i] = split64(y[i]);
+    rhs_ds(cf.cds, tb.f, yd, kd);
+#pragma unroll
+    for (int i = 0; i < 10; i++) k[i] = ds_to_f64(kd[i]);
   }
 }
 
@@ -378,8 +568,7 @@ __device__ __forceinline__ void eval_rhs(const Coef<double>& c64, const Coef<flo
 // Writes y5 (the 5th-order solution), k7 = f(y5) and returns the mean of the
 // squared scaled error components, s = err^2 (err = RMS norm).
 template <int PREC>
-__device__ __forceinline__ double dp5_attempt(const Coef<double>& c64, const Coef<float>& c32,
-                                              const double* __restrict__ tab, const Ctl& ctl, const double* y,
+__device__ __forceinline__ double dp5_attempt(const Coefs& cf, const Tabs& tb, const Ctl& ctl, const double* y,
                                               const double* k1, double h, double* y5, double* k7) {
   double k2[10], k3[10], k4[10], k5[10], k6[10], ys[10];
   {
@@ -387,39 +576,39 @@ __device__ __forceinline__ double dp5_attempt(const Coef<double>& c64, const Coe
 #pragma unroll
     for (int i = 0; i < 10; i++) ys[i] = fma(a1, k1[i], y[i]);
   }
-  eval_rhs<PREC>(c64, c32, tab, ys, k2);
+  eval_rhs<PREC>(cf, tb, ys, k2);
   {
     const double a1 = h * DP_A31, a2 = h * DP_A32;
 #pragma unroll
     for (int i = 0; i < 10; i++) ys[i] = fma(a2, k2[i], fma(a1, k1[i], y[i]));
   }
-  eval_rhs<PREC>(c64, c32, tab, ys, k3);
+  eval_rhs<PREC>(cf, tb, ys, k3);
   {
     const double a1 = h * DP_A41, a2 = h * DP_A42, a3 = h * DP_A43;
 #pragma unroll
     for (int i = 0; i < 10; i++) ys[i] = fma(a3, k3[i], fma(a2, k2[i], fma(a1, k1[i], y[i])));
   }
-  eval_rhs<PREC>(c64, c32, tab, ys, k4);
+  eval_rhs<PREC>(cf, tb, ys, k4);
   {
     const double a1 = h * DP_A51, a2 = h * DP_A52, a3 = h * DP_A53, a4 = h * DP_A54;
 #pragma unroll
     for (int i = 0; i < 10; i++) ys[i] = fma(a4, k4[i], fma(a3, k3[i], fma(a2, k2[i], fma(a1, k1[i], y[i]))));
   }
-  eval_rhs<PREC>(c64, c32, tab, ys, k5);
+  eval_rhs<PREC>(cf, tb, ys, k5);
   {
     const double a1 = h * DP_A61, a2 = h * DP_A62, a3 = h * DP_A63, a4 = h * DP_A64, a5 = h * DP_A65;
 #pragma unroll
     for (int i = 0; i < 10; i++)
       ys[i] = fma(a5, k5[i], fma(a4, k4[i], fma(a3, k3[i], fma(a2, k2[i], fma(a1, k1[i], y[i])))));
   }
-  eval_rhs<PREC>(c64, c32, tab, ys, k6);
+  eval_rhs<PREC>(cf, tb, ys, k6);
   {
     const double b1 = h * DP_B1, b3 = h * DP_B3, b4 = h * DP_B4, b5 = h * DP_B5, b6 = h * DP_B6;
 #pragma unroll
     for (int i = 0; i < 10; i++)
       y5[i] = fma(b6, k6[i], fma(b5, k5[i], fma(b4, k4[i], fma(b3, k3[i], fma(b1, k1[i], y[i])))));
   }
-  eval_rhs<PREC>(c64, c32, tab, y5, k7);
+  eval_rhs<PREC>(cf, tb, y5, k7);
   const double e1 = h * DP_E1, e3 = h * DP_E3, e4 = h * DP_E4, e5 = h * DP_E5, e6 = h * DP_E6, e7 = h * DP_E7;
   double sum = 0.0;
 #pragma unroll
@@ -428,6 +617,81 @@ __device__ __forceinline__ double dp5_attempt(const Coef<double>& c64, const Coe
     const double sc = fma(ctl.rtol, max_abs(y[i], y5[i]), ctl.atol);
     const double q = e * rcp_pos(sc);
     sum = fma(q, q, sum);
+  }
+  return sum * 0.1;
+}
+
+// Stage tableau for the rolled attempt: row r is stage s = r + 2; entry 0 is
+// the coefficient of k1, entry 1 + m the coefficient of the rate computed m + 1
+// stages earlier (k_{s-1-m}); the last row is b (first same as last).  Stage s
+// uses s - 2 earlier rates (the k2 weight of b is 0, so stage 7 uses 4).
+__constant__ double c_dp_rows[6][6] = {
+    {DP_A21, 0, 0, 0, 0, 0},
+    {DP_A31, DP_A32, 0, 0, 0, 0},
+    {DP_A41, DP_A43, DP_A42, 0, 0, 0},
+    {DP_A51, DP_A54, DP_A53, DP_A52, 0, 0},
+    {DP_A61, DP_A65, DP_A64, DP_A63, DP_A62, 0},
+    {DP_B1, DP_B6, DP_B5, DP_B4, DP_B3, 0},
+};
+
+// The same attempt as dp5_attempt with the six stages rolled into one loop, so
+// the right-hand side is emitted once: the double-single right-hand side is
+// large enough that six inlined copies overflow the instruction cache.  The
+// earlier rates sit in a register queue q (q[0] newest), shifted after each
+// stage; each stage adds only its non-zero terms (a uniform branch).
+template <int PREC>
+__device__ __forceinline__ double dp5_attempt_rolled(const Coefs& cf, const Tabs& tb, const Ctl& ctl, const double* y,
+                                                     const double* k1, double h, double* y5, double* k7) {
+  double q[5][10], ys[10], kn[10];
+#pragma unroll 1
+  for (int r = 0; r < 6; r++) {
+    const double c0 = h * c_dp_rows[r][0];
+#pragma unroll
+    for (int i = 0; i < 10; i++) ys[i] = fma(c0, k1[i], y[i]);
+    const int nt = (r < 5) ? r : 4;
+    if (nt > 0) {
+      const double c = h * c_dp_rows[r][1];
+#pragma unroll
+      for (int i = 0; i < 10; i++) ys[i] = fma(c, q[0][i], ys[i]);
+      if (nt > 1) {
+        const double c2 = h * c_dp_rows[r][2];
+#pragma unroll
+        for (int i = 0; i < 10; i++) ys[i] = fma(c2, q[1][i], ys[i]);
+        if (nt > 2) {
+          const double c3 = h * c_dp_rows[r][3];
+#pragma unroll
+          for (int i = 0; i < 10; i++) ys[i] = fma(c3, q[2][i], ys[i]);
+          if (nt > 3) {
+            const double c4 = h * c_dp_rows[r][4];
+#pragma unroll
+            for (int i = 0; i < 10; i++) ys[i] = fma(c4, q[3][i], ys[i]);
+          }
+        }
+      }
+    }
+    eval_rhs<PREC>(cf, tb, ys, kn);
+    if (r < 5) {
+#pragma unroll
+      for (int i = 0; i < 10; i++) {
+        q[4][i] = q[3][i];
+        q[3][i] = q[2][i];
+        q[2][i] = q[1][i];
+        q[1][i] = q[0][i];
+        q[0][i] = kn[i];
+      }
+    }
+  }
+  // q holds k6, k5, k4, k3, k2; ys is y5 and kn is k7.
+  const double e1 = h * DP_E1, e3 = h * DP_E3, e4 = h * DP_E4, e5 = h * DP_E5, e6 = h * DP_E6, e7 = h * DP_E7;
+  double sum = 0.0;
+#pragma unroll
+  for (int i = 0; i < 10; i++) {
+    y5[i] = ys[i];
+    k7[i] = kn[i];
+    const double e = fma(e7, kn[i], fma(e6, q[0][i], fma(e5, q[1][i], fma(e4, q[2][i], fma(e3, q[3][i], e1 * k1[i])))));
+    const double sc = fma(ctl.rtol, max_abs(y[i], ys[i]), ctl.atol);
+    const double qq = e * rcp_pos(sc);
+    sum = fma(qq, qq, sum);
   }
   return sum * 0.1;
 }

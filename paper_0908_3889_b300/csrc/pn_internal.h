@@ -15,7 +15,7 @@ struct KArgs {
   pn_outputs out;
   int64_t n;
   unsigned long long* queue;  // persistent schedule: next unclaimed binary index
-  const double* tab;          // 256 doubles: (1/F_j, ln F_j) of the logarithm table
+  const double* tab;          // logarithm tables: 256 doubles (1/F_j, ln F_j), then 512 floats (pairs)
   Ctl ctl;
 };
 
@@ -47,7 +47,9 @@ bool check_params(const pn_params* p, std::string* why);
 bool check_io(const pn_inputs* in, const pn_outputs* out);
 Ctl ctl_from(const pn_params& p);
 
-// Host-side table for log_tang: tab[2j] = 1/F_j, tab[2j+1] = ln F_j, F_j = 1 + (2j+1)/256.
-void fill_log_table(double* tab256);
+// Host-side logarithm tables (kLogTabBytes): tab[2j] = 1/F_j, tab[2j+1] = ln F_j for log_tang, then
+// 512 floats for ds_log: (1/F_j hi, lo, ln F_j hi, lo), F_j = 1 + (2j+1)/256.
+constexpr size_t kLogTabBytes = 256 * sizeof(double) + 512 * sizeof(float);
+void fill_log_table(double* tab);
 
 }  // namespace pn

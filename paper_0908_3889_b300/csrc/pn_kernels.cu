@@ -29,9 +29,21 @@ struct Lane {
   double t, h, h_lo, h_hi, wf;
   int32_t n_acc, n_rej, n_land, attempts, land_it;
   bool landing, last_rej;
-  Coef<double> c64;
-  Coef<float> c32;
+  Coefs cf;
 };
+
+// Shared-memory copies of the logarithm tables the kernel's precision needs.
+template <int PREC>
+__device__ __forceinline__ Tabs load_tabs(const double* __restrict__ g, double* s_tab, float* s_tabf) {
+  if constexpr (PREC == 0) {
+    for (int q = threadIdx.x; q < 256; q += blockDim.x) s_tab[q] = g[q];
+  } else if constexpr (PREC == 2) {
+    const float* gf = (const float*)(g + 256);
+    for (int q = threadIdx.x; q < 512; q += blockDim.x) s_tabf[q] = gf[q];
+  }
+  __syncthreads();
+  return Tabs{s_tab, s_tabf};
+}
 
 __device__ __forceinline__ void write_result(const pn_outputs& o, int64_t i, const double* y, double t, int32_t n_acc,
                                              int32_t n_rej, int32_t n_land, int32_t status) {
@@ -62,8 +74,8 @@ __device__ __forceinline__ double* fld(double* ws, int64_t stride, int f) { retu
 template <int PREC>
 __global__ void __launch_bounds__(256) k_setup(const KArgs a, double* __restrict__ ws, int64_t stride) {
   __shared__ double s_tab[256];
-  for (int q = threadIdx.x; q < 256; q += blockDim.x) s_tab[q] = a.tab[q];
-  __syncthreads();
+  __shared__ float s_tabf[512];
+  const Tabs tb = load_tabs<PREC>(a.tab, s_tab, s_tabf);
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= a.n) return;
   const pn_inputs& in = a.in;
@@ -87,15 +99,18 @@ __global__ void __launch_bounds__(256) k_setup(const KArgs a, double* __restrict
     fld(ws, stride, 36)[i] = dnan();
     return;
   }
-  const Coef<double> c = make_coef(m1, m2, a.ctl.terms);
-  const Coef<float> cf = to_f32(c);
+  Coefs cf;
+  cf.c64 = make_coef(m1, m2, a.ctl.terms);
+  if constexpr (PREC == 1) cf.c32 = to_f32(cf.c64);
+  if constexpr (PREC == 2) cf.cds = to_ds(cf.c64);
+  const Coef<double>& c = cf.c64;
   // Initial state (Secs. II, V): omega_0, S_i = chi_i m_i^2 S_i-hat, L-hat(0).
   double y[10], k[10];
   y[0] = w0;
   y[1] = chi1 * (m1 * m1) * s1x; y[2] = chi1 * (m1 * m1) * s1y; y[3] = chi1 * (m1 * m1) * s1z;
   y[4] = chi2 * (m2 * m2) * s2x; y[5] = chi2 * (m2 * m2) * s2y; y[6] = chi2 * (m2 * m2) * s2z;
   y[7] = lx; y[8] = ly; y[9] = lz;
-  eval_rhs<PREC>(c, cf, s_tab, y, k);
+  eval_rhs<PREC>(cf, tb, y, k);
   const double* cv = &c.K;
 #pragma unroll
   for (int f = 0; f < 16; f++) fld(ws, stride, f)[i] = cv[f];
@@ -115,14 +130,11 @@ __device__ __forceinline__ bool lane_load(Lane& L, const Ctl& ctl, const double*
   const double wf = ws[(size_t)36 * stride + i];
   if (!finite64(wf)) return false;
   L.i = i;
-  double* cv = &L.c64.K;
+  double* cv = &L.cf.c64.K;
 #pragma unroll
   for (int f = 0; f < 16; f++) cv[f] = ws[(size_t)f * stride + i];
-  if constexpr (PREC == 1) {
-    float* fv = &L.c32.K;
-#pragma unroll
-    for (int f = 0; f < 16; f++) fv[f] = f64_to_f32(cv[f]);
-  }
+  if constexpr (PREC == 1) L.cf.c32 = to_f32(L.cf.c64);
+  if constexpr (PREC == 2) L.cf.cds = to_ds(L.cf.c64);
 #pragma unroll
   for (int f = 0; f < 10; f++) {
     L.y[f] = ws[(size_t)(16 + f) * stride + i];
@@ -224,8 +236,8 @@ template <int PREC, bool PERSIST>
 __global__ void __launch_bounds__(kMaxBlock) k_integrate(const KArgs a, const double* __restrict__ ws,
                                                          int64_t stride) {
   __shared__ double s_tab[256];
-  for (int q = threadIdx.x; q < 256; q += blockDim.x) s_tab[q] = a.tab[q];
-  __syncthreads();
+  __shared__ float s_tabf[512];
+  const Tabs tb = load_tabs<PREC>(a.tab, s_tab, s_tabf);
 
   const unsigned lane = threadIdx.x & 31u;
   Lane L;
@@ -252,7 +264,8 @@ __global__ void __launch_bounds__(kMaxBlock) k_integrate(const KArgs a, const do
     if (__all_sync(0xffffffffu, !have && exhausted)) break;
     if (have) {
       double y5[10], k7[10];
-      const double s = dp5_attempt<PREC>(L.c64, L.c32, s_tab, a.ctl, L.y, L.k1, L.h, y5, k7);
+      const double s = (PREC == 2) ? dp5_attempt_rolled<PREC>(L.cf, tb, a.ctl, L.y, L.k1, L.h, y5, k7)
+                                   : dp5_attempt<PREC>(L.cf, tb, a.ctl, L.y, L.k1, L.h, y5, k7);
       L.attempts++;
       int32_t st;
       if (lane_decide(L, a.ctl, y5, k7, s, &st)) {
@@ -270,6 +283,7 @@ static const void* integrate_fn() {
 
 static const void* pick(int prec, bool persistent) {
   if (prec == PN_MIXED) return persistent ? integrate_fn<1, true>() : integrate_fn<1, false>();
+  if (prec == PN_MIXED_DS) return persistent ? integrate_fn<2, true>() : integrate_fn<2, false>();
   return persistent ? integrate_fn<0, true>() : integrate_fn<0, false>();
 }
 
@@ -280,6 +294,7 @@ cudaError_t launch_setup(int prec, const KArgs& a, double* ws, int64_t stride, c
   const int block = 256;
   const unsigned grid = (unsigned)((a.n + block - 1) / block);
   if (prec == PN_MIXED) k_setup<1><<<grid, block, 0, s>>>(a, ws, stride);
+  else if (prec == PN_MIXED_DS) k_setup<2><<<grid, block, 0, s>>>(a, ws, stride);
   else k_setup<0><<<grid, block, 0, s>>>(a, ws, stride);
   return cudaGetLastError();
 }
@@ -290,6 +305,9 @@ cudaError_t launch_integrate(int prec, bool persistent, int block, int grid, con
   if (prec == PN_MIXED) {
     if (persistent) k_integrate<1, true><<<grid, block, 0, s>>>(a, ws, stride);
     else k_integrate<1, false><<<grid, block, 0, s>>>(a, ws, stride);
+  } else if (prec == PN_MIXED_DS) {
+    if (persistent) k_integrate<2, true><<<grid, block, 0, s>>>(a, ws, stride);
+    else k_integrate<2, false><<<grid, block, 0, s>>>(a, ws, stride);
   } else {
     if (persistent) k_integrate<0, true><<<grid, block, 0, s>>>(a, ws, stride);
     else k_integrate<0, false><<<grid, block, 0, s>>>(a, ws, stride);
@@ -479,10 +497,17 @@ cudaError_t launch_stats(int64_t n, const pn_inputs& in, const pn_outputs& out, 
 }
 
 void fill_log_table(double* tab) {
+  float* tabf = (float*)(tab + 256);
   for (int j = 0; j < 128; j++) {
     const long double F = 1.0L + (long double)(2 * j + 1) / 256.0L;
-    tab[2 * j] = (double)(1.0L / F);
-    tab[2 * j + 1] = (double)logl(F);
+    const long double inv = 1.0L / F, ln = logl(F);
+    tab[2 * j] = (double)inv;
+    tab[2 * j + 1] = (double)ln;
+    const float ih = (float)inv, lh = (float)ln;
+    tabf[4 * j] = ih;
+    tabf[4 * j + 1] = (float)(inv - (long double)ih);
+    tabf[4 * j + 2] = lh;
+    tabf[4 * j + 3] = (float)(ln - (long double)lh);
   }
 }
 

@@ -29,8 +29,8 @@ namespace {
 
 constexpr int64_t kNoAllocMax = 16384;  // binaries per call
 constexpr size_t kQueueOff = 0;         // unsigned long long work-queue counter
-constexpr size_t kTabOff = 256;         // 256 doubles of the logarithm table
-constexpr size_t kSetupOff = 256 + 256 * sizeof(double);
+constexpr size_t kTabOff = 256;         // the logarithm tables (pn::kLogTabBytes)
+constexpr size_t kSetupOff = 256 + 4096;
 constexpr size_t kNoAllocBytes = kSetupOff + (size_t)37 * kNoAllocMax * sizeof(double);
 
 static __device__ __align__(256) unsigned char g_scratch[kNoAllocBytes];
@@ -38,7 +38,7 @@ static __device__ __align__(256) unsigned char g_scratch[kNoAllocBytes];
 constexpr int kMaxDevices = 64;
 std::mutex g_mu;
 unsigned char* g_ptr[kMaxDevices] = {};  // device address of g_scratch per device, once looked up
-double g_host_tab[256];
+double g_host_tab[pn::kLogTabBytes / sizeof(double)];
 
 int scratch_for_current_device(unsigned char** out, std::string* why) {
   int dev = 0;
@@ -50,7 +50,8 @@ int scratch_for_current_device(unsigned char** out, std::string* why) {
     void* p = nullptr;
     e = cudaGetSymbolAddress(&p, g_scratch);
     if (e != cudaSuccess) { *why = std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e); return PN_E_CUDA; }
-    if (pn::setup_fields() * (size_t)kNoAllocMax * sizeof(double) + kSetupOff > kNoAllocBytes) {
+    if (pn::setup_fields() * (size_t)kNoAllocMax * sizeof(double) + kSetupOff > kNoAllocBytes ||
+        kTabOff + pn::kLogTabBytes > kSetupOff) {
       *why = "set-up table does not fit the scratch area";
       return PN_E_ARG;
     }

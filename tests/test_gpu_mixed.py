@@ -72,3 +72,43 @@ def test_mixed_small_ensembles(pn, orc, schedule):
         assert np.array_equal(g["status"], o["status"])
         for k in ("dot_s1s2", "dot_ls1", "dot_ls2"):
             assert np.median(e[k]) <= DOT_TOL and np.max(e[k]) <= 5e-3, (name, k, np.median(e[k]), np.max(e[k]))
+
+
+# ---------------------------------------------------------------------------
+# Double-single right-hand side (PN_MIXED_DS): rates accurate to ~1e-13, so the
+# step decisions are those of the FP64 run and the 1e-6 bar on the final scalar
+# products holds for every binary, not just the typical one.
+# ---------------------------------------------------------------------------
+def test_ds_full_size_subsample_meets_dot_bar(pn, orc):
+    import torch
+    from gpu_util import decided_alike
+    ens = workloads.config("C3")
+    n = ens["m1"].shape[0]
+    inp = pn.to_device(ens)
+    with pn.Batch(n, pn.params(precision=2)) as b:
+        out = b.integrate(inp)
+        torch.cuda.synchronize()
+    idx = workloads.subsample(n, 4096, seed=workloads.SEED_BASE + 104)
+    g = {k: v[..., idx] for k, v in pn.to_numpy(out).items()}
+    o = orc.integrate(workloads.take(ens, idx))
+    assert np.array_equal(g["status"], o["status"])
+    e = mixed_errors(g, o)
+    report = {k: (float(np.max(v)), float(np.median(v))) for k, v in e.items()}
+    print("double-single vs FP64 (max, median):", report, "same decisions:", float(np.mean(decided_alike(g, o))))
+    for k in ("dot_s1s2", "dot_ls1", "dot_ls2"):
+        assert report[k][0] <= DOT_TOL, (k, report[k])
+    assert np.mean(decided_alike(g, o)) >= 0.999
+
+
+@pytest.mark.parametrize("schedule", [1, 2])
+def test_ds_small_ensembles(pn, orc, schedule):
+    import torch
+    for name in ("C0", "C2", "C4"):
+        ens = workloads.config(name, n=2000)
+        o = orc.integrate(ens)
+        g = pn.to_numpy(pn.integrate(pn.to_device(ens), precision=2, schedule=schedule))
+        torch.cuda.synchronize()
+        e = mixed_errors(g, o)
+        assert np.array_equal(g["status"], o["status"])
+        for k in ("dot_s1s2", "dot_ls1", "dot_ls2"):
+            assert np.max(e[k]) <= DOT_TOL, (name, k, np.max(e[k]))
