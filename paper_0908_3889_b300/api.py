@@ -292,3 +292,60 @@ def integrate(inputs: dict, **kw) -> dict:
     n = int(inputs["m1"].shape[0])
     with Batch(max(n, 1), params(**kw)) as b:
         return b.integrate(inputs)
+
+
+class PNAdjointFn(torch.autograd.Function):
+    """Final outputs as a differentiable function of the initial spin directions and the mass ratio.
+
+    apply(s1hat (3, n), s2hat (3, n), q (n,), chi1, chi2, omega0, omega_f, lhat (3, n), prm=None)
+    returns (dot_s1s2, dot_ls1, dot_ls2, Lhat (3, n), S1 (3, n), S2 (3, n), t); m1 = q/(1+q),
+    m2 = 1/(1+q) (M = 1).  backward calls pn_batch_adjoint: reverse mode through the accepted
+    Dormand-Prince steps with the step sizes held fixed and the stop at omega_f differentiated as an
+    implicit function.  Needs PN_FP64 and PN_STOP_LAND.
+    """
+
+    @staticmethod
+    def forward(ctx, s1hat, s2hat, q, chi1, chi2, omega0, omega_f, lhat, prm=None):
+        n = int(q.shape[0])
+        inp = alloc_inputs(n, q.device)
+        inp["s1hat"].copy_(s1hat.detach())
+        inp["s2hat"].copy_(s2hat.detach())
+        qd = q.detach()
+        inp["m1"].copy_(qd / (1.0 + qd))
+        inp["m2"].copy_(1.0 / (1.0 + qd))
+        for k, v in (("chi1", chi1), ("chi2", chi2), ("omega0", omega0), ("omega_f", omega_f), ("lhat", lhat)):
+            inp[k].copy_(v.detach())
+        b = Batch(n, prm or params())
+        out = b.integrate(inp)
+        ctx.pn = (b, inp, n)
+        return (out["dot_s1s2"].clone(), out["dot_ls1"].clone(), out["dot_ls2"].clone(), out["Lhat"].clone(),
+                out["S1"].clone(), out["S2"].clone(), out["t"].clone())
+
+    @staticmethod
+    def backward(ctx, g12, gl1, gl2, gL, gS1, gS2, gt):
+        b, inp, n = ctx.pn
+        cot = {}
+        for k, g in (("dot_s1s2", g12), ("dot_ls1", gl1), ("dot_ls2", gl2), ("t", gt)):
+            if g is not None:
+                cot[k] = g.contiguous()
+        for name, g in (("L", gL), ("S1", gS1), ("S2", gS2)):
+            if g is not None:
+                g = g.contiguous()
+                for c, ax in enumerate("xyz"):
+                    cot[name + ax] = g[c].contiguous()
+        grads = {f: torch.empty(n, dtype=torch.float64, device=inp["m1"].device) for f in N.GRAD_FIELDS}
+        pn_batch_adjoint(b.handle, n, inp, cot, grads)
+        b.close()
+        gs1 = torch.stack([grads["s1x"], grads["s1y"], grads["s1z"]])
+        gs2 = torch.stack([grads["s2x"], grads["s2y"], grads["s2z"]])
+        return gs1, gs2, grads["q"], None, None, None, None, None, None
+
+
+def adjoint(inputs: dict, cotangents: dict, n: int | None = None, **kw) -> dict:
+    """Gradients of sum_i cotangents_i . outputs_i w.r.t. s1x..s2z and q (pn_batch_adjoint)."""
+    n = int(inputs["m1"].shape[0]) if n is None else n
+    grads = {f: torch.empty(n, dtype=torch.float64, device=inputs["m1"].device) for f in N.GRAD_FIELDS}
+    with Batch(max(n, 1), params(**kw)) as b:
+        pn_batch_adjoint(b.handle, n, inputs, cotangents, grads)
+        torch.cuda.synchronize()
+    return grads

@@ -26,7 +26,7 @@ struct pn_batch {
   double* d_stat_part = nullptr;
   double* d_stat_total = nullptr;
   double* d_setup = nullptr;  // per-binary set-up table, setup_fields() x n_max doubles
-  cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+  cudaEvent_t ev[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};  // integrate, autotune, adjoint
   bool timed_integrate = false, timed_adjoint = false;
   // graph of the last persistent launch
   cudaGraphExec_t gexec = nullptr;
@@ -38,6 +38,16 @@ struct pn_batch {
     bool valid = false;
     int schedule = PN_SCHED_PERSISTENT, block = 128, bpt = 1;
   } tuned[3];
+  // adjoint workspace: recorded steps and checkpoints, per-lane segment states
+  double* d_rec_h = nullptr;
+  double* d_rec_ck = nullptr;
+  int32_t rec_cap = 0, rec_every = 0;
+  int* d_overflow = nullptr;
+  double* d_seg = nullptr;
+  int64_t seg_lanes = 0;
+  int32_t seg_every = 0;
+  double* d_adj_out = nullptr;   // forward outputs when the caller passes none
+  int32_t* d_adj_out_i = nullptr;
   // staging for pn_batch_integrate_host
   double* d_stage_d = nullptr;
   int32_t* d_stage_i = nullptr;
@@ -178,6 +188,12 @@ extern "C" void pn_batch_destroy(pn_batch* b) {
   cudaFree(b->d_stat_part);
   cudaFree(b->d_stat_total);
   cudaFree(b->d_setup);
+  cudaFree(b->d_rec_h);
+  cudaFree(b->d_rec_ck);
+  cudaFree(b->d_overflow);
+  cudaFree(b->d_seg);
+  cudaFree(b->d_adj_out);
+  cudaFree(b->d_adj_out_i);
   cudaFree(b->d_stage_d);
   cudaFree(b->d_stage_i);
   delete b;
@@ -202,7 +218,7 @@ extern "C" int pn_batch_init(pn_batch** out, int64_t n_max, const pn_params* p, 
   if (e == cudaSuccess) e = cudaMalloc(&b->d_tab, pn::kLogTabBytes);
   if (e == cudaSuccess) e = cudaMalloc(&b->d_stat_part, (size_t)pn::kStatGrid * pn::kStatWords * sizeof(double));
   if (e == cudaSuccess) e = cudaMalloc(&b->d_stat_total, pn::kStatWords * sizeof(double));
-  for (int k = 0; k < 4 && e == cudaSuccess; k++) e = cudaEventCreate(&b->ev[k]);
+  for (int k = 0; k < 6 && e == cudaSuccess; k++) e = cudaEventCreate(&b->ev[k]);
   if (e == cudaSuccess) {
     double tab[pn::kLogTabBytes / sizeof(double)];
     pn::fill_log_table(tab);
@@ -440,9 +456,147 @@ extern "C" int pn_batch_autotune(pn_batch* b, int64_t n, const pn_inputs* in, pn
 
 extern "C" int pn_batch_adjoint(pn_batch* b, int64_t n, const pn_inputs* in, const pn_cotangents* gbar,
                                 pn_grads* grad, pn_outputs* out) {
-  (void)n; (void)in; (void)gbar; (void)grad; (void)out;
   if (!b) return fail(nullptr, PN_E_ARG, "batch is NULL");
-  return fail(b, PN_E_UNIMPLEMENTED, "pn_batch_adjoint is not built yet");
+  if (n < 0 || n > b->n_max) return fail(b, PN_E_ARG, "n must be in [0, n_max]");
+  if (!inputs_ok(in)) return fail(b, PN_E_ARG, "NULL input pointer");
+  if (!gbar) return fail(b, PN_E_ARG, "cotangents struct is NULL");
+  if (!grad || !grad->s1x || !grad->s1y || !grad->s1z || !grad->s2x || !grad->s2y || !grad->s2z || !grad->q)
+    return fail(b, PN_E_ARG, "NULL gradient pointer");
+  if (out && !outputs_ok(out)) return fail(b, PN_E_ARG, "NULL output pointer");
+  if (b->p.precision != PN_FP64 || b->p.stop_mode != PN_STOP_LAND || b->p.fixed_step)
+    return fail(b, PN_E_UNIMPLEMENTED, "the adjoint needs precision PN_FP64, PN_STOP_LAND and adaptive steps");
+  if (n == 0) return PN_OK;
+  const size_t N = (size_t)b->n_max;
+  pn_outputs o;
+  if (out) {
+    o = *out;
+  } else {
+    if (!b->d_adj_out) {
+      if (cudaMalloc(&b->d_adj_out, 14 * N * sizeof(double)) != cudaSuccess ||
+          cudaMalloc(&b->d_adj_out_i, 4 * N * sizeof(int32_t)) != cudaSuccess) {
+        cudaGetLastError();
+        cudaFree(b->d_adj_out);
+        b->d_adj_out = nullptr;
+        return fail(b, PN_E_NOMEM, "adjoint output allocation failed");
+      }
+    }
+    double* D = b->d_adj_out;
+    double** op[14] = {&o.S1x, &o.S1y, &o.S1z, &o.S2x, &o.S2y, &o.S2z, &o.Lx, &o.Ly, &o.Lz, &o.omega, &o.t,
+                       &o.dot_s1s2, &o.dot_ls1, &o.dot_ls2};
+    for (int k = 0; k < 14; k++) *op[k] = D + (size_t)k * N;
+    o.n_acc = b->d_adj_out_i;
+    o.n_rej = b->d_adj_out_i + N;
+    o.n_land = b->d_adj_out_i + 2 * N;
+    o.status = b->d_adj_out_i + 3 * N;
+  }
+  if (!b->d_overflow && cudaMalloc(&b->d_overflow, sizeof(int)) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(b, PN_E_NOMEM, "adjoint flag allocation failed");
+  }
+  if (!b->d_setup) {
+    if (cudaMalloc(&b->d_setup, (size_t)pn::setup_fields() * N * sizeof(double)) != cudaSuccess) {
+      cudaGetLastError();
+      b->d_setup = nullptr;
+      return fail(b, PN_E_NOMEM, "set-up table allocation failed");
+    }
+  }
+  const int every = b->p.ckpt_every;
+  KArgs a;
+  std::memset(&a, 0, sizeof(a));
+  a.in = *in;
+  a.out = o;
+  a.n = n;
+  a.queue = b->d_queue;
+  a.tab = b->d_tab;
+  a.ctl = make_ctl(b->p);
+  PN_CUDA(b, cudaEventRecord(b->ev[4], b->stream));
+
+  // Forward pass recording the accepted steps; grow the record and rerun if a
+  // binary needed more steps than it holds.
+  int32_t cap = b->rec_cap > 0 ? b->rec_cap : 256;
+  for (int attempt = 0; attempt < 2; attempt++) {
+    if (cap % every) cap += every - cap % every;
+    if (b->rec_cap != cap || b->rec_every != every || !b->d_rec_h) {
+      cudaFree(b->d_rec_h);
+      cudaFree(b->d_rec_ck);
+      b->d_rec_h = b->d_rec_ck = nullptr;
+      b->rec_cap = b->rec_every = 0;
+      if (cudaMalloc(&b->d_rec_h, (size_t)cap * N * sizeof(double)) != cudaSuccess ||
+          cudaMalloc(&b->d_rec_ck, ((size_t)cap / every + 1) * 10 * N * sizeof(double)) != cudaSuccess) {
+        cudaGetLastError();
+        cudaFree(b->d_rec_h);
+        b->d_rec_h = nullptr;
+        b->d_rec_ck = nullptr;
+        return fail(b, PN_E_NOMEM, "adjoint record allocation failed");
+      }
+      b->rec_cap = cap;
+      b->rec_every = every;
+    }
+    pn::RecArgs rec;
+    rec.h = b->d_rec_h;
+    rec.ck = b->d_rec_ck;
+    rec.overflow = b->d_overflow;
+    rec.stride = b->n_max;
+    rec.cap = cap;
+    rec.every = every;
+    const int block = 128;
+    int per_sm = 0;
+    PN_CUDA(b, pn::record_occupancy(block, &per_sm));
+    const int64_t full = (n + block - 1) / block, capg = (int64_t)b->num_sms * (per_sm > 0 ? per_sm : 1);
+    const int grid = (int)(full < capg ? full : capg);
+    PN_CUDA(b, cudaMemsetAsync(b->d_overflow, 0, sizeof(int), b->stream));
+    PN_CUDA(b, cudaMemsetAsync(b->d_queue, 0, sizeof(unsigned long long), b->stream));
+    PN_CUDA(b, pn::launch_setup(PN_FP64, a, b->d_setup, b->n_max, b->stream));
+    PN_CUDA(b, pn::launch_integrate_record(a, b->d_setup, b->n_max, rec, block, grid, b->stream));
+    int overflow = 0;
+    PN_CUDA(b, cudaMemcpyAsync(&overflow, b->d_overflow, sizeof(int), cudaMemcpyDeviceToHost, b->stream));
+    PN_CUDA(b, cudaStreamSynchronize(b->stream));
+    if (!overflow) break;
+    if (attempt == 1) return fail(b, PN_E_ARG, "adjoint: step record overflow after growing it");
+    // size the record to the longest binary
+    double t[pn::kStatWords];
+    PN_CUDA(b, pn::launch_stats(n, *in, o, b->d_stat_part, b->d_stat_total, b->stream));
+    PN_CUDA(b, cudaMemcpyAsync(t, b->d_stat_total, sizeof(t), cudaMemcpyDeviceToHost, b->stream));
+    PN_CUDA(b, cudaStreamSynchronize(b->stream));
+    cap = (int32_t)t[12] + 1;
+  }
+
+  // Reverse sweep, persistent: one binary per claim, lane-private segment buffer.
+  const int block = 128;
+  int per_sm = 0;
+  PN_CUDA(b, pn::adjoint_occupancy(block, &per_sm));
+  const int64_t full = (n + block - 1) / block, capg = (int64_t)b->num_sms * (per_sm > 0 ? per_sm : 1);
+  const int grid = (int)(full < capg ? full : capg);
+  const int64_t lanes = (int64_t)grid * block;
+  if (!b->d_seg || b->seg_lanes < lanes || b->seg_every != every) {
+    cudaFree(b->d_seg);
+    b->d_seg = nullptr;
+    b->seg_lanes = 0;
+    if (cudaMalloc(&b->d_seg, (size_t)lanes * every * 10 * sizeof(double)) != cudaSuccess) {
+      cudaGetLastError();
+      b->d_seg = nullptr;
+      return fail(b, PN_E_NOMEM, "adjoint segment allocation failed");
+    }
+    b->seg_lanes = lanes;
+    b->seg_every = every;
+  }
+  pn::AdjArgs aa;
+  std::memset(&aa, 0, sizeof(aa));
+  aa.k = a;
+  aa.h = b->d_rec_h;
+  aa.ck = b->d_rec_ck;
+  aa.seg = b->d_seg;
+  aa.stride = b->n_max;
+  aa.seg_stride = b->seg_lanes;
+  aa.cap = b->rec_cap;
+  aa.every = every;
+  aa.gbar = *gbar;
+  aa.grad = *grad;
+  PN_CUDA(b, cudaMemsetAsync(b->d_queue, 0, sizeof(unsigned long long), b->stream));
+  PN_CUDA(b, pn::launch_adjoint(aa, block, grid, b->stream));
+  PN_CUDA(b, cudaEventRecord(b->ev[5], b->stream));
+  b->timed_adjoint = true;
+  return PN_OK;
 }
 
 extern "C" int pn_batch_sample(pn_batch* b, uint64_t seed, const pn_dist* d, int64_t n, const pn_inputs* in) {
@@ -495,7 +649,7 @@ extern "C" int pn_batch_stats(pn_batch* b, int64_t n, const pn_inputs* in, const
   host->std_final_s1s2 = N > 1 ? std::sqrt((t[32] - t[31] * t[31] / N) / (N - 1)) : NAN;
   float ms = 0.f;
   host->ms_last_integrate = (b->timed_integrate && cudaEventElapsedTime(&ms, b->ev[0], b->ev[1]) == cudaSuccess) ? ms : NAN;
-  host->ms_last_adjoint = NAN;
+  host->ms_last_adjoint = (b->timed_adjoint && cudaEventElapsedTime(&ms, b->ev[4], b->ev[5]) == cudaSuccess) ? ms : NAN;
   cudaGetLastError();
   return PN_OK;
 }

@@ -21,6 +21,32 @@ struct KArgs {
 
 constexpr int kMaxBlock = 256;
 
+// Recording of accepted steps and checkpoints by the forward pass of the adjoint.
+struct RecArgs {
+  double* h;         // cap x stride step sizes
+  double* ck;        // (cap/every + 1) x 10 x stride checkpoint states
+  int* overflow;     // set to 1 if a binary needs more than cap accepted steps
+  int64_t stride;    // >= n
+  int32_t cap, every;
+};
+
+struct AdjArgs {
+  KArgs k;           // inputs, forward outputs, n, queue, log table, controls
+  const double* h;   // recorded step sizes (RecArgs layout)
+  const double* ck;  // recorded checkpoints
+  double* seg;       // per-lane segment states: every x 10 x seg_stride
+  int64_t stride, seg_stride;
+  int32_t cap, every;
+  pn_cotangents gbar;
+  pn_grads grad;
+};
+
+cudaError_t launch_integrate_record(const KArgs& a, const double* ws, int64_t stride, const RecArgs& rec, int block,
+                                    int grid, cudaStream_t s);
+cudaError_t record_occupancy(int block, int* blocks_per_sm);
+cudaError_t launch_adjoint(const AdjArgs& a, int block, int grid, cudaStream_t s);
+cudaError_t adjoint_occupancy(int block, int* blocks_per_sm);
+
 // Set-up table: setup_fields() doubles per binary, field-major with the given stride (>= n).
 int setup_fields();
 // Validate every binary, write BAD_INPUT results, and fill the set-up table.

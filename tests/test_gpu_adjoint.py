@@ -1,0 +1,145 @@
+"""Hand-written adjoint (pn_batch_adjoint) against the oracle's forward-mode gradient and against
+central finite differences of the replayed map (needs a B300)."""
+import numpy as np
+import pytest
+
+import workloads
+
+pytestmark = pytest.mark.gpu
+
+GRAD_TOL = 1e-9  # relative, vs the oracle's dual-number gradient of the same discrete map
+
+
+@pytest.fixture(scope="module")
+def pn():
+    import torch
+    import paper_0908_3889_b300 as pn
+    from paper_0908_3889_b300.build import build
+    assert torch.cuda.is_available()
+    build()
+    return pn
+
+
+OUT = ("dot_s1s2", "dot_ls1", "dot_ls2", "Lx", "Ly", "Lz", "S1x", "S1y", "S1z", "S2x", "S2y", "S2z", "t")
+PAR = ("s1x", "s1y", "s1z", "s2x", "s2y", "s2z", "q")
+
+
+def cotangents(n, seed):
+    rng = np.random.default_rng(seed)
+    g = rng.normal(size=(13, n))
+    g[12] *= 1e-4  # t is O(1e4): keep its term comparable
+    return g
+
+
+def run_adjoint(pn, ens, g, **kw):
+    import torch
+    inp = pn.to_device(ens)
+    cot = {k: torch.from_numpy(np.ascontiguousarray(g[j])).cuda() for j, k in enumerate(OUT)}
+    grads = pn.adjoint(inp, cot, **kw)
+    return np.stack([grads[p].cpu().numpy() for p in PAR])
+
+
+def oracle_grads(orc, ens, g):
+    n = ens["m1"].shape[0]
+    res = np.empty((7, n))
+    for i in range(n):
+        _, jac, _ = orc.grad(ens, i)
+        res[:, i] = g[:, i] @ jac
+    return res
+
+
+def rel_err(a, b):
+    scale = np.maximum(np.abs(b), np.max(np.abs(b), axis=0, keepdims=True) * 1e-6)
+    return np.max(np.abs(a - b) / scale)
+
+
+@pytest.mark.parametrize("name", ["C4", "C1", "C0"])
+def test_adjoint_matches_oracle_forward_mode(pn, orc, name):
+    ens = workloads.config(name, n=128, seed=900 + len(name))
+    g = cotangents(128, 7)
+    got = run_adjoint(pn, ens, g)
+    ref = oracle_grads(orc, ens, g)
+    assert np.all(np.isfinite(got))
+    assert rel_err(got, ref) < GRAD_TOL, rel_err(got, ref)
+
+
+def test_adjoint_full_size_subsample(pn, orc):
+    """65,536 binaries (q ~ U[1,4], chi = 1, omega 0.01 -> 0.05), checkpoint every 64 steps; a 256 subsample
+    against the oracle."""
+    ens = workloads.config("C4")
+    n = ens["m1"].shape[0]
+    g = cotangents(n, 11)
+    got = run_adjoint(pn, ens, g)
+    idx = workloads.subsample(n, 256, seed=workloads.SEED_BASE + 105)
+    ref = oracle_grads(orc, workloads.take(ens, idx), g[:, idx])
+    assert np.all(np.isfinite(got))
+    assert rel_err(got[:, idx], ref) < GRAD_TOL
+
+
+def test_checkpoint_stride_does_not_change_gradients(pn):
+    ens = workloads.config("C2", n=500, seed=77)
+    g = cotangents(500, 3)
+    base = run_adjoint(pn, ens, g, ckpt_every=64)
+    for k in (1, 7, 200):
+        other = run_adjoint(pn, ens, g, ckpt_every=k)
+        assert np.array_equal(base, other), k
+
+
+def test_adjoint_matches_central_differences(pn, orc):
+    """FD (h = 1e-6, central) of the replayed map: same accepted steps, re-landed exactly on omega_f."""
+    ens = workloads.config("C4", n=12, seed=31)
+    g = cotangents(12, 5)
+    got = run_adjoint(pn, ens, g)
+    d = 1e-6
+    for i in range(12):
+        rows, hs = orc.trace(ens, i)
+        fd = np.empty(7)
+        for k in range(7):
+            vals = []
+            for sgn in (1, -1):
+                p = workloads.take(ens, np.array([i]))
+                if k < 3:
+                    p["s1hat"][k, 0] += sgn * d
+                elif k < 6:
+                    p["s2hat"][k - 3, 0] += sgn * d
+                else:
+                    q = p["m1"][0] / p["m2"][0] + sgn * d
+                    p["m1"][0], p["m2"][0] = q / (1 + q), 1 / (1 + q)
+                y, t = orc.replay(p, 0, hs)
+                S1, S2, L = y[1:4], y[4:7], y[7:10]
+                n1, n2, nl = np.linalg.norm(S1), np.linalg.norm(S2), np.linalg.norm(L)
+                out = np.concatenate([[S1 @ S2 / (n1 * n2), L @ S1 / (nl * n1), L @ S2 / (nl * n2)], L, S1, S2, [t]])
+                vals.append(g[:, i] @ out)
+            fd[k] = (vals[0] - vals[1]) / (2 * d)
+        assert np.max(np.abs(got[:, i] - fd)) <= 2e-6 * max(1.0, np.max(np.abs(fd))), (i, got[:, i], fd)
+
+
+def test_autograd_function_backward(pn):
+    import torch
+    ens = workloads.config("C4", n=64, seed=41)
+    dev = "cuda"
+    T = lambda a: torch.tensor(a, dtype=torch.float64, device=dev)
+    s1 = T(ens["s1hat"]).requires_grad_(True)
+    s2 = T(ens["s2hat"]).requires_grad_(True)
+    q = T(ens["m1"] / ens["m2"]).requires_grad_(True)
+    outs = pn.PNAdjointFn.apply(s1, s2, q, T(ens["chi1"]), T(ens["chi2"]), T(ens["omega0"]), T(ens["omega_f"]),
+                                T(ens["lhat"]))
+    loss = outs[0].sum() + 0.5 * outs[3][2].sum()
+    loss.backward()
+    g = np.zeros((13, 64))
+    g[0] = 1.0
+    g[5] = 0.5
+    ref = run_adjoint(pn, ens, g)
+    got = np.concatenate([s1.grad.cpu().numpy(), s2.grad.cpu().numpy(), q.grad.cpu().numpy()[None]])
+    assert np.allclose(got, ref, rtol=1e-9, atol=1e-12)  # m1, m2 round-trip through q = m1/m2
+
+
+def test_adjoint_refuses_other_modes(pn):
+    import torch
+    ens = workloads.config("C4", n=8)
+    inp = pn.to_device(ens)
+    grads = {f: torch.empty(8, dtype=torch.float64, device="cuda") for f in pn.native.GRAD_FIELDS}
+    for kw in (dict(precision=1), dict(stop_mode=1)):
+        with pn.Batch(8, pn.params(**kw)) as b:
+            with pytest.raises(pn.PNError, match="UNIMPLEMENTED"):
+                pn.pn_batch_adjoint(b.handle, 8, inp, {}, grads)
