@@ -67,6 +67,7 @@ def parse_args():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-mixed", action="store_true")
+    ap.add_argument("--no-extras", action="store_true")
     return ap.parse_args()
 
 
@@ -75,6 +76,27 @@ def dist_env():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     return rank, world, local
+
+
+def rank_seed(rank: int) -> int:
+    """Each rank integrates its own ensemble of the same shape (independent binaries: weak scaling)."""
+    import workloads
+    return workloads.SEED_BASE + 1 + 1000 * rank
+
+
+def aggregate_rate(world: int, n_per_rank: int, steps: int, max_ms: float) -> float:
+    """Whole-job inspirals/s: all ranks' binaries over the slowest rank's time."""
+    return world * n_per_rank * steps / (max_ms * 1e-3)
+
+
+def reduce_max(x: float, tdist, device) -> float:
+    """Max over ranks (a timing reduction only; no data moves between ranks)."""
+    if tdist is None:
+        return x
+    import torch
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
+    return float(t.item())
 
 
 class ClockSampler:
@@ -204,14 +226,10 @@ def main():
         torch.cuda.synchronize()
 
     def max_over_ranks(x: float) -> float:
-        if not tdist:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device=dev)
-        tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
-        return float(t.item())
+        return reduce_max(x, tdist, dev)
 
     n = args.n
-    ens = workloads.config("C1", n=n, seed=workloads.SEED_BASE + 1 + 1000 * rank)
+    ens = workloads.config("C1", n=n, seed=rank_seed(rank))
     inp = pn.to_device(ens, device=dev)
     out = pn.alloc_outputs(n, dev)
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)  # 256 MB > L2 (126 MB)
@@ -248,7 +266,7 @@ def main():
         st = b.stats(inp, out)
     total_ms = max_over_ranks(total_ms)
     ms_step = total_ms / args.steps
-    value = world * n * args.steps / (total_ms * 1e-3)
+    value = aggregate_rate(world, n, args.steps, total_ms)
     attempts = st["acc_total"] + st["rej_total"] + st["land_total"]
     flops_launch = FLOPS_ATTEMPT * attempts
     achieved = flops_launch / (ms_step * 1e-3)
@@ -277,7 +295,7 @@ def main():
             errs[k] = {"max": float(d.max()), "p99": float(torch.quantile(d[:1_000_000].float(), 0.99)),
                        "p50": float(d.median())}
         m_attempts = mst["acc_total"] + mst["rej_total"] + mst["land_total"]
-        return {"value": world * n * args.steps / (mix_ms * 1e-3), "unit": "inspirals/s",
+        return {"value": aggregate_rate(world, n, args.steps, mix_ms), "unit": "inspirals/s",
                 "ms_per_step": mix_ms / args.steps, "speedup_vs_fp64": total_ms / mix_ms,
                 "dot_err_vs_fp64": errs, "schedule": {1: "plain", 2: "persistent"}.get(tn["schedule"]),
                 "block": tn["block"], "fp64_pipe_achieved_tflops": (FLOPS_STEP * m_attempts) /
@@ -305,8 +323,50 @@ def main():
                 pn.pn_batch_integrate_host(b.handle, n, hin, hout)
             barrier()
             e2e_s = max_over_ranks(time.perf_counter() - t0)
-        e2e = {"value": world * n * args.steps / e2e_s, "unit": "inspirals/s",
+        e2e = {"value": aggregate_rate(world, n, args.steps, e2e_s * 1e3), "unit": "inspirals/s",
                "h2d_bytes_per_step": 15 * 8 * n, "d2h_bytes_per_step": (14 * 8 + 4 * 4) * n}
+
+    # Extras: the uneven-length ensemble (persistent vs plain schedule) and the adjoint.
+    extras = None
+    if not args.no_extras:
+        extras = {}
+        c2 = workloads.config("C2", seed=workloads.SEED_BASE + 2 + 1000 * rank)
+        n2 = c2["m1"].shape[0]
+        inp2 = pn.to_device(c2, device=dev)
+        out2 = pn.alloc_outputs(n2, dev)
+        for name, sched in (("plain", 1), ("persistent", 2)):
+            for prec, pname in ((0, "fp64"), (2, "mixed_ds")):
+                with pn.Batch(n2, pn.params(precision=prec, schedule=sched, block=256)) as b:
+                    b.integrate(inp2, out2)
+                    torch.cuda.synchronize()
+                    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    e0.record()
+                    b.integrate(inp2, out2)
+                    e1.record()
+                    e1.synchronize()
+                    ms2 = max_over_ranks(e0.elapsed_time(e1))
+                extras[f"uneven_C2_{pname}_{name}"] = {"value": aggregate_rate(world, n2, 1, ms2),
+                                                      "unit": "inspirals/s", "ms": ms2}
+        del inp2, out2
+        c4 = workloads.config("C4", seed=workloads.SEED_BASE + 4 + 1000 * rank)
+        n4 = c4["m1"].shape[0]
+        inp4 = pn.to_device(c4, device=dev)
+        cot = {"dot_s1s2": torch.ones(n4, dtype=torch.float64, device=dev)}
+        grads = {f: torch.empty(n4, dtype=torch.float64, device=dev) for f in pn.native.GRAD_FIELDS}
+        with pn.Batch(n4) as b:
+            pn.pn_batch_adjoint(b.handle, n4, inp4, cot, grads)
+            ms_adj = []
+            for _ in range(3):
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record()
+                pn.pn_batch_adjoint(b.handle, n4, inp4, cot, grads)  # recording forward + reverse sweep
+                e1.record()
+                e1.synchronize()
+                ms_adj.append(e0.elapsed_time(e1))
+        ms4 = max_over_ranks(min(ms_adj))
+        extras["adjoint_C4"] = {"value": aggregate_rate(world, n4, 1, ms4), "unit": "gradients/s", "ms": ms4,
+                                "workload": "65,536 binaries, q ~ U[1,4], chi = 1, omega 0.01 -> 0.05; "
+                                            "d(S1-hat.S2-hat final)/d(S1-hat, S2-hat, q), checkpoint every 64"}
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
@@ -334,7 +394,7 @@ def main():
                            "parallelism": f"replicas x{world}", "attempts_per_binary": attempts / n,
                            "kernel_sha": sha},
                 "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": args.steps,
-                "clocks": clocks, "mixed": mixed, "mixed_ds": mixed_ds,
+                "clocks": clocks, "mixed": mixed, "mixed_ds": mixed_ds, "extras": extras,
                 "fp32_fma_peak_tflops": (f32_peak or 0) / 1e12, "fp64_fma_peak_tflops": (f64_peak or 0) / 1e12}
         print(json.dumps(line), flush=True)
     if tdist:
