@@ -967,9 +967,11 @@ __device__ __forceinline__ double step_factor(const Ctl& ctl, double s, double f
 
 // Root in (0, 1] of the cubic Hermite interpolant of omega over a step (end
 // values w0, w1; end slopes times h: d0, d1), three Newton steps from the
-// linear guess.  Once per binary, plain FP64.
+// linear guess.  Once per binary.  Divisions use rcp_pos (positive normal
+// denominators in a monotone chirp); a non-positive one gives a value the
+// caller's bracket check rejects.
 __device__ __forceinline__ double hermite_root(double w0, double d0, double w1, double d1, double wf) {
-  double s = (wf - w0) / (w1 - w0);
+  double s = (wf - w0) * rcp_pos(w1 - w0);
 #pragma unroll
   for (int it = 0; it < 3; it++) {
     const double s2 = s * s, s3 = s2 * s;
@@ -977,7 +979,7 @@ __device__ __forceinline__ double hermite_root(double w0, double d0, double w1, 
                       (s3 - s2) * d1;
     const double dps = (6.0 * s2 - 6.0 * s) * w0 + (3.0 * s2 - 4.0 * s + 1.0) * d0 + (6.0 * s - 6.0 * s2) * w1 +
                        (3.0 * s2 - 2.0 * s) * d1;
-    s = s - (ps - wf) / dps;
+    s = s - (ps - wf) * rcp_pos(dps);
   }
   return s;
 }

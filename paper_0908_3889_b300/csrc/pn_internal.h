@@ -51,10 +51,14 @@ cudaError_t adjoint_occupancy(int block, int* blocks_per_sm);
 int setup_fields();
 // Validate every binary, write BAD_INPUT results, and fill the set-up table.
 cudaError_t launch_setup(int prec, const KArgs& a, double* ws, int64_t stride, cudaStream_t s);
-// Integration kernel launch (reads the set-up table).  prec: PN_FP64 / PN_MIXED;
+// Integration kernel launch (reads the set-up table) followed by the output
+// scalar products (k_dots).  prec: PN_FP64 / PN_MIXED / PN_MIXED_DS;
 // persistent: work-queue schedule.
 cudaError_t launch_integrate(int prec, bool persistent, int block, int grid, const KArgs& a, const double* ws,
                              int64_t stride, cudaStream_t s);
+// The integration kernel alone.
+cudaError_t launch_integrate_only(int prec, bool persistent, int block, int grid, const KArgs& a, const double* ws,
+                                  int64_t stride, cudaStream_t s);
 // Resident blocks per SM of that kernel at this block size.
 cudaError_t integrate_occupancy(int prec, bool persistent, int block, int* blocks_per_sm);
 

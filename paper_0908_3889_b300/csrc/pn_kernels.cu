@@ -45,6 +45,9 @@ __device__ __forceinline__ Tabs load_tabs(const double* __restrict__ g, double* 
   return Tabs{s_tab, s_tabf};
 }
 
+// Final state, time, counters and status of binary i.  The scalar products are
+// filled in afterwards by k_dots, a converged pass over all binaries, so the
+// integration kernel spends no FP64 work on them in divergent code.
 __device__ __forceinline__ void write_result(const pn_outputs& o, int64_t i, const double* y, double t, int32_t n_acc,
                                              int32_t n_rej, int32_t n_land, int32_t status) {
   o.S1x[i] = y[1]; o.S1y[i] = y[2]; o.S1z[i] = y[3];
@@ -53,13 +56,22 @@ __device__ __forceinline__ void write_result(const pn_outputs& o, int64_t i, con
   o.omega[i] = y[0];
   o.t[i] = t;
   o.n_acc[i] = n_acc; o.n_rej[i] = n_rej; o.n_land[i] = n_land; o.status[i] = status;
-  // Sec. V's scalar products of the unit vectors (NaN for a zero spin: 0/0).
-  const double n1 = sqrt(y[1] * y[1] + y[2] * y[2] + y[3] * y[3]);
-  const double n2 = sqrt(y[4] * y[4] + y[5] * y[5] + y[6] * y[6]);
-  const double nl = sqrt(y[7] * y[7] + y[8] * y[8] + y[9] * y[9]);
-  o.dot_s1s2[i] = (y[1] * y[4] + y[2] * y[5] + y[3] * y[6]) / (n1 * n2);
-  o.dot_ls1[i] = (y[7] * y[1] + y[8] * y[2] + y[9] * y[3]) / (nl * n1);
-  o.dot_ls2[i] = (y[7] * y[4] + y[8] * y[5] + y[9] * y[6]) / (nl * n2);
+}
+
+// Sec. V's scalar products of the final unit vectors, S1-hat.S2-hat, L-hat.S1-hat,
+// L-hat.S2-hat (NaN for a zero spin: 0/0; NaN for BAD_INPUT binaries).
+__global__ void __launch_bounds__(256) k_dots(const pn_outputs o, int64_t n) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const double a0 = o.S1x[i], a1 = o.S1y[i], a2 = o.S1z[i];
+  const double b0 = o.S2x[i], b1 = o.S2y[i], b2 = o.S2z[i];
+  const double l0 = o.Lx[i], l1 = o.Ly[i], l2 = o.Lz[i];
+  const double n1 = sqrt(a0 * a0 + a1 * a1 + a2 * a2);
+  const double n2 = sqrt(b0 * b0 + b1 * b1 + b2 * b2);
+  const double nl = sqrt(l0 * l0 + l1 * l1 + l2 * l2);
+  o.dot_s1s2[i] = (a0 * b0 + a1 * b1 + a2 * b2) / (n1 * n2);
+  o.dot_ls1[i] = (l0 * a0 + l1 * a1 + l2 * a2) / (nl * n1);
+  o.dot_ls2[i] = (l0 * b0 + l1 * b1 + l2 * b2) / (nl * n2);
 }
 
 // Per-binary set-up table (structure of arrays, `stride` doubles per field):
@@ -186,13 +198,18 @@ __device__ __forceinline__ bool lane_decide(Lane& L, const Ctl& ctl, double* y5,
   for (int c = 0; c < 10; c++) fin = fin && finite64(y5[c]);
   if (!fin) { *status = PN_ST_NONFINITE; return true; }
   const double tolw = ctl.land_tol * L.wf;
+  // Growth factor for the next step, computed by every lane of the warp at once
+  // (accepted: at most fac_max, or 1 right after a rejection; rejected: at most 1).
+  const bool accepted = ctl.fixed_step || le_pos(s, 1.0);
+  const double fac = step_factor(ctl, s, (accepted && !L.last_rej) ? ctl.fac_max : 1.0);
+  const double rk7 = rcp_pos(k7[0]);  // 1 / (domega/dt) at y5
 
   if (L.landing) {
     L.n_land++;
     L.land_it++;
     const double g = y5[0] - L.wf;
     if (fabs(g) <= tolw) {  // converged: move onto omega_f along f
-      const double dh = -g / k7[0];
+      const double dh = -g * rk7;
 #pragma unroll
       for (int c = 0; c < 10; c++) y5[c] = fma(dh, k7[c], y5[c]);
       lane_commit<RECORD>(L, y5, L.h + dh, rec);
@@ -205,13 +222,13 @@ __device__ __forceinline__ bool lane_decide(Lane& L, const Ctl& ctl, double* y5,
       return true;
     }
     if (g > 0.0) L.h_hi = L.h; else L.h_lo = L.h;
-    double hn = L.h - g / k7[0];
+    double hn = fma(-g, rk7, L.h);
     if (!(hn > L.h_lo && hn < L.h_hi)) hn = 0.5 * (L.h_lo + L.h_hi);
     L.h = hn;
     return false;
   }
 
-  if (ctl.fixed_step || le_pos(s, 1.0)) {
+  if (accepted) {
     if (y5[0] >= L.wf) {
       const double g = y5[0] - L.wf;
       if (ctl.stop_mode == PN_STOP_FIRST_CROSS) {
@@ -220,7 +237,7 @@ __device__ __forceinline__ bool lane_decide(Lane& L, const Ctl& ctl, double* y5,
         return true;
       }
       if (fabs(g) <= tolw) {
-        const double dh = -g / k7[0];
+        const double dh = -g * rk7;
 #pragma unroll
         for (int c = 0; c < 10; c++) y5[c] = fma(dh, k7[c], y5[c]);
         lane_commit<RECORD>(L, y5, L.h + dh, rec);
@@ -238,12 +255,12 @@ __device__ __forceinline__ bool lane_decide(Lane& L, const Ctl& ctl, double* y5,
       lane_commit<RECORD>(L, y5, L.h, rec);
 #pragma unroll
       for (int c = 0; c < 10; c++) L.k1[c] = k7[c];
-      if (!ctl.fixed_step) L.h = L.h * step_factor(ctl, s, L.last_rej ? 1.0 : ctl.fac_max);
+      if (!ctl.fixed_step) L.h = L.h * fac;
       L.last_rej = false;
     }
   } else {
     L.n_rej++;
-    L.h = L.h * step_factor(ctl, s, 1.0);
+    L.h = L.h * fac;
     L.last_rej = true;
     if (L.h < ctl.h_min) { *status = PN_ST_H_UNDERFLOW; return true; }
   }
@@ -323,9 +340,22 @@ cudaError_t launch_setup(int prec, const KArgs& a, double* ws, int64_t stride, c
   return cudaGetLastError();
 }
 
+static cudaError_t launch_dots(const pn_outputs& o, int64_t n, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  k_dots<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(o, n);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_integrate(int prec, bool persistent, int block, int grid, const KArgs& a, const double* ws,
                              int64_t stride, cudaStream_t s) {
   if (grid <= 0) return cudaSuccess;
+  const cudaError_t e = launch_integrate_only(prec, persistent, block, grid, a, ws, stride, s);
+  if (e != cudaSuccess) return e;
+  return launch_dots(a.out, a.n, s);
+}
+
+cudaError_t launch_integrate_only(int prec, bool persistent, int block, int grid, const KArgs& a, const double* ws,
+                                  int64_t stride, cudaStream_t s) {
   if (prec == PN_MIXED) {
     if (persistent) k_integrate<1, true><<<grid, block, 0, s>>>(a, ws, stride);
     else k_integrate<1, false><<<grid, block, 0, s>>>(a, ws, stride);
@@ -469,7 +499,9 @@ cudaError_t launch_integrate_record(const KArgs& a, const double* ws, int64_t st
                                     int grid, cudaStream_t s) {
   if (grid <= 0) return cudaSuccess;
   k_integrate<0, true, true><<<grid, block, 0, s>>>(a, ws, stride, rec);
-  return cudaGetLastError();
+  const cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  return launch_dots(a.out, a.n, s);
 }
 
 cudaError_t record_occupancy(int block, int* blocks_per_sm) {
