@@ -184,6 +184,24 @@ typedef struct {
   int64_t n_tuned;    /* binaries in the tuning prefix */
 } pn_tune_result;
 
+/* Quantities for the analysis entry points (Sec. V's scalar products of unit vectors). */
+#define PN_Q_FINAL_S1S2 0 /* S1-hat.S2-hat at omega_f */
+#define PN_Q_FINAL_LS1 1  /* L-hat.S1-hat at omega_f */
+#define PN_Q_FINAL_LS2 2  /* L-hat.S2-hat at omega_f */
+#define PN_Q_INIT_S1S2 3  /* S1-hat.S2-hat at omega_0 (from the inputs) */
+#define PN_Q_INIT_LS1 4   /* L-hat.S1-hat at omega_0 */
+#define PN_Q_INIT_LS2 5   /* L-hat.S2-hat at omega_0 */
+
+/* Histogram specification: 1-D if ny == 1 (quantity_y ignored), else 2-D with
+ * x along the slow index (counts[kx * ny + ky]).  A value in [lo, hi] goes to
+ * bin min(nb - 1, floor((x - lo) * (nb / (hi - lo)))); others are not counted.
+ * nx * ny <= 8192. */
+typedef struct {
+  int32_t quantity_x, quantity_y;
+  int32_t nx, ny;
+  double x_lo, x_hi, y_lo, y_hi;
+} pn_hist_spec;
+
 typedef struct pn_batch pn_batch; /* opaque: owns only its workspace */
 
 /* Library ABI version (PN_ABI_VERSION). */
@@ -249,6 +267,22 @@ int pn_batch_adjoint(pn_batch *b, int64_t n, const pn_inputs *in, const pn_cotan
  * (counts per status, step totals, Pearson r of Sec. V A).  Synchronises.
  * Errors: PN_E_ARG, PN_E_CUDA. */
 int pn_batch_stats(pn_batch *b, int64_t n, const pn_inputs *in, const pn_outputs *out, pn_stats *host);
+
+/* Histogram of outputs 0..n-1 (Sec. V A: 20 and 100 bins of the final
+ * S1-hat.S2-hat; 79 x 79 bins of initial vs final).  Only binaries with
+ * status OK and finite values count.  Writes nx * ny counts to host_counts and
+ * synchronises.  Errors: PN_E_ARG (bad spec, NULL pointers), PN_E_CUDA. */
+int pn_batch_histogram(pn_batch *b, int64_t n, const pn_inputs *in, const pn_outputs *out, const pn_hist_spec *spec,
+                       int64_t *host_counts);
+
+/* Gaussian kernel density estimate of one quantity (Sec. V A):
+ * p(x) = 1/(N h) sum_j K((x - x_j)/h), K(u) = exp(-u^2/2)/sqrt(2 pi), with
+ * h = 1.06 sigma N^(-1/5) (sigma the sample standard deviation, N the number of
+ * binaries with status OK and a finite value), evaluated at the m points of
+ * host_grid (m <= 65536) into host_density; the bandwidth goes to *host_h (may be
+ * NULL).  Synchronises.  Errors: PN_E_ARG, PN_E_NOMEM, PN_E_CUDA. */
+int pn_batch_kde(pn_batch *b, int64_t n, const pn_inputs *in, const pn_outputs *out, int32_t quantity,
+                 const double *host_grid, int64_t m, double *host_density, double *host_h);
 
 /* Release the workspace (waits for the stream).  NULL is ignored. */
 void pn_batch_destroy(pn_batch *b);

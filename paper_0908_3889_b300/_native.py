@@ -74,6 +74,14 @@ class pn_stats(C.Structure):
                 ("ms_last_integrate", C.c_double), ("ms_last_adjoint", C.c_double)]
 
 
+class pn_hist_spec(C.Structure):
+    _fields_ = [("quantity_x", C.c_int32), ("quantity_y", C.c_int32), ("nx", C.c_int32), ("ny", C.c_int32),
+                ("x_lo", C.c_double), ("x_hi", C.c_double), ("y_lo", C.c_double), ("y_hi", C.c_double)]
+
+
+PN_Q_FINAL_S1S2, PN_Q_FINAL_LS1, PN_Q_FINAL_LS2, PN_Q_INIT_S1S2, PN_Q_INIT_LS1, PN_Q_INIT_LS2 = range(6)
+
+
 class pn_tune_result(C.Structure):
     _fields_ = [("schedule", C.c_int32), ("block", C.c_int32), ("bpt", C.c_int32), ("n_candidates", C.c_int32),
                 ("best_ms", C.c_double), ("n_tuned", C.c_int64)]
@@ -94,6 +102,10 @@ SIGNATURES = {
                                    C.POINTER(pn_grads), C.POINTER(pn_outputs)]),
     "pn_batch_stats": (C.c_int, [C.c_void_p, C.c_int64, C.POINTER(pn_inputs), C.POINTER(pn_outputs),
                                  C.POINTER(pn_stats)]),
+    "pn_batch_histogram": (C.c_int, [C.c_void_p, C.c_int64, C.POINTER(pn_inputs), C.POINTER(pn_outputs),
+                                     C.POINTER(pn_hist_spec), C.POINTER(C.c_int64)]),
+    "pn_batch_kde": (C.c_int, [C.c_void_p, C.c_int64, C.POINTER(pn_inputs), C.POINTER(pn_outputs), C.c_int32,
+                               C.POINTER(C.c_double), C.c_int64, C.POINTER(C.c_double), C.POINTER(C.c_double)]),
     "pn_batch_destroy": (None, [C.c_void_p]),
     "pn_integrate_noalloc": (C.c_int, [C.c_int64, C.POINTER(pn_params), C.POINTER(pn_inputs), C.POINTER(pn_outputs),
                                        C.c_void_p]),

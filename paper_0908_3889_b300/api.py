@@ -217,6 +217,28 @@ def pn_batch_stats(h, n: int, inputs: dict, outputs: dict) -> dict:
     return d
 
 
+def pn_batch_histogram(h, n: int, inputs: dict, outputs: dict, quantity_x: int, nx: int, x_range=(-1.0, 1.0),
+                       quantity_y: int = 0, ny: int = 1, y_range=(-1.0, 1.0)) -> np.ndarray:
+    """Counts as int64: shape (nx,) for a 1-D histogram, (nx, ny) for 2-D (x = quantity_x)."""
+    sp = N.pn_hist_spec(quantity_x=quantity_x, quantity_y=quantity_y, nx=nx, ny=ny, x_lo=x_range[0], x_hi=x_range[1],
+                        y_lo=y_range[0], y_hi=y_range[1])
+    counts = np.zeros(nx * ny, dtype=np.int64)
+    _check(_lib().pn_batch_histogram(h, int(n), C.byref(inputs_struct(inputs, n)), C.byref(outputs_struct(outputs, n)),
+                                     C.byref(sp), counts.ctypes.data_as(C.POINTER(C.c_int64))), h)
+    return counts if ny == 1 else counts.reshape(nx, ny)
+
+
+def pn_batch_kde(h, n: int, inputs: dict, outputs: dict, quantity: int, grid) -> tuple:
+    """(density at grid, bandwidth h = 1.06 sigma N^-1/5)."""
+    g = np.ascontiguousarray(grid, dtype=np.float64)
+    dens = np.empty_like(g)
+    bw = C.c_double()
+    _check(_lib().pn_batch_kde(h, int(n), C.byref(inputs_struct(inputs, n)), C.byref(outputs_struct(outputs, n)),
+                               int(quantity), g.ctypes.data_as(C.POINTER(C.c_double)), g.shape[0],
+                               dens.ctypes.data_as(C.POINTER(C.c_double)), C.byref(bw)), h)
+    return dens, bw.value
+
+
 def pn_batch_destroy(h) -> None:
     if h:
         _lib().pn_batch_destroy(h)
@@ -273,6 +295,12 @@ class Batch:
     def stats(self, inputs: dict, outputs: dict, n: int | None = None) -> dict:
         n = int(inputs["m1"].shape[0]) if n is None else n
         return pn_batch_stats(self.handle, n, inputs, outputs)
+
+    def histogram(self, inputs: dict, outputs: dict, quantity_x: int, nx: int, **kw) -> np.ndarray:
+        return pn_batch_histogram(self.handle, int(inputs["m1"].shape[0]), inputs, outputs, quantity_x, nx, **kw)
+
+    def kde(self, inputs: dict, outputs: dict, quantity: int, grid) -> tuple:
+        return pn_batch_kde(self.handle, int(inputs["m1"].shape[0]), inputs, outputs, quantity, grid)
 
     def autotune(self, inputs: dict, n: int | None = None) -> dict:
         n = int(inputs["m1"].shape[0]) if n is None else n

@@ -1,0 +1,144 @@
+// pn_analysis.cu -- device statistics of the paper's analysis (Sec. V):
+// histograms of the final (and initial) scalar products, the 79 x 79 initial
+// vs final histogram, and the Gaussian kernel density estimate with the
+// bandwidth h = 1.06 sigma N^(-1/5) (Silverman 1986) that Sec. V A uses.
+//
+// Only binaries with status PN_ST_OK and a finite value take part.  Binning
+// rule (both axes): a value x in [lo, hi] goes to bin
+//   k = min(nbins - 1, (int) floor((x - lo) * (nbins / (hi - lo)))),
+// values outside [lo, hi] are not counted (numpy.histogram's convention).
+
+#include <cmath>
+
+#include "pn_internal.h"
+
+namespace pn {
+
+// Value of a quantity for binary i (NaN if the binary does not take part).
+__device__ __forceinline__ double quantity(int q, const pn_inputs& in, const pn_outputs& out, int64_t i) {
+  if (out.status[i] != PN_ST_OK) return dnan();
+  switch (q) {
+    case PN_Q_FINAL_S1S2: return out.dot_s1s2[i];
+    case PN_Q_FINAL_LS1: return out.dot_ls1[i];
+    case PN_Q_FINAL_LS2: return out.dot_ls2[i];
+    default: break;
+  }
+  const double ax = in.s1x[i], ay = in.s1y[i], az = in.s1z[i];
+  const double bx = in.s2x[i], by = in.s2y[i], bz = in.s2z[i];
+  const double lx = in.lx[i], ly = in.ly[i], lz = in.lz[i];
+  const double na = sqrt(ax * ax + ay * ay + az * az), nb = sqrt(bx * bx + by * by + bz * bz);
+  const double nl = sqrt(lx * lx + ly * ly + lz * lz);
+  switch (q) {
+    case PN_Q_INIT_S1S2: return (ax * bx + ay * by + az * bz) / (na * nb);
+    case PN_Q_INIT_LS1: return (lx * ax + ly * ay + lz * az) / (nl * na);
+    case PN_Q_INIT_LS2: return (lx * bx + ly * by + lz * bz) / (nl * nb);
+    default: return dnan();
+  }
+}
+
+__device__ __forceinline__ int bin_of(double x, double lo, double hi, double norm, int nb) {
+  if (!(x >= lo && x <= hi)) return -1;  // outside, or NaN
+  int k = (int)floor(__dmul_rn(__dsub_rn(x, lo), norm));
+  return k < nb ? k : nb - 1;
+}
+
+// 1-D (ny = 1) or 2-D histogram; counts in shared memory per block, then one
+// atomicAdd per bin per block.  nx * ny <= kMaxHistBins.
+__global__ void __launch_bounds__(256) k_histogram(pn_inputs in, pn_outputs out, int64_t n, pn_hist_spec sp,
+                                                   unsigned long long* counts) {
+  extern __shared__ unsigned int h[];
+  const int nbins = sp.nx * sp.ny;
+  for (int k = threadIdx.x; k < nbins; k += blockDim.x) h[k] = 0u;
+  __syncthreads();
+  const double nx_norm = (double)sp.nx / (sp.x_hi - sp.x_lo);
+  const double ny_norm = sp.ny > 1 ? (double)sp.ny / (sp.y_hi - sp.y_lo) : 0.0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const int kx = bin_of(quantity(sp.quantity_x, in, out, i), sp.x_lo, sp.x_hi, nx_norm, sp.nx);
+    if (kx < 0) continue;
+    int k = kx;
+    if (sp.ny > 1) {
+      const int ky = bin_of(quantity(sp.quantity_y, in, out, i), sp.y_lo, sp.y_hi, ny_norm, sp.ny);
+      if (ky < 0) continue;
+      k = kx * sp.ny + ky;
+    }
+    atomicAdd(&h[k], 1u);
+  }
+  __syncthreads();
+  for (int k = threadIdx.x; k < nbins; k += blockDim.x)
+    if (h[k]) atomicAdd(&counts[k], (unsigned long long)h[k]);
+}
+
+// Sum and sum of squares (for the bandwidth) and count of one quantity.
+__global__ void __launch_bounds__(256) k_moments(pn_inputs in, pn_outputs out, int64_t n, int q, double* part) {
+  __shared__ double sh[3][8];
+  double s = 0.0, s2 = 0.0, c = 0.0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const double x = quantity(q, in, out, i);
+    if (!isfinite(x)) continue;
+    s += x;
+    s2 += x * x;
+    c += 1.0;
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    s += __shfl_xor_sync(0xffffffffu, s, o);
+    s2 += __shfl_xor_sync(0xffffffffu, s2, o);
+    c += __shfl_xor_sync(0xffffffffu, c, o);
+  }
+  if ((threadIdx.x & 31) == 0) { sh[0][threadIdx.x >> 5] = s; sh[1][threadIdx.x >> 5] = s2; sh[2][threadIdx.x >> 5] = c; }
+  __syncthreads();
+  if (threadIdx.x < 3) {
+    double v = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); w++) v += sh[threadIdx.x][w];
+    part[(size_t)blockIdx.x * 3 + threadIdx.x] = v;
+  }
+}
+
+// Gaussian KDE at grid point m: p(x_m) = 1/(N h) sum_j exp(-(x_m - x_j)^2 / (2 h^2)) / sqrt(2 pi).
+// One block per grid point; deterministic block reduction.
+__global__ void __launch_bounds__(256) k_kde(pn_inputs in, pn_outputs out, int64_t n, int q, const double* grid,
+                                             double h, double count, double* density) {
+  __shared__ double sh[8];
+  const double x = grid[blockIdx.x];
+  const double inv_h = 1.0 / h;
+  double s = 0.0;
+  for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
+    const double xi = quantity(q, in, out, i);
+    if (!isfinite(xi)) continue;
+    const double u = (x - xi) * inv_h;
+    s += exp(-0.5 * u * u);
+  }
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double v = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); w++) v += sh[w];
+    density[blockIdx.x] = v * (0.3989422804014327 / (count * h));  // 1/sqrt(2 pi)
+  }
+}
+
+cudaError_t launch_histogram(const pn_inputs& in, const pn_outputs& out, int64_t n, const pn_hist_spec& sp,
+                             unsigned long long* counts, cudaStream_t s) {
+  const int nbins = sp.nx * sp.ny;
+  cudaError_t e = cudaMemsetAsync(counts, 0, (size_t)nbins * sizeof(unsigned long long), s);
+  if (e != cudaSuccess || n <= 0) return e;
+  int64_t blocks = (n + 255) / 256;
+  if (blocks > 1184) blocks = 1184;
+  k_histogram<<<(unsigned)blocks, 256, (size_t)nbins * sizeof(unsigned int), s>>>(in, out, n, sp, counts);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_moments(const pn_inputs& in, const pn_outputs& out, int64_t n, int q, double* part, int blocks,
+                           cudaStream_t s) {
+  k_moments<<<blocks, 256, 0, s>>>(in, out, n, q, part);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_kde(const pn_inputs& in, const pn_outputs& out, int64_t n, int q, const double* grid, int64_t m,
+                       double h, double count, double* density, cudaStream_t s) {
+  if (m <= 0) return cudaSuccess;
+  k_kde<<<(unsigned)m, 256, 0, s>>>(in, out, n, q, grid, h, count, density);
+  return cudaGetLastError();
+}
+
+}  // namespace pn

@@ -47,6 +47,9 @@ struct pn_batch {
   int64_t seg_lanes = 0;
   int32_t seg_every = 0;
   double* d_adj_out = nullptr;   // forward outputs when the caller passes none
+  unsigned long long* d_hist = nullptr;  // analysis scratch: histogram counts
+  double* d_ana = nullptr;               // analysis scratch: moments, KDE grid and density
+  int64_t ana_cap = 0;
   int32_t* d_adj_out_i = nullptr;
   // staging for pn_batch_integrate_host
   double* d_stage_d = nullptr;
@@ -193,6 +196,8 @@ extern "C" void pn_batch_destroy(pn_batch* b) {
   cudaFree(b->d_overflow);
   cudaFree(b->d_seg);
   cudaFree(b->d_adj_out);
+  cudaFree(b->d_hist);
+  cudaFree(b->d_ana);
   cudaFree(b->d_adj_out_i);
   cudaFree(b->d_stage_d);
   cudaFree(b->d_stage_i);
@@ -476,6 +481,8 @@ extern "C" int pn_batch_adjoint(pn_batch* b, int64_t n, const pn_inputs* in, con
           cudaMalloc(&b->d_adj_out_i, 4 * N * sizeof(int32_t)) != cudaSuccess) {
         cudaGetLastError();
         cudaFree(b->d_adj_out);
+  cudaFree(b->d_hist);
+  cudaFree(b->d_ana);
         b->d_adj_out = nullptr;
         return fail(b, PN_E_NOMEM, "adjoint output allocation failed");
       }
@@ -651,5 +658,71 @@ extern "C" int pn_batch_stats(pn_batch* b, int64_t n, const pn_inputs* in, const
   host->ms_last_integrate = (b->timed_integrate && cudaEventElapsedTime(&ms, b->ev[0], b->ev[1]) == cudaSuccess) ? ms : NAN;
   host->ms_last_adjoint = (b->timed_adjoint && cudaEventElapsedTime(&ms, b->ev[4], b->ev[5]) == cudaSuccess) ? ms : NAN;
   cudaGetLastError();
+  return PN_OK;
+}
+
+extern "C" int pn_batch_histogram(pn_batch* b, int64_t n, const pn_inputs* in, const pn_outputs* out,
+                                  const pn_hist_spec* sp, int64_t* host_counts) {
+  if (!b) return fail(nullptr, PN_E_ARG, "batch is NULL");
+  if (n < 0 || n > b->n_max) return fail(b, PN_E_ARG, "n must be in [0, n_max]");
+  if (!inputs_ok(in) || !outputs_ok(out) || !sp || !host_counts) return fail(b, PN_E_ARG, "NULL pointer");
+  const bool two = sp->ny > 1;
+  if (sp->nx < 1 || sp->ny < 1 || (int64_t)sp->nx * sp->ny > pn::kMaxHistBins) return fail(b, PN_E_ARG, "bad bin counts");
+  if (sp->quantity_x < 0 || sp->quantity_x > 5 || (two && (sp->quantity_y < 0 || sp->quantity_y > 5)))
+    return fail(b, PN_E_ARG, "bad quantity");
+  if (!(sp->x_hi > sp->x_lo) || (two && !(sp->y_hi > sp->y_lo))) return fail(b, PN_E_ARG, "need lo < hi");
+  if (!b->d_hist && cudaMalloc(&b->d_hist, pn::kMaxHistBins * sizeof(unsigned long long)) != cudaSuccess) {
+    cudaGetLastError();
+    b->d_hist = nullptr;
+    return fail(b, PN_E_NOMEM, "histogram scratch allocation failed");
+  }
+  cudaError_t e = pn::launch_histogram(*in, *out, n, *sp, b->d_hist, b->stream);
+  if (e != cudaSuccess) return cuda_fail(b, e, "histogram kernel launch");
+  const size_t nb = (size_t)sp->nx * sp->ny;
+  PN_CUDA(b, cudaMemcpyAsync(host_counts, b->d_hist, nb * sizeof(int64_t), cudaMemcpyDeviceToHost, b->stream));
+  PN_CUDA(b, cudaStreamSynchronize(b->stream));
+  return PN_OK;
+}
+
+extern "C" int pn_batch_kde(pn_batch* b, int64_t n, const pn_inputs* in, const pn_outputs* out, int32_t q,
+                            const double* host_grid, int64_t m, double* host_density, double* host_h) {
+  if (!b) return fail(nullptr, PN_E_ARG, "batch is NULL");
+  if (n < 0 || n > b->n_max) return fail(b, PN_E_ARG, "n must be in [0, n_max]");
+  if (!inputs_ok(in) || !outputs_ok(out) || !host_grid || !host_density) return fail(b, PN_E_ARG, "NULL pointer");
+  if (q < 0 || q > 5) return fail(b, PN_E_ARG, "bad quantity");
+  if (m < 1 || m > 65536) return fail(b, PN_E_ARG, "m must be in [1, 65536]");
+  const int blocks = 296;
+  const int64_t need = 3 * blocks + 2 * m;
+  if (b->ana_cap < need) {
+    cudaFree(b->d_ana);
+    b->d_ana = nullptr;
+    b->ana_cap = 0;
+    if (cudaMalloc(&b->d_ana, (size_t)need * sizeof(double)) != cudaSuccess) {
+      cudaGetLastError();
+      return fail(b, PN_E_NOMEM, "KDE scratch allocation failed");
+    }
+    b->ana_cap = need;
+  }
+  double* part = b->d_ana;
+  double* grid = b->d_ana + 3 * blocks;
+  double* dens = grid + m;
+  cudaError_t e = pn::launch_moments(*in, *out, n, q, part, blocks, b->stream);
+  if (e != cudaSuccess) return cuda_fail(b, e, "moments kernel launch");
+  double hp[3 * 296];
+  PN_CUDA(b, cudaMemcpyAsync(hp, part, sizeof(hp), cudaMemcpyDeviceToHost, b->stream));
+  PN_CUDA(b, cudaStreamSynchronize(b->stream));
+  double s = 0, s2 = 0, cnt = 0;
+  for (int k = 0; k < blocks; k++) { s += hp[3 * k]; s2 += hp[3 * k + 1]; cnt += hp[3 * k + 2]; }
+  if (cnt < 2) return fail(b, PN_E_ARG, "KDE needs at least two binaries with finite values");
+  const double mean = s / cnt;
+  const double var = (s2 - cnt * mean * mean) / (cnt - 1.0);
+  const double h = 1.06 * std::sqrt(var > 0 ? var : 0.0) * std::pow(cnt, -0.2);
+  if (!(h > 0)) return fail(b, PN_E_ARG, "KDE bandwidth is zero (all values equal)");
+  PN_CUDA(b, cudaMemcpyAsync(grid, host_grid, (size_t)m * sizeof(double), cudaMemcpyHostToDevice, b->stream));
+  e = pn::launch_kde(*in, *out, n, q, grid, m, h, cnt, dens, b->stream);
+  if (e != cudaSuccess) return cuda_fail(b, e, "KDE kernel launch");
+  PN_CUDA(b, cudaMemcpyAsync(host_density, dens, (size_t)m * sizeof(double), cudaMemcpyDeviceToHost, b->stream));
+  PN_CUDA(b, cudaStreamSynchronize(b->stream));
+  if (host_h) *host_h = h;
   return PN_OK;
 }

@@ -70,6 +70,15 @@ constexpr int kStatGrid = 296;
 cudaError_t launch_stats(int64_t n, const pn_inputs& in, const pn_outputs& out, double* part, double* total,
                          cudaStream_t s);
 
+// Analysis (pn_analysis.cu).
+constexpr int kMaxHistBins = 8192;
+cudaError_t launch_histogram(const pn_inputs& in, const pn_outputs& out, int64_t n, const pn_hist_spec& sp,
+                             unsigned long long* counts, cudaStream_t s);
+cudaError_t launch_moments(const pn_inputs& in, const pn_outputs& out, int64_t n, int q, double* part, int blocks,
+                           cudaStream_t s);
+cudaError_t launch_kde(const pn_inputs& in, const pn_outputs& out, int64_t n, int q, const double* grid, int64_t m,
+                       double h, double count, double* density, cudaStream_t s);
+
 // Parameter and pointer checks shared by the C entry points (pn_capi.cu), and
 // the thread-local error message that pn_last_error(NULL) returns.
 int set_thread_error(int code, const std::string& msg);

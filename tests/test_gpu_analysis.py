@@ -1,0 +1,142 @@
+"""Device statistics of Sec. V (histograms, KDE, Pearson r) and the paper's printed statistics
+reproduced on the GPU at the paper's N = 100,000 (needs a B300)."""
+import os
+
+import numpy as np
+import pytest
+from scipy import stats as sstats
+
+import workloads
+
+pytestmark = pytest.mark.gpu
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+@pytest.fixture(scope="module")
+def pn():
+    import torch
+    import paper_0908_3889_b300 as pn
+    from paper_0908_3889_b300.build import build
+    assert torch.cuda.is_available()
+    build()
+    return pn
+
+
+def paper_values():
+    vals = {}
+    for line in open(os.path.join(GOLDEN, "paper_values.txt")):
+        line = line.split("#")[0].strip()
+        if line:
+            k, rest = line.split("=")
+            v, tol = rest.split()
+            vals[k.strip()] = (float(v), float(tol))
+    return vals
+
+
+def run(pn, ens, **kw):
+    import torch
+    inp = pn.to_device(ens)
+    b = pn.Batch(ens["m1"].shape[0], pn.params(**kw))
+    out = b.integrate(inp)
+    torch.cuda.synchronize()
+    return b, inp, out
+
+
+def np_bins(x, lo, hi, nb):
+    """The documented binning rule, in FP64 like the kernel: floor((x - lo) * (nb / (hi - lo))), top edge in last bin."""
+    x = x[np.isfinite(x) & (x >= lo) & (x <= hi)]
+    k = np.floor((x - lo) * (nb / (hi - lo))).astype(np.int64)
+    return np.minimum(k, nb - 1), x
+
+
+def test_histograms_exact(pn):
+    ens = workloads.config("SCIENCE", n=100_000)
+    b, inp, out = run(pn, ens)
+    g = pn.to_numpy(out)
+    ok = g["status"] == 0
+    fin = np.where(ok, g["dot_s1s2"], np.nan)
+    for nb in (20, 100):
+        got = b.histogram(inp, out, pn.native.PN_Q_FINAL_S1S2, nb)
+        k, x = np_bins(fin, -1.0, 1.0, nb)
+        assert np.array_equal(got, np.bincount(k, minlength=nb))
+        assert np.array_equal(got, np.histogram(x, bins=nb, range=(-1, 1))[0])
+    init = (ens["s1hat"] * ens["s2hat"]).sum(0) / (np.linalg.norm(ens["s1hat"], axis=0) * np.linalg.norm(ens["s2hat"], axis=0))
+    got2 = b.histogram(inp, out, pn.native.PN_Q_INIT_S1S2, 79, quantity_y=pn.native.PN_Q_FINAL_S1S2, ny=79)
+    m = ok & np.isfinite(fin) & np.isfinite(init)
+    kx = np.minimum(np.floor((init[m] + 1.0) * (79 / 2.0)).astype(np.int64), 78)
+    ky = np.minimum(np.floor((fin[m] + 1.0) * (79 / 2.0)).astype(np.int64), 78)
+    ref = np.zeros((79, 79), dtype=np.int64)
+    np.add.at(ref, (kx, ky), 1)
+    assert got2.shape == (79, 79) and np.array_equal(got2, ref)
+    b.close()
+
+
+def test_kde_matches_direct_sum(pn):
+    ens = workloads.config("SCIENCE", n=20_000)
+    b, inp, out = run(pn, ens)
+    x = pn.to_numpy(out)["dot_s1s2"]
+    grid = np.linspace(-1.2, 1.2, 97)
+    dens, h = b.kde(inp, out, pn.native.PN_Q_FINAL_S1S2, grid)
+    n = x.shape[0]
+    h_ref = 1.06 * np.std(x, ddof=1) * n ** -0.2  # Silverman's rule, Sec. V A
+    assert h == pytest.approx(h_ref, rel=1e-12)
+    u = (grid[:, None] - x[None, :]) / h_ref
+    ref = np.exp(-0.5 * u * u).sum(1) / (n * h_ref * np.sqrt(2 * np.pi))
+    assert np.allclose(dens, ref, rtol=1e-11, atol=1e-14)
+    b.close()
+
+
+def test_paper_statistics_at_paper_size(pn):
+    """Sec. V A: equal mass, chi = 1, omega 0.00395 -> 0.05, N = 100,000: r(S1.S2) = 0.99, r(L.S_i) = 0.65,
+    final S1.S2 uniform (20-bin histogram, KDE near 1/2 inside)."""
+    pv = paper_values()
+    ens = workloads.config("SCIENCE", n=100_000)
+    b, inp, out = run(pn, ens)
+    st = b.stats(inp, out)
+    assert st["count_by_status"][0] == 100_000
+    for key, got in (("pearson_s1s2_eqmass_chi1", st["pearson_s1s2"]), ("pearson_ls1_eqmass_chi1", st["pearson_ls1"]),
+                     ("pearson_ls2_eqmass_chi1", st["pearson_ls2"])):
+        v, tol = pv[key]
+        assert abs(got - v) <= tol, (key, got)
+    h20 = b.histogram(inp, out, pn.native.PN_Q_FINAL_S1S2, int(pv["final_s1s2_uniform_bins"][0]))
+    assert sstats.chisquare(h20).pvalue > 1e-3
+    dens, _ = b.kde(inp, out, pn.native.PN_Q_FINAL_S1S2, np.linspace(-0.8, 0.8, 33))
+    assert np.max(np.abs(dens - 0.5)) < 0.05
+    b.close()
+
+
+def test_paper_correlation_vs_chi_and_mass(pn):
+    """Sec. V C: r(S1.S2) > 0.98 for equal masses at every chi; Sec. V D: m1 = 0.4, chi = 0.05 gives r = -0.14;
+    Sec. V B (Fig. 5): r falls quickly as the masses become unequal."""
+    pv = paper_values()
+    lo = pv["pearson_s1s2_min_over_chi"][0]
+    for chi in (0.1, 0.3, 0.5, 0.7, 0.9):
+        ens = workloads.ensemble(100_000, 600 + int(chi * 10), chi=(chi, chi), omega0=(0.00395, 0.00395))
+        b, inp, out = run(pn, ens)
+        assert b.stats(inp, out)["pearson_s1s2"] > lo, chi
+        b.close()
+    v, tol = pv["pearson_s1s2_m04_chi005"]
+    ens = workloads.ensemble(100_000, 77, q=(0.4 / 0.6, 0.4 / 0.6), chi=(0.05, 0.05), omega0=(0.00395, 0.00395))
+    b, inp, out = run(pn, ens)
+    assert abs(b.stats(inp, out)["pearson_s1s2"] - v) <= tol
+    b.close()
+    rs = []
+    for m1 in (0.5, 0.45, 0.4, 0.3):
+        q = m1 / (1 - m1)
+        ens = workloads.ensemble(100_000, 700 + int(m1 * 100), q=(q, q), omega0=(0.00395, 0.00395))
+        b, inp, out = run(pn, ens)
+        rs.append(b.stats(inp, out)["pearson_s1s2"])
+        b.close()
+    assert rs[0] > 0.98 and all(a > c for a, c in zip(rs, rs[1:])) and rs[-1] < 0.6, rs
+
+
+def test_analysis_argument_errors(pn):
+    ens = workloads.config("C0", n=16)
+    b, inp, out = run(pn, ens)
+    with pytest.raises(pn.PNError):
+        b.histogram(inp, out, 9, 10)
+    with pytest.raises(pn.PNError):
+        b.histogram(inp, out, 0, 100, quantity_y=0, ny=100)  # 10,000 > 8,192 bins
+    with pytest.raises(pn.PNError):
+        b.histogram(inp, out, 0, 10, x_range=(1.0, -1.0))
+    b.close()
