@@ -364,6 +364,24 @@ def main():
                 e1.synchronize()
                 ms_adj.append(e0.elapsed_time(e1))
         ms4 = max_over_ranks(min(ms_adj))
+        # Sec. IV's performance workload: one test inspiral, omega 0.004 -> 0.1, replicated (lock-step).
+        pp = workloads.config("PAPER_PERF", n=1_048_576, seed=workloads.SEED_BASE + 6 + 1000 * rank)
+        inpp = pn.to_device(pp, device=dev)
+        outp = pn.alloc_outputs(pp["m1"].shape[0], dev)
+        with pn.Batch(pp["m1"].shape[0], pn.params(precision=0)) as b:
+            b.integrate(inpp, outp)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            b.integrate(inpp, outp)
+            e1.record()
+            e1.synchronize()
+            msp = max_over_ranks(e0.elapsed_time(e1))
+        extras["paper_test_inspiral_fp64"] = {
+            "value": aggregate_rate(world, pp["m1"].shape[0], 1, msp), "unit": "inspirals/s", "ms": msp,
+            "workload": "one seeded inspiral, omega 0.004 -> 0.1, 1,048,576 copies (Sec. IV lock-step test)",
+            "paper_gpu_2009": {"value": 2700.0, "unit": "inspirals/s", "hardware": "1 GPU of a Tesla S1070, FP32"}}
+        del inpp, outp
         extras["adjoint_C4"] = {"value": aggregate_rate(world, n4, 1, ms4), "unit": "gradients/s", "ms": ms4,
                                 "workload": "65,536 binaries, q ~ U[1,4], chi = 1, omega 0.01 -> 0.05; "
                                             "d(S1-hat.S2-hat final)/d(S1-hat, S2-hat, q), checkpoint every 64"}

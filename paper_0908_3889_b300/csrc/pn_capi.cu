@@ -181,7 +181,7 @@ extern "C" const char* pn_last_error(const pn_batch* b) { return b ? b->err.c_st
 
 extern "C" void pn_batch_destroy(pn_batch* b) {
   if (!b) return;
-  if (b->stream || true) cudaStreamSynchronize(b->stream);
+  cudaStreamSynchronize(b->stream);
   if (b->gexec) cudaGraphExecDestroy(b->gexec);
   if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
   for (auto& e : b->ev)
