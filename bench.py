@@ -46,7 +46,7 @@ FLOPS_ATTEMPT = 6 * FLOPS_RHS + FLOPS_STEP
 # DRAM traffic of the integration kernel per binary from an ncu capture
 # (dram__bytes_read.sum + dram__bytes_write.sum, profiles/); valid only while
 # the kernel sources hash to KERNEL_SHA.
-PROFILED = {"kernel_sha": "b6d28cb6eb4de6f5", "dram_bytes_per_binary": (39.04896e6 + 0.297728e6) / 131072}
+PROFILED = {"kernel_sha": "e38c1335f1c57aac", "dram_bytes_per_binary": (38.902016e6 + 0.040704e6) / 131072}
 
 
 def kernel_sha() -> str:
@@ -68,6 +68,10 @@ def parse_args():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-mixed", action="store_true")
     ap.add_argument("--no-extras", action="store_true")
+    ap.add_argument("--profile-case", choices=("integrate", "adjoint"), default=None,
+                    help="no timing, the small cases the ncu section captures run: 'integrate' integrates the "
+                         "first --n binaries of the workload once per precision (persistent schedule, 256 "
+                         "threads); 'adjoint' runs one pn_batch_adjoint over the 65,536-binary adjoint ensemble")
     return ap.parse_args()
 
 
@@ -232,6 +236,24 @@ def main():
     ens = workloads.config("C1", n=n, seed=rank_seed(rank))
     inp = pn.to_device(ens, device=dev)
     out = pn.alloc_outputs(n, dev)
+    if args.profile_case == "adjoint":
+        c4 = workloads.config("C4")
+        n4 = c4["m1"].shape[0]
+        inp4 = pn.to_device(c4, device=dev)
+        cot = {"dot_s1s2": torch.ones(n4, dtype=torch.float64, device=dev)}
+        grads = {f: torch.empty(n4, dtype=torch.float64, device=dev) for f in pn.native.GRAD_FIELDS}
+        with pn.Batch(n4) as b:
+            pn.pn_batch_adjoint(b.handle, n4, inp4, cot, grads)
+            torch.cuda.synchronize()
+        print(json.dumps({"profile_case": "C4 adjoint", "n": n4}))
+        return
+    if args.profile_case == "integrate":
+        for prec in (pn.native.PN_FP64, pn.native.PN_MIXED, pn.native.PN_MIXED_DS):
+            with pn.Batch(n, pn.params(precision=prec, schedule=pn.native.PN_SCHED_PERSISTENT, block=256)) as b:
+                b.integrate(inp, out)
+                torch.cuda.synchronize()
+        print(json.dumps({"profile_case": "C1", "n": n, "precisions": [0, 1, 2]}))
+        return
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)  # 256 MB > L2 (126 MB)
 
     f64_peak, f32_peak = peak_probe()
@@ -408,10 +430,13 @@ def main():
                 "vs_baseline": None, "dtype": "f64", "data": "synthetic",
                 "config": {"workload": WORKLOAD, "n_binaries_per_gpu": n, "precision": "fp64",
                            "schedule": {1: "plain", 2: "persistent"}.get(tune["schedule"], tune["schedule"]),
-                           "block": tune["block"], "l2": "flushed before each step (256 MB write)",
+                           "block": tune["block"], "binaries_per_thread": tune["bpt"],
+                           "l2": "flushed before each step (256 MB write)",
                            "parallelism": f"replicas x{world}", "attempts_per_binary": attempts / n,
                            "kernel_sha": sha},
-                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": args.steps,
+                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
+                # per step: k_setup + k_integrate + k_dots (the queue reset is a memset node)
+                "gpu_launches": 3 * args.steps,
                 "clocks": clocks, "mixed": mixed, "mixed_ds": mixed_ds, "extras": extras,
                 "fp32_fma_peak_tflops": (f32_peak or 0) / 1e12, "fp64_fma_peak_tflops": (f64_peak or 0) / 1e12}
         print(json.dumps(line), flush=True)

@@ -102,7 +102,8 @@ typedef struct {
   int32_t precision;     /* PN_FP64, PN_MIXED or PN_MIXED_DS */
   int32_t schedule;      /* PN_SCHED_* */
   int32_t block;         /* threads per block (multiple of 32, <= 512); 0 = autotuned / default */
-  int32_t bpt;           /* binaries per thread, 1 or 2; 0 = autotuned / default */
+  int32_t bpt;           /* plain schedule: binaries each thread integrates in turn, 1 or 2;
+                            0 = autotuned / default 1 */
   int32_t ckpt_every;    /* adjoint: accepted steps between state checkpoints, default 64 */
 } pn_params;
 
@@ -242,8 +243,9 @@ int pn_batch_integrate(pn_batch *b, int64_t n, const pn_inputs *in, pn_outputs *
  * PN_E_ARG, PN_E_NOMEM, PN_E_CUDA. */
 int pn_batch_integrate_host(pn_batch *b, int64_t n, const pn_inputs *host_in, pn_outputs *host_out);
 
-/* Time the candidate (schedule, block, binaries-per-thread) configurations of
- * the current precision on the first min(n, 262144) binaries of *in (writing
+/* Time the candidate launch shapes of the current precision -- plain schedule x
+ * {64, 128, 256} threads x {1, 2} binaries per thread, persistent schedule x
+ * {64, 128, 256} threads -- on the first min(n, 262144) binaries of *in (writing
  * *scratch_out), keep the fastest for later calls with schedule/block/bpt = 0,
  * and report it in *res (may be NULL).  Synchronises.  Errors: PN_E_ARG, PN_E_CUDA. */
 int pn_batch_autotune(pn_batch *b, int64_t n, const pn_inputs *in, pn_outputs *scratch_out,

@@ -11,7 +11,8 @@ LIB = os.path.join(HERE, "libpn_b300.so")
 PEAK_LIB = os.path.join(HERE, "libpn_peak.so")
 PEAK_SRC = os.path.join(HERE, "csrc", "peak_probe.cu")
 SOURCES = [os.path.join(HERE, "csrc", "pn_kernels.cu"), os.path.join(HERE, "csrc", "pn_capi.cu"),
-           os.path.join(HERE, "csrc", "pn_noalloc.cu"), os.path.join(HERE, "csrc", "pn_analysis.cu")]
+           os.path.join(HERE, "csrc", "pn_noalloc.cu"), os.path.join(HERE, "csrc", "pn_analysis.cu"),
+           os.path.join(HERE, "csrc", "pn_adjoint.cu")]
 # the integrator's own headers (the peak probe is built separately)
 NVCC_FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-lineinfo", "-std=c++17",
               "-Xcompiler", "-fPIC", "-shared"]

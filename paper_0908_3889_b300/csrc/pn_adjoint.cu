@@ -1,0 +1,502 @@
+// pn_adjoint.cu -- reverse mode (discrete adjoint) of the FP64 integration.
+//
+// Gradients of the loss sum_i gbar_i . out_i (final dot products, S1, S2,
+// L-hat, t of each binary) with respect to the initial spin directions and the
+// mass ratio q, through the accepted Dormand-Prince steps of the forward run
+// (Sec. II) with their step sizes held fixed.  The stop at omega_f is
+// differentiated as an implicit function: the landing step size h* is the root
+// of omega5(y_{N-1}, h*) = omega_f, so with mu = ybar_f . d y5/dh + tbar and
+// nu = d omega5/dh the cotangent passed back through the landing step is
+// ybar_f - (mu/nu) e_omega (two reverse sweeps of that step).
+//
+// The forward pass (k_integrate with recording) keeps the accepted step sizes
+// and the state every `every` accepted steps.  The reverse sweep takes one
+// such segment at a time: it recomputes the segment's steps from its
+// checkpoint with the forward kernel's stage arithmetic, keeping each step's
+// six stage states, then walks the steps backwards.
+//
+// Work layout on the GPU:
+//  - The FP64 pipe spends the same cycles on a warp instruction whatever its
+//    active mask, and a binary's work is set by its accepted-step count N.  So
+//    the binaries are first ordered by N (counting sort, longest first), and
+//    each warp claims 32 consecutive entries of that order: its lanes walk the
+//    same segments and steps in lock-step, and the longest binaries start first.
+//  - The stage states go to a lane-private segment buffer (every x 60 doubles
+//    per lane, lane-contiguous so the warp's accesses coalesce).  The reverse
+//    step then runs no forward stage: each stage costs one rhs64_vjp, which
+//    hands back the stage rate for the step-size cotangent as well.
+
+#include "pn_device.cuh"
+#include "pn_internal.h"
+
+namespace pn {
+namespace {
+
+// ---------------------------------------------------------------------------
+// Reverse mode (adjoint) of the FP64 right-hand side.
+// rhs64_vjp recomputes rhs64's intermediates at y and returns
+//   yb = (df/dy)^T fb   and adds (df/dc)^T fb to cb (the 16 coefficients),
+// each line of the reverse sweep undoing one line of rhs64, in reverse order;
+// it also returns f = f(y) itself (the stage rate k_s the step-size cotangent needs).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void cross_vjp(const double* a, const double* b, const double* cb_, double* ab, double* bb) {
+  // c = a x b:  ab += b x cb,  bb += cb x a
+  ab[0] += b[1] * cb_[2] - b[2] * cb_[1];
+  ab[1] += b[2] * cb_[0] - b[0] * cb_[2];
+  ab[2] += b[0] * cb_[1] - b[1] * cb_[0];
+  bb[0] += cb_[1] * a[2] - cb_[2] * a[1];
+  bb[1] += cb_[2] * a[0] - cb_[0] * a[2];
+  bb[2] += cb_[0] * a[1] - cb_[1] * a[0];
+}
+
+__device__ __noinline__ void rhs64_vjp(const Coef<double>& c, const double* __restrict__ tab, const double* y,
+                                       const double* fb, double* yb, Coef<double>& cb, double* f) {
+  // ---- forward (as rhs64) ----
+  const double w = y[0];
+  const double S1[3] = {y[1], y[2], y[3]}, S2[3] = {y[4], y[5], y[6]}, L[3] = {y[7], y[8], y[9]};
+  double r = inv_cbrt(w);
+  if ((hi32(w) & 0x7fffffffu) - (897u << 20) >= ((1151u - 897u) << 20)) r = dnan();
+  const double r2 = r * r;
+  const double v = w * r2;
+  const double v2 = v * v;
+  const double lw = log_tang(w, tab);
+  const double LS1 = L[0] * S1[0] + L[1] * S1[1] + L[2] * S1[2];
+  const double LS2 = L[0] * S2[0] + L[1] * S2[1] + L[2] * S2[2];
+  const double S12 = S1[0] * S2[0] + S1[1] * S2[1] + S1[2] * S2[2];
+  const double so = fma(c.w1, LS1, fma(c.w2, LS2, -c.tail));
+  const double c2p = fma(c.ss721, LS1 * LS2, fma(-c.ss247, S12, c.c2));
+  const double c3p = fma(c.clog, lw, c.c3l);
+  const double P6 = fma(v, c.c35, c3p);
+  const double P5 = fma(v, P6, c.c25);
+  const double P4 = fma(v, P5, c2p);
+  const double P3 = fma(v, P4, -so);
+  const double P2 = fma(v, P3, c.c1);
+  const double P = fma(v2, P2, 1.0);
+  const double w2 = w * w;
+  const double Q = (w2 * w) * v2;
+  double A1[3], A2[3], C[3];
+  A1[0] = L[1] * S1[2] - L[2] * S1[1]; A1[1] = L[2] * S1[0] - L[0] * S1[2]; A1[2] = L[0] * S1[1] - L[1] * S1[0];
+  A2[0] = L[1] * S2[2] - L[2] * S2[1]; A2[1] = L[2] * S2[0] - L[0] * S2[2]; A2[2] = L[0] * S2[1] - L[1] * S2[0];
+  C[0] = S1[1] * S2[2] - S1[2] * S2[1]; C[1] = S1[2] * S2[0] - S1[0] * S2[2]; C[2] = S1[0] * S2[1] - S1[1] * S2[0];
+  const double pre = c.prec * w2;
+  const double al1 = fma(c.a1, r, -3.0 * LS2), al2 = fma(c.a2, r, -3.0 * LS1);
+  const double p1 = pre * al1, p2 = pre * al2;
+  double d1[3], d2[3];
+  for (int k = 0; k < 3; k++) {
+    d1[k] = p1 * A1[k] - pre * C[k];
+    d2[k] = p2 * A2[k] + pre * C[k];
+  }
+  const double lf = v * c.nie;
+  f[0] = (Q * c.K) * P;
+  for (int k = 0; k < 3; k++) {
+    f[1 + k] = d1[k];
+    f[4 + k] = d2[k];
+    f[7 + k] = lf * (d1[k] + d2[k]);
+  }
+  // ---- reverse ----
+  double S1b[3] = {0, 0, 0}, S2b[3] = {0, 0, 0}, Lb[3] = {0, 0, 0};
+  double d1b[3], d2b[3], A1b[3], A2b[3], Cb[3];
+  double lfb = 0.0;
+  for (int k = 0; k < 3; k++) lfb += fb[7 + k] * (d1[k] + d2[k]);  // f_L = lf (d1 + d2)
+  for (int k = 0; k < 3; k++) {
+    d1b[k] = fb[1 + k] + lf * fb[7 + k];
+    d2b[k] = fb[4 + k] + lf * fb[7 + k];
+  }
+  double vb = lfb * c.nie;  // lf = v nie
+  cb.nie += lfb * v;
+  double p1b = 0.0, p2b = 0.0, preb = 0.0;  // d1 = p1 A1 - pre C, d2 = p2 A2 + pre C
+  for (int k = 0; k < 3; k++) {
+    p1b += d1b[k] * A1[k];
+    p2b += d2b[k] * A2[k];
+    A1b[k] = p1 * d1b[k];
+    A2b[k] = p2 * d2b[k];
+    Cb[k] = pre * (d2b[k] - d1b[k]);
+    preb += C[k] * (d2b[k] - d1b[k]);
+  }
+  preb += p1b * al1 + p2b * al2;  // p_i = pre al_i
+  const double al1b = p1b * pre, al2b = p2b * pre;
+  cb.a1 += al1b * r;  // al1 = a1 r - 3 LS2, al2 = a2 r - 3 LS1
+  cb.a2 += al2b * r;
+  double rb = al1b * c.a1 + al2b * c.a2;
+  double LS2b = -3.0 * al1b, LS1b = -3.0 * al2b;
+  double w2b = preb * c.prec;  // pre = prec w2
+  cb.prec += preb * w2;
+  cross_vjp(S1, S2, Cb, S1b, S2b);  // C = S1 x S2
+  cross_vjp(L, S1, A1b, Lb, S1b);   // A1 = L x S1
+  cross_vjp(L, S2, A2b, Lb, S2b);   // A2 = L x S2
+  const double f0b = fb[0];  // f0 = Q K P
+  const double Qb = f0b * c.K * P;
+  cb.K += f0b * Q * P;
+  const double Pb = f0b * Q * c.K;
+  w2b += Qb * w * v2;  // Q = w2 w v2
+  double wb = Qb * w2 * v2;
+  double v2b = Qb * w2 * w;
+  wb += 2.0 * w * w2b;  // w2 = w^2
+  v2b += Pb * P2;       // P = v2 P2 + 1
+  const double P2b = Pb * v2;
+  vb += P2b * P3;       // P2 = v P3 + c1
+  const double P3b = P2b * v;
+  cb.c1 += P2b;
+  vb += P3b * P4;       // P3 = v P4 - so
+  const double P4b = P3b * v;
+  const double sob = -P3b;
+  vb += P4b * P5;       // P4 = v P5 + c2p
+  const double P5b = P4b * v;
+  const double c2pb = P4b;
+  vb += P5b * P6;       // P5 = v P6 + c25
+  const double P6b = P5b * v;
+  cb.c25 += P5b;
+  vb += P6b * c.c35;    // P6 = v c35 + c3p
+  cb.c35 += P6b * v;
+  const double c3pb = P6b;
+  cb.clog += c3pb * lw;  // c3p = clog lw + c3l
+  const double lwb = c3pb * c.clog;
+  cb.c3l += c3pb;
+  cb.ss721 += c2pb * LS1 * LS2;  // c2p = ss721 LS1 LS2 - ss247 S12 + c2
+  LS1b += c2pb * c.ss721 * LS2;
+  LS2b += c2pb * c.ss721 * LS1;
+  cb.ss247 -= c2pb * S12;
+  const double S12b = -c2pb * c.ss247;
+  cb.c2 += c2pb;
+  cb.w1 += sob * LS1;  // so = w1 LS1 + w2 LS2 - tail
+  LS1b += sob * c.w1;
+  cb.w2 += sob * LS2;
+  LS2b += sob * c.w2;
+  cb.tail -= sob;
+  for (int k = 0; k < 3; k++) {  // LS1 = L.S1, LS2 = L.S2, S12 = S1.S2
+    Lb[k] += LS1b * S1[k] + LS2b * S2[k];
+    S1b[k] += LS1b * L[k] + S12b * S2[k];
+    S2b[k] += LS2b * L[k] + S12b * S1[k];
+  }
+  const double r3 = r2 * r;  // = 1/w
+  wb += lwb * r3;            // lw = ln|w|
+  vb += 2.0 * v * v2b;       // v2 = v^2
+  wb += vb * r2;             // v = w r^2
+  rb += vb * 2.0 * w * r;
+  wb += rb * (-1.0 / 3.0) * r * r3;  // r = w^(-1/3): dr/dw = -r/(3w)
+  yb[0] = wb;
+  for (int k = 0; k < 3; k++) {
+    yb[1 + k] = S1b[k];
+    yb[4 + k] = S2b[k];
+    yb[7 + k] = Lb[k];
+  }
+}
+
+// Reverse mode of make_coef: (m1b, m2b) += (dc/dm)^T cb, from the closed forms
+// w1 = 113/12 + (25/4) m2/m1, w2 = 113/12 + (25/4) m1/m2, ss247 = 247/(48 eta),
+// ss721 = 721/(48 eta), a1 = 4 m1 m2 + 3 m2^2, a2 = 4 m1 m2 + 3 m1^2, nie = -1/eta,
+// and the eta-polynomials of the non-spin coefficients (M = 1, eta = m1 m2).
+__device__ __forceinline__ void coef_vjp(const Coef<double>& cb, double m1, double m2, TermCfg tc, double* m1b,
+                                         double* m2b) {
+  const double eta = m1 * m2;
+  const uint32_t mk = tc.mask;
+  double etab = cb.K * (96.0 / 5.0);
+  if (mk & 2u) {
+    *m1b += cb.w1 * (-6.25 * m2 / (m1 * m1)) + cb.w2 * (6.25 / m2);
+    *m2b += cb.w1 * (6.25 / m1) + cb.w2 * (-6.25 * m1 / (m2 * m2));
+  }
+  if (mk & 16u) etab += (cb.ss247 * 247.0 + cb.ss721 * 721.0) * (-1.0 / (48.0 * eta * eta));
+  if (mk & 1u) etab += cb.c1 * (-924.0 / 336.0);
+  if (mk & 8u) etab += cb.c2 * (13661.0 / 2016.0 + 2.0 * 59.0 / 18.0 * eta);
+  if (mk & 32u) etab += cb.c25 * (-15876.0 * PN_PI / 672.0);
+  if (mk & 64u) {
+    const double theta = 1039.0 / 4620.0;
+    const double c31 = -273811877.0 / 1088640.0 + 451.0 / 48.0 * PN_PI * PN_PI;
+    const double dth = (tc.theta_mode == 0) ? c31 - 88.0 / 3.0 * theta : c31 - 2.0 * 88.0 / 3.0 * theta * eta;
+    etab += cb.c3l * (dth + 2.0 * 541.0 / 896.0 * eta - 3.0 * 5605.0 / 2592.0 * eta * eta);
+  }
+  if (mk & 128u) etab += cb.c35 * (358675.0 / 6048.0 + 2.0 * 91495.0 / 1512.0 * eta) * PN_PI;
+  *m1b += cb.a1 * (4.0 * m2) + cb.a2 * (4.0 * m2 + 6.0 * m1);
+  *m2b += cb.a1 * (4.0 * m1 + 6.0 * m2) + cb.a2 * (4.0 * m1);
+  etab += cb.nie / (eta * eta);
+  *m1b += etab * m2;
+  *m2b += etab * m1;
+}
+
+// Full Dormand-Prince lower-triangular tableau (rows: stages 1..6, the row of
+// stage 1 empty) and the 5th-order weights.
+__constant__ double c_dp_A[6][6] = {
+    {0, 0, 0, 0, 0, 0},
+    {DP_A21, 0, 0, 0, 0, 0},
+    {DP_A31, DP_A32, 0, 0, 0, 0},
+    {DP_A41, DP_A42, DP_A43, 0, 0, 0},
+    {DP_A51, DP_A52, DP_A53, DP_A54, 0, 0},
+    {DP_A61, DP_A62, DP_A63, DP_A64, DP_A65, 0},
+};
+__constant__ double c_dp_B[6] = {DP_B1, 0.0, DP_B3, DP_B4, DP_B5, DP_B6};
+
+// One Dormand-Prince step y -> y5 with a fixed h (the map the accepted steps
+// apply; same FP64 arithmetic as the forward kernel's stages), writing the six
+// stage states Y_0 = y, ..., Y_5 to sp[(10 s + k) * ss].  With y5 == nullptr
+// only the stage states are made (the last rate k_6 is then not needed).
+__device__ __forceinline__ void dp5_stages(const Coef<double>& c, const double* __restrict__ tab, const double* y,
+                                           double h, double* sp, size_t ss, double* y5) {
+  double K[6][10], ys[10];
+  for (int i = 0; i < 10; i++) sp[(size_t)i * ss] = y[i];
+  rhs64(c, tab, y, K[0]);
+#pragma unroll 1
+  for (int s = 1; s < 6; s++) {
+    for (int i = 0; i < 10; i++) ys[i] = y[i];
+    for (int j = 0; j < s; j++) {
+      const double a = h * c_dp_A[s][j];
+      if (a != 0.0)
+        for (int i = 0; i < 10; i++) ys[i] = fma(a, K[j][i], ys[i]);
+    }
+    for (int i = 0; i < 10; i++) sp[(size_t)(10 * s + i) * ss] = ys[i];
+    if (s < 5 || y5) rhs64(c, tab, ys, K[s]);
+  }
+  if (!y5) return;
+  for (int i = 0; i < 10; i++) y5[i] = y[i];
+  for (int j = 0; j < 6; j++) {
+    const double b = h * c_dp_B[j];
+    if (b != 0.0)
+      for (int i = 0; i < 10; i++) y5[i] = fma(b, K[j][i], y5[i]);
+  }
+}
+
+// Reverse mode of one step from its stored stage states: on entry lam is the
+// cotangent of y5, on exit the cotangent of y; the coefficient cotangents are
+// added to cb; returns the cotangent of h.  With
+//   y5 = y + h sum_j b_j k_j,  Y_s = y + h sum_{j<s} a_sj k_j,  k_s = f(Y_s)
+// and kp_j = b_j lam + sum_{s>j} a_sj Yb_s (the cotangent of k_j is h kp_j):
+//   Yb_s = J(Y_s)^T (h kp_s),  yb = lam + sum_s Yb_s,  hb = sum_j k_j . kp_j.
+__device__ double dp5_step_vjp(const Coef<double>& c, const double* __restrict__ tab, const double* sp, size_t ss,
+                               double h, double* lam, Coef<double>& cb) {
+  double kp[6][10], yb[10];
+  for (int j = 0; j < 6; j++)
+    for (int i = 0; i < 10; i++) kp[j][i] = c_dp_B[j] * lam[i];
+  for (int i = 0; i < 10; i++) yb[i] = lam[i];
+  double hb = 0.0;
+#pragma unroll 1
+  for (int s = 5; s >= 0; s--) {
+    double Ys[10], fb[10], Yb[10], ks[10];
+    for (int i = 0; i < 10; i++) {
+      Ys[i] = sp[(size_t)(10 * s + i) * ss];
+      fb[i] = h * kp[s][i];
+    }
+    rhs64_vjp(c, tab, Ys, fb, Yb, cb, ks);
+    for (int i = 0; i < 10; i++) {
+      hb = fma(ks[i], kp[s][i], hb);
+      yb[i] += Yb[i];
+    }
+    for (int j = 0; j < s; j++) {
+      const double a = c_dp_A[s][j];
+      if (a != 0.0)
+        for (int i = 0; i < 10; i++) kp[j][i] = fma(a, Yb[i], kp[j][i]);
+    }
+  }
+  for (int i = 0; i < 10; i++) lam[i] = yb[i];
+  return hb;
+}
+
+__device__ __forceinline__ double gval(const double* p, int64_t i) { return p ? p[i] : 0.0; }
+
+// Sort key of binary i: its accepted-step count when the sweep walks its
+// record, 0 when its gradients are NaN (status not OK, or no usable record).
+__device__ __forceinline__ int32_t sweep_key(const pn_outputs& o, int64_t i, int32_t cap) {
+  const int32_t N = o.n_acc[i];
+  return (o.status[i] == PN_ST_OK && N >= 1 && N <= cap) ? N : 0;
+}
+
+// Counting sort of the binaries by sweep_key, largest key first.
+__global__ void k_order_count(const pn_outputs o, int64_t n, int32_t cap, unsigned long long* bins) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int32_t key = sweep_key(o, i, cap);
+  const unsigned peers = __match_any_sync(__activemask(), key);
+  if ((int)(threadIdx.x & 31u) == __ffs(peers) - 1) atomicAdd(&bins[key], (unsigned long long)__popc(peers));
+}
+
+// In place: bins[k] <- number of binaries with a key above k (one block of 1024 threads).
+__global__ void __launch_bounds__(1024) k_order_scan(unsigned long long* bins, int32_t nb) {
+  __shared__ unsigned long long warp_tot[32];
+  __shared__ unsigned long long carry;
+  const unsigned lane = threadIdx.x & 31u, wid = threadIdx.x >> 5;
+  if (threadIdx.x == 0) carry = 0;
+  __syncthreads();
+  for (int32_t base = 0; base < nb; base += 1024) {
+    const int32_t r = base + (int32_t)threadIdx.x;  // rank from the top key down
+    const int32_t k = nb - 1 - r;
+    const unsigned long long v = (r < nb) ? bins[k] : 0ull;
+    unsigned long long x = v;  // inclusive scan within the warp
+    for (int d = 1; d < 32; d <<= 1) {
+      const unsigned long long t = __shfl_up_sync(0xffffffffu, x, d);
+      if ((int)lane >= d) x += t;
+    }
+    if (lane == 31u) warp_tot[wid] = x;
+    __syncthreads();
+    if (wid == 0) {
+      unsigned long long w = warp_tot[lane];
+      for (int d = 1; d < 32; d <<= 1) {
+        const unsigned long long t = __shfl_up_sync(0xffffffffu, w, d);
+        if ((int)lane >= d) w += t;
+      }
+      warp_tot[lane] = w;  // inclusive over warps
+    }
+    __syncthreads();
+    const unsigned long long before = carry + (wid ? warp_tot[wid - 1] : 0ull) + x - v;
+    if (r < nb) bins[k] = before;
+    __syncthreads();
+    if (threadIdx.x == 0) carry += warp_tot[31];
+    __syncthreads();
+  }
+}
+
+__global__ void k_order_scatter(const pn_outputs o, int64_t n, int32_t cap, unsigned long long* cursor,
+                                int64_t* order) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int32_t key = sweep_key(o, i, cap);
+  const unsigned lane = threadIdx.x & 31u;
+  const unsigned peers = __match_any_sync(__activemask(), key);
+  const int leader = __ffs(peers) - 1;
+  unsigned long long base = 0;
+  if ((int)lane == leader) base = atomicAdd(&cursor[key], (unsigned long long)__popc(peers));
+  base = __shfl_sync(peers, base, leader);
+  order[base + __popc(peers & ((1u << lane) - 1u))] = i;
+}
+
+// Gradients of binary i; sp0 is the lane's segment buffer (stride ss).
+__device__ void adjoint_one(const AdjArgs& a, const double* __restrict__ tab, int64_t i, double* sp0, size_t ss) {
+  const pn_outputs& o = a.k.out;
+  const pn_grads& g = a.grad;
+  const int32_t N = o.n_acc[i];
+  if (o.status[i] != PN_ST_OK || N < 1 || N > a.cap) {
+    const double nan = dnan();
+    g.s1x[i] = nan; g.s1y[i] = nan; g.s1z[i] = nan; g.s2x[i] = nan; g.s2y[i] = nan; g.s2z[i] = nan; g.q[i] = nan;
+    return;
+  }
+  const pn_inputs& in = a.k.in;
+  const double m1 = in.m1[i], m2 = in.m2[i], chi1 = in.chi1[i], chi2 = in.chi2[i];
+  const Coef<double> c = make_coef(m1, m2, a.k.ctl.terms);
+  // Cotangent of the final state from the output cotangents.
+  const double S1[3] = {o.S1x[i], o.S1y[i], o.S1z[i]}, S2[3] = {o.S2x[i], o.S2y[i], o.S2z[i]};
+  const double L[3] = {o.Lx[i], o.Ly[i], o.Lz[i]};
+  double lam[10];
+  const pn_cotangents& gb = a.gbar;
+  lam[0] = 0.0;
+  lam[7] = gval(gb.Lx, i); lam[8] = gval(gb.Ly, i); lam[9] = gval(gb.Lz, i);
+  lam[1] = gval(gb.S1x, i); lam[2] = gval(gb.S1y, i); lam[3] = gval(gb.S1z, i);
+  lam[4] = gval(gb.S2x, i); lam[5] = gval(gb.S2y, i); lam[6] = gval(gb.S2z, i);
+  const double n1 = sqrt(S1[0] * S1[0] + S1[1] * S1[1] + S1[2] * S1[2]);
+  const double n2 = sqrt(S2[0] * S2[0] + S2[1] * S2[1] + S2[2] * S2[2]);
+  const double nl = sqrt(L[0] * L[0] + L[1] * L[1] + L[2] * L[2]);
+  const double g12 = gval(gb.dot_s1s2, i), gl1 = gval(gb.dot_ls1, i), gl2 = gval(gb.dot_ls2, i);
+  if (g12 != 0.0) {  // d (a.b/(|a||b|)) / da = (b/|b| - d a/|a|) / |a|
+    const double d = (S1[0] * S2[0] + S1[1] * S2[1] + S1[2] * S2[2]) / (n1 * n2);
+    for (int k = 0; k < 3; k++) {
+      lam[1 + k] += g12 * (S2[k] / n2 - d * S1[k] / n1) / n1;
+      lam[4 + k] += g12 * (S1[k] / n1 - d * S2[k] / n2) / n2;
+    }
+  }
+  if (gl1 != 0.0) {
+    const double d = (L[0] * S1[0] + L[1] * S1[1] + L[2] * S1[2]) / (nl * n1);
+    for (int k = 0; k < 3; k++) {
+      lam[7 + k] += gl1 * (S1[k] / n1 - d * L[k] / nl) / nl;
+      lam[1 + k] += gl1 * (L[k] / nl - d * S1[k] / n1) / n1;
+    }
+  }
+  if (gl2 != 0.0) {
+    const double d = (L[0] * S2[0] + L[1] * S2[1] + L[2] * S2[2]) / (nl * n2);
+    for (int k = 0; k < 3; k++) {
+      lam[7 + k] += gl2 * (S2[k] / n2 - d * L[k] / nl) / nl;
+      lam[4 + k] += gl2 * (L[k] / nl - d * S2[k] / n2) / n2;
+    }
+  }
+  const double tbar = gval(gb.t, i);
+  Coef<double> cb;
+  double* cbv = &cb.K;
+  for (int f = 0; f < 16; f++) cbv[f] = 0.0;
+
+  const int32_t every = a.every;
+  const int32_t nseg = (N + every - 1) / every;
+  const size_t step_words = (size_t)kAdjStageWords * ss;
+#pragma unroll 1
+  for (int32_t seg = nseg - 1; seg >= 0; seg--) {
+    const int32_t n0 = seg * every;
+    const int32_t n1s = (n0 + every < N) ? n0 + every : N;
+    double y[10];
+    for (int k = 0; k < 10; k++) y[k] = a.ck[((size_t)seg * 10 + k) * a.stride + i];
+#pragma unroll 1
+    for (int32_t n = n0; n < n1s; n++) {  // recompute the segment, keeping the stage states
+      double y5[10];
+      const bool more = n + 1 < n1s;
+      dp5_stages(c, tab, y, a.h[(size_t)n * a.stride + i], sp0 + (size_t)(n - n0) * step_words, ss,
+                 more ? y5 : nullptr);
+      if (more)
+        for (int k = 0; k < 10; k++) y[k] = y5[k];
+    }
+#pragma unroll 1
+    for (int32_t n = n1s - 1; n >= n0; n--) {
+      const double* sp = sp0 + (size_t)(n - n0) * step_words;
+      const double hn = a.h[(size_t)n * a.stride + i];
+      if (n == N - 1) {  // landing step: implicit h*
+        Coef<double> cA, cB;
+        double* av = &cA.K;
+        double* bv = &cB.K;
+        for (int f = 0; f < 16; f++) { av[f] = 0.0; bv[f] = 0.0; }
+        double lA[10];
+        for (int k = 0; k < 10; k++) lA[k] = 0.0;
+        lA[0] = 1.0;
+        const double nu = dp5_step_vjp(c, tab, sp, ss, hn, lA, cA);
+        const double mu = dp5_step_vjp(c, tab, sp, ss, hn, lam, cB) + tbar;
+        const double ratio = mu / nu;
+        for (int k = 0; k < 10; k++) lam[k] -= ratio * lA[k];
+        for (int f = 0; f < 16; f++) cbv[f] += bv[f] - ratio * av[f];
+      } else {
+        (void)dp5_step_vjp(c, tab, sp, ss, hn, lam, cb);
+      }
+    }
+  }
+  // Initial state S_i = chi_i m_i^2 S_i-hat, and the mass ratio q = m1/m2 (M = 1).
+  const double s1[3] = {in.s1x[i], in.s1y[i], in.s1z[i]}, s2[3] = {in.s2x[i], in.s2y[i], in.s2z[i]};
+  const double f1 = chi1 * (m1 * m1), f2 = chi2 * (m2 * m2);
+  g.s1x[i] = f1 * lam[1]; g.s1y[i] = f1 * lam[2]; g.s1z[i] = f1 * lam[3];
+  g.s2x[i] = f2 * lam[4]; g.s2y[i] = f2 * lam[5]; g.s2z[i] = f2 * lam[6];
+  double m1b = 2.0 * chi1 * m1 * (lam[1] * s1[0] + lam[2] * s1[1] + lam[3] * s1[2]);
+  double m2b = 2.0 * chi2 * m2 * (lam[4] * s2[0] + lam[5] * s2[1] + lam[6] * s2[2]);
+  coef_vjp(cb, m1, m2, a.k.ctl.terms, &m1b, &m2b);
+  g.q[i] = (m1b - m2b) * (m2 * m2);  // dm1/dq = m2^2 = -dm2/dq
+}
+
+// Persistent sweep: each warp claims 32 consecutive entries of the order.
+// blockDim.x must be a multiple of 32.
+__global__ void __launch_bounds__(128) k_adjoint(const AdjArgs a) {
+  __shared__ double s_tab[256];
+  for (int q = threadIdx.x; q < 256; q += blockDim.x) s_tab[q] = a.k.tab[q];
+  __syncthreads();
+  const int64_t slot = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const unsigned lane = threadIdx.x & 31u;
+  double* sp0 = a.seg + slot;
+  for (;;) {
+    unsigned long long base = 0;
+    if (lane == 0) base = atomicAdd(a.k.queue, 32ull);
+    base = __shfl_sync(0xffffffffu, base, 0);
+    if (base >= (unsigned long long)a.k.n) break;
+    const int64_t p = (int64_t)base + lane;
+    if (p < a.k.n) adjoint_one(a, s_tab, a.order[p], sp0, (size_t)a.seg_stride);
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_adjoint(const AdjArgs& a, int block, int grid, cudaStream_t s) {
+  if (grid <= 0 || a.k.n <= 0) return cudaSuccess;
+  const int32_t nb = a.cap + 1;
+  const unsigned eg = (unsigned)((a.k.n + 255) / 256);
+  cudaError_t e = cudaMemsetAsync(a.bins, 0, (size_t)nb * sizeof(unsigned long long), s);
+  if (e != cudaSuccess) return e;
+  k_order_count<<<eg, 256, 0, s>>>(a.k.out, a.k.n, a.cap, a.bins);
+  k_order_scan<<<1, 1024, 0, s>>>(a.bins, nb);
+  k_order_scatter<<<eg, 256, 0, s>>>(a.k.out, a.k.n, a.cap, a.bins, a.order);
+  e = cudaMemsetAsync(a.k.queue, 0, sizeof(unsigned long long), s);
+  if (e != cudaSuccess) return e;
+  k_adjoint<<<grid, block, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t adjoint_occupancy(int block, int* blocks_per_sm) {
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, (const void*)k_adjoint, block, 0);
+}
+
+}  // namespace pn

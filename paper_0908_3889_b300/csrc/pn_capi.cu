@@ -51,6 +51,9 @@ struct pn_batch {
   double* d_ana = nullptr;               // analysis scratch: moments, KDE grid and density
   int64_t ana_cap = 0;
   int32_t* d_adj_out_i = nullptr;
+  int64_t* d_adj_order = nullptr;        // reverse sweep: binaries ordered by step count
+  unsigned long long* d_adj_bins = nullptr;
+  int64_t adj_bins_cap = 0;
   // staging for pn_batch_integrate_host
   double* d_stage_d = nullptr;
   int32_t* d_stage_i = nullptr;
@@ -141,7 +144,7 @@ static bool params_valid(const pn_params* p, std::string* why) {
   if (p->schedule < PN_SCHED_AUTO || p->schedule > PN_SCHED_PERSISTENT) return bad("bad schedule");
   if (p->block != 0 && (p->block < 32 || p->block > pn::kMaxBlock || p->block % 32 != 0))
     return bad("block must be 0 or a multiple of 32 in [32, 256]");
-  if (p->bpt != 0 && p->bpt != 1) return bad("bpt must be 0 or 1 in this build");
+  if (p->bpt < 0 || p->bpt > 2) return bad("bpt must be 0 (autotuned/default), 1 or 2");
   if (p->ckpt_every < 1) return bad("ckpt_every must be >= 1");
   return true;
 }
@@ -199,6 +202,8 @@ extern "C" void pn_batch_destroy(pn_batch* b) {
   cudaFree(b->d_hist);
   cudaFree(b->d_ana);
   cudaFree(b->d_adj_out_i);
+  cudaFree(b->d_adj_order);
+  cudaFree(b->d_adj_bins);
   cudaFree(b->d_stage_d);
   cudaFree(b->d_stage_i);
   delete b;
@@ -255,19 +260,24 @@ struct Shape {
   bool persistent;
   int block;
   int grid;
+  int bpt;  // plain schedule: binaries per thread
 };
 
-Shape choose_shape(pn_batch* b, int64_t n, int prec, int sched_override = -1, int block_override = 0) {
+Shape choose_shape(pn_batch* b, int64_t n, int prec, int sched_override = -1, int block_override = 0,
+                   int bpt_override = 0) {
   const pn_params& p = b->p;
   const pn_batch::Tuned& tu = b->tuned[prec];
   int sched = sched_override >= 0 ? sched_override : p.schedule;
   if (sched == PN_SCHED_AUTO) sched = tu.valid ? tu.schedule : PN_SCHED_PERSISTENT;
   int block = block_override ? block_override : p.block;
   if (block == 0) block = tu.valid ? tu.block : 128;
+  int bpt = bpt_override ? bpt_override : p.bpt;
+  if (bpt == 0) bpt = tu.valid ? tu.bpt : 1;
   Shape s;
   s.persistent = (sched == PN_SCHED_PERSISTENT);
   s.block = block;
-  const int64_t full = (n + block - 1) / block;
+  s.bpt = s.persistent ? 1 : bpt;
+  const int64_t full = (n + (int64_t)block * s.bpt - 1) / ((int64_t)block * s.bpt);
   if (s.persistent) {
     int per_sm = 0;
     if (pn::integrate_occupancy(prec, true, block, &per_sm) != cudaSuccess || per_sm < 1) per_sm = 1;
@@ -291,6 +301,7 @@ int run_integrate(pn_batch* b, int64_t n, const pn_inputs* in, pn_outputs* out, 
   a.queue = b->d_queue;
   a.tab = b->d_tab;
   a.ctl = make_ctl(b->p);
+  a.bpt = sh.bpt;
   if (n == 0 || sh.grid == 0) return PN_OK;
   if (!b->d_setup) {
     cudaError_t e = cudaMalloc(&b->d_setup, (size_t)pn::setup_fields() * (size_t)b->n_max * sizeof(double));
@@ -417,41 +428,46 @@ extern "C" int pn_batch_autotune(pn_batch* b, int64_t n, const pn_inputs* in, pn
   if (!outputs_ok(scratch)) return fail(b, PN_E_ARG, "NULL output pointer");
   const int prec = b->p.precision;
   const int64_t nt = n < 262144 ? n : 262144;
-  const int scheds[2] = {PN_SCHED_PLAIN, PN_SCHED_PERSISTENT};
-  const int blocks[3] = {64, 128, 256};
+  // Candidates: plain schedule x {64, 128, 256} threads x {1, 2} binaries per thread, and the
+  // persistent schedule x {64, 128, 256} threads.
+  struct Cand { int sched, block, bpt; };
+  const Cand cands[9] = {{PN_SCHED_PLAIN, 64, 1},  {PN_SCHED_PLAIN, 128, 1}, {PN_SCHED_PLAIN, 256, 1},
+                         {PN_SCHED_PLAIN, 64, 2},  {PN_SCHED_PLAIN, 128, 2}, {PN_SCHED_PLAIN, 256, 2},
+                         {PN_SCHED_PERSISTENT, 64, 1}, {PN_SCHED_PERSISTENT, 128, 1},
+                         {PN_SCHED_PERSISTENT, 256, 1}};
   double best = 1e300;
-  int bs = PN_SCHED_PERSISTENT, bb = 128, nc = 0;
-  for (int si = 0; si < 2; si++)
-    for (int bi = 0; bi < 3; bi++) {
-      const Shape sh = choose_shape(b, nt, prec, scheds[si], blocks[bi]);
-      int rc = run_integrate(b, nt, in, scratch, prec, sh);  // warm-up
+  int bs = PN_SCHED_PERSISTENT, bb = 128, bp = 1, nc = 0;
+  for (const Cand& cd : cands) {
+    const Shape sh = choose_shape(b, nt, prec, cd.sched, cd.block, cd.bpt);
+    int rc = run_integrate(b, nt, in, scratch, prec, sh);  // warm-up
+    if (rc != PN_OK) return rc;
+    float tmin = 1e30f;
+    for (int rep = 0; rep < 2; rep++) {
+      PN_CUDA(b, cudaEventRecord(b->ev[2], b->stream));
+      rc = run_integrate(b, nt, in, scratch, prec, sh);
       if (rc != PN_OK) return rc;
-      float tmin = 1e30f;
-      for (int rep = 0; rep < 2; rep++) {
-        PN_CUDA(b, cudaEventRecord(b->ev[2], b->stream));
-        rc = run_integrate(b, nt, in, scratch, prec, sh);
-        if (rc != PN_OK) return rc;
-        PN_CUDA(b, cudaEventRecord(b->ev[3], b->stream));
-        PN_CUDA(b, cudaEventSynchronize(b->ev[3]));
-        float ms = 0.f;
-        PN_CUDA(b, cudaEventElapsedTime(&ms, b->ev[2], b->ev[3]));
-        if (ms < tmin) tmin = ms;
-      }
-      nc++;
-      if (tmin < best) {
-        best = tmin;
-        bs = scheds[si];
-        bb = blocks[bi];
-      }
+      PN_CUDA(b, cudaEventRecord(b->ev[3], b->stream));
+      PN_CUDA(b, cudaEventSynchronize(b->ev[3]));
+      float ms = 0.f;
+      PN_CUDA(b, cudaEventElapsedTime(&ms, b->ev[2], b->ev[3]));
+      if (ms < tmin) tmin = ms;
     }
+    nc++;
+    if (tmin < best) {
+      best = tmin;
+      bs = cd.sched;
+      bb = cd.block;
+      bp = cd.bpt;
+    }
+  }
   b->tuned[prec].valid = true;
   b->tuned[prec].schedule = bs;
   b->tuned[prec].block = bb;
-  b->tuned[prec].bpt = 1;
+  b->tuned[prec].bpt = bp;
   if (res) {
     res->schedule = bs;
     res->block = bb;
-    res->bpt = 1;
+    res->bpt = bp;
     res->n_candidates = nc;
     res->best_ms = best;
     res->n_tuned = nt;
@@ -481,9 +497,8 @@ extern "C" int pn_batch_adjoint(pn_batch* b, int64_t n, const pn_inputs* in, con
           cudaMalloc(&b->d_adj_out_i, 4 * N * sizeof(int32_t)) != cudaSuccess) {
         cudaGetLastError();
         cudaFree(b->d_adj_out);
-  cudaFree(b->d_hist);
-  cudaFree(b->d_ana);
         b->d_adj_out = nullptr;
+        b->d_adj_out_i = nullptr;
         return fail(b, PN_E_NOMEM, "adjoint output allocation failed");
       }
     }
@@ -568,7 +583,8 @@ extern "C" int pn_batch_adjoint(pn_batch* b, int64_t n, const pn_inputs* in, con
     cap = (int32_t)t[12] + 1;
   }
 
-  // Reverse sweep, persistent: one binary per claim, lane-private segment buffer.
+  // Reverse sweep, persistent: binaries ordered by step count, 32 per warp
+  // claim, lane-private stage-state buffer.
   const int block = 128;
   int per_sm = 0;
   PN_CUDA(b, pn::adjoint_occupancy(block, &per_sm));
@@ -579,7 +595,7 @@ extern "C" int pn_batch_adjoint(pn_batch* b, int64_t n, const pn_inputs* in, con
     cudaFree(b->d_seg);
     b->d_seg = nullptr;
     b->seg_lanes = 0;
-    if (cudaMalloc(&b->d_seg, (size_t)lanes * every * 10 * sizeof(double)) != cudaSuccess) {
+    if (cudaMalloc(&b->d_seg, (size_t)lanes * every * pn::kAdjStageWords * sizeof(double)) != cudaSuccess) {
       cudaGetLastError();
       b->d_seg = nullptr;
       return fail(b, PN_E_NOMEM, "adjoint segment allocation failed");
@@ -587,19 +603,36 @@ extern "C" int pn_batch_adjoint(pn_batch* b, int64_t n, const pn_inputs* in, con
     b->seg_lanes = lanes;
     b->seg_every = every;
   }
+  if (!b->d_adj_order || b->adj_bins_cap < (int64_t)b->rec_cap + 1) {
+    cudaFree(b->d_adj_order);
+    cudaFree(b->d_adj_bins);
+    b->d_adj_order = nullptr;
+    b->d_adj_bins = nullptr;
+    b->adj_bins_cap = 0;
+    if (cudaMalloc(&b->d_adj_order, N * sizeof(int64_t)) != cudaSuccess ||
+        cudaMalloc(&b->d_adj_bins, ((size_t)b->rec_cap + 1) * sizeof(unsigned long long)) != cudaSuccess) {
+      cudaGetLastError();
+      cudaFree(b->d_adj_order);
+      b->d_adj_order = nullptr;
+      b->d_adj_bins = nullptr;
+      return fail(b, PN_E_NOMEM, "adjoint ordering allocation failed");
+    }
+    b->adj_bins_cap = (int64_t)b->rec_cap + 1;
+  }
   pn::AdjArgs aa;
   std::memset(&aa, 0, sizeof(aa));
   aa.k = a;
   aa.h = b->d_rec_h;
   aa.ck = b->d_rec_ck;
   aa.seg = b->d_seg;
+  aa.bins = b->d_adj_bins;
+  aa.order = b->d_adj_order;
   aa.stride = b->n_max;
   aa.seg_stride = b->seg_lanes;
   aa.cap = b->rec_cap;
   aa.every = every;
   aa.gbar = *gbar;
   aa.grad = *grad;
-  PN_CUDA(b, cudaMemsetAsync(b->d_queue, 0, sizeof(unsigned long long), b->stream));
   PN_CUDA(b, pn::launch_adjoint(aa, block, grid, b->stream));
   PN_CUDA(b, cudaEventRecord(b->ev[5], b->stream));
   b->timed_adjoint = true;

@@ -500,180 +500,6 @@ struct Tabs {
 };
 
 // ---------------------------------------------------------------------------
-// Reverse mode (adjoint) of the FP64 right-hand side.
-// rhs64_vjp recomputes rhs64's intermediates at y and returns
-//   yb = (df/dy)^T fb   and adds (df/dc)^T fb to cb (the 16 coefficients),
-// each line of the reverse sweep undoing one line of rhs64, in reverse order.
-// ---------------------------------------------------------------------------
-__device__ __forceinline__ void cross_vjp(const double* a, const double* b, const double* cb_, double* ab, double* bb) {
-  // c = a x b:  ab += b x cb,  bb += cb x a
-  ab[0] += b[1] * cb_[2] - b[2] * cb_[1];
-  ab[1] += b[2] * cb_[0] - b[0] * cb_[2];
-  ab[2] += b[0] * cb_[1] - b[1] * cb_[0];
-  bb[0] += cb_[1] * a[2] - cb_[2] * a[1];
-  bb[1] += cb_[2] * a[0] - cb_[0] * a[2];
-  bb[2] += cb_[0] * a[1] - cb_[1] * a[0];
-}
-
-static __device__ __noinline__ void rhs64_vjp(const Coef<double>& c, const double* __restrict__ tab, const double* y,
-                                       const double* fb, double* yb, Coef<double>& cb) {
-  // ---- forward (as rhs64) ----
-  const double w = y[0];
-  const double S1[3] = {y[1], y[2], y[3]}, S2[3] = {y[4], y[5], y[6]}, L[3] = {y[7], y[8], y[9]};
-  double r = inv_cbrt(w);
-  if ((hi32(w) & 0x7fffffffu) - (897u << 20) >= ((1151u - 897u) << 20)) r = dnan();
-  const double r2 = r * r;
-  const double v = w * r2;
-  const double v2 = v * v;
-  const double lw = log_tang(w, tab);
-  const double LS1 = L[0] * S1[0] + L[1] * S1[1] + L[2] * S1[2];
-  const double LS2 = L[0] * S2[0] + L[1] * S2[1] + L[2] * S2[2];
-  const double S12 = S1[0] * S2[0] + S1[1] * S2[1] + S1[2] * S2[2];
-  const double so = fma(c.w1, LS1, fma(c.w2, LS2, -c.tail));
-  const double c2p = fma(c.ss721, LS1 * LS2, fma(-c.ss247, S12, c.c2));
-  const double c3p = fma(c.clog, lw, c.c3l);
-  const double P6 = fma(v, c.c35, c3p);
-  const double P5 = fma(v, P6, c.c25);
-  const double P4 = fma(v, P5, c2p);
-  const double P3 = fma(v, P4, -so);
-  const double P2 = fma(v, P3, c.c1);
-  const double P = fma(v2, P2, 1.0);
-  const double w2 = w * w;
-  const double Q = (w2 * w) * v2;
-  double A1[3], A2[3], C[3];
-  A1[0] = L[1] * S1[2] - L[2] * S1[1]; A1[1] = L[2] * S1[0] - L[0] * S1[2]; A1[2] = L[0] * S1[1] - L[1] * S1[0];
-  A2[0] = L[1] * S2[2] - L[2] * S2[1]; A2[1] = L[2] * S2[0] - L[0] * S2[2]; A2[2] = L[0] * S2[1] - L[1] * S2[0];
-  C[0] = S1[1] * S2[2] - S1[2] * S2[1]; C[1] = S1[2] * S2[0] - S1[0] * S2[2]; C[2] = S1[0] * S2[1] - S1[1] * S2[0];
-  const double pre = c.prec * w2;
-  const double al1 = fma(c.a1, r, -3.0 * LS2), al2 = fma(c.a2, r, -3.0 * LS1);
-  const double p1 = pre * al1, p2 = pre * al2;
-  double d1[3], d2[3];
-  for (int k = 0; k < 3; k++) {
-    d1[k] = p1 * A1[k] - pre * C[k];
-    d2[k] = p2 * A2[k] + pre * C[k];
-  }
-  const double lf = v * c.nie;
-  // ---- reverse ----
-  double S1b[3] = {0, 0, 0}, S2b[3] = {0, 0, 0}, Lb[3] = {0, 0, 0};
-  double d1b[3], d2b[3], A1b[3], A2b[3], Cb[3];
-  double lfb = 0.0;
-  for (int k = 0; k < 3; k++) lfb += fb[7 + k] * (d1[k] + d2[k]);  // f_L = lf (d1 + d2)
-  for (int k = 0; k < 3; k++) {
-    d1b[k] = fb[1 + k] + lf * fb[7 + k];
-    d2b[k] = fb[4 + k] + lf * fb[7 + k];
-  }
-  double vb = lfb * c.nie;  // lf = v nie
-  cb.nie += lfb * v;
-  double p1b = 0.0, p2b = 0.0, preb = 0.0;  // d1 = p1 A1 - pre C, d2 = p2 A2 + pre C
-  for (int k = 0; k < 3; k++) {
-    p1b += d1b[k] * A1[k];
-    p2b += d2b[k] * A2[k];
-    A1b[k] = p1 * d1b[k];
-    A2b[k] = p2 * d2b[k];
-    Cb[k] = pre * (d2b[k] - d1b[k]);
-    preb += C[k] * (d2b[k] - d1b[k]);
-  }
-  preb += p1b * al1 + p2b * al2;  // p_i = pre al_i
-  const double al1b = p1b * pre, al2b = p2b * pre;
-  cb.a1 += al1b * r;  // al1 = a1 r - 3 LS2, al2 = a2 r - 3 LS1
-  cb.a2 += al2b * r;
-  double rb = al1b * c.a1 + al2b * c.a2;
-  double LS2b = -3.0 * al1b, LS1b = -3.0 * al2b;
-  double w2b = preb * c.prec;  // pre = prec w2
-  cb.prec += preb * w2;
-  cross_vjp(S1, S2, Cb, S1b, S2b);  // C = S1 x S2
-  cross_vjp(L, S1, A1b, Lb, S1b);   // A1 = L x S1
-  cross_vjp(L, S2, A2b, Lb, S2b);   // A2 = L x S2
-  const double f0b = fb[0];  // f0 = Q K P
-  const double Qb = f0b * c.K * P;
-  cb.K += f0b * Q * P;
-  const double Pb = f0b * Q * c.K;
-  w2b += Qb * w * v2;  // Q = w2 w v2
-  double wb = Qb * w2 * v2;
-  double v2b = Qb * w2 * w;
-  wb += 2.0 * w * w2b;  // w2 = w^2
-  v2b += Pb * P2;       // P = v2 P2 + 1
-  const double P2b = Pb * v2;
-  vb += P2b * P3;       // P2 = v P3 + c1
-  const double P3b = P2b * v;
-  cb.c1 += P2b;
-  vb += P3b * P4;       // P3 = v P4 - so
-  const double P4b = P3b * v;
-  const double sob = -P3b;
-  vb += P4b * P5;       // P4 = v P5 + c2p
-  const double P5b = P4b * v;
-  const double c2pb = P4b;
-  vb += P5b * P6;       // P5 = v P6 + c25
-  const double P6b = P5b * v;
-  cb.c25 += P5b;
-  vb += P6b * c.c35;    // P6 = v c35 + c3p
-  cb.c35 += P6b * v;
-  const double c3pb = P6b;
-  cb.clog += c3pb * lw;  // c3p = clog lw + c3l
-  const double lwb = c3pb * c.clog;
-  cb.c3l += c3pb;
-  cb.ss721 += c2pb * LS1 * LS2;  // c2p = ss721 LS1 LS2 - ss247 S12 + c2
-  LS1b += c2pb * c.ss721 * LS2;
-  LS2b += c2pb * c.ss721 * LS1;
-  cb.ss247 -= c2pb * S12;
-  const double S12b = -c2pb * c.ss247;
-  cb.c2 += c2pb;
-  cb.w1 += sob * LS1;  // so = w1 LS1 + w2 LS2 - tail
-  LS1b += sob * c.w1;
-  cb.w2 += sob * LS2;
-  LS2b += sob * c.w2;
-  cb.tail -= sob;
-  for (int k = 0; k < 3; k++) {  // LS1 = L.S1, LS2 = L.S2, S12 = S1.S2
-    Lb[k] += LS1b * S1[k] + LS2b * S2[k];
-    S1b[k] += LS1b * L[k] + S12b * S2[k];
-    S2b[k] += LS2b * L[k] + S12b * S1[k];
-  }
-  const double r3 = r2 * r;  // = 1/w
-  wb += lwb * r3;            // lw = ln|w|
-  vb += 2.0 * v * v2b;       // v2 = v^2
-  wb += vb * r2;             // v = w r^2
-  rb += vb * 2.0 * w * r;
-  wb += rb * (-1.0 / 3.0) * r * r3;  // r = w^(-1/3): dr/dw = -r/(3w)
-  yb[0] = wb;
-  for (int k = 0; k < 3; k++) {
-    yb[1 + k] = S1b[k];
-    yb[4 + k] = S2b[k];
-    yb[7 + k] = Lb[k];
-  }
-}
-
-// Reverse mode of make_coef: (m1b, m2b) += (dc/dm)^T cb, from the closed forms
-// w1 = 113/12 + (25/4) m2/m1, w2 = 113/12 + (25/4) m1/m2, ss247 = 247/(48 eta),
-// ss721 = 721/(48 eta), a1 = 4 m1 m2 + 3 m2^2, a2 = 4 m1 m2 + 3 m1^2, nie = -1/eta,
-// and the eta-polynomials of the non-spin coefficients (M = 1, eta = m1 m2).
-__device__ __forceinline__ void coef_vjp(const Coef<double>& cb, double m1, double m2, TermCfg tc, double* m1b,
-                                         double* m2b) {
-  const double eta = m1 * m2;
-  const uint32_t mk = tc.mask;
-  double etab = cb.K * (96.0 / 5.0);
-  if (mk & 2u) {
-    *m1b += cb.w1 * (-6.25 * m2 / (m1 * m1)) + cb.w2 * (6.25 / m2);
-    *m2b += cb.w1 * (6.25 / m1) + cb.w2 * (-6.25 * m1 / (m2 * m2));
-  }
-  if (mk & 16u) etab += (cb.ss247 * 247.0 + cb.ss721 * 721.0) * (-1.0 / (48.0 * eta * eta));
-  if (mk & 1u) etab += cb.c1 * (-924.0 / 336.0);
-  if (mk & 8u) etab += cb.c2 * (13661.0 / 2016.0 + 2.0 * 59.0 / 18.0 * eta);
-  if (mk & 32u) etab += cb.c25 * (-15876.0 * PN_PI / 672.0);
-  if (mk & 64u) {
-    const double theta = 1039.0 / 4620.0;
-    const double c31 = -273811877.0 / 1088640.0 + 451.0 / 48.0 * PN_PI * PN_PI;
-    const double dth = (tc.theta_mode == 0) ? c31 - 88.0 / 3.0 * theta : c31 - 2.0 * 88.0 / 3.0 * theta * eta;
-    etab += cb.c3l * (dth + 2.0 * 541.0 / 896.0 * eta - 3.0 * 5605.0 / 2592.0 * eta * eta);
-  }
-  if (mk & 128u) etab += cb.c35 * (358675.0 / 6048.0 + 2.0 * 91495.0 / 1512.0 * eta) * PN_PI;
-  *m1b += cb.a1 * (4.0 * m2) + cb.a2 * (4.0 * m2 + 6.0 * m1);
-  *m2b += cb.a1 * (4.0 * m1 + 6.0 * m2) + cb.a2 * (4.0 * m1);
-  etab += cb.nie / (eta * eta);
-  *m1b += etab * m2;
-  *m2b += etab * m1;
-}
-
-// ---------------------------------------------------------------------------
 // Dormand & Prince (1980) RK5(4)7M coefficients (published table).
 // ---------------------------------------------------------------------------
 #define DP_A21 (1.0 / 5.0)
@@ -868,89 +694,6 @@ __device__ __forceinline__ double dp5_attempt_rolled(const Coefs& cf, const Tabs
     sum = fma(qq, qq, sum);
   }
   return sum * 0.1;
-}
-
-// Full Dormand-Prince lower-triangular tableau for the adjoint (rows: stages
-// 1..6, the row of stage 1 empty) and the 5th-order weights.
-__constant__ double c_dp_A[6][6] = {
-    {0, 0, 0, 0, 0, 0},
-    {DP_A21, 0, 0, 0, 0, 0},
-    {DP_A31, DP_A32, 0, 0, 0, 0},
-    {DP_A41, DP_A42, DP_A43, 0, 0, 0},
-    {DP_A51, DP_A52, DP_A53, DP_A54, 0, 0},
-    {DP_A61, DP_A62, DP_A63, DP_A64, DP_A65, 0},
-};
-__constant__ double c_dp_B[6] = {DP_B1, 0.0, DP_B3, DP_B4, DP_B5, DP_B6};
-
-// One Dormand-Prince step y -> y5 with a fixed h (the map the accepted steps
-// apply), FP64.  Same arithmetic as the rolled attempt's stages.
-__device__ __forceinline__ void dp5_step(const Coef<double>& c, const double* __restrict__ tab, const double* y,
-                                         double h, double* y5) {
-  double K[6][10], ys[10];
-  rhs64(c, tab, y, K[0]);
-#pragma unroll 1
-  for (int s = 1; s < 6; s++) {
-    for (int i = 0; i < 10; i++) ys[i] = y[i];
-    for (int j = 0; j < s; j++) {
-      const double a = h * c_dp_A[s][j];
-      if (a != 0.0)
-        for (int i = 0; i < 10; i++) ys[i] = fma(a, K[j][i], ys[i]);
-    }
-    rhs64(c, tab, ys, K[s]);
-  }
-  for (int i = 0; i < 10; i++) y5[i] = y[i];
-  for (int j = 0; j < 6; j++) {
-    const double b = h * c_dp_B[j];
-    if (b != 0.0)
-      for (int i = 0; i < 10; i++) y5[i] = fma(b, K[j][i], y5[i]);
-  }
-}
-
-// Reverse mode of dp5_step with respect to y, h and the coefficients:
-// on entry lam is the cotangent of y5, on exit the cotangent of y; the
-// coefficient cotangents are added to cb; returns the cotangent of h.
-//   y5 = y + h sum_j b_j k_j,  Y_s = y + h sum_{j<s} a_sj k_j,  k_s = f(Y_s)
-//   kb_j = h b_j lam + sum_{s>j} h a_sj Yb_s,  Yb_s = J(Y_s)^T kb_s
-static __device__ double dp5_step_vjp(const Coef<double>& c, const double* __restrict__ tab, const double* y, double h,
-                               double* lam, Coef<double>& cb) {
-  double Y[6][10], K[6][10], Kb[6][10];
-  for (int i = 0; i < 10; i++) Y[0][i] = y[i];
-  rhs64(c, tab, y, K[0]);
-#pragma unroll 1
-  for (int s = 1; s < 6; s++) {
-    for (int i = 0; i < 10; i++) Y[s][i] = y[i];
-    for (int j = 0; j < s; j++) {
-      const double a = h * c_dp_A[s][j];
-      if (a != 0.0)
-        for (int i = 0; i < 10; i++) Y[s][i] = fma(a, K[j][i], Y[s][i]);
-    }
-    rhs64(c, tab, Y[s], K[s]);
-  }
-  double hb = 0.0, yb[10];
-  for (int i = 0; i < 10; i++) yb[i] = lam[i];
-  for (int j = 0; j < 6; j++) {
-    const double b = c_dp_B[j];
-    for (int i = 0; i < 10; i++) {
-      Kb[j][i] = h * b * lam[i];
-      hb += lam[i] * b * K[j][i];
-    }
-  }
-#pragma unroll 1
-  for (int s = 5; s >= 0; s--) {
-    double Yb[10];
-    rhs64_vjp(c, tab, Y[s], Kb[s], Yb, cb);
-    for (int i = 0; i < 10; i++) yb[i] += Yb[i];
-    for (int j = 0; j < s; j++) {
-      const double a = c_dp_A[s][j];
-      if (a != 0.0)
-        for (int i = 0; i < 10; i++) {
-          Kb[j][i] += h * a * Yb[i];
-          hb += Yb[i] * a * K[j][i];
-        }
-    }
-  }
-  for (int i = 0; i < 10; i++) lam[i] = yb[i];
-  return hb;
 }
 
 // Growth factor of the step control: clamp(safety * s^(-1/10), fac_min, fmax)

@@ -17,6 +17,8 @@ struct KArgs {
   unsigned long long* queue;  // persistent schedule: next unclaimed binary index
   const double* tab;          // logarithm tables: 256 doubles (1/F_j, ln F_j), then 512 floats (pairs)
   Ctl ctl;
+  int32_t bpt;                // plain schedule: binaries each thread integrates in turn (0 or 1: one)
+  int32_t pad_;
 };
 
 constexpr int kMaxBlock = 256;
@@ -30,11 +32,16 @@ struct RecArgs {
   int32_t cap, every;
 };
 
+// Doubles the reverse sweep keeps per recomputed step: the six stage states.
+constexpr int kAdjStageWords = 60;
+
 struct AdjArgs {
   KArgs k;           // inputs, forward outputs, n, queue, log table, controls
   const double* h;   // recorded step sizes (RecArgs layout)
   const double* ck;  // recorded checkpoints
-  double* seg;       // per-lane segment states: every x 10 x seg_stride
+  double* seg;       // per-lane stage states: every x kAdjStageWords x seg_stride
+  unsigned long long* bins;  // cap + 1 counters for the ordering by step count
+  int64_t* order;    // n binary indices, longest record first
   int64_t stride, seg_stride;
   int32_t cap, every;
   pn_cotangents gbar;
@@ -44,6 +51,8 @@ struct AdjArgs {
 cudaError_t launch_integrate_record(const KArgs& a, const double* ws, int64_t stride, const RecArgs& rec, int block,
                                     int grid, cudaStream_t s);
 cudaError_t record_occupancy(int block, int* blocks_per_sm);
+// Orders the binaries by accepted-step count (bins, order), resets the queue
+// and launches the reverse sweep (pn_adjoint.cu).
 cudaError_t launch_adjoint(const AdjArgs& a, int block, int grid, cudaStream_t s);
 cudaError_t adjoint_occupancy(int block, int* blocks_per_sm);
 

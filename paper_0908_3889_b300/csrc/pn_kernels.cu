@@ -278,6 +278,10 @@ __global__ void __launch_bounds__(kMaxBlock) k_integrate(const KArgs a, const do
   const unsigned lane = threadIdx.x & 31u;
   Lane L;
   bool have = false, exhausted = false;
+  // Plain schedule: thread g takes binaries g, g + T, ..., g + (bpt - 1) T in turn
+  // (T = threads in the grid), so every round of a warp reads consecutive binaries.
+  const int32_t bpt = a.bpt > 1 ? a.bpt : 1;
+  int32_t taken = 0;
   for (;;) {
     const bool need = !have && !exhausted;
     int64_t idx = -1;
@@ -291,7 +295,10 @@ __global__ void __launch_bounds__(kMaxBlock) k_integrate(const KArgs a, const do
         if (need) idx = (int64_t)(base + (unsigned long long)__popc((int)(m & ((1u << lane) - 1u))));
       }
     } else {
-      if (need) idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+      if (need) {
+        idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x + (int64_t)taken * gridDim.x * blockDim.x;
+        taken++;
+      }
     }
     if (need) {
       if (idx >= 0 && idx < a.n) {
@@ -300,7 +307,7 @@ __global__ void __launch_bounds__(kMaxBlock) k_integrate(const KArgs a, const do
 #pragma unroll
           for (int c = 0; c < 10; c++) rec.ck[(size_t)c * rec.stride + idx] = L.y[c];
       }
-      if (!PERSIST || idx >= a.n) exhausted = true;
+      if ((!PERSIST && taken >= bpt) || idx >= a.n) exhausted = true;
     }
     if (__all_sync(0xffffffffu, !have && exhausted)) break;
     if (have) {
@@ -373,128 +380,6 @@ cudaError_t integrate_occupancy(int prec, bool persistent, int block, int* block
   return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, pick(prec, persistent), block, 0);
 }
 
-// ---------------------------------------------------------------------------
-// Adjoint: reverse sweep through the recorded accepted steps of each binary.
-// The loss is sum_i gbar_i . out_i; the accepted step sizes are held fixed and
-// the landing step size h* is the implicit root of omega5(y_{N-1}, h*) = omega_f:
-// with mu = ybar_f . d y5/dh + tbar and nu = d omega5/dh, the cotangent passed
-// back through the landing step is ybar_f - (mu/nu) e_omega (both from reverse
-// sweeps of that step).  States of one checkpoint segment at a time are
-// recomputed from the checkpoint with the same step map the forward pass used.
-// ---------------------------------------------------------------------------
-__device__ __forceinline__ double gval(const double* p, int64_t i) { return p ? p[i] : 0.0; }
-
-__device__ void adjoint_one(const AdjArgs& a, const double* __restrict__ tab, int64_t i, int64_t slot) {
-  const pn_outputs& o = a.k.out;
-  const pn_grads& g = a.grad;
-  const int32_t N = o.n_acc[i];
-  if (o.status[i] != PN_ST_OK || N < 1 || N > a.cap) {
-    const double nan = dnan();
-    g.s1x[i] = nan; g.s1y[i] = nan; g.s1z[i] = nan; g.s2x[i] = nan; g.s2y[i] = nan; g.s2z[i] = nan; g.q[i] = nan;
-    return;
-  }
-  const pn_inputs& in = a.k.in;
-  const double m1 = in.m1[i], m2 = in.m2[i], chi1 = in.chi1[i], chi2 = in.chi2[i];
-  const Coef<double> c = make_coef(m1, m2, a.k.ctl.terms);
-  // Cotangent of the final state from the output cotangents.
-  const double S1[3] = {o.S1x[i], o.S1y[i], o.S1z[i]}, S2[3] = {o.S2x[i], o.S2y[i], o.S2z[i]};
-  const double L[3] = {o.Lx[i], o.Ly[i], o.Lz[i]};
-  double lam[10];
-  const pn_cotangents& gb = a.gbar;
-  lam[0] = 0.0;
-  lam[7] = gval(gb.Lx, i); lam[8] = gval(gb.Ly, i); lam[9] = gval(gb.Lz, i);
-  lam[1] = gval(gb.S1x, i); lam[2] = gval(gb.S1y, i); lam[3] = gval(gb.S1z, i);
-  lam[4] = gval(gb.S2x, i); lam[5] = gval(gb.S2y, i); lam[6] = gval(gb.S2z, i);
-  const double n1 = sqrt(S1[0] * S1[0] + S1[1] * S1[1] + S1[2] * S1[2]);
-  const double n2 = sqrt(S2[0] * S2[0] + S2[1] * S2[1] + S2[2] * S2[2]);
-  const double nl = sqrt(L[0] * L[0] + L[1] * L[1] + L[2] * L[2]);
-  const double g12 = gval(gb.dot_s1s2, i), gl1 = gval(gb.dot_ls1, i), gl2 = gval(gb.dot_ls2, i);
-  if (g12 != 0.0) {  // d (a.b/(|a||b|)) / da = (b/|b| - d a/|a|) / |a|
-    const double d = (S1[0] * S2[0] + S1[1] * S2[1] + S1[2] * S2[2]) / (n1 * n2);
-    for (int k = 0; k < 3; k++) {
-      lam[1 + k] += g12 * (S2[k] / n2 - d * S1[k] / n1) / n1;
-      lam[4 + k] += g12 * (S1[k] / n1 - d * S2[k] / n2) / n2;
-    }
-  }
-  if (gl1 != 0.0) {
-    const double d = (L[0] * S1[0] + L[1] * S1[1] + L[2] * S1[2]) / (nl * n1);
-    for (int k = 0; k < 3; k++) {
-      lam[7 + k] += gl1 * (S1[k] / n1 - d * L[k] / nl) / nl;
-      lam[1 + k] += gl1 * (L[k] / nl - d * S1[k] / n1) / n1;
-    }
-  }
-  if (gl2 != 0.0) {
-    const double d = (L[0] * S2[0] + L[1] * S2[1] + L[2] * S2[2]) / (nl * n2);
-    for (int k = 0; k < 3; k++) {
-      lam[7 + k] += gl2 * (S2[k] / n2 - d * L[k] / nl) / nl;
-      lam[4 + k] += gl2 * (L[k] / nl - d * S2[k] / n2) / n2;
-    }
-  }
-  const double tbar = gval(gb.t, i);
-  Coef<double> cb;
-  double* cbv = &cb.K;
-  for (int f = 0; f < 16; f++) cbv[f] = 0.0;
-
-  const int32_t every = a.every;
-  const int32_t nseg = (N + every - 1) / every;
-  const size_t ss = (size_t)a.seg_stride;
-  for (int32_t seg = nseg - 1; seg >= 0; seg--) {
-    const int32_t n0 = seg * every;
-    const int32_t n1s = (n0 + every < N) ? n0 + every : N;
-    double y[10];
-    for (int k = 0; k < 10; k++) y[k] = a.ck[((size_t)seg * 10 + k) * a.stride + i];
-    for (int32_t n = n0; n < n1s; n++) {
-      for (int k = 0; k < 10; k++) a.seg[((size_t)(n - n0) * 10 + k) * ss + slot] = y[k];
-      if (n + 1 < n1s) {
-        double y5[10];
-        dp5_step(c, tab, y, a.h[(size_t)n * a.stride + i], y5);
-        for (int k = 0; k < 10; k++) y[k] = y5[k];
-      }
-    }
-    for (int32_t n = n1s - 1; n >= n0; n--) {
-      for (int k = 0; k < 10; k++) y[k] = a.seg[((size_t)(n - n0) * 10 + k) * ss + slot];
-      const double hn = a.h[(size_t)n * a.stride + i];
-      if (n == N - 1) {  // landing step: implicit h*
-        Coef<double> cA, cB;
-        double* av = &cA.K;
-        double* bv = &cB.K;
-        for (int f = 0; f < 16; f++) { av[f] = 0.0; bv[f] = 0.0; }
-        double lA[10];
-        for (int k = 0; k < 10; k++) lA[k] = 0.0;
-        lA[0] = 1.0;
-        const double nu = dp5_step_vjp(c, tab, y, hn, lA, cA);
-        const double mu = dp5_step_vjp(c, tab, y, hn, lam, cB) + tbar;
-        const double ratio = mu / nu;
-        for (int k = 0; k < 10; k++) lam[k] -= ratio * lA[k];
-        for (int f = 0; f < 16; f++) cbv[f] += bv[f] - ratio * av[f];
-      } else {
-        (void)dp5_step_vjp(c, tab, y, hn, lam, cb);
-      }
-    }
-  }
-  // Initial state S_i = chi_i m_i^2 S_i-hat, and the mass ratio q = m1/m2 (M = 1).
-  const double s1[3] = {in.s1x[i], in.s1y[i], in.s1z[i]}, s2[3] = {in.s2x[i], in.s2y[i], in.s2z[i]};
-  const double f1 = chi1 * (m1 * m1), f2 = chi2 * (m2 * m2);
-  g.s1x[i] = f1 * lam[1]; g.s1y[i] = f1 * lam[2]; g.s1z[i] = f1 * lam[3];
-  g.s2x[i] = f2 * lam[4]; g.s2y[i] = f2 * lam[5]; g.s2z[i] = f2 * lam[6];
-  double m1b = 2.0 * chi1 * m1 * (lam[1] * s1[0] + lam[2] * s1[1] + lam[3] * s1[2]);
-  double m2b = 2.0 * chi2 * m2 * (lam[4] * s2[0] + lam[5] * s2[1] + lam[6] * s2[2]);
-  coef_vjp(cb, m1, m2, a.k.ctl.terms, &m1b, &m2b);
-  g.q[i] = (m1b - m2b) * (m2 * m2);  // dm1/dq = m2^2 = -dm2/dq
-}
-
-__global__ void __launch_bounds__(128) k_adjoint(const AdjArgs a) {
-  __shared__ double s_tab[256];
-  for (int q = threadIdx.x; q < 256; q += blockDim.x) s_tab[q] = a.k.tab[q];
-  __syncthreads();
-  const int64_t slot = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  for (;;) {  // one binary per claim; no warp-collective operations here
-    const int64_t i = (int64_t)atomicAdd(a.k.queue, 1ull);
-    if (i >= a.k.n) break;
-    adjoint_one(a, s_tab, i, slot);
-  }
-}
-
 cudaError_t launch_integrate_record(const KArgs& a, const double* ws, int64_t stride, const RecArgs& rec, int block,
                                     int grid, cudaStream_t s) {
   if (grid <= 0) return cudaSuccess;
@@ -506,16 +391,6 @@ cudaError_t launch_integrate_record(const KArgs& a, const double* ws, int64_t st
 
 cudaError_t record_occupancy(int block, int* blocks_per_sm) {
   return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, (const void*)k_integrate<0, true, true>, block, 0);
-}
-
-cudaError_t launch_adjoint(const AdjArgs& a, int block, int grid, cudaStream_t s) {
-  if (grid <= 0) return cudaSuccess;
-  k_adjoint<<<grid, block, 0, s>>>(a);
-  return cudaGetLastError();
-}
-
-cudaError_t adjoint_occupancy(int block, int* blocks_per_sm) {
-  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, (const void*)k_adjoint, block, 0);
 }
 
 // ---------------------------------------------------------------------------

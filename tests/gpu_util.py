@@ -41,3 +41,42 @@ def assert_fp64_parity(g, o, max_divergent=0, tol=FP64_TOL):
     bad = {k: v for k, v in e.items() if not v <= tol}
     assert not bad, f"FP64 parity exceeded {tol}: {bad}"
     return e
+
+
+def per_binary_errors(g, o):
+    """Per-binary scaled deviations (same scaling as parity_errors), one array per output."""
+    e = {"t": np.abs(g["t"] - o["t"]) / np.abs(o["t"]),
+         "omega": np.abs(g["omega"] - o["omega"]) / np.abs(o["omega"])}
+    for k in ("S1", "S2", "Lhat"):
+        scale = np.linalg.norm(o[k], axis=0)
+        d = np.max(np.abs(g[k] - o[k]), axis=0)
+        e[k] = np.where(scale > 0, d / np.where(scale > 0, scale, 1.0), d)
+    for k in ("dot_s1s2", "dot_ls1", "dot_ls2"):
+        e[k] = np.nan_to_num(np.abs(g[k] - o[k]), nan=0.0)
+    return e
+
+
+def ulp_response(orc, ens):
+    """Per-binary largest change of the oracle's outputs (default parameters) when one input (omega0,
+    m1 with m2 = 1 - m1, a component of each spin direction, chi2) or h0 moves by one ulp: the conditioning of each
+    binary's result under roundoff-sized perturbations.  Binaries whose perturbed run takes other step
+    decisions are left out of that run's maximum."""
+    o = orc.integrate(ens)
+    runs = []
+    for key, comp in (("omega0", None), ("m1", None), ("s1hat", 0), ("s2hat", 2), ("chi2", None)):
+        e2 = {k: v.copy() for k, v in ens.items()}
+        a = e2[key] if comp is None else e2[key][comp]
+        a[:] = np.nextafter(a, np.inf)
+        if key == "m1":
+            e2["m2"] = 1.0 - e2["m1"]
+        runs.append(orc.integrate(e2))
+    for h in (np.nextafter(10.0, np.inf), np.nextafter(10.0, 0.0)):
+        runs.append(orc.integrate(ens, orc.params(h0=float(h))))
+    resp = None
+    for p in runs:
+        e = per_binary_errors(p, o)
+        same = decided_alike(p, o)
+        for k in e:
+            e[k] = np.where(same, e[k], 0.0)
+        resp = e if resp is None else {k: np.maximum(resp[k], e[k]) for k in e}
+    return o, resp
