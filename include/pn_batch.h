@@ -8,8 +8,8 @@
  * with total mass M = m1 + m2 = 1, S_i = chi_i m_i^2 S_i-hat, from a circular
  * orbit at omega_0 with L-hat = z-hat (Sec. V) up to omega_f, with the
  * Dormand-Prince 5(4) method at error tolerance 5e-7 and first step h = 10
- * (Sec. II).  The binaries are independent ("embarrassingly parallel",
- * Sec. I); one call integrates a whole batch on one GPU.
+ * (Sec. II).  No binary depends on another (Sec. I), so one call
+ * integrates a whole batch on one GPU.
  *
  * Conventions for every entry point:
  *  - Return value: PN_OK (0) or a negative PN_E_* code.  Per-binary failures
