@@ -68,6 +68,9 @@ def parse_args():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-mixed", action="store_true")
     ap.add_argument("--no-extras", action="store_true")
+    ap.add_argument("--shape", default=None,
+                    help="fixed launch shape 'plain|persistent:BLOCK[:BPT]' for every precision instead of the "
+                         "autotuner (a run under a profiler uses it: the tuner's own timings are distorted there)")
     ap.add_argument("--profile-case", choices=("integrate", "adjoint"), default=None,
                     help="no timing, the small cases the ncu section captures run: 'integrate' integrates the "
                          "first --n binaries of the workload once per precision (persistent schedule, 256 "
@@ -280,10 +283,23 @@ def main():
         ck = clocks.stop() if clocks else None
         return total_ms, wall, ck
 
+    fixed = None
+    if args.shape:
+        parts = args.shape.split(":")
+        fixed = {"schedule": {"plain": 1, "persistent": 2}[parts[0]], "block": int(parts[1]),
+                 "bpt": int(parts[2]) if len(parts) > 2 else 1}
+
+    def shaped(b, prec_params):
+        """Fix the batch's launch shape, or let the autotuner choose it; returns the shape."""
+        if fixed is None:
+            return b.autotune(inp)
+        b.set_params(pn.params(**prec_params, **fixed))
+        return dict(fixed)
+
     # FP64 headline.
     prm = pn.params(precision=0)
     with pn.Batch(n, prm) as b:
-        tune = b.autotune(inp)
+        tune = shaped(b, {"precision": 0})
         total_ms, wall, clocks = timed_run(b, args.steps, args.warmup)
         st = b.stats(inp, out)
     total_ms = max_over_ranks(total_ms)
@@ -306,7 +322,7 @@ def main():
     # double-single right-hand side on the FP32 pipe (PN_MIXED_DS).
     def mixed_run(prec):
         with pn.Batch(n, pn.params(precision=prec)) as b:
-            tn = b.autotune(inp)
+            tn = shaped(b, {"precision": prec})
             mix_ms, _, _ = timed_run(b, args.steps, 1)
             mst = b.stats(inp, out)
         mix_ms = max_over_ranks(mix_ms)
@@ -336,7 +352,7 @@ def main():
         hin = pn.to_device(ens, device="cpu", pin_memory=True)
         hout = pn.alloc_outputs(n, pin_memory=True)
         with pn.Batch(n, prm) as b:
-            b.autotune(inp)
+            shaped(b, {"precision": 0})
             for _ in range(max(1, args.warmup)):
                 pn.pn_batch_integrate_host(b.handle, n, hin, hout)
             barrier()

@@ -143,3 +143,32 @@ def test_adjoint_refuses_other_modes(pn):
         with pn.Batch(8, pn.params(**kw)) as b:
             with pytest.raises(pn.PNError, match="UNIMPLEMENTED"):
                 pn.pn_batch_adjoint(b.handle, 8, inp, {}, grads)
+
+
+def test_adjoint_uneven_lengths_bad_inputs_and_record_growth(pn, orc):
+    """Binaries of very different lengths (the ordering by step count puts several lengths in one warp),
+    a few invalid inputs (their gradients are NaN, the rest unaffected), and one binary longer than the
+    default 256-step record, which makes the library grow the record and rerun the recording pass."""
+    n = 70
+    ens = workloads.config("C2", n=n, seed=4242)
+    ens["omega0"][0] = 0.0025  # ~300 accepted steps
+    bad = np.array([5, 17, 40])
+    ens["m2"][bad] = ens["m1"][bad]  # m1 + m2 != 1: BAD_INPUT
+    g = cotangents(n, 19)
+    got = run_adjoint(pn, ens, g)
+    assert np.all(np.isnan(got[:, bad]))
+    good = np.setdiff1d(np.arange(n), bad)
+    o = orc.integrate(ens)
+    assert o["n_acc"][0] > 256 and np.all(o["status"][bad] == 4)
+    ref = oracle_grads(orc, workloads.take(ens, good), g[:, good])
+    assert np.all(np.isfinite(got[:, good]))
+    assert rel_err(got[:, good], ref) < GRAD_TOL
+
+
+@pytest.mark.parametrize("n", [1, 33])
+def test_adjoint_small_ragged_batches(pn, orc, n):
+    ens = workloads.config("C4", n=n, seed=600 + n)
+    g = cotangents(n, n)
+    got = run_adjoint(pn, ens, g)
+    ref = oracle_grads(orc, ens, g)
+    assert rel_err(got, ref) < GRAD_TOL
