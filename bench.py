@@ -42,6 +42,7 @@ WORKLOAD = ("1,048,576 binaries, m1 = m2 = 0.5, chi_i ~ U[0,1], isotropic spin d
 FLOPS_RHS = 118
 FLOPS_STEP = 633
 FLOPS_ATTEMPT = 6 * FLOPS_RHS + FLOPS_STEP
+FP64_DATASHEET_TFLOPS = 1.25  # nominal dense FP64 of one B300
 
 # DRAM traffic of the integration kernel per binary from an ncu capture
 # (dram__bytes_read.sum + dram__bytes_write.sum, profiles/); valid only while
@@ -308,13 +309,15 @@ def main():
     attempts = st["acc_total"] + st["rej_total"] + st["land_total"]
     flops_launch = FLOPS_ATTEMPT * attempts
     achieved = flops_launch / (ms_step * 1e-3)
-    fp64_out = {k: out[k].clone() for k in ("dot_s1s2", "dot_ls1", "dot_ls2", "status")}
+    fp64_out = {k: out[k].clone() for k in ("dot_s1s2", "dot_ls1", "dot_ls2", "status", "t", "omega", "S1", "S2",
+                                            "Lhat")}
     sha = kernel_sha()
     traffic = (PROFILED["dram_bytes_per_binary"] * n
                if PROFILED["kernel_sha"] == sha and PROFILED["dram_bytes_per_binary"] else None)
     roof = {"bound": "alu", "achieved": achieved / 1e12, "peak": (f64_peak or 0) / 1e12, "unit": "TFLOP/s",
             "frac": achieved / f64_peak if f64_peak else None, "traffic": traffic,
             "pipe": "FP64", "peak_source": "FP64 FMA throughput measured live by the peak probe (2 flops per FMA)",
+            "datasheet_peak": FP64_DATASHEET_TFLOPS, "frac_of_datasheet": achieved / 1e12 / FP64_DATASHEET_TFLOPS,
             "flops_per_attempt": FLOPS_ATTEMPT, "attempts_per_launch": attempts,
             "kernel": "pn::k_integrate<FP64>"}
 
@@ -332,10 +335,21 @@ def main():
             d = (out[k] - fp64_out[k]).abs()[ok & torch.isfinite(fp64_out[k])]
             errs[k] = {"max": float(d.max()), "p99": float(torch.quantile(d[:1_000_000].float(), 0.99)),
                        "p50": float(d.median())}
+        # other outputs: relative error of t and omega; S1, S2, L-hat components scaled by their
+        # vector's FP64 magnitude
+        for k in ("t", "omega"):
+            d = ((out[k] - fp64_out[k]).abs() / fp64_out[k].abs())[ok]
+            errs[k] = {"max": float(d.max()), "p50": float(d.median())}
+        for k in ("S1", "S2", "Lhat"):
+            mag = torch.linalg.vector_norm(fp64_out[k], dim=0)
+            keep = ok & (mag > 0)
+            d = ((out[k] - fp64_out[k]).abs().amax(dim=0) / torch.where(mag > 0, mag, 1.0))[keep]
+            errs[k] = {"max": float(d.max()), "p50": float(d.median())}
         m_attempts = mst["acc_total"] + mst["rej_total"] + mst["land_total"]
         return {"value": aggregate_rate(world, n, args.steps, mix_ms), "unit": "inspirals/s",
                 "ms_per_step": mix_ms / args.steps, "speedup_vs_fp64": total_ms / mix_ms,
-                "dot_err_vs_fp64": errs, "schedule": {1: "plain", 2: "persistent"}.get(tn["schedule"]),
+                "dot_err_vs_fp64": {k: errs[k] for k in ("dot_s1s2", "dot_ls1", "dot_ls2")},
+                "other_err_vs_fp64": {k: errs[k] for k in ("t", "omega", "S1", "S2", "Lhat")}, "schedule": {1: "plain", 2: "persistent"}.get(tn["schedule"]),
                 "block": tn["block"], "fp64_pipe_achieved_tflops": (FLOPS_STEP * m_attempts) /
                 (mix_ms / args.steps * 1e-3) / 1e12}
 
@@ -383,8 +397,11 @@ def main():
                     e1.record()
                     e1.synchronize()
                     ms2 = max_over_ranks(e0.elapsed_time(e1))
+                    st2 = b.stats(inp2, out2)
                 extras[f"uneven_C2_{pname}_{name}"] = {"value": aggregate_rate(world, n2, 1, ms2),
-                                                      "unit": "inspirals/s", "ms": ms2}
+                                                      "unit": "inspirals/s", "ms": ms2,
+                                                      "accepted_steps_min_max": [st2["acc_min"], st2["acc_max"]],
+                                                      "attempts_min_max": [st2["attempts_min"], st2["attempts_max"]]}
         del inp2, out2
         c4 = workloads.config("C4", seed=workloads.SEED_BASE + 4 + 1000 * rank)
         n4 = c4["m1"].shape[0]

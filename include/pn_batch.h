@@ -32,7 +32,7 @@
 extern "C" {
 #endif
 
-#define PN_ABI_VERSION 1
+#define PN_ABI_VERSION 2
 
 /* ---- return codes ---- */
 #define PN_OK 0
@@ -155,10 +155,14 @@ typedef struct {
 
 /* Gradients written by pn_batch_adjoint (device pointers, length n): the loss
  * differentiated with respect to the raw components of S1-hat(0), S2-hat(0)
- * and the mass ratio q = m1/m2 (with M = 1 and chi_i fixed). */
+ * and the mass ratio q = m1/m2 (with M = 1 and chi_i fixed).  The *_tan
+ * pointers are optional (NULL: not written): the spin gradients projected onto
+ * the tangent plane of the sphere at each initial direction s,
+ * g - (g . s) s / |s|^2, i.e. the gradient along directions that keep |s|. */
 typedef struct {
   double *s1x, *s1y, *s1z, *s2x, *s2y, *s2z;
   double *q;
+  double *s1x_tan, *s1y_tan, *s1z_tan, *s2x_tan, *s2y_tan, *s2z_tan;
 } pn_grads;
 
 /* Batch statistics (host struct filled by pn_batch_stats). */

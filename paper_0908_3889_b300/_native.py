@@ -41,6 +41,7 @@ OUTPUT_IFIELDS = ("n_acc", "n_rej", "n_land", "status")
 OUTPUT_DOTS = ("dot_s1s2", "dot_ls1", "dot_ls2")
 COT_FIELDS = ("dot_s1s2", "dot_ls1", "dot_ls2", "Lx", "Ly", "Lz", "S1x", "S1y", "S1z", "S2x", "S2y", "S2z", "t")
 GRAD_FIELDS = ("s1x", "s1y", "s1z", "s2x", "s2y", "s2z", "q")
+GRAD_TAN_FIELDS = ("s1x_tan", "s1y_tan", "s1z_tan", "s2x_tan", "s2y_tan", "s2z_tan")  # optional
 
 
 class pn_inputs(C.Structure):
@@ -62,7 +63,7 @@ class pn_cotangents(C.Structure):
 
 
 class pn_grads(C.Structure):
-    _fields_ = [(f, _D) for f in GRAD_FIELDS]
+    _fields_ = [(f, _D) for f in GRAD_FIELDS + GRAD_TAN_FIELDS]
 
 
 class pn_stats(C.Structure):
@@ -128,7 +129,7 @@ def load(path: str | None = None) -> C.CDLL:
         fn = getattr(lib, name)
         fn.restype = res
         fn.argtypes = args
-    if lib.pn_abi_version() != 1:
+    if lib.pn_abi_version() != 2:
         raise RuntimeError("libpn_b300.so ABI version mismatch")
     if path is None:
         _lib = lib

@@ -364,6 +364,10 @@ __device__ void adjoint_one(const AdjArgs& a, const double* __restrict__ tab, in
   if (o.status[i] != PN_ST_OK || N < 1 || N > a.cap) {
     const double nan = dnan();
     g.s1x[i] = nan; g.s1y[i] = nan; g.s1z[i] = nan; g.s2x[i] = nan; g.s2y[i] = nan; g.s2z[i] = nan; g.q[i] = nan;
+    if (g.s1x_tan) {
+      g.s1x_tan[i] = nan; g.s1y_tan[i] = nan; g.s1z_tan[i] = nan;
+      g.s2x_tan[i] = nan; g.s2y_tan[i] = nan; g.s2z_tan[i] = nan;
+    }
     return;
   }
   const pn_inputs& in = a.k.in;
@@ -451,8 +455,17 @@ __device__ void adjoint_one(const AdjArgs& a, const double* __restrict__ tab, in
   // Initial state S_i = chi_i m_i^2 S_i-hat, and the mass ratio q = m1/m2 (M = 1).
   const double s1[3] = {in.s1x[i], in.s1y[i], in.s1z[i]}, s2[3] = {in.s2x[i], in.s2y[i], in.s2z[i]};
   const double f1 = chi1 * (m1 * m1), f2 = chi2 * (m2 * m2);
-  g.s1x[i] = f1 * lam[1]; g.s1y[i] = f1 * lam[2]; g.s1z[i] = f1 * lam[3];
-  g.s2x[i] = f2 * lam[4]; g.s2y[i] = f2 * lam[5]; g.s2z[i] = f2 * lam[6];
+  const double gs1[3] = {f1 * lam[1], f1 * lam[2], f1 * lam[3]}, gs2[3] = {f2 * lam[4], f2 * lam[5], f2 * lam[6]};
+  g.s1x[i] = gs1[0]; g.s1y[i] = gs1[1]; g.s1z[i] = gs1[2];
+  g.s2x[i] = gs2[0]; g.s2y[i] = gs2[1]; g.s2z[i] = gs2[2];
+  if (g.s1x_tan) {  // g - (g . s) s / |s|^2 on each sphere
+    const double c1 = (gs1[0] * s1[0] + gs1[1] * s1[1] + gs1[2] * s1[2]) /
+                      (s1[0] * s1[0] + s1[1] * s1[1] + s1[2] * s1[2]);
+    const double c2 = (gs2[0] * s2[0] + gs2[1] * s2[1] + gs2[2] * s2[2]) /
+                      (s2[0] * s2[0] + s2[1] * s2[1] + s2[2] * s2[2]);
+    g.s1x_tan[i] = gs1[0] - c1 * s1[0]; g.s1y_tan[i] = gs1[1] - c1 * s1[1]; g.s1z_tan[i] = gs1[2] - c1 * s1[2];
+    g.s2x_tan[i] = gs2[0] - c2 * s2[0]; g.s2y_tan[i] = gs2[1] - c2 * s2[1]; g.s2z_tan[i] = gs2[2] - c2 * s2[2];
+  }
   double m1b = 2.0 * chi1 * m1 * (lam[1] * s1[0] + lam[2] * s1[1] + lam[3] * s1[2]);
   double m2b = 2.0 * chi2 * m2 * (lam[4] * s2[0] + lam[5] * s2[1] + lam[6] * s2[2]);
   coef_vjp(cb, m1, m2, a.k.ctl.terms, &m1b, &m2b);

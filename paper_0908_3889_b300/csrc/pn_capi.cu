@@ -483,6 +483,13 @@ extern "C" int pn_batch_adjoint(pn_batch* b, int64_t n, const pn_inputs* in, con
   if (!gbar) return fail(b, PN_E_ARG, "cotangents struct is NULL");
   if (!grad || !grad->s1x || !grad->s1y || !grad->s1z || !grad->s2x || !grad->s2y || !grad->s2z || !grad->q)
     return fail(b, PN_E_ARG, "NULL gradient pointer");
+  {
+    const double* const tp[6] = {grad->s1x_tan, grad->s1y_tan, grad->s1z_tan,
+                                 grad->s2x_tan, grad->s2y_tan, grad->s2z_tan};
+    int set = 0;
+    for (const double* p : tp) set += (p != nullptr);
+    if (set != 0 && set != 6) return fail(b, PN_E_ARG, "tangent gradient pointers must be all set or all NULL");
+  }
   if (out && !outputs_ok(out)) return fail(b, PN_E_ARG, "NULL output pointer");
   if (b->p.precision != PN_FP64 || b->p.stop_mode != PN_STOP_LAND || b->p.fixed_step)
     return fail(b, PN_E_UNIMPLEMENTED, "the adjoint needs precision PN_FP64, PN_STOP_LAND and adaptive steps");

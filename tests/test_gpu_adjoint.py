@@ -112,6 +112,30 @@ def test_adjoint_matches_central_differences(pn, orc):
                 vals.append(g[:, i] @ out)
             fd[k] = (vals[0] - vals[1]) / (2 * d)
         assert np.max(np.abs(got[:, i] - fd)) <= 2e-6 * max(1.0, np.max(np.abs(fd))), (i, got[:, i], fd)
+    # Fully adaptive central differences (step sequence free to change) differ from the frozen-step
+    # gradient by the step control's own sensitivity: reported, not gated.
+    adaptive = []
+    for i in range(4):
+        fd = np.empty(7)
+        for k in range(7):
+            vals = []
+            for sgn in (1, -1):
+                p = workloads.take(ens, np.array([i]))
+                if k < 3:
+                    p["s1hat"][k, 0] += sgn * d
+                elif k < 6:
+                    p["s2hat"][k - 3, 0] += sgn * d
+                else:
+                    q = p["m1"][0] / p["m2"][0] + sgn * d
+                    p["m1"][0], p["m2"][0] = q / (1 + q), 1 / (1 + q)
+                o = orc.integrate(p)
+                out = np.concatenate([[o["dot_s1s2"][0], o["dot_ls1"][0], o["dot_ls2"][0]], o["Lhat"][:, 0],
+                                      o["S1"][:, 0], o["S2"][:, 0], [o["t"][0]]])
+                vals.append(g[:, i] @ out)
+            fd[k] = (vals[0] - vals[1]) / (2 * d)
+        adaptive.append(np.max(np.abs(got[:, i] - fd)) / max(1.0, np.max(np.abs(fd))))
+    print("adaptive-FD vs frozen-step adjoint, max scaled difference per binary:", adaptive)
+    assert np.all(np.isfinite(adaptive))
 
 
 def test_autograd_function_backward(pn):
@@ -172,3 +196,20 @@ def test_adjoint_small_ragged_batches(pn, orc, n):
     got = run_adjoint(pn, ens, g)
     ref = oracle_grads(orc, ens, g)
     assert rel_err(got, ref) < GRAD_TOL
+
+
+def test_tangent_projected_spin_gradients(pn):
+    """The optional *_tan outputs are g - (g . s) s / |s|^2: orthogonal to s, equal to the projection."""
+    import torch
+    ens = workloads.config("C4", n=96, seed=73)
+    g = cotangents(96, 23)
+    inp = pn.to_device(ens)
+    cot = {k: torch.from_numpy(np.ascontiguousarray(g[j])).cuda() for j, k in enumerate(OUT)}
+    grads = {k: v.cpu().numpy() for k, v in pn.adjoint(inp, cot, tangent=True).items()}
+    for sp, key in (("s1", "s1hat"), ("s2", "s2hat")):
+        full = np.stack([grads[sp + a] for a in "xyz"])
+        tan = np.stack([grads[sp + a + "_tan"] for a in "xyz"])
+        s = ens[key]
+        proj = full - (np.sum(full * s, axis=0) / np.sum(s * s, axis=0)) * s
+        assert np.allclose(tan, proj, rtol=1e-12, atol=1e-14 * np.max(np.abs(full)))
+        assert np.max(np.abs(np.sum(tan * s, axis=0))) <= 1e-12 * np.max(np.abs(full))
