@@ -621,6 +621,77 @@ __device__ __forceinline__ double dp5_attempt(const Coefs& cf, const Tabs& tb, c
   return sum * 0.1;
 }
 
+// The mixed-precision attempt (FP32 right-hand side).  The stage inputs
+// Y_2..Y_6 only feed the FP32 right-hand side, which rounds them to FP32 on
+// entry, so they are formed in FP32 from the FP32-rounded state; the new state
+// y5 = y + h sum_j b_j k_j (the state accumulation), the embedded error
+// estimate, its norm and the step control are FP64, with the FP32 rates widened
+// exactly.  Conversions between the two formats are integer operations.
+__device__ __forceinline__ double dp5_attempt_f32(const Coef<float>& c, const Ctl& ctl, const double* y,
+                                                  const double* k1, double h, double* y5, double* k7) {
+  float yf[10], f1[10], f2[10], f3[10], f4[10], f5[10], f6[10], f7[10], ys[10];
+  const float hf = f64_to_f32(h);
+#pragma unroll
+  for (int i = 0; i < 10; i++) {
+    yf[i] = f64_to_f32(y[i]);
+    f1[i] = f64_to_f32(k1[i]);  // k1 is an FP32 rate widened: exact
+  }
+  {
+    const float a1 = hf * (float)DP_A21;
+#pragma unroll
+    for (int i = 0; i < 10; i++) ys[i] = fmaf(a1, f1[i], yf[i]);
+  }
+  rhs32(c, ys, f2);
+  {
+    const float a1 = hf * (float)DP_A31, a2 = hf * (float)DP_A32;
+#pragma unroll
+    for (int i = 0; i < 10; i++) ys[i] = fmaf(a2, f2[i], fmaf(a1, f1[i], yf[i]));
+  }
+  rhs32(c, ys, f3);
+  {
+    const float a1 = hf * (float)DP_A41, a2 = hf * (float)DP_A42, a3 = hf * (float)DP_A43;
+#pragma unroll
+    for (int i = 0; i < 10; i++) ys[i] = fmaf(a3, f3[i], fmaf(a2, f2[i], fmaf(a1, f1[i], yf[i])));
+  }
+  rhs32(c, ys, f4);
+  {
+    const float a1 = hf * (float)DP_A51, a2 = hf * (float)DP_A52, a3 = hf * (float)DP_A53, a4 = hf * (float)DP_A54;
+#pragma unroll
+    for (int i = 0; i < 10; i++) ys[i] = fmaf(a4, f4[i], fmaf(a3, f3[i], fmaf(a2, f2[i], fmaf(a1, f1[i], yf[i]))));
+  }
+  rhs32(c, ys, f5);
+  {
+    const float a1 = hf * (float)DP_A61, a2 = hf * (float)DP_A62, a3 = hf * (float)DP_A63, a4 = hf * (float)DP_A64,
+                a5 = hf * (float)DP_A65;
+#pragma unroll
+    for (int i = 0; i < 10; i++)
+      ys[i] = fmaf(a5, f5[i], fmaf(a4, f4[i], fmaf(a3, f3[i], fmaf(a2, f2[i], fmaf(a1, f1[i], yf[i])))));
+  }
+  rhs32(c, ys, f6);
+  {
+    const double b1 = h * DP_B1, b3 = h * DP_B3, b4 = h * DP_B4, b5 = h * DP_B5, b6 = h * DP_B6;
+#pragma unroll
+    for (int i = 0; i < 10; i++) {
+      y5[i] = fma(b6, f32_to_f64(f6[i]), fma(b5, f32_to_f64(f5[i]), fma(b4, f32_to_f64(f4[i]),
+              fma(b3, f32_to_f64(f3[i]), fma(b1, k1[i], y[i])))));
+      ys[i] = f64_to_f32(y5[i]);
+    }
+  }
+  rhs32(c, ys, f7);
+  const double e1 = h * DP_E1, e3 = h * DP_E3, e4 = h * DP_E4, e5 = h * DP_E5, e6 = h * DP_E6, e7 = h * DP_E7;
+  double sum = 0.0;
+#pragma unroll
+  for (int i = 0; i < 10; i++) {
+    k7[i] = f32_to_f64(f7[i]);
+    const double e = fma(e7, k7[i], fma(e6, f32_to_f64(f6[i]), fma(e5, f32_to_f64(f5[i]), fma(e4, f32_to_f64(f4[i]),
+                     fma(e3, f32_to_f64(f3[i]), e1 * k1[i])))));
+    const double sc = fma(ctl.rtol, max_abs(y[i], y5[i]), ctl.atol);
+    const double q = e * rcp_pos(sc);
+    sum = fma(q, q, sum);
+  }
+  return sum * 0.1;
+}
+
 // Stage tableau for the rolled attempt: row r is stage s = r + 2; entry 0 is
 // the coefficient of k1, entry 1 + m the coefficient of the rate computed m + 1
 // stages earlier (k_{s-1-m}); the last row is b (first same as last).  Stage s

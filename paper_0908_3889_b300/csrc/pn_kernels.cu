@@ -312,8 +312,10 @@ __global__ void __launch_bounds__(kMaxBlock) k_integrate(const KArgs a, const do
     if (__all_sync(0xffffffffu, !have && exhausted)) break;
     if (have) {
       double y5[10], k7[10];
-      const double s = (PREC == 2) ? dp5_attempt_rolled<PREC>(L.cf, tb, a.ctl, L.y, L.k1, L.h, y5, k7)
-                                   : dp5_attempt<PREC>(L.cf, tb, a.ctl, L.y, L.k1, L.h, y5, k7);
+      double s;
+      if constexpr (PREC == 2) s = dp5_attempt_rolled<PREC>(L.cf, tb, a.ctl, L.y, L.k1, L.h, y5, k7);
+      else if constexpr (PREC == 1) s = dp5_attempt_f32(L.cf.c32, a.ctl, L.y, L.k1, L.h, y5, k7);
+      else s = dp5_attempt<PREC>(L.cf, tb, a.ctl, L.y, L.k1, L.h, y5, k7);
       L.attempts++;
       int32_t st;
       if (lane_decide<RECORD>(L, a.ctl, y5, k7, s, &st, rec)) {
