@@ -155,14 +155,18 @@ typedef struct {
 
 /* Gradients written by pn_batch_adjoint (device pointers, length n): the loss
  * differentiated with respect to the raw components of S1-hat(0), S2-hat(0)
- * and the mass ratio q = m1/m2 (with M = 1 and chi_i fixed).  The *_tan
- * pointers are optional (NULL: not written): the spin gradients projected onto
- * the tangent plane of the sphere at each initial direction s,
- * g - (g . s) s / |s|^2, i.e. the gradient along directions that keep |s|. */
+ * and the mass ratio q = m1/m2 (with M = 1 and chi_i fixed).  Two optional
+ * groups (NULL first pointer: group not written; all-or-none within a group):
+ *  - *_tan: the spin gradients projected onto the tangent plane of the sphere
+ *    at each initial direction s, g - (g . s) s / |s|^2;
+ *  - *_dtheta, *_dphi: derivatives with respect to the polar and azimuthal
+ *    angles of each initial direction, s = |s| (sin t cos p, sin t sin p,
+ *    cos t) with |s| held fixed (at a pole, p = 0 is taken). */
 typedef struct {
   double *s1x, *s1y, *s1z, *s2x, *s2y, *s2z;
   double *q;
   double *s1x_tan, *s1y_tan, *s1z_tan, *s2x_tan, *s2y_tan, *s2z_tan;
+  double *s1_dtheta, *s1_dphi, *s2_dtheta, *s2_dphi;
 } pn_grads;
 
 /* Batch statistics (host struct filled by pn_batch_stats). */

@@ -42,6 +42,7 @@ OUTPUT_DOTS = ("dot_s1s2", "dot_ls1", "dot_ls2")
 COT_FIELDS = ("dot_s1s2", "dot_ls1", "dot_ls2", "Lx", "Ly", "Lz", "S1x", "S1y", "S1z", "S2x", "S2y", "S2z", "t")
 GRAD_FIELDS = ("s1x", "s1y", "s1z", "s2x", "s2y", "s2z", "q")
 GRAD_TAN_FIELDS = ("s1x_tan", "s1y_tan", "s1z_tan", "s2x_tan", "s2y_tan", "s2z_tan")  # optional
+GRAD_ANGLE_FIELDS = ("s1_dtheta", "s1_dphi", "s2_dtheta", "s2_dphi")  # optional
 
 
 class pn_inputs(C.Structure):
@@ -63,7 +64,7 @@ class pn_cotangents(C.Structure):
 
 
 class pn_grads(C.Structure):
-    _fields_ = [(f, _D) for f in GRAD_FIELDS + GRAD_TAN_FIELDS]
+    _fields_ = [(f, _D) for f in GRAD_FIELDS + GRAD_TAN_FIELDS + GRAD_ANGLE_FIELDS]
 
 
 class pn_stats(C.Structure):

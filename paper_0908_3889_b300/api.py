@@ -204,7 +204,7 @@ def pn_batch_adjoint(h, n: int, inputs: dict, cotangents: dict, grads: dict, out
     for f in N.GRAD_FIELDS:
         _check_tensor(grads[f], n, torch.float64, f, None, dev)
         setattr(gs, f, _dptr(grads[f]))
-    for f in N.GRAD_TAN_FIELDS:  # optional
+    for f in N.GRAD_TAN_FIELDS + N.GRAD_ANGLE_FIELDS:  # optional
         if grads.get(f) is not None:
             _check_tensor(grads[f], n, torch.float64, f, None, dev)
             setattr(gs, f, _dptr(grads[f]))
@@ -373,11 +373,14 @@ class PNAdjointFn(torch.autograd.Function):
         return gs1, gs2, grads["q"], None, None, None, None, None, None
 
 
-def adjoint(inputs: dict, cotangents: dict, n: int | None = None, tangent: bool = False, **kw) -> dict:
+def adjoint(inputs: dict, cotangents: dict, n: int | None = None, tangent: bool = False, angles: bool = False,
+            **kw) -> dict:
     """Gradients of sum_i cotangents_i . outputs_i w.r.t. s1x..s2z and q (pn_batch_adjoint); with
-    tangent=True also the spin gradients projected onto the sphere's tangent plane (s1x_tan ...)."""
+    tangent=True also the spin gradients projected onto the sphere's tangent plane (s1x_tan ...), with
+    angles=True the derivatives w.r.t. the polar and azimuthal angles of each initial spin direction
+    (s1_dtheta, s1_dphi, s2_dtheta, s2_dphi)."""
     n = int(inputs["m1"].shape[0]) if n is None else n
-    fields = N.GRAD_FIELDS + (N.GRAD_TAN_FIELDS if tangent else ())
+    fields = N.GRAD_FIELDS + (N.GRAD_TAN_FIELDS if tangent else ()) + (N.GRAD_ANGLE_FIELDS if angles else ())
     grads = {f: torch.empty(n, dtype=torch.float64, device=inputs["m1"].device) for f in fields}
     with Batch(max(n, 1), params(**kw)) as b:
         pn_batch_adjoint(b.handle, n, inputs, cotangents, grads)

@@ -356,6 +356,18 @@ __global__ void k_order_scatter(const pn_outputs o, int64_t n, int32_t cap, unsi
   order[base + __popc(peers & ((1u << lane) - 1u))] = i;
 }
 
+// Derivatives of a loss with gradient gv (with respect to the components of s)
+// along the polar and azimuthal angles of s at fixed |s|:
+//   ds/dp = (-s_y, s_x, 0),  ds/dt = (s_z s_x / rho, s_z s_y / rho, -rho) with
+//   rho = sqrt(s_x^2 + s_y^2) = |s| sin t; at a pole (rho = 0) p = 0 is taken:
+//   ds/dt = (s_z, 0, 0).
+__device__ __forceinline__ void angle_grads(const double* gv, const double* s, double* dt, double* dp) {
+  const double rho = sqrt(s[0] * s[0] + s[1] * s[1]);
+  *dp = gv[1] * s[0] - gv[0] * s[1];
+  if (rho > 0.0) *dt = (gv[0] * s[0] + gv[1] * s[1]) * (s[2] / rho) - gv[2] * rho;
+  else *dt = gv[0] * s[2];
+}
+
 // Gradients of binary i; sp0 is the lane's segment buffer (stride ss).
 __device__ void adjoint_one(const AdjArgs& a, const double* __restrict__ tab, int64_t i, double* sp0, size_t ss) {
   const pn_outputs& o = a.k.out;
@@ -368,6 +380,7 @@ __device__ void adjoint_one(const AdjArgs& a, const double* __restrict__ tab, in
       g.s1x_tan[i] = nan; g.s1y_tan[i] = nan; g.s1z_tan[i] = nan;
       g.s2x_tan[i] = nan; g.s2y_tan[i] = nan; g.s2z_tan[i] = nan;
     }
+    if (g.s1_dtheta) { g.s1_dtheta[i] = nan; g.s1_dphi[i] = nan; g.s2_dtheta[i] = nan; g.s2_dphi[i] = nan; }
     return;
   }
   const pn_inputs& in = a.k.in;
@@ -465,6 +478,12 @@ __device__ void adjoint_one(const AdjArgs& a, const double* __restrict__ tab, in
                       (s2[0] * s2[0] + s2[1] * s2[1] + s2[2] * s2[2]);
     g.s1x_tan[i] = gs1[0] - c1 * s1[0]; g.s1y_tan[i] = gs1[1] - c1 * s1[1]; g.s1z_tan[i] = gs1[2] - c1 * s1[2];
     g.s2x_tan[i] = gs2[0] - c2 * s2[0]; g.s2y_tan[i] = gs2[1] - c2 * s2[1]; g.s2z_tan[i] = gs2[2] - c2 * s2[2];
+  }
+  if (g.s1_dtheta) {  // d/dt and d/dp of s = |s| (sin t cos p, sin t sin p, cos t), |s| fixed
+    double dt1, dp1, dt2, dp2;
+    angle_grads(gs1, s1, &dt1, &dp1);
+    angle_grads(gs2, s2, &dt2, &dp2);
+    g.s1_dtheta[i] = dt1; g.s1_dphi[i] = dp1; g.s2_dtheta[i] = dt2; g.s2_dphi[i] = dp2;
   }
   double m1b = 2.0 * chi1 * m1 * (lam[1] * s1[0] + lam[2] * s1[1] + lam[3] * s1[2]);
   double m2b = 2.0 * chi2 * m2 * (lam[4] * s2[0] + lam[5] * s2[1] + lam[6] * s2[2]);

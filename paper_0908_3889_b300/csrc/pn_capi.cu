@@ -489,6 +489,10 @@ extern "C" int pn_batch_adjoint(pn_batch* b, int64_t n, const pn_inputs* in, con
     int set = 0;
     for (const double* p : tp) set += (p != nullptr);
     if (set != 0 && set != 6) return fail(b, PN_E_ARG, "tangent gradient pointers must be all set or all NULL");
+    const double* const ap[4] = {grad->s1_dtheta, grad->s1_dphi, grad->s2_dtheta, grad->s2_dphi};
+    set = 0;
+    for (const double* p : ap) set += (p != nullptr);
+    if (set != 0 && set != 4) return fail(b, PN_E_ARG, "angle gradient pointers must be all set or all NULL");
   }
   if (out && !outputs_ok(out)) return fail(b, PN_E_ARG, "NULL output pointer");
   if (b->p.precision != PN_FP64 || b->p.stop_mode != PN_STOP_LAND || b->p.fixed_step)

@@ -213,3 +213,81 @@ def test_tangent_projected_spin_gradients(pn):
         proj = full - (np.sum(full * s, axis=0) / np.sum(s * s, axis=0)) * s
         assert np.allclose(tan, proj, rtol=1e-12, atol=1e-14 * np.max(np.abs(full)))
         assert np.max(np.abs(np.sum(tan * s, axis=0))) <= 1e-12 * np.max(np.abs(full))
+
+
+def _angles(s):
+    return np.arccos(np.clip(s[2] / np.linalg.norm(s, axis=0), -1, 1)), np.arctan2(s[1], s[0])
+
+
+def _direction(theta, phi, norm):
+    return norm * np.stack([np.sin(theta) * np.cos(phi), np.sin(theta) * np.sin(phi), np.cos(theta)])
+
+
+def test_angle_gradients_chain_rule_and_replayed_fd(pn, orc):
+    """d/dtheta, d/dphi of each initial spin direction: equal to the chain rule applied to the component
+    gradients, and to central differences (h = 1e-6) of the replayed map in the angles."""
+    import torch
+    n = 10
+    ens = workloads.config("C4", n=n, seed=91)
+    g = cotangents(n, 29)
+    inp = pn.to_device(ens)
+    cot = {k: torch.from_numpy(np.ascontiguousarray(g[j])).cuda() for j, k in enumerate(OUT)}
+    gr = {k: v.cpu().numpy() for k, v in pn.adjoint(inp, cot, angles=True).items()}
+    for sp, key in (("s1", "s1hat"), ("s2", "s2hat")):
+        s = ens[key]
+        th, ph = _angles(s)
+        full = np.stack([gr[sp + a] for a in "xyz"])
+        d_th = np.stack([np.cos(th) * np.cos(ph), np.cos(th) * np.sin(ph), -np.sin(th)])
+        d_ph = np.stack([-np.sin(th) * np.sin(ph), np.sin(th) * np.cos(ph), np.zeros(n)])
+        scale = np.max(np.abs(full))
+        assert np.allclose(gr[sp + "_dtheta"], np.sum(full * d_th, axis=0), rtol=1e-10, atol=1e-12 * scale)
+        assert np.allclose(gr[sp + "_dphi"], np.sum(full * d_ph, axis=0), rtol=1e-10, atol=1e-12 * scale)
+    d = 1e-6
+    for i in range(4):
+        rows, hs = orc.trace(ens, i)
+        for sp, key in (("s1", "s1hat"), ("s2", "s2hat")):
+            for which in ("theta", "phi"):
+                vals = []
+                for sgn in (1, -1):
+                    p = workloads.take(ens, np.array([i]))
+                    th, ph = _angles(p[key])
+                    if which == "theta":
+                        th = th + sgn * d
+                    else:
+                        ph = ph + sgn * d
+                    p[key] = _direction(th, ph, np.linalg.norm(p[key], axis=0))
+                    y, t = orc.replay(p, 0, hs)
+                    S1, S2, L = y[1:4], y[4:7], y[7:10]
+                    n1, n2, nl = np.linalg.norm(S1), np.linalg.norm(S2), np.linalg.norm(L)
+                    out = np.concatenate([[S1 @ S2 / (n1 * n2), L @ S1 / (nl * n1), L @ S2 / (nl * n2)], L, S1, S2,
+                                          [t]])
+                    vals.append(g[:, i] @ out)
+                fd = (vals[0] - vals[1]) / (2 * d)
+                got = gr[f"{sp}_d{which}"][i]
+                assert abs(got - fd) <= 2e-6 * max(1.0, abs(fd)), (i, sp, which, got, fd)
+
+
+def test_gradient_step_on_angles_moves_the_final_alignment(pn):
+    """Sensitivity exploration with the adjoint: one gradient-ascent step on the four initial spin angles
+    of each binary raises its final S1-hat.S2-hat by the first-order amount eps |grad|^2."""
+    import torch
+    n = 512
+    ens = workloads.config("C4", n=n, seed=57)
+    inp = pn.to_device(ens)
+    cot = {"dot_s1s2": torch.ones(n, dtype=torch.float64, device="cuda")}
+    gr = {k: v.cpu().numpy() for k, v in pn.adjoint(inp, cot, angles=True).items()}
+    grad = np.stack([gr["s1_dtheta"], gr["s1_dphi"], gr["s2_dtheta"], gr["s2_dphi"]])
+    base = pn.to_numpy(pn.integrate(inp))["dot_s1s2"]
+    eps = 1e-4 / np.maximum(np.linalg.norm(grad, axis=0), 1e-3)  # angle step of 1e-4 rad along the gradient
+    moved = {k: v.copy() for k, v in ens.items()}
+    for k, key in ((0, "s1hat"), (2, "s2hat")):
+        th, ph = _angles(ens[key])
+        moved[key] = _direction(th + eps * grad[k], ph + eps * grad[k + 1], np.linalg.norm(ens[key], axis=0))
+    after = pn.to_numpy(pn.integrate(pn.to_device(moved)))["dot_s1s2"]
+    gain = after - base
+    predicted = eps * np.sum(grad * grad, axis=0)
+    big = predicted > 1e-5  # well above the step-control noise of the adaptive re-integration
+    assert big.sum() > n // 2
+    ratio = gain[big] / predicted[big]
+    assert np.mean(gain[big] > 0) >= 0.98
+    assert abs(np.median(ratio) - 1.0) < 0.05, np.median(ratio)
