@@ -49,6 +49,9 @@ extern "C" {
 #define PN_ST_BAD_INPUT 4   /* non-finite input, m_i <= 0, |m1+m2-1| > 1e-12, chi outside [0,1],
                                omega_0 <= 0, omega_f <= omega_0, or | |L-hat_0| - 1 | > 1e-12 */
 #define PN_ST_LAND_MAXIT 5  /* the stop at omega_f did not converge in land_max_iter retakes */
+#define PN_ST_RUNNING 6     /* pn_batch_integrate_budget / pn_batch_resume: the call's attempt budget ran
+                               out; the binary's full state is kept for pn_batch_resume, and the outputs
+                               hold its current state */
 
 /* ---- parameter enums ---- */
 #define PN_FP64 0  /* everything in FP64 */
@@ -243,6 +246,27 @@ int pn_batch_sample(pn_batch *b, uint64_t seed, const pn_dist *d, int64_t n, con
  * n out of range), PN_E_CUDA (launch failure).  Uses the schedule, block and
  * binaries-per-thread of the parameters, or the autotuned choice for 0. */
 int pn_batch_integrate(pn_batch *b, int64_t n, const pn_inputs *in, pn_outputs *out);
+
+/* Bounded integration with resume.  pn_batch_integrate_budget starts binaries
+ * 0..n-1 like pn_batch_integrate, but each binary makes at most `budget`
+ * Dormand-Prince attempts (budget >= 1) in this call; a binary still running
+ * then gets status PN_ST_RUNNING, its current state in *out, and its complete
+ * integrator state (y, f(y), t, step size, landing bracket, counters, flags)
+ * kept in library-owned device memory (n_max x 24 doubles + 6 int32,
+ * allocated on first use).  pn_batch_resume continues exactly those binaries
+ * of 0..n-1 whose status in *out is PN_ST_RUNNING, for at most `budget` more
+ * attempts each (budget = 0: until they finish); other binaries are not
+ * touched.  The same *in, *out and parameters must be passed to the calls of
+ * one run, and no other integration of the batch may come between them (the
+ * set-up table is shared).  A run continued until no binary is PN_ST_RUNNING
+ * gives results bit-identical to one pn_batch_integrate call.  Bounded calls
+ * keep each kernel launch short (for time slicing, or for inspecting or
+ * copying the state between calls).  Asynchronous; count the binaries still
+ * running with pn_batch_stats (count_by_status[PN_ST_RUNNING]).
+ * Errors: PN_E_ARG (NULL pointers, n out of range, budget < 1 for the first
+ * call or < 0 for resume), PN_E_NOMEM, PN_E_CUDA. */
+int pn_batch_integrate_budget(pn_batch *b, int64_t n, const pn_inputs *in, pn_outputs *out, int32_t budget);
+int pn_batch_resume(pn_batch *b, int64_t n, const pn_inputs *in, pn_outputs *out, int32_t budget);
 
 /* Same as pn_batch_integrate with HOST input and output arrays: copies the
  * inputs to the library's device staging buffers (allocated on first use,

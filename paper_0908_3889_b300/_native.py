@@ -12,7 +12,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libpn_b300.so")
 
 PN_OK, PN_E_ARG, PN_E_CUDA, PN_E_NOMEM, PN_E_UNIMPLEMENTED = 0, -1, -2, -3, -4
-PN_ST_OK, PN_ST_MAX_STEPS, PN_ST_H_UNDERFLOW, PN_ST_NONFINITE, PN_ST_BAD_INPUT, PN_ST_LAND_MAXIT = range(6)
+PN_ST_OK, PN_ST_MAX_STEPS, PN_ST_H_UNDERFLOW, PN_ST_NONFINITE, PN_ST_BAD_INPUT, PN_ST_LAND_MAXIT, PN_ST_RUNNING = range(7)
 PN_FP64, PN_MIXED, PN_MIXED_DS = 0, 1, 2
 PN_STOP_LAND, PN_STOP_FIRST_CROSS = 0, 1
 PN_THETA_BCV2, PN_THETA_AS_PRINTED = 0, 1
@@ -98,6 +98,9 @@ SIGNATURES = {
     "pn_batch_sample": (C.c_int, [C.c_void_p, C.c_uint64, C.POINTER(pn_dist), C.c_int64, C.POINTER(pn_inputs)]),
     "pn_batch_integrate": (C.c_int, [C.c_void_p, C.c_int64, C.POINTER(pn_inputs), C.POINTER(pn_outputs)]),
     "pn_batch_integrate_host": (C.c_int, [C.c_void_p, C.c_int64, C.POINTER(pn_inputs), C.POINTER(pn_outputs)]),
+    "pn_batch_integrate_budget": (C.c_int, [C.c_void_p, C.c_int64, C.POINTER(pn_inputs), C.POINTER(pn_outputs),
+                                            C.c_int32]),
+    "pn_batch_resume": (C.c_int, [C.c_void_p, C.c_int64, C.POINTER(pn_inputs), C.POINTER(pn_outputs), C.c_int32]),
     "pn_batch_autotune": (C.c_int, [C.c_void_p, C.c_int64, C.POINTER(pn_inputs), C.POINTER(pn_outputs),
                                     C.POINTER(pn_tune_result)]),
     "pn_batch_adjoint": (C.c_int, [C.c_void_p, C.c_int64, C.POINTER(pn_inputs), C.POINTER(pn_cotangents),

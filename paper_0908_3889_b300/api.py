@@ -173,6 +173,16 @@ def pn_batch_integrate(h, n: int, inputs: dict, outputs: dict) -> None:
                                      C.byref(outputs_struct(outputs, n))), h)
 
 
+def pn_batch_integrate_budget(h, n: int, inputs: dict, outputs: dict, budget: int) -> None:
+    _check(_lib().pn_batch_integrate_budget(h, int(n), C.byref(inputs_struct(inputs, n)),
+                                            C.byref(outputs_struct(outputs, n)), int(budget)), h)
+
+
+def pn_batch_resume(h, n: int, inputs: dict, outputs: dict, budget: int = 0) -> None:
+    _check(_lib().pn_batch_resume(h, int(n), C.byref(inputs_struct(inputs, n)), C.byref(outputs_struct(outputs, n)),
+                                  int(budget)), h)
+
+
 def _host_inputs_struct(inp: dict, n: int) -> N.pn_inputs:
     for k in INPUT_KEYS:
         _check_tensor(inp[k], n, torch.float64, k, 3 if k in VEC_INPUTS else None, torch.device("cpu"))
@@ -243,6 +253,15 @@ def pn_batch_kde(h, n: int, inputs: dict, outputs: dict, quantity: int, grid) ->
     return dens, bw.value
 
 
+def pn_integrate_noalloc(n: int, prm: N.pn_params, inputs: dict, outputs: dict, stream=None) -> None:
+    """The library's no-allocation entry point (n <= 16384 binaries, persistent schedule)."""
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    sp = stream.cuda_stream if hasattr(stream, "cuda_stream") else stream
+    _check(_lib().pn_integrate_noalloc(int(n), C.byref(prm), C.byref(inputs_struct(inputs, n)),
+                                       C.byref(outputs_struct(outputs, n)), C.c_void_p(sp)), None)
+
+
 def pn_batch_destroy(h) -> None:
     if h:
         _lib().pn_batch_destroy(h)
@@ -289,6 +308,20 @@ class Batch:
         n = int(inputs["m1"].shape[0]) if n is None else n
         outputs = alloc_outputs(n, inputs["m1"].device) if outputs is None else outputs
         pn_batch_integrate(self.handle, n, inputs, outputs)
+        return outputs
+
+    def integrate_budget(self, inputs: dict, outputs: dict | None = None, budget: int = 64,
+                         n: int | None = None) -> dict:
+        """Start a bounded run (pn_batch_integrate_budget): at most `budget` attempts per binary."""
+        n = int(inputs["m1"].shape[0]) if n is None else n
+        outputs = alloc_outputs(n, inputs["m1"].device) if outputs is None else outputs
+        pn_batch_integrate_budget(self.handle, n, inputs, outputs, budget)
+        return outputs
+
+    def resume(self, inputs: dict, outputs: dict, budget: int = 0, n: int | None = None) -> dict:
+        """Continue the binaries left PN_ST_RUNNING (pn_batch_resume); budget 0 runs them to the end."""
+        n = int(inputs["m1"].shape[0]) if n is None else n
+        pn_batch_resume(self.handle, n, inputs, outputs, budget)
         return outputs
 
     def sample(self, seed: int, dist: N.pn_dist, n: int, inputs: dict | None = None, device="cuda") -> dict:

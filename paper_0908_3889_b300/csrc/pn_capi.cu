@@ -54,6 +54,9 @@ struct pn_batch {
   int64_t* d_adj_order = nullptr;        // reverse sweep: binaries ordered by step count
   unsigned long long* d_adj_bins = nullptr;
   int64_t adj_bins_cap = 0;
+  // saved integrator states between bounded calls (pn_batch_integrate_budget / pn_batch_resume)
+  double* d_rs = nullptr;
+  int32_t* d_ri = nullptr;
   // staging for pn_batch_integrate_host
   double* d_stage_d = nullptr;
   int32_t* d_stage_i = nullptr;
@@ -206,6 +209,8 @@ extern "C" void pn_batch_destroy(pn_batch* b) {
   cudaFree(b->d_adj_bins);
   cudaFree(b->d_stage_d);
   cudaFree(b->d_stage_i);
+  cudaFree(b->d_rs);
+  cudaFree(b->d_ri);
   delete b;
 }
 
@@ -292,7 +297,11 @@ Shape choose_shape(pn_batch* b, int64_t n, int prec, int sched_override = -1, in
 // Launch one integration of n binaries with the given shape on b->stream.
 // The persistent shape goes through a CUDA graph (queue reset + kernel),
 // captured on a private stream and re-used while the arguments repeat.
-int run_integrate(pn_batch* b, int64_t n, const pn_inputs* in, pn_outputs* out, int prec, const Shape& sh) {
+// With budget > 0 or resume set (bounded calls) the launches go straight onto
+// b->stream: a resumed launch runs no set-up pass, and such calls are not the
+// repeated identical launches the graph is for.
+int run_integrate(pn_batch* b, int64_t n, const pn_inputs* in, pn_outputs* out, int prec, const Shape& sh,
+                  int32_t budget = 0, int32_t resume = 0) {
   KArgs a;
   std::memset(&a, 0, sizeof(a));
   a.in = *in;
@@ -302,8 +311,11 @@ int run_integrate(pn_batch* b, int64_t n, const pn_inputs* in, pn_outputs* out, 
   a.tab = b->d_tab;
   a.ctl = make_ctl(b->p);
   a.bpt = sh.bpt;
+  a.budget = budget;
+  a.resume = resume;
   if (n == 0 || sh.grid == 0) return PN_OK;
   if (!b->d_setup) {
+    if (resume) return fail(b, PN_E_ARG, "resume without a bounded run to continue");
     cudaError_t e = cudaMalloc(&b->d_setup, (size_t)pn::setup_fields() * (size_t)b->n_max * sizeof(double));
     if (e != cudaSuccess) {
       b->d_setup = nullptr;
@@ -312,6 +324,30 @@ int run_integrate(pn_batch* b, int64_t n, const pn_inputs* in, pn_outputs* out, 
     }
   }
   const int64_t stride = b->n_max;
+  if (budget > 0 || resume) {
+    if (!b->d_rs) {
+      if (resume) return fail(b, PN_E_ARG, "resume without a bounded run to continue");
+      if (cudaMalloc(&b->d_rs, (size_t)pn::kResumeD * (size_t)b->n_max * sizeof(double)) != cudaSuccess ||
+          cudaMalloc(&b->d_ri, (size_t)pn::kResumeI * (size_t)b->n_max * sizeof(int32_t)) != cudaSuccess) {
+        cudaGetLastError();
+        cudaFree(b->d_rs);
+        b->d_rs = nullptr;
+        b->d_ri = nullptr;
+        return fail(b, PN_E_NOMEM, "resume state allocation failed");
+      }
+    }
+    a.rs = b->d_rs;
+    a.ri = b->d_ri;
+    a.rs_stride = b->n_max;
+    if (sh.persistent) PN_CUDA(b, cudaMemsetAsync(b->d_queue, 0, sizeof(unsigned long long), b->stream));
+    if (!resume) {
+      cudaError_t e = pn::launch_setup(prec, a, b->d_setup, stride, b->stream);
+      if (e != cudaSuccess) return cuda_fail(b, e, "set-up kernel launch");
+    }
+    cudaError_t e = pn::launch_integrate(prec, sh.persistent, sh.block, sh.grid, a, b->d_setup, stride, b->stream);
+    if (e != cudaSuccess) return cuda_fail(b, e, "integrate kernel launch");
+    return PN_OK;
+  }
   if (!sh.persistent) {
     cudaError_t e = pn::launch_setup(prec, a, b->d_setup, stride, b->stream);
     if (e != cudaSuccess) return cuda_fail(b, e, "set-up kernel launch");
@@ -371,6 +407,32 @@ extern "C" int pn_batch_integrate(pn_batch* b, int64_t n, const pn_inputs* in, p
   PN_CUDA(b, cudaEventRecord(b->ev[1], b->stream));
   b->timed_integrate = true;
   return PN_OK;
+}
+
+static int integrate_bounded(pn_batch* b, int64_t n, const pn_inputs* in, pn_outputs* out, int32_t budget,
+                             int32_t resume) {
+  if (!b) return fail(nullptr, PN_E_ARG, "batch is NULL");
+  if (n < 0 || n > b->n_max) return fail(b, PN_E_ARG, "n must be in [0, n_max]");
+  if (!inputs_ok(in)) return fail(b, PN_E_ARG, "NULL input pointer");
+  if (!outputs_ok(out)) return fail(b, PN_E_ARG, "NULL output pointer");
+  if (resume ? budget < 0 : budget < 1) return fail(b, PN_E_ARG, resume ? "budget must be >= 0" : "budget must be >= 1");
+  const int prec = b->p.precision;
+  const Shape sh = choose_shape(b, n, prec);
+  PN_CUDA(b, cudaEventRecord(b->ev[0], b->stream));
+  const int rc = run_integrate(b, n, in, out, prec, sh, budget, resume);
+  if (rc != PN_OK) return rc;
+  PN_CUDA(b, cudaEventRecord(b->ev[1], b->stream));
+  b->timed_integrate = true;
+  return PN_OK;
+}
+
+extern "C" int pn_batch_integrate_budget(pn_batch* b, int64_t n, const pn_inputs* in, pn_outputs* out,
+                                         int32_t budget) {
+  return integrate_bounded(b, n, in, out, budget, 0);
+}
+
+extern "C" int pn_batch_resume(pn_batch* b, int64_t n, const pn_inputs* in, pn_outputs* out, int32_t budget) {
+  return integrate_bounded(b, n, in, out, budget, 1);
 }
 
 extern "C" int pn_batch_integrate_host(pn_batch* b, int64_t n, const pn_inputs* hin, pn_outputs* hout) {

@@ -18,8 +18,19 @@ struct KArgs {
   const double* tab;          // logarithm tables: 256 doubles (1/F_j, ln F_j), then 512 floats (pairs)
   Ctl ctl;
   int32_t bpt;                // plain schedule: binaries each thread integrates in turn (0 or 1: one)
+  int32_t budget;             // attempts per binary in this launch (0: no limit)
+  int32_t resume;             // 1: continue the binaries whose status is PN_ST_RUNNING from the saved state
   int32_t pad_;
+  double* rs;                 // saved integrator state, kResumeD doubles per binary (field-major, rs_stride)
+  int32_t* ri;                // saved integrator state, kResumeI int32 per binary (field-major, rs_stride)
+  int64_t rs_stride;
 };
+
+// Saved state of a binary between bounded calls: y[10], f(y)[10], t, h, h_lo,
+// h_hi; n_acc, n_rej, n_land, attempts, land_it, flags (bit 0 landing, bit 1
+// last attempt rejected).
+constexpr int kResumeD = 24;
+constexpr int kResumeI = 6;
 
 constexpr int kMaxBlock = 256;
 

@@ -28,6 +28,7 @@ struct Lane {
   double k1[10];  // f(y), carried across accepted steps (first same as last)
   double t, h, h_lo, h_hi, wf;
   int32_t n_acc, n_rej, n_land, attempts, land_it;
+  int32_t stop_at;  // attempts count at which this launch's budget runs out
   bool landing, last_rej;
   Coefs cf;
 };
@@ -134,11 +135,14 @@ __global__ void __launch_bounds__(256) k_setup(const KArgs a, double* __restrict
   fld(ws, stride, 36)[i] = wf;
 }
 
-// Pick up binary i from the set-up table.  Returns false if its result was
-// already written (invalid input).
-template <int PREC>
-__device__ __forceinline__ bool lane_load(Lane& L, const Ctl& ctl, const double* __restrict__ ws, int64_t stride,
+// Pick up binary i: its coefficients from the set-up table and its state either
+// from the set-up table (a fresh start) or, in a resumed launch, from the saved
+// state of a binary left PN_ST_RUNNING.  Returns false if there is nothing to
+// do for it (invalid input already written, or not running in a resume).
+template <int PREC, bool BOUNDED>
+__device__ __forceinline__ bool lane_load(Lane& L, const KArgs& a, const double* __restrict__ ws, int64_t stride,
                                           int64_t i) {
+  if (BOUNDED && a.resume && a.out.status[i] != PN_ST_RUNNING) return false;
   const double wf = ws[(size_t)36 * stride + i];
   if (!finite64(wf)) return false;
   L.i = i;
@@ -147,20 +151,66 @@ __device__ __forceinline__ bool lane_load(Lane& L, const Ctl& ctl, const double*
   for (int f = 0; f < 16; f++) cv[f] = ws[(size_t)f * stride + i];
   if constexpr (PREC == 1) L.cf.c32 = to_f32(L.cf.c64);
   if constexpr (PREC == 2) L.cf.cds = to_ds(L.cf.c64);
+  L.wf = wf;
+  if (BOUNDED && a.resume) {
+    const size_t rst = (size_t)a.rs_stride;
+#pragma unroll
+    for (int f = 0; f < 10; f++) {
+      L.y[f] = a.rs[f * rst + i];
+      L.k1[f] = a.rs[(10 + f) * rst + i];
+    }
+    L.t = a.rs[20 * rst + i];
+    L.h = a.rs[21 * rst + i];
+    L.h_lo = a.rs[22 * rst + i];
+    L.h_hi = a.rs[23 * rst + i];
+    L.n_acc = a.ri[0 * rst + i];
+    L.n_rej = a.ri[1 * rst + i];
+    L.n_land = a.ri[2 * rst + i];
+    L.attempts = a.ri[3 * rst + i];
+    L.land_it = a.ri[4 * rst + i];
+    const int32_t fl = a.ri[5 * rst + i];
+    L.landing = (fl & 1) != 0;
+    L.last_rej = (fl & 2) != 0;
+  } else {
+#pragma unroll
+    for (int f = 0; f < 10; f++) {
+      L.y[f] = ws[(size_t)(16 + f) * stride + i];
+      L.k1[f] = ws[(size_t)(26 + f) * stride + i];
+    }
+    L.t = 0.0;
+    L.h = a.ctl.h0;
+    L.h_lo = 0.0;
+    L.h_hi = 0.0;
+    L.n_acc = L.n_rej = L.n_land = L.attempts = L.land_it = 0;
+    L.landing = false;
+    L.last_rej = false;
+  }
+  if constexpr (BOUNDED)
+    L.stop_at = (a.budget > 0 && L.attempts <= 0x7fffffff - a.budget) ? L.attempts + a.budget : 0x7fffffff;
+  return true;
+}
+
+// Keep the state of a binary whose launch budget ran out, and report it as
+// running (its current state in the outputs).
+__device__ __forceinline__ void lane_save(const KArgs& a, const Lane& L) {
+  const size_t rst = (size_t)a.rs_stride;
+  const int64_t i = L.i;
 #pragma unroll
   for (int f = 0; f < 10; f++) {
-    L.y[f] = ws[(size_t)(16 + f) * stride + i];
-    L.k1[f] = ws[(size_t)(26 + f) * stride + i];
+    a.rs[f * rst + i] = L.y[f];
+    a.rs[(10 + f) * rst + i] = L.k1[f];
   }
-  L.t = 0.0;
-  L.h = ctl.h0;
-  L.h_lo = 0.0;
-  L.h_hi = 0.0;
-  L.wf = wf;
-  L.n_acc = L.n_rej = L.n_land = L.attempts = L.land_it = 0;
-  L.landing = false;
-  L.last_rej = false;
-  return true;
+  a.rs[20 * rst + i] = L.t;
+  a.rs[21 * rst + i] = L.h;
+  a.rs[22 * rst + i] = L.h_lo;
+  a.rs[23 * rst + i] = L.h_hi;
+  a.ri[0 * rst + i] = L.n_acc;
+  a.ri[1 * rst + i] = L.n_rej;
+  a.ri[2 * rst + i] = L.n_land;
+  a.ri[3 * rst + i] = L.attempts;
+  a.ri[4 * rst + i] = L.land_it;
+  a.ri[5 * rst + i] = (L.landing ? 1 : 0) | (L.last_rej ? 2 : 0);
+  write_result(a.out, i, L.y, L.t, L.n_acc, L.n_rej, L.n_land, PN_ST_RUNNING);
 }
 
 // Recording of the accepted steps for the adjoint: h[n * stride + i] is the
@@ -268,7 +318,10 @@ __device__ __forceinline__ bool lane_decide(Lane& L, const Ctl& ctl, double* y5,
   return false;
 }
 
-template <int PREC, bool PERSIST, bool RECORD = false>
+// BOUNDED: the launch may stop binaries at a per-launch attempt budget and may
+// resume saved ones (pn_batch_integrate_budget / pn_batch_resume); the default
+// launches are compiled without that bookkeeping.
+template <int PREC, bool PERSIST, bool RECORD = false, bool BOUNDED = false>
 __global__ void __launch_bounds__(kMaxBlock) k_integrate(const KArgs a, const double* __restrict__ ws,
                                                          int64_t stride, const RecArgs rec = RecArgs{}) {
   __shared__ double s_tab[256];
@@ -302,7 +355,7 @@ __global__ void __launch_bounds__(kMaxBlock) k_integrate(const KArgs a, const do
     }
     if (need) {
       if (idx >= 0 && idx < a.n) {
-        have = lane_load<PREC>(L, a.ctl, ws, stride, idx);
+        have = lane_load<PREC, BOUNDED>(L, a, ws, stride, idx);
         if (RECORD && have)
 #pragma unroll
           for (int c = 0; c < 10; c++) rec.ck[(size_t)c * rec.stride + idx] = L.y[c];
@@ -320,6 +373,9 @@ __global__ void __launch_bounds__(kMaxBlock) k_integrate(const KArgs a, const do
       int32_t st;
       if (lane_decide<RECORD>(L, a.ctl, y5, k7, s, &st, rec)) {
         write_result(a.out, L.i, L.y, L.t, L.n_acc, L.n_rej, L.n_land, st);
+        have = false;
+      } else if (BOUNDED && L.attempts >= L.stop_at) {
+        lane_save(a, L);
         have = false;
       }
     }
@@ -363,8 +419,27 @@ cudaError_t launch_integrate(int prec, bool persistent, int block, int grid, con
   return launch_dots(a.out, a.n, s);
 }
 
+template <bool BOUNDED>
+static void launch_integrate_variant(int prec, bool persistent, int block, int grid, const KArgs& a,
+                                     const double* ws, int64_t stride, cudaStream_t s) {
+  if (prec == PN_MIXED) {
+    if (persistent) k_integrate<1, true, false, BOUNDED><<<grid, block, 0, s>>>(a, ws, stride);
+    else k_integrate<1, false, false, BOUNDED><<<grid, block, 0, s>>>(a, ws, stride);
+  } else if (prec == PN_MIXED_DS) {
+    if (persistent) k_integrate<2, true, false, BOUNDED><<<grid, block, 0, s>>>(a, ws, stride);
+    else k_integrate<2, false, false, BOUNDED><<<grid, block, 0, s>>>(a, ws, stride);
+  } else {
+    if (persistent) k_integrate<0, true, false, BOUNDED><<<grid, block, 0, s>>>(a, ws, stride);
+    else k_integrate<0, false, false, BOUNDED><<<grid, block, 0, s>>>(a, ws, stride);
+  }
+}
+
 cudaError_t launch_integrate_only(int prec, bool persistent, int block, int grid, const KArgs& a, const double* ws,
                                   int64_t stride, cudaStream_t s) {
+  if (a.budget > 0 || a.resume) {
+    launch_integrate_variant<true>(prec, persistent, block, grid, a, ws, stride, s);
+    return cudaGetLastError();
+  }
   if (prec == PN_MIXED) {
     if (persistent) k_integrate<1, true><<<grid, block, 0, s>>>(a, ws, stride);
     else k_integrate<1, false><<<grid, block, 0, s>>>(a, ws, stride);
