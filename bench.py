@@ -297,6 +297,8 @@ def main():
         b.set_params(pn.params(**prec_params, **fixed))
         return dict(fixed)
 
+    nvtx = torch.cuda.nvtx  # phase ranges for profilers
+    nvtx.range_push("fp64 headline")
     # FP64 headline.
     prm = pn.params(precision=0)
     with pn.Batch(n, prm) as b:
@@ -353,6 +355,8 @@ def main():
                 "block": tn["block"], "fp64_pipe_achieved_tflops": (FLOPS_STEP * m_attempts) /
                 (mix_ms / args.steps * 1e-3) / 1e12}
 
+    nvtx.range_pop()
+    nvtx.range_push("mixed precision")
     mixed = mixed_ds = None
     if not args.no_mixed:
         mixed = mixed_run(1)
@@ -360,6 +364,8 @@ def main():
         mixed_ds = mixed_run(2)
         mixed_ds["rhs"] = "double-single (pairs of FP32) on the FP32 pipe"
 
+    nvtx.range_pop()
+    nvtx.range_push("end to end")
     # End to end through the host-buffer entry point (pinned host memory).
     e2e = None
     if not args.no_e2e:
@@ -378,6 +384,8 @@ def main():
         e2e = {"value": aggregate_rate(world, n, args.steps, e2e_s * 1e3), "unit": "inspirals/s",
                "h2d_bytes_per_step": 15 * 8 * n, "d2h_bytes_per_step": (14 * 8 + 4 * 4) * n}
 
+    nvtx.range_pop()
+    nvtx.range_push("extras")
     # Extras: the uneven-length ensemble (persistent vs plain schedule) and the adjoint.
     extras = None
     if not args.no_extras:
@@ -441,6 +449,7 @@ def main():
                                 "workload": "65,536 binaries, q ~ U[1,4], chi = 1, omega 0.01 -> 0.05; "
                                             "d(S1-hat.S2-hat final)/d(S1-hat, S2-hat, q), checkpoint every 64"}
 
+    nvtx.range_pop()
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         rate, m, threads, dt = cpu_oracle_rate(ens, target_s=10.0)
