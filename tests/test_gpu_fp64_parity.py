@@ -266,3 +266,46 @@ def test_stats_match_numpy(pn):
     assert abs(st["pearson_s1s2"] - np.corrcoef(x0, g["dot_s1s2"])[0, 1]) < 1e-10
     assert abs(st["pearson_s1s2"] - 0.99) < 0.01  # Sec. V A prints r = 0.99
     assert st["ms_last_integrate"] > 0
+
+
+def test_degenerate_configurations(pn, orc):
+    """The method's special cases, FP64 against the oracle, and the properties that hold exactly (also in
+    both mixed precisions): zero spins (L-hat stays z, dots NaN), spins along L-hat (aligned or
+    anti-aligned: nothing precesses), one spin zero, q = 10, omega_f barely above omega0 (the first step
+    already crosses), and a tiny spin (1e-12)."""
+    n = 6 * 32
+    ens = workloads.config("C2", n=n, seed=4711)
+    blocks = np.arange(n) // 32
+    z = np.array([0.0, 0.0, 1.0])
+    zero = blocks == 0
+    ens["chi1"][zero] = 0.0
+    ens["chi2"][zero] = 0.0
+    aligned = blocks == 1
+    sign = np.where(np.arange(n) % 2 == 0, 1.0, -1.0)
+    ens["s1hat"][:, aligned] = z[:, None] * sign[aligned]
+    ens["s2hat"][:, aligned] = -z[:, None] * sign[aligned]
+    one_zero = blocks == 2
+    ens["chi2"][one_zero] = 0.0
+    q10 = blocks == 3
+    ens["m1"][q10], ens["m2"][q10] = 10.0 / 11.0, 1.0 / 11.0
+    short = blocks == 4
+    ens["omega_f"][short] = ens["omega0"][short] * (1 + 1e-5)
+    tiny = blocks == 5
+    ens["chi1"][tiny] = 1e-12
+    o = orc.integrate(ens)
+    g = run_gpu(pn, ens)
+    assert np.all(o["status"] == 0)
+    assert_fp64_parity(g, o)
+    # exact properties on the GPU side
+    assert np.all(g["Lhat"][:, zero] == z[:, None]) and np.all(g["S1"][:, zero] == 0.0)
+    assert np.all(np.isnan(g["dot_s1s2"][zero])) and np.all(np.isnan(g["dot_ls1"][one_zero | zero]) == zero[one_zero | zero])
+    assert np.all(np.isnan(g["dot_ls2"][one_zero]))
+    assert np.all(g["Lhat"][:, aligned] == z[:, None])
+    assert np.allclose(g["dot_s1s2"][aligned], -1.0, rtol=0, atol=1e-15)
+    assert np.all(g["n_acc"][short] == 1) and np.allclose(g["omega"][short], ens["omega_f"][short], rtol=1e-12)
+    assert np.all(np.isfinite(g["dot_s1s2"][tiny]))
+    for precision in (1, 2):
+        m = run_gpu(pn, ens, precision=precision)
+        assert np.all(m["status"] == 0)
+        assert np.all(m["Lhat"][:, zero | aligned] == z[:, None]) and np.all(m["S1"][:, zero] == 0.0)
+        assert np.all(m["n_acc"][short] == 1)
