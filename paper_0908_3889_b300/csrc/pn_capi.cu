@@ -228,6 +228,7 @@ extern "C" int pn_batch_init(pn_batch** out, int64_t n_max, const pn_params* p, 
   b->stream = (cudaStream_t)cuda_stream;
   cudaError_t e = cudaGetDevice(&b->device);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&b->num_sms, cudaDevAttrMultiProcessorCount, b->device);
+  if (e == cudaSuccess) e = pn::prepare_integrate_kernels();
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking);
   if (e == cudaSuccess) e = cudaMalloc(&b->d_queue, sizeof(unsigned long long));
   if (e == cudaSuccess) e = cudaMalloc(&b->d_tab, pn::kLogTabBytes);

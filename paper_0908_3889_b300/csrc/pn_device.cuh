@@ -692,77 +692,130 @@ __device__ __forceinline__ double dp5_attempt_f32(const Coef<float>& c, const Ct
   return sum * 0.1;
 }
 
-// Stage tableau for the rolled attempt: row r is stage s = r + 2; entry 0 is
-// the coefficient of k1, entry 1 + m the coefficient of the rate computed m + 1
-// stages earlier (k_{s-1-m}); the last row is b (first same as last).  Stage s
-// uses s - 2 earlier rates (the k2 weight of b is 0, so stage 7 uses 4).
-__constant__ double c_dp_rows[6][6] = {
-    {DP_A21, 0, 0, 0, 0, 0},
-    {DP_A31, DP_A32, 0, 0, 0, 0},
-    {DP_A41, DP_A43, DP_A42, 0, 0, 0},
-    {DP_A51, DP_A54, DP_A53, DP_A52, 0, 0},
-    {DP_A61, DP_A65, DP_A64, DP_A63, DP_A62, 0},
-    {DP_B1, DP_B6, DP_B5, DP_B4, DP_B3, 0},
+// ---------------------------------------------------------------------------
+// The double-single attempt.  Its stage inputs feed the double-single
+// right-hand side and so need ~48-bit accuracy: they are formed on the FP32
+// pipe by compensated sums (Dot2 of Ogita, Rump & Oishi 2005) of double-single
+// rates, not by FP64 sums.  The state accumulation y5 = y + h sum_j b_j k_j, the
+// error norm and the step control stay FP64.  The rates and stage vectors live
+// in a per-thread shared-memory workspace so that the loops over the ten
+// components can stay rolled: with them unrolled (or with the vectors in
+// registers) the stage loop no longer fits the instruction cache.
+// ---------------------------------------------------------------------------
+struct dsc {  // a double-single constant: hi the nearest float, lo the nearest float to the rest
+  float hi, lo;
+};
+#define PN_DSC(x) {(float)(x), (float)((x) - (double)(float)(x))}
+// Row r: coefficients of k1..k_{r+1} for stage r + 2; row 5 is b (first same as last).
+__constant__ dsc c_dp_a_ds[6][6] = {
+    {PN_DSC(DP_A21), {0, 0}, {0, 0}, {0, 0}, {0, 0}, {0, 0}},
+    {PN_DSC(DP_A31), PN_DSC(DP_A32), {0, 0}, {0, 0}, {0, 0}, {0, 0}},
+    {PN_DSC(DP_A41), PN_DSC(DP_A42), PN_DSC(DP_A43), {0, 0}, {0, 0}, {0, 0}},
+    {PN_DSC(DP_A51), PN_DSC(DP_A52), PN_DSC(DP_A53), PN_DSC(DP_A54), {0, 0}, {0, 0}},
+    {PN_DSC(DP_A61), PN_DSC(DP_A62), PN_DSC(DP_A63), PN_DSC(DP_A64), PN_DSC(DP_A65), {0, 0}},
+    {PN_DSC(DP_B1), {0, 0}, PN_DSC(DP_B3), PN_DSC(DP_B4), PN_DSC(DP_B5), PN_DSC(DP_B6)},
+};
+// b - bhat for k1, k3, k4, k5, k6, k7 (the k2 weight is 0).
+__constant__ dsc c_dp_e_ds[6] = {PN_DSC(DP_E1), PN_DSC(DP_E3), PN_DSC(DP_E4),
+                                 PN_DSC(DP_E5), PN_DSC(DP_E6), PN_DSC(DP_E7)};
+#undef PN_DSC
+
+// Compensated sum of products c_j x_j: s collects the rounded leading products
+// exactly through two_sum, e the rounding errors of those sums, the products'
+// own errors and the cross terms c.hi x.lo + c.lo x.hi.  dot_val(s, e) carries
+// ~2^-48 relative error unless the sum cancels.
+struct dacc {
+  float s, e;
+};
+__device__ __forceinline__ dacc dot_first(dsc c, ds x) {
+  const float p = __fmul_rn(c.hi, x.hi);
+  float e = __fmaf_rn(c.hi, x.hi, -p);
+  e = __fmaf_rn(c.hi, x.lo, e);
+  e = __fmaf_rn(c.lo, x.hi, e);
+  return dacc{p, e};
+}
+__device__ __forceinline__ dacc dot_add(dacc a, dsc c, ds x) {
+  const float p = __fmul_rn(c.hi, x.hi);
+  float e = __fmaf_rn(c.hi, x.hi, -p);
+  e = __fmaf_rn(c.hi, x.lo, e);
+  e = __fmaf_rn(c.lo, x.hi, e);
+  const ds t = two_sum(a.s, p);
+  return dacc{t.hi, __fadd_rn(a.e, __fadd_rn(t.lo, e))};
+}
+__device__ __forceinline__ ds dot_val(dacc a) { return two_sum(a.s, a.e); }
+
+// Per-thread workspace of dp5_attempt_ds in shared memory, lane-interleaved so
+// that a warp's accesses are 32 consecutive 8-byte words: vector v, component
+// c of thread t at base[(v * 10 + c) * nthreads + t].  Vectors 0..5 hold the
+// rates k1..k6, 6 the state split into pairs (then the increment of y5), 7 the
+// stage input (then k7); the error estimate goes to vector 1 once k2 is no
+// longer needed (its weight in b and in b - bhat is 0).
+constexpr int kDsVectors = 8;
+constexpr int kDsWorkBytes = kDsVectors * 10 * 8;  // per thread
+struct DsWork {
+  float2* base;
+  int nt, t;
+  __device__ __forceinline__ ds get(int v, int c) const {
+    const float2 x = base[(v * 10 + c) * nt + t];
+    return ds{x.x, x.y};
+  }
+  __device__ __forceinline__ void put(int v, int c, ds a) const { base[(v * 10 + c) * nt + t] = make_float2(a.hi, a.lo); }
 };
 
-// The same attempt as dp5_attempt with the six stages rolled into one loop, so
-// the right-hand side is emitted once: the double-single right-hand side is
-// large enough that six inlined copies overflow the instruction cache.  The
-// earlier rates sit in a register queue q (q[0] newest), shifted after each
-// stage; each stage adds only its non-zero terms (a uniform branch).
-template <int PREC>
-__device__ __forceinline__ double dp5_attempt_rolled(const Coefs& cf, const Tabs& tb, const Ctl& ctl, const double* y,
-                                                     const double* k1, double h, double* y5, double* k7) {
-  double q[5][10], ys[10], kn[10];
+__device__ __forceinline__ double dp5_attempt_ds(const Coefs& cf, const Tabs& tb, const Ctl& ctl, const double* y,
+                                                 const double* k1, double h, double* y5, double* k7,
+                                                 const DsWork& w) {
+  const ds hd = split64(h);
+#pragma unroll
+  for (int c = 0; c < 10; c++) {
+    w.put(6, c, split64(y[c]));
+    w.put(0, c, split64(k1[c]));
+  }
+  ds kn[10];
 #pragma unroll 1
   for (int r = 0; r < 6; r++) {
-    const double c0 = h * c_dp_rows[r][0];
-#pragma unroll
-    for (int i = 0; i < 10; i++) ys[i] = fma(c0, k1[i], y[i]);
-    const int nt = (r < 5) ? r : 4;
-    if (nt > 0) {
-      const double c = h * c_dp_rows[r][1];
-#pragma unroll
-      for (int i = 0; i < 10; i++) ys[i] = fma(c, q[0][i], ys[i]);
-      if (nt > 1) {
-        const double c2 = h * c_dp_rows[r][2];
-#pragma unroll
-        for (int i = 0; i < 10; i++) ys[i] = fma(c2, q[1][i], ys[i]);
-        if (nt > 2) {
-          const double c3 = h * c_dp_rows[r][3];
-#pragma unroll
-          for (int i = 0; i < 10; i++) ys[i] = fma(c3, q[2][i], ys[i]);
-          if (nt > 3) {
-            const double c4 = h * c_dp_rows[r][4];
-#pragma unroll
-            for (int i = 0; i < 10; i++) ys[i] = fma(c4, q[3][i], ys[i]);
-          }
-        }
-      }
+    const dsc a0 = c_dp_a_ds[r][0], a1 = c_dp_a_ds[r][1], a2 = c_dp_a_ds[r][2], a3 = c_dp_a_ds[r][3],
+              a4 = c_dp_a_ds[r][4], a5 = c_dp_a_ds[r][5];
+#pragma unroll 2
+    for (int c = 0; c < 10; c++) {
+      dacc acc = dot_first(a0, w.get(0, c));
+      if (r >= 1 && r < 5) acc = dot_add(acc, a1, w.get(1, c));  // b2 = 0
+      if (r >= 2) acc = dot_add(acc, a2, w.get(2, c));
+      if (r >= 3) acc = dot_add(acc, a3, w.get(3, c));
+      if (r >= 4) acc = dot_add(acc, a4, w.get(4, c));
+      if (r >= 5) acc = dot_add(acc, a5, w.get(5, c));
+      const ds inc = ds_mul(hd, dot_val(acc));  // h sum_j a_sj k_j
+      w.put(7, c, ds_add(w.get(6, c), inc));
+      if (r == 5) w.put(6, c, inc);
     }
-    eval_rhs<PREC>(cf, tb, ys, kn);
-    if (r < 5) {
+    ds yin[10];
 #pragma unroll
-      for (int i = 0; i < 10; i++) {
-        q[4][i] = q[3][i];
-        q[3][i] = q[2][i];
-        q[2][i] = q[1][i];
-        q[1][i] = q[0][i];
-        q[0][i] = kn[i];
-      }
-    }
+    for (int c = 0; c < 10; c++) yin[c] = w.get(7, c);
+    rhs_ds(cf.cds, tb.f, yin, kn);  // k_{r+2}; for r = 5, k7 at the double-single y5
+    const int slot = (r < 5) ? r + 1 : 7;
+#pragma unroll
+    for (int c = 0; c < 10; c++) w.put(slot, c, kn[c]);
   }
-  // q holds k6, k5, k4, k3, k2; ys is y5 and kn is k7.
-  const double e1 = h * DP_E1, e3 = h * DP_E3, e4 = h * DP_E4, e5 = h * DP_E5, e6 = h * DP_E6, e7 = h * DP_E7;
+#pragma unroll 2
+  for (int c = 0; c < 10; c++) {  // embedded error estimate h sum_j (b_j - bhat_j) k_j
+    dacc acc = dot_first(c_dp_e_ds[0], w.get(0, c));
+    acc = dot_add(acc, c_dp_e_ds[1], w.get(2, c));
+    acc = dot_add(acc, c_dp_e_ds[2], w.get(3, c));
+    acc = dot_add(acc, c_dp_e_ds[3], w.get(4, c));
+    acc = dot_add(acc, c_dp_e_ds[4], w.get(5, c));
+    acc = dot_add(acc, c_dp_e_ds[5], w.get(7, c));
+    w.put(1, c, ds_mul(hd, dot_val(acc)));
+  }
   double sum = 0.0;
 #pragma unroll
-  for (int i = 0; i < 10; i++) {
-    y5[i] = ys[i];
-    k7[i] = kn[i];
-    const double e = fma(e7, kn[i], fma(e6, q[0][i], fma(e5, q[1][i], fma(e4, q[2][i], fma(e3, q[3][i], e1 * k1[i])))));
-    const double sc = fma(ctl.rtol, max_abs(y[i], ys[i]), ctl.atol);
-    const double qq = e * rcp_pos(sc);
-    sum = fma(qq, qq, sum);
+  for (int c = 0; c < 10; c++) {
+    const ds inc = w.get(6, c);
+    y5[c] = y[c] + (f32_to_f64(inc.hi) + f32_to_f64(inc.lo));
+    k7[c] = ds_to_f64(kn[c]);
+    const double e = ds_to_f64(w.get(1, c));
+    const double sc = fma(ctl.rtol, max_abs(y[c], y5[c]), ctl.atol);
+    const double q = e * rcp_pos(sc);
+    sum = fma(q, q, sum);
   }
   return sum * 0.1;
 }

@@ -80,6 +80,9 @@ cudaError_t launch_integrate(int prec, bool persistent, int block, int grid, con
 cudaError_t launch_integrate_only(int prec, bool persistent, int block, int grid, const KArgs& a, const double* ws,
                                   int64_t stride, cudaStream_t s);
 // Resident blocks per SM of that kernel at this block size.
+// Allows the double-single integration kernels their shared-memory workspace
+// (call once per device before launching them).
+cudaError_t prepare_integrate_kernels();
 cudaError_t integrate_occupancy(int prec, bool persistent, int block, int* blocks_per_sm);
 
 cudaError_t launch_sample(uint64_t seed, const pn_dist& d, int64_t n, const pn_inputs& in, cudaStream_t s);

@@ -321,11 +321,12 @@ __device__ __forceinline__ bool lane_decide(Lane& L, const Ctl& ctl, double* y5,
 // BOUNDED: the launch may stop binaries at a per-launch attempt budget and may
 // resume saved ones (pn_batch_integrate_budget / pn_batch_resume); the default
 // launches are compiled without that bookkeeping.
-template <int PREC, bool PERSIST, bool RECORD = false, bool BOUNDED = false>
-__global__ void __launch_bounds__(kMaxBlock) k_integrate(const KArgs a, const double* __restrict__ ws,
-                                                         int64_t stride, const RecArgs rec = RecArgs{}) {
+template <int PREC, bool PERSIST, bool RECORD, bool BOUNDED>
+__device__ __forceinline__ void integrate_body(const KArgs& a, const double* __restrict__ ws, int64_t stride,
+                                               const RecArgs& rec) {
   __shared__ double s_tab[256];
   __shared__ float s_tabf[512];
+  extern __shared__ float2 s_dsw[];  // double-single workspace (PREC 2: kDsWorkBytes per thread)
   const Tabs tb = load_tabs<PREC>(a.tab, s_tab, s_tabf);
 
   const unsigned lane = threadIdx.x & 31u;
@@ -366,7 +367,9 @@ __global__ void __launch_bounds__(kMaxBlock) k_integrate(const KArgs a, const do
     if (have) {
       double y5[10], k7[10];
       double s;
-      if constexpr (PREC == 2) s = dp5_attempt_rolled<PREC>(L.cf, tb, a.ctl, L.y, L.k1, L.h, y5, k7);
+      if constexpr (PREC == 2)
+        s = dp5_attempt_ds(L.cf, tb, a.ctl, L.y, L.k1, L.h, y5, k7,
+                           DsWork{s_dsw, (int)blockDim.x, (int)threadIdx.x});
       else if constexpr (PREC == 1) s = dp5_attempt_f32(L.cf.c32, a.ctl, L.y, L.k1, L.h, y5, k7);
       else s = dp5_attempt<PREC>(L.cf, tb, a.ctl, L.y, L.k1, L.h, y5, k7);
       L.attempts++;
@@ -382,9 +385,25 @@ __global__ void __launch_bounds__(kMaxBlock) k_integrate(const KArgs a, const do
   }
 }
 
+template <int PREC, bool PERSIST, bool RECORD = false, bool BOUNDED = false>
+__global__ void __launch_bounds__(kMaxBlock) k_integrate(const KArgs a, const double* __restrict__ ws, int64_t stride,
+                                                         const RecArgs rec = RecArgs{}) {
+  integrate_body<PREC, PERSIST, RECORD, BOUNDED>(a, ws, stride, rec);
+}
+
+// The double-single kernel, held to 168 registers: with its rates in shared
+// memory that fits three warps per scheduler (10 warps/SM with 64-thread blocks).
+template <bool PERSIST, bool BOUNDED = false>
+__global__ void __maxnreg__(168) k_integrate_ds(const KArgs a,
+                                                                             const double* __restrict__ ws,
+                                                                             int64_t stride) {
+  integrate_body<2, PERSIST, false, BOUNDED>(a, ws, stride, RecArgs{});
+}
+
 template <int PREC, bool PERSIST>
 static const void* integrate_fn() {
-  return (const void*)k_integrate<PREC, PERSIST>;
+  if constexpr (PREC == 2) return (const void*)k_integrate_ds<PERSIST>;
+  else return (const void*)k_integrate<PREC, PERSIST>;
 }
 
 static const void* pick(int prec, bool persistent) {
@@ -419,15 +438,32 @@ cudaError_t launch_integrate(int prec, bool persistent, int block, int grid, con
   return launch_dots(a.out, a.n, s);
 }
 
+// Dynamic shared memory of an integration launch: the double-single workspace.
+static size_t integrate_smem(int prec, int block) {
+  return prec == PN_MIXED_DS ? (size_t)kDsWorkBytes * (size_t)block : 0;
+}
+
+cudaError_t prepare_integrate_kernels() {
+  const int bytes = kDsWorkBytes * kMaxBlock;
+  const void* fns[4] = {(const void*)k_integrate_ds<true>, (const void*)k_integrate_ds<false>,
+                        (const void*)k_integrate_ds<true, true>, (const void*)k_integrate_ds<false, true>};
+  for (const void* f : fns) {
+    const cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
 template <bool BOUNDED>
 static void launch_integrate_variant(int prec, bool persistent, int block, int grid, const KArgs& a,
                                      const double* ws, int64_t stride, cudaStream_t s) {
+  const size_t sm = integrate_smem(prec, block);
   if (prec == PN_MIXED) {
     if (persistent) k_integrate<1, true, false, BOUNDED><<<grid, block, 0, s>>>(a, ws, stride);
     else k_integrate<1, false, false, BOUNDED><<<grid, block, 0, s>>>(a, ws, stride);
   } else if (prec == PN_MIXED_DS) {
-    if (persistent) k_integrate<2, true, false, BOUNDED><<<grid, block, 0, s>>>(a, ws, stride);
-    else k_integrate<2, false, false, BOUNDED><<<grid, block, 0, s>>>(a, ws, stride);
+    if (persistent) k_integrate_ds<true, BOUNDED><<<grid, block, sm, s>>>(a, ws, stride);
+    else k_integrate_ds<false, BOUNDED><<<grid, block, sm, s>>>(a, ws, stride);
   } else {
     if (persistent) k_integrate<0, true, false, BOUNDED><<<grid, block, 0, s>>>(a, ws, stride);
     else k_integrate<0, false, false, BOUNDED><<<grid, block, 0, s>>>(a, ws, stride);
@@ -444,8 +480,9 @@ cudaError_t launch_integrate_only(int prec, bool persistent, int block, int grid
     if (persistent) k_integrate<1, true><<<grid, block, 0, s>>>(a, ws, stride);
     else k_integrate<1, false><<<grid, block, 0, s>>>(a, ws, stride);
   } else if (prec == PN_MIXED_DS) {
-    if (persistent) k_integrate<2, true><<<grid, block, 0, s>>>(a, ws, stride);
-    else k_integrate<2, false><<<grid, block, 0, s>>>(a, ws, stride);
+    const size_t sm = integrate_smem(prec, block);
+    if (persistent) k_integrate_ds<true><<<grid, block, sm, s>>>(a, ws, stride);
+    else k_integrate_ds<false><<<grid, block, sm, s>>>(a, ws, stride);
   } else {
     if (persistent) k_integrate<0, true><<<grid, block, 0, s>>>(a, ws, stride);
     else k_integrate<0, false><<<grid, block, 0, s>>>(a, ws, stride);
@@ -454,7 +491,8 @@ cudaError_t launch_integrate_only(int prec, bool persistent, int block, int grid
 }
 
 cudaError_t integrate_occupancy(int prec, bool persistent, int block, int* blocks_per_sm) {
-  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, pick(prec, persistent), block, 0);
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, pick(prec, persistent), block,
+                                                       integrate_smem(prec, block));
 }
 
 cudaError_t launch_integrate_record(const KArgs& a, const double* ws, int64_t stride, const RecArgs& rec, int block,

@@ -92,7 +92,8 @@ extern "C" int pn_integrate_noalloc(int64_t n, const pn_params* p, const pn_inpu
   double* table = (double*)(base + kSetupOff);
 
   int dev = 0, sms = 0, per_sm = 0;
-  cudaError_t e = cudaGetDevice(&dev);
+  cudaError_t e = pn::prepare_integrate_kernels();
+  if (e == cudaSuccess) e = cudaGetDevice(&dev);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   const int block = 128;
   if (e == cudaSuccess) e = pn::integrate_occupancy(p->precision, true, block, &per_sm);
