@@ -626,65 +626,74 @@ __device__ __forceinline__ double dp5_attempt(const Coefs& cf, const Tabs& tb, c
 // entry, so they are formed in FP32 from the FP32-rounded state; the new state
 // y5 = y + h sum_j b_j k_j (the state accumulation), the embedded error
 // estimate, its norm and the step control are FP64, with the FP32 rates widened
-// exactly.  Conversions between the two formats are integer operations.
+// exactly.  Conversions between the two formats are integer operations.  The
+// six stages run as one loop so that the right-hand side is emitted once
+// (seven inlined copies overflow the instruction cache); the rates k1..k6 sit
+// in a per-thread shared-memory workspace (lane-interleaved: rate j, component
+// c of thread t at base[(j * 10 + c) * nthreads + t]) so no register queue has
+// to be shifted between stages.
+constexpr int kF32WorkBytes = 6 * 10 * 4;  // per thread
+struct F32Work {
+  float* base;
+  int nt, t;
+  __device__ __forceinline__ float get(int j, int c) const { return base[(j * 10 + c) * nt + t]; }
+  __device__ __forceinline__ void put(int j, int c, float v) const { base[(j * 10 + c) * nt + t] = v; }
+};
+// Rows of the stage tableau in FP32: coefficients of k1..k_{r+1} for stage r + 2.
+__constant__ float c_dp_a_f[5][5] = {
+    {(float)DP_A21, 0, 0, 0, 0},
+    {(float)DP_A31, (float)DP_A32, 0, 0, 0},
+    {(float)DP_A41, (float)DP_A42, (float)DP_A43, 0, 0},
+    {(float)DP_A51, (float)DP_A52, (float)DP_A53, (float)DP_A54, 0},
+    {(float)DP_A61, (float)DP_A62, (float)DP_A63, (float)DP_A64, (float)DP_A65},
+};
+
 __device__ __forceinline__ double dp5_attempt_f32(const Coef<float>& c, const Ctl& ctl, const double* y,
-                                                  const double* k1, double h, double* y5, double* k7) {
-  float yf[10], f1[10], f2[10], f3[10], f4[10], f5[10], f6[10], f7[10], ys[10];
+                                                  const double* k1, double h, double* y5, double* k7,
+                                                  const F32Work& w) {
+  float yf[10], ys[10], kn[10];
   const float hf = f64_to_f32(h);
 #pragma unroll
   for (int i = 0; i < 10; i++) {
     yf[i] = f64_to_f32(y[i]);
-    f1[i] = f64_to_f32(k1[i]);  // k1 is an FP32 rate widened: exact
+    w.put(0, i, f64_to_f32(k1[i]));  // k1 is an FP32 rate widened: exact
   }
-  {
-    const float a1 = hf * (float)DP_A21;
+#pragma unroll 1
+  for (int r = 0; r < 6; r++) {
+    if (r < 5) {
+      const float a0 = hf * c_dp_a_f[r][0], a1 = hf * c_dp_a_f[r][1], a2 = hf * c_dp_a_f[r][2],
+                  a3 = hf * c_dp_a_f[r][3], a4 = hf * c_dp_a_f[r][4];
 #pragma unroll
-    for (int i = 0; i < 10; i++) ys[i] = fmaf(a1, f1[i], yf[i]);
-  }
-  rhs32(c, ys, f2);
-  {
-    const float a1 = hf * (float)DP_A31, a2 = hf * (float)DP_A32;
+      for (int i = 0; i < 10; i++) {
+        float acc = fmaf(a0, w.get(0, i), yf[i]);
+        if (r >= 1) acc = fmaf(a1, w.get(1, i), acc);
+        if (r >= 2) acc = fmaf(a2, w.get(2, i), acc);
+        if (r >= 3) acc = fmaf(a3, w.get(3, i), acc);
+        if (r >= 4) acc = fmaf(a4, w.get(4, i), acc);
+        ys[i] = acc;
+      }
+    } else {  // the 5th-order solution, accumulated in FP64
+      const double b1 = h * DP_B1, b3 = h * DP_B3, b4 = h * DP_B4, b5 = h * DP_B5, b6 = h * DP_B6;
 #pragma unroll
-    for (int i = 0; i < 10; i++) ys[i] = fmaf(a2, f2[i], fmaf(a1, f1[i], yf[i]));
-  }
-  rhs32(c, ys, f3);
-  {
-    const float a1 = hf * (float)DP_A41, a2 = hf * (float)DP_A42, a3 = hf * (float)DP_A43;
+      for (int i = 0; i < 10; i++) {
+        y5[i] = fma(b6, f32_to_f64(w.get(5, i)), fma(b5, f32_to_f64(w.get(4, i)), fma(b4, f32_to_f64(w.get(3, i)),
+                fma(b3, f32_to_f64(w.get(2, i)), fma(b1, k1[i], y[i])))));
+        ys[i] = f64_to_f32(y5[i]);
+      }
+    }
+    rhs32(c, ys, kn);  // k_{r+2}; for r = 5, k7 = f(y5)
+    if (r < 5) {
 #pragma unroll
-    for (int i = 0; i < 10; i++) ys[i] = fmaf(a3, f3[i], fmaf(a2, f2[i], fmaf(a1, f1[i], yf[i])));
-  }
-  rhs32(c, ys, f4);
-  {
-    const float a1 = hf * (float)DP_A51, a2 = hf * (float)DP_A52, a3 = hf * (float)DP_A53, a4 = hf * (float)DP_A54;
-#pragma unroll
-    for (int i = 0; i < 10; i++) ys[i] = fmaf(a4, f4[i], fmaf(a3, f3[i], fmaf(a2, f2[i], fmaf(a1, f1[i], yf[i]))));
-  }
-  rhs32(c, ys, f5);
-  {
-    const float a1 = hf * (float)DP_A61, a2 = hf * (float)DP_A62, a3 = hf * (float)DP_A63, a4 = hf * (float)DP_A64,
-                a5 = hf * (float)DP_A65;
-#pragma unroll
-    for (int i = 0; i < 10; i++)
-      ys[i] = fmaf(a5, f5[i], fmaf(a4, f4[i], fmaf(a3, f3[i], fmaf(a2, f2[i], fmaf(a1, f1[i], yf[i])))));
-  }
-  rhs32(c, ys, f6);
-  {
-    const double b1 = h * DP_B1, b3 = h * DP_B3, b4 = h * DP_B4, b5 = h * DP_B5, b6 = h * DP_B6;
-#pragma unroll
-    for (int i = 0; i < 10; i++) {
-      y5[i] = fma(b6, f32_to_f64(f6[i]), fma(b5, f32_to_f64(f5[i]), fma(b4, f32_to_f64(f4[i]),
-              fma(b3, f32_to_f64(f3[i]), fma(b1, k1[i], y[i])))));
-      ys[i] = f64_to_f32(y5[i]);
+      for (int i = 0; i < 10; i++) w.put(r + 1, i, kn[i]);
     }
   }
-  rhs32(c, ys, f7);
   const double e1 = h * DP_E1, e3 = h * DP_E3, e4 = h * DP_E4, e5 = h * DP_E5, e6 = h * DP_E6, e7 = h * DP_E7;
   double sum = 0.0;
 #pragma unroll
   for (int i = 0; i < 10; i++) {
-    k7[i] = f32_to_f64(f7[i]);
-    const double e = fma(e7, k7[i], fma(e6, f32_to_f64(f6[i]), fma(e5, f32_to_f64(f5[i]), fma(e4, f32_to_f64(f4[i]),
-                     fma(e3, f32_to_f64(f3[i]), e1 * k1[i])))));
+    k7[i] = f32_to_f64(kn[i]);
+    const double e = fma(e7, k7[i], fma(e6, f32_to_f64(w.get(5, i)), fma(e5, f32_to_f64(w.get(4, i)),
+                     fma(e4, f32_to_f64(w.get(3, i)), fma(e3, f32_to_f64(w.get(2, i)), e1 * k1[i])))));
     const double sc = fma(ctl.rtol, max_abs(y[i], y5[i]), ctl.atol);
     const double q = e * rcp_pos(sc);
     sum = fma(q, q, sum);

@@ -326,7 +326,7 @@ __device__ __forceinline__ void integrate_body(const KArgs& a, const double* __r
                                                const RecArgs& rec) {
   __shared__ double s_tab[256];
   __shared__ float s_tabf[512];
-  extern __shared__ float2 s_dsw[];  // double-single workspace (PREC 2: kDsWorkBytes per thread)
+  extern __shared__ float2 s_dsw[];  // per-thread stage workspace (PREC 1: kF32WorkBytes, PREC 2: kDsWorkBytes)
   const Tabs tb = load_tabs<PREC>(a.tab, s_tab, s_tabf);
 
   const unsigned lane = threadIdx.x & 31u;
@@ -370,7 +370,9 @@ __device__ __forceinline__ void integrate_body(const KArgs& a, const double* __r
       if constexpr (PREC == 2)
         s = dp5_attempt_ds(L.cf, tb, a.ctl, L.y, L.k1, L.h, y5, k7,
                            DsWork{s_dsw, (int)blockDim.x, (int)threadIdx.x});
-      else if constexpr (PREC == 1) s = dp5_attempt_f32(L.cf.c32, a.ctl, L.y, L.k1, L.h, y5, k7);
+      else if constexpr (PREC == 1)
+        s = dp5_attempt_f32(L.cf.c32, a.ctl, L.y, L.k1, L.h, y5, k7,
+                            F32Work{reinterpret_cast<float*>(s_dsw), (int)blockDim.x, (int)threadIdx.x});
       else s = dp5_attempt<PREC>(L.cf, tb, a.ctl, L.y, L.k1, L.h, y5, k7);
       L.attempts++;
       int32_t st;
@@ -391,18 +393,17 @@ __global__ void __launch_bounds__(kMaxBlock) k_integrate(const KArgs a, const do
   integrate_body<PREC, PERSIST, RECORD, BOUNDED>(a, ws, stride, rec);
 }
 
-// The double-single kernel, held to 168 registers: with its rates in shared
-// memory that fits three warps per scheduler (10 warps/SM with 64-thread blocks).
-template <bool PERSIST, bool BOUNDED = false>
-__global__ void __maxnreg__(168) k_integrate_ds(const KArgs a,
-                                                                             const double* __restrict__ ws,
-                                                                             int64_t stride) {
-  integrate_body<2, PERSIST, false, BOUNDED>(a, ws, stride, RecArgs{});
+// The two mixed-precision kernels (PREC 1: FP32 right-hand side, PREC 2:
+// double-single), held to 168 registers: with their rates in shared memory
+// that fits three warps per scheduler.
+template <int PREC, bool PERSIST, bool BOUNDED = false>
+__global__ void __maxnreg__(168) k_integrate_mx(const KArgs a, const double* __restrict__ ws, int64_t stride) {
+  integrate_body<PREC, PERSIST, false, BOUNDED>(a, ws, stride, RecArgs{});
 }
 
 template <int PREC, bool PERSIST>
 static const void* integrate_fn() {
-  if constexpr (PREC == 2) return (const void*)k_integrate_ds<PERSIST>;
+  if constexpr (PREC != 0) return (const void*)k_integrate_mx<PREC, PERSIST>;
   else return (const void*)k_integrate<PREC, PERSIST>;
 }
 
@@ -440,15 +441,24 @@ cudaError_t launch_integrate(int prec, bool persistent, int block, int grid, con
 
 // Dynamic shared memory of an integration launch: the double-single workspace.
 static size_t integrate_smem(int prec, int block) {
-  return prec == PN_MIXED_DS ? (size_t)kDsWorkBytes * (size_t)block : 0;
+  if (prec == PN_MIXED_DS) return (size_t)kDsWorkBytes * (size_t)block;
+  if (prec == PN_MIXED) return (size_t)kF32WorkBytes * (size_t)block;
+  return 0;
 }
 
 cudaError_t prepare_integrate_kernels() {
-  const int bytes = kDsWorkBytes * kMaxBlock;
-  const void* fns[4] = {(const void*)k_integrate_ds<true>, (const void*)k_integrate_ds<false>,
-                        (const void*)k_integrate_ds<true, true>, (const void*)k_integrate_ds<false, true>};
-  for (const void* f : fns) {
-    const cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  const void* ds[4] = {(const void*)k_integrate_mx<2, true>, (const void*)k_integrate_mx<2, false>,
+                       (const void*)k_integrate_mx<2, true, true>, (const void*)k_integrate_mx<2, false, true>};
+  const void* f32[4] = {(const void*)k_integrate_mx<1, true>, (const void*)k_integrate_mx<1, false>,
+                        (const void*)k_integrate_mx<1, true, true>, (const void*)k_integrate_mx<1, false, true>};
+  for (const void* f : ds) {
+    const cudaError_t e =
+        cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, kDsWorkBytes * kMaxBlock);
+    if (e != cudaSuccess) return e;
+  }
+  for (const void* f : f32) {
+    const cudaError_t e =
+        cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, kF32WorkBytes * kMaxBlock);
     if (e != cudaSuccess) return e;
   }
   return cudaSuccess;
@@ -459,11 +469,11 @@ static void launch_integrate_variant(int prec, bool persistent, int block, int g
                                      const double* ws, int64_t stride, cudaStream_t s) {
   const size_t sm = integrate_smem(prec, block);
   if (prec == PN_MIXED) {
-    if (persistent) k_integrate<1, true, false, BOUNDED><<<grid, block, 0, s>>>(a, ws, stride);
-    else k_integrate<1, false, false, BOUNDED><<<grid, block, 0, s>>>(a, ws, stride);
+    if (persistent) k_integrate_mx<1, true, BOUNDED><<<grid, block, sm, s>>>(a, ws, stride);
+    else k_integrate_mx<1, false, BOUNDED><<<grid, block, sm, s>>>(a, ws, stride);
   } else if (prec == PN_MIXED_DS) {
-    if (persistent) k_integrate_ds<true, BOUNDED><<<grid, block, sm, s>>>(a, ws, stride);
-    else k_integrate_ds<false, BOUNDED><<<grid, block, sm, s>>>(a, ws, stride);
+    if (persistent) k_integrate_mx<2, true, BOUNDED><<<grid, block, sm, s>>>(a, ws, stride);
+    else k_integrate_mx<2, false, BOUNDED><<<grid, block, sm, s>>>(a, ws, stride);
   } else {
     if (persistent) k_integrate<0, true, false, BOUNDED><<<grid, block, 0, s>>>(a, ws, stride);
     else k_integrate<0, false, false, BOUNDED><<<grid, block, 0, s>>>(a, ws, stride);
@@ -477,12 +487,13 @@ cudaError_t launch_integrate_only(int prec, bool persistent, int block, int grid
     return cudaGetLastError();
   }
   if (prec == PN_MIXED) {
-    if (persistent) k_integrate<1, true><<<grid, block, 0, s>>>(a, ws, stride);
-    else k_integrate<1, false><<<grid, block, 0, s>>>(a, ws, stride);
+    const size_t sm = integrate_smem(prec, block);
+    if (persistent) k_integrate_mx<1, true><<<grid, block, sm, s>>>(a, ws, stride);
+    else k_integrate_mx<1, false><<<grid, block, sm, s>>>(a, ws, stride);
   } else if (prec == PN_MIXED_DS) {
     const size_t sm = integrate_smem(prec, block);
-    if (persistent) k_integrate_ds<true><<<grid, block, sm, s>>>(a, ws, stride);
-    else k_integrate_ds<false><<<grid, block, sm, s>>>(a, ws, stride);
+    if (persistent) k_integrate_mx<2, true><<<grid, block, sm, s>>>(a, ws, stride);
+    else k_integrate_mx<2, false><<<grid, block, sm, s>>>(a, ws, stride);
   } else {
     if (persistent) k_integrate<0, true><<<grid, block, 0, s>>>(a, ws, stride);
     else k_integrate<0, false><<<grid, block, 0, s>>>(a, ws, stride);
