@@ -451,7 +451,7 @@ def main():
 
     nvtx.range_pop()
     cpu = None
-    if rank == 0 and not args.no_cpu_baseline:
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:  # the host baseline is an N = 1 figure
         rate, m, threads, dt = cpu_oracle_rate(ens, target_s=10.0)
         rate1, m1_, _, _ = cpu_oracle_rate(workloads.take(ens, np.arange(4096)), target_s=2.0, threads=1)
         import oracle
