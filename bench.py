@@ -72,6 +72,13 @@ def parse_args():
     ap.add_argument("--shape", default=None,
                     help="fixed launch shape 'plain|persistent:BLOCK[:BPT]' for every precision instead of the "
                          "autotuner (a run under a profiler uses it: the tuner's own timings are distorted there)")
+    ap.add_argument("--science", choices=("ks",), default=None,
+                    help="instead of the benchmark: Sec. V B's uniformity test at the paper's size (equal mass, "
+                         "chi = 0.7, isotropic spins, M omega 0.00395 -> 0.05, 362,799,815 inspirals), sampled "
+                         "and integrated on the device in chunks, final S1-hat.S2-hat binned into 2^20 bins, "
+                         "one-sample KS test against U[-1, 1]")
+    ap.add_argument("--science-n", type=int, default=362_799_815)
+    ap.add_argument("--science-precision", type=int, default=0, help="0 FP64, 1 FP32 RHS, 2 double-single")
     ap.add_argument("--profile-case", choices=("integrate", "adjoint"), default=None,
                     help="no timing, the small cases the ncu section captures run: 'integrate' integrates the "
                          "first --n binaries of the workload once per precision (persistent schedule, 256 "
@@ -173,6 +180,55 @@ def cpu_oracle_rate(ens, target_s: float = 10.0, threads: int = 0):
     return m / dt, m, int(r["threads_used"]), dt
 
 
+def science_ks(args, pn, torch, dev):
+    """Sec. V B: is the final S1-hat.S2-hat uniform?  Device sampling (pn_batch_sample), integration and a
+    2^20-bin histogram per chunk of 2^24 binaries; the counts are summed on the host and tested with
+    pn_ks_uniform.  Prints one JSON line."""
+    total, chunk, bins = args.science_n, 1 << 24, 1 << 20
+    d = pn.dist(q=(1.0, 1.0), q_mode=0, chi=(0.7, 0.7), chi_mode=0, omega0=(0.00395, 0.00395), omega_f=0.05)
+    counts = np.zeros(bins, dtype=np.int64)
+    status = np.zeros(8, dtype=np.int64)
+    attempts = 0
+    ms = 0.0
+    t0 = time.perf_counter()
+    with pn.Batch(min(chunk, total), pn.params(precision=args.science_precision)) as b:
+        inp = pn.alloc_inputs(min(chunk, total), dev)
+        out = pn.alloc_outputs(min(chunk, total), dev)
+        done, c = 0, 0
+        while done < total:
+            n = min(chunk, total - done)
+            pn.pn_batch_sample(b.handle, workloads_seed(c), d, n, inp)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            pn.pn_batch_integrate(b.handle, n, inp, out)
+            e1.record()
+            counts += pn.pn_batch_histogram(b.handle, n, inp, out, pn.native.PN_Q_FINAL_S1S2, bins)
+            ms += e0.elapsed_time(e1)
+            st = b.stats(inp, out, n)
+            status += np.array(st["count_by_status"], dtype=np.int64)
+            attempts += st["acc_total"] + st["rej_total"] + st["land_total"]
+            done += n
+            c += 1
+    wall = time.perf_counter() - t0
+    ks = pn.pn_ks_uniform(counts, -1.0, 1.0)
+    hist100 = counts.reshape(100, -1).sum(axis=1) if bins % 100 == 0 else np.add.reduceat(
+        counts, (np.arange(100) * bins) // 100)
+    line = {"science": "Sec. V B uniformity of the final S1-hat.S2-hat (one-sample KS against U[-1, 1])",
+            "n": total, "chunks": c, "precision": args.science_precision,
+            "workload": "m1 = m2 = 0.5, chi1 = chi2 = 0.7, isotropic spin directions, L-hat = z, "
+                        "M omega 0.00395 -> 0.05, DP5(4) tol 5e-7, h0 = 10",
+            "integrate_ms": ms, "inspirals_per_s": total / (ms * 1e-3), "wall_s": wall,
+            "attempts_per_binary": attempts / total, "count_by_status": status.tolist(),
+            "ks": ks, "histogram_100_bins": hist100.tolist(),
+            "paper": {"n": 362_799_815, "p_value": 5.17e-5, "hardware": "Tesla S1070 GPUs, FP32"}}
+    print(json.dumps(line), flush=True)
+
+
+def workloads_seed(chunk: int) -> int:
+    """Seed of chunk c of the science run (counter-based draws: chunks are independent)."""
+    return 0x0908_3889_5B00 + chunk
+
+
 def reference_arm(args, rank, world):
     """The oracle, as it stands, on the host cores: the base contract's reference arm for this path."""
     if rank != 0:
@@ -240,6 +296,9 @@ def main():
     ens = workloads.config("C1", n=n, seed=rank_seed(rank))
     inp = pn.to_device(ens, device=dev)
     out = pn.alloc_outputs(n, dev)
+    if args.science == "ks":
+        science_ks(args, pn, torch, dev)
+        return
     if args.profile_case == "adjoint":
         c4 = workloads.config("C4")
         n4 = c4["m1"].shape[0]

@@ -303,11 +303,28 @@ int pn_batch_adjoint(pn_batch *b, int64_t n, const pn_inputs *in, const pn_cotan
 int pn_batch_stats(pn_batch *b, int64_t n, const pn_inputs *in, const pn_outputs *out, pn_stats *host);
 
 /* Histogram of outputs 0..n-1 (Sec. V A: 20 and 100 bins of the final
- * S1-hat.S2-hat; 79 x 79 bins of initial vs final).  Only binaries with
- * status OK and finite values count.  Writes nx * ny counts to host_counts and
+ * S1-hat.S2-hat; 79 x 79 bins of initial vs final; Sec. V B's KS test uses
+ * fine 1-D bins).  nx * ny <= 4,194,304 bins.  Only binaries with status OK
+ * and finite values count.  Writes nx * ny counts to host_counts and
  * synchronises.  Errors: PN_E_ARG (bad spec, NULL pointers), PN_E_CUDA. */
 int pn_batch_histogram(pn_batch *b, int64_t n, const pn_inputs *in, const pn_outputs *out, const pn_hist_spec *spec,
                        int64_t *host_counts);
+
+/* One-sample Kolmogorov-Smirnov test of binned values against the uniform
+ * distribution on [lo, hi] (Sec. V B tests the final S1-hat.S2-hat this way):
+ * counts[0..n_bins-1] of equal-width bins, e.g. from pn_batch_histogram (any
+ * number of calls summed).  The binned empirical CDF brackets the statistic:
+ * d_lo <= D <= d_hi (d_lo is D at the bin edges; with N values in n_bins bins
+ * the two differ by at most the largest bin's share).  p_at_d_lo and
+ * p_at_d_hi are the asymptotic Kolmogorov p-values at those D (with Stephens'
+ * sqrt(N) + 0.12 + 0.11/sqrt(N) scaling).  Host only: needs no GPU or batch.
+ * Errors: PN_E_ARG (NULL pointers, n_bins < 1, lo >= hi, a negative count). */
+typedef struct {
+  int64_t n;              /* number of values (sum of counts) */
+  double d_lo, d_hi;      /* bounds on the KS statistic D */
+  double p_at_d_lo, p_at_d_hi;
+} pn_ks_result;
+int pn_ks_uniform(const int64_t *counts, int32_t n_bins, double lo, double hi, pn_ks_result *res);
 
 /* Gaussian kernel density estimate of one quantity (Sec. V A):
  * p(x) = 1/(N h) sum_j K((x - x_j)/h), K(u) = exp(-u^2/2)/sqrt(2 pi), with

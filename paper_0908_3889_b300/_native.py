@@ -81,6 +81,11 @@ class pn_hist_spec(C.Structure):
                 ("x_lo", C.c_double), ("x_hi", C.c_double), ("y_lo", C.c_double), ("y_hi", C.c_double)]
 
 
+class pn_ks_result(C.Structure):
+    _fields_ = [("n", C.c_int64), ("d_lo", C.c_double), ("d_hi", C.c_double), ("p_at_d_lo", C.c_double),
+                ("p_at_d_hi", C.c_double)]
+
+
 PN_Q_FINAL_S1S2, PN_Q_FINAL_LS1, PN_Q_FINAL_LS2, PN_Q_INIT_S1S2, PN_Q_INIT_LS1, PN_Q_INIT_LS2 = range(6)
 
 
@@ -111,6 +116,8 @@ SIGNATURES = {
                                      C.POINTER(pn_hist_spec), C.POINTER(C.c_int64)]),
     "pn_batch_kde": (C.c_int, [C.c_void_p, C.c_int64, C.POINTER(pn_inputs), C.POINTER(pn_outputs), C.c_int32,
                                C.POINTER(C.c_double), C.c_int64, C.POINTER(C.c_double), C.POINTER(C.c_double)]),
+    "pn_ks_uniform": (C.c_int, [C.POINTER(C.c_int64), C.c_int32, C.c_double, C.c_double,
+                                C.POINTER(pn_ks_result)]),
     "pn_batch_destroy": (None, [C.c_void_p]),
     "pn_integrate_noalloc": (C.c_int, [C.c_int64, C.POINTER(pn_params), C.POINTER(pn_inputs), C.POINTER(pn_outputs),
                                        C.c_void_p]),

@@ -253,6 +253,16 @@ def pn_batch_kde(h, n: int, inputs: dict, outputs: dict, quantity: int, grid) ->
     return dens, bw.value
 
 
+def pn_ks_uniform(counts, lo: float = -1.0, hi: float = 1.0) -> dict:
+    """Kolmogorov-Smirnov test of binned counts against U[lo, hi] (host only): n, d_lo <= D <= d_hi and
+    the p-values at both bounds."""
+    c = np.ascontiguousarray(np.asarray(counts), dtype=np.int64)
+    r = N.pn_ks_result()
+    _check(_lib().pn_ks_uniform(c.ctypes.data_as(C.POINTER(C.c_int64)), int(c.shape[0]), float(lo), float(hi),
+                                C.byref(r)), None)
+    return {f: getattr(r, f) for f, _ in N.pn_ks_result._fields_}
+
+
 def pn_integrate_noalloc(n: int, prm: N.pn_params, inputs: dict, outputs: dict, stream=None) -> None:
     """The library's no-allocation entry point (n <= 16384 binaries, persistent schedule)."""
     if stream is None:

@@ -68,6 +68,31 @@ __global__ void __launch_bounds__(256) k_histogram(pn_inputs in, pn_outputs out,
     if (h[k]) atomicAdd(&counts[k], (unsigned long long)h[k]);
 }
 
+// The same histogram with the counts directly in global memory, for bin counts
+// beyond the shared-memory copy (up to kMaxHistBinsGlobal).  Lanes of a warp
+// that fall in the same bin add their count once (match_any).
+__global__ void __launch_bounds__(256) k_histogram_global(pn_inputs in, pn_outputs out, int64_t n, pn_hist_spec sp,
+                                                          unsigned long long* counts) {
+  const double nx_norm = (double)sp.nx / (sp.x_hi - sp.x_lo);
+  const double ny_norm = sp.ny > 1 ? (double)sp.ny / (sp.y_hi - sp.y_lo) : 0.0;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  const int64_t rounds = (n + stride - 1) / stride;  // every lane of a warp runs the same rounds
+  const unsigned lane = threadIdx.x & 31u;
+  for (int64_t r = 0; r < rounds; r++) {
+    const int64_t i = r * stride + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    int k = -1;
+    if (i < n) {
+      k = bin_of(quantity(sp.quantity_x, in, out, i), sp.x_lo, sp.x_hi, nx_norm, sp.nx);
+      if (k >= 0 && sp.ny > 1) {
+        const int ky = bin_of(quantity(sp.quantity_y, in, out, i), sp.y_lo, sp.y_hi, ny_norm, sp.ny);
+        k = ky < 0 ? -1 : k * sp.ny + ky;
+      }
+    }
+    const unsigned peers = __match_any_sync(0xffffffffu, k);
+    if (k >= 0 && (int)lane == __ffs(peers) - 1) atomicAdd(&counts[k], (unsigned long long)__popc(peers));
+  }
+}
+
 // Sum and sum of squares (for the bandwidth) and count of one quantity.
 __global__ void __launch_bounds__(256) k_moments(pn_inputs in, pn_outputs out, int64_t n, int q, double* part) {
   __shared__ double sh[3][8];
@@ -124,7 +149,10 @@ cudaError_t launch_histogram(const pn_inputs& in, const pn_outputs& out, int64_t
   if (e != cudaSuccess || n <= 0) return e;
   int64_t blocks = (n + 255) / 256;
   if (blocks > 1184) blocks = 1184;
-  k_histogram<<<(unsigned)blocks, 256, (size_t)nbins * sizeof(unsigned int), s>>>(in, out, n, sp, counts);
+  if (nbins <= kMaxHistBins)
+    k_histogram<<<(unsigned)blocks, 256, (size_t)nbins * sizeof(unsigned int), s>>>(in, out, n, sp, counts);
+  else
+    k_histogram_global<<<(unsigned)blocks, 256, 0, s>>>(in, out, n, sp, counts);
   return cudaGetLastError();
 }
 
@@ -142,3 +170,59 @@ cudaError_t launch_kde(const pn_inputs& in, const pn_outputs& out, int64_t n, in
 }
 
 }  // namespace pn
+
+// ---------------------------------------------------------------------------
+// One-sample Kolmogorov-Smirnov test against the uniform distribution on
+// [lo, hi], from binned counts (Sec. V B tests the final S1-hat.S2-hat for
+// uniformity this way).  The empirical CDF F_n is known exactly at the bin
+// edges e_k, so d_lo = max_k |F_n(e_k) - F(e_k)| <= D; inside bin k, F_n lies
+// between F_n(e_k) and F_n(e_k+1) and F between F(e_k) and F(e_k+1), so
+// D <= d_hi = max_k max(F(e_k+1) - F_n(e_k), F_n(e_k+1) - F(e_k)).  The
+// p-values use the limiting Kolmogorov distribution,
+// Q(t) = 2 sum_{j>=1} (-1)^(j-1) exp(-2 j^2 t^2), at t = (sqrt(N) + 0.12 +
+// 0.11/sqrt(N)) D (Stephens' small-sample correction).
+// ---------------------------------------------------------------------------
+static double kolmogorov_q(double t) {
+  if (t < 0.2) return 1.0;  // the series converges slowly there; Q is 1 to 1e-20
+  double s = 0.0, sign = 1.0;
+  for (int j = 1; j <= 200; j++) {
+    const double term = std::exp(-2.0 * j * j * t * t);
+    s += sign * term;
+    if (term < 1e-300 || term < 1e-17 * std::fabs(s)) break;
+    sign = -sign;
+  }
+  const double q = 2.0 * s;
+  return q < 0.0 ? 0.0 : (q > 1.0 ? 1.0 : q);
+}
+
+extern "C" int pn_ks_uniform(const int64_t* counts, int32_t n_bins, double lo, double hi, pn_ks_result* res) {
+  if (!counts || !res) return pn::set_thread_error(PN_E_ARG, "NULL pointer");
+  if (n_bins < 1) return pn::set_thread_error(PN_E_ARG, "n_bins must be >= 1");
+  if (!(hi > lo) || !std::isfinite(lo) || !std::isfinite(hi)) return pn::set_thread_error(PN_E_ARG, "need lo < hi");
+  int64_t n = 0;
+  for (int32_t k = 0; k < n_bins; k++) {
+    if (counts[k] < 0) return pn::set_thread_error(PN_E_ARG, "negative count");
+    n += counts[k];
+  }
+  res->n = n;
+  res->d_lo = res->d_hi = 0.0;
+  res->p_at_d_lo = res->p_at_d_hi = 1.0;
+  if (n == 0) return PN_OK;
+  const double inv_n = 1.0 / (double)n;
+  int64_t cum = 0;
+  double d_lo = 0.0, d_hi = 0.0;
+  for (int32_t k = 0; k < n_bins; k++) {
+    const double f0 = (double)k / n_bins, f1 = (double)(k + 1) / n_bins;  // F at the bin's edges
+    const double g0 = cum * inv_n;
+    cum += counts[k];
+    const double g1 = cum * inv_n;  // F_n at the bin's edges
+    d_lo = std::fmax(d_lo, std::fmax(std::fabs(g0 - f0), std::fabs(g1 - f1)));
+    d_hi = std::fmax(d_hi, std::fmax(f1 - g0, g1 - f0));
+  }
+  const double sn = std::sqrt((double)n), corr = sn + 0.12 + 0.11 / sn;
+  res->d_lo = d_lo;
+  res->d_hi = d_hi;
+  res->p_at_d_lo = kolmogorov_q(corr * d_lo);
+  res->p_at_d_hi = kolmogorov_q(corr * d_hi);
+  return PN_OK;
+}

@@ -47,7 +47,8 @@ struct pn_batch {
   int64_t seg_lanes = 0;
   int32_t seg_every = 0;
   double* d_adj_out = nullptr;   // forward outputs when the caller passes none
-  unsigned long long* d_hist = nullptr;  // analysis scratch: histogram counts
+  unsigned long long* d_hist = nullptr;  // analysis scratch: histogram counts (hist_cap bins)
+  int64_t hist_cap = 0;
   double* d_ana = nullptr;               // analysis scratch: moments, KDE grid and density
   int64_t ana_cap = 0;
   int32_t* d_adj_out_i = nullptr;
@@ -774,14 +775,22 @@ extern "C" int pn_batch_histogram(pn_batch* b, int64_t n, const pn_inputs* in, c
   if (n < 0 || n > b->n_max) return fail(b, PN_E_ARG, "n must be in [0, n_max]");
   if (!inputs_ok(in) || !outputs_ok(out) || !sp || !host_counts) return fail(b, PN_E_ARG, "NULL pointer");
   const bool two = sp->ny > 1;
-  if (sp->nx < 1 || sp->ny < 1 || (int64_t)sp->nx * sp->ny > pn::kMaxHistBins) return fail(b, PN_E_ARG, "bad bin counts");
+  if (sp->nx < 1 || sp->ny < 1 || (int64_t)sp->nx * sp->ny > pn::kMaxHistBinsGlobal)
+    return fail(b, PN_E_ARG, "bad bin counts");
   if (sp->quantity_x < 0 || sp->quantity_x > 5 || (two && (sp->quantity_y < 0 || sp->quantity_y > 5)))
     return fail(b, PN_E_ARG, "bad quantity");
   if (!(sp->x_hi > sp->x_lo) || (two && !(sp->y_hi > sp->y_lo))) return fail(b, PN_E_ARG, "need lo < hi");
-  if (!b->d_hist && cudaMalloc(&b->d_hist, pn::kMaxHistBins * sizeof(unsigned long long)) != cudaSuccess) {
-    cudaGetLastError();
+  const int64_t need_bins = (int64_t)sp->nx * sp->ny > pn::kMaxHistBins ? (int64_t)sp->nx * sp->ny : pn::kMaxHistBins;
+  if (b->hist_cap < need_bins) {
+    cudaFree(b->d_hist);
     b->d_hist = nullptr;
-    return fail(b, PN_E_NOMEM, "histogram scratch allocation failed");
+    b->hist_cap = 0;
+    if (cudaMalloc(&b->d_hist, (size_t)need_bins * sizeof(unsigned long long)) != cudaSuccess) {
+      cudaGetLastError();
+      b->d_hist = nullptr;
+      return fail(b, PN_E_NOMEM, "histogram scratch allocation failed");
+    }
+    b->hist_cap = need_bins;
   }
   cudaError_t e = pn::launch_histogram(*in, *out, n, *sp, b->d_hist, b->stream);
   if (e != cudaSuccess) return cuda_fail(b, e, "histogram kernel launch");

@@ -94,7 +94,8 @@ cudaError_t launch_stats(int64_t n, const pn_inputs& in, const pn_outputs& out, 
                          cudaStream_t s);
 
 // Analysis (pn_analysis.cu).
-constexpr int kMaxHistBins = 8192;
+constexpr int kMaxHistBins = 8192;             // counts in shared memory up to this many bins
+constexpr int kMaxHistBinsGlobal = 1 << 22;  // counts in global memory beyond
 cudaError_t launch_histogram(const pn_inputs& in, const pn_outputs& out, int64_t n, const pn_hist_spec& sp,
                              unsigned long long* counts, cudaStream_t s);
 cudaError_t launch_moments(const pn_inputs& in, const pn_outputs& out, int64_t n, int q, double* part, int blocks,

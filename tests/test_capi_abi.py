@@ -42,7 +42,7 @@ def test_struct_layouts_match_header(native, tmp_path):
     structs = {"pn_params": native.pn_params, "pn_inputs": native.pn_inputs, "pn_outputs": native.pn_outputs,
                "pn_dist": native.pn_dist, "pn_cotangents": native.pn_cotangents, "pn_grads": native.pn_grads,
                "pn_stats": native.pn_stats, "pn_tune_result": native.pn_tune_result,
-               "pn_hist_spec": native.pn_hist_spec}
+               "pn_hist_spec": native.pn_hist_spec, "pn_ks_result": native.pn_ks_result}
     lines = ["#include <stddef.h>", f'#include "{HEADER}"', "long probe(int k) { switch (k) {"]
     k = 0
     expect = []

@@ -136,7 +136,30 @@ def test_analysis_argument_errors(pn):
     with pytest.raises(pn.PNError):
         b.histogram(inp, out, 9, 10)
     with pytest.raises(pn.PNError):
-        b.histogram(inp, out, 0, 100, quantity_y=0, ny=100)  # 10,000 > 8,192 bins
+        b.histogram(inp, out, 0, 4096, quantity_y=0, ny=2048)  # 8,388,608 > 4,194,304 bins
     with pytest.raises(pn.PNError):
         b.histogram(inp, out, 0, 10, x_range=(1.0, -1.0))
     b.close()
+
+
+def test_fine_histogram_and_ks_of_sec_vb_workload(pn):
+    """Sec. V B's uniformity test on a 1,048,576-binary sample of its workload (equal mass, chi = 0.7,
+    omega 0.00395 -> 0.05), drawn on the device: the 2^20-bin histogram (global-memory counts) equals the
+    binning rule applied to the outputs, and pn_ks_uniform's bounds bracket scipy's exact KS statistic."""
+    import torch
+    n, bins = 1 << 20, 1 << 20
+    d = pn.dist(q=(1.0, 1.0), chi=(0.7, 0.7), omega0=(0.00395, 0.00395), omega_f=0.05)
+    with pn.Batch(n) as b:
+        inp = b.sample(0x5B, d, n)
+        out = b.integrate(inp)
+        torch.cuda.synchronize()
+        got = pn.pn_batch_histogram(b.handle, n, inp, out, pn.native.PN_Q_FINAL_S1S2, bins)
+        g = pn.to_numpy(out)
+    fin = np.where(g["status"] == 0, g["dot_s1s2"], np.nan)
+    k, x = np_bins(fin, -1.0, 1.0, bins)
+    assert np.array_equal(got, np.bincount(k, minlength=bins))
+    ks = pn.pn_ks_uniform(got, -1.0, 1.0)
+    exact = sstats.kstest(x, sstats.uniform(loc=-1, scale=2).cdf)
+    assert ks["n"] == x.shape[0] == n
+    assert ks["d_lo"] <= exact.statistic <= ks["d_hi"]
+    assert ks["d_hi"] - ks["d_lo"] < 1e-4
