@@ -14,7 +14,10 @@
 //               different lengths do not leave lanes idle.
 // Inputs and outputs are structure-of-arrays: lane i touches element i of
 // each array, so every load and store of a warp is one coalesced 256-byte
-// transaction.
+// transaction.  The FP64 kernel keeps its stage rates in registers
+// (k_integrate); the two mixed-precision kernels keep theirs in a per-thread
+// shared-memory workspace and are held to 168 registers (k_integrate_mx), so
+// their stage loops stay small and three warps fit per scheduler.
 
 #include <cmath>
 
