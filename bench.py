@@ -85,10 +85,11 @@ def parse_args():
                          "one-sample KS test against U[-1, 1]")
     ap.add_argument("--science-n", type=int, default=362_799_815)
     ap.add_argument("--science-precision", type=int, default=0, help="0 FP64, 1 FP32 RHS, 2 double-single")
-    ap.add_argument("--profile-case", choices=("integrate", "adjoint"), default=None,
+    ap.add_argument("--profile-case", choices=("integrate", "adjoint", "adjoint_ds"), default=None,
                     help="no timing, the small cases the ncu section captures run: 'integrate' integrates the "
                          "first --n binaries of the workload once per precision (persistent schedule, 256 "
-                         "threads); 'adjoint' runs one pn_batch_adjoint over the 65,536-binary adjoint ensemble")
+                         "threads); 'adjoint' runs one pn_batch_adjoint over the 65,536-binary adjoint ensemble, "
+                         "'adjoint_ds' the same with the double-single reverse sweep")
     return ap.parse_args()
 
 
@@ -305,16 +306,16 @@ def main():
     if args.science == "ks":
         science_ks(args, pn, torch, dev)
         return
-    if args.profile_case == "adjoint":
+    if args.profile_case in ("adjoint", "adjoint_ds"):
         c4 = workloads.config("C4")
         n4 = c4["m1"].shape[0]
         inp4 = pn.to_device(c4, device=dev)
         cot = {"dot_s1s2": torch.ones(n4, dtype=torch.float64, device=dev)}
         grads = {f: torch.empty(n4, dtype=torch.float64, device=dev) for f in pn.native.GRAD_FIELDS}
-        with pn.Batch(n4) as b:
+        with pn.Batch(n4, pn.params(precision=2 if args.profile_case == "adjoint_ds" else 0)) as b:
             pn.pn_batch_adjoint(b.handle, n4, inp4, cot, grads)
             torch.cuda.synchronize()
-        print(json.dumps({"profile_case": "C4 adjoint", "n": n4}))
+        print(json.dumps({"profile_case": "C4 " + args.profile_case, "n": n4}))
         return
     if args.profile_case == "integrate":
         for prec in (pn.native.PN_FP64, pn.native.PN_MIXED, pn.native.PN_MIXED_DS):
@@ -481,17 +482,21 @@ def main():
         inp4 = pn.to_device(c4, device=dev)
         cot = {"dot_s1s2": torch.ones(n4, dtype=torch.float64, device=dev)}
         grads = {f: torch.empty(n4, dtype=torch.float64, device=dev) for f in pn.native.GRAD_FIELDS}
-        with pn.Batch(n4) as b:
-            pn.pn_batch_adjoint(b.handle, n4, inp4, cot, grads)
-            ms_adj = []
-            for _ in range(3):
-                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-                e0.record()
-                pn.pn_batch_adjoint(b.handle, n4, inp4, cot, grads)  # recording forward + reverse sweep
-                e1.record()
-                e1.synchronize()
-                ms_adj.append(e0.elapsed_time(e1))
-        ms4 = max_over_ranks(min(ms_adj))
+        def adjoint_ms(precision):
+            with pn.Batch(n4, pn.params(precision=precision)) as b:
+                pn.pn_batch_adjoint(b.handle, n4, inp4, cot, grads)
+                ms_adj = []
+                for _ in range(3):
+                    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    e0.record()
+                    pn.pn_batch_adjoint(b.handle, n4, inp4, cot, grads)  # recording forward + reverse sweep
+                    e1.record()
+                    e1.synchronize()
+                    ms_adj.append(e0.elapsed_time(e1))
+            return max_over_ranks(min(ms_adj))
+
+        ms4 = adjoint_ms(0)
+        ms4ds = adjoint_ms(2)
         # Sec. IV's performance workload: one test inspiral, omega 0.004 -> 0.1, replicated (lock-step).
         pp = workloads.config("PAPER_PERF", n=1_048_576, seed=workloads.SEED_BASE + 6 + 1000 * rank)
         inpp = pn.to_device(pp, device=dev)
@@ -513,6 +518,8 @@ def main():
         extras["adjoint_C4"] = {"value": aggregate_rate(world, n4, 1, ms4), "unit": "gradients/s", "ms": ms4,
                                 "workload": "65,536 binaries, q ~ U[1,4], chi = 1, omega 0.01 -> 0.05; "
                                             "d(S1-hat.S2-hat final)/d(S1-hat, S2-hat, q), checkpoint every 64"}
+        extras["adjoint_C4_ds_sweep"] = {"value": aggregate_rate(world, n4, 1, ms4ds), "unit": "gradients/s",
+                                         "ms": ms4ds, "sweep": "double-single reverse sweep (FP64 forward record)"}
 
     nvtx.range_pop()
     cpu = None

@@ -289,6 +289,236 @@ __device__ double dp5_step_vjp(const Coef<double>& c, const double* __restrict__
   return hb;
 }
 
+// ---------------------------------------------------------------------------
+// The same reverse sweep in double-single arithmetic (pn_batch_adjoint with
+// PN_MIXED_DS): the segment recompute and the vector-Jacobian products run in
+// pairs of FP32 (~48-bit significands) on the FP32 pipe, each line undoing the
+// matching line of the forward pass as in rhs64_vjp.  Constants that are not
+// exact in FP32 enter as double-single pairs.  The recorded step sizes and
+// checkpoints are the FP64 forward run's; the states between checkpoints are
+// recomputed with double-single stage sums and FP64 state accumulation, so the
+// gradient is evaluated within ~1e-13 of the FP64 trajectory.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ ds dfma(ds a, ds b, ds c) { return ds_add(ds_mul(a, b), c); }
+__device__ __forceinline__ ds dzero() { return ds{0.0f, 0.0f}; }
+__device__ __forceinline__ ds dconst(dsc k) { return ds{k.hi, k.lo}; }
+
+__device__ __forceinline__ void cross_ds(const ds* a, const ds* b, ds* c) {
+  c[0] = ds_sub(ds_mul(a[1], b[2]), ds_mul(a[2], b[1]));
+  c[1] = ds_sub(ds_mul(a[2], b[0]), ds_mul(a[0], b[2]));
+  c[2] = ds_sub(ds_mul(a[0], b[1]), ds_mul(a[1], b[0]));
+}
+// c = a x b:  ab += b x cb,  bb += cb x a
+__device__ __forceinline__ void cross_vjp_ds(const ds* a, const ds* b, const ds* cb_, ds* ab, ds* bb) {
+  ds t[3];
+  cross_ds(b, cb_, t);
+  for (int k = 0; k < 3; k++) ab[k] = ds_add(ab[k], t[k]);
+  cross_ds(cb_, a, t);
+  for (int k = 0; k < 3; k++) bb[k] = ds_add(bb[k], t[k]);
+}
+__device__ __forceinline__ ds dot3_ds(const ds* a, const ds* b) {
+  return dfma(a[2], b[2], dfma(a[1], b[1], ds_mul(a[0], b[0])));
+}
+
+__device__ __noinline__ void rhs_ds_vjp(const Coef<ds>& c, const float* __restrict__ tabf, const ds* y, const ds* fb,
+                                        ds* yb, Coef<ds>& cb, ds* f) {
+  const dsc kThird = {(float)(1.0 / 3.0), (float)(1.0 / 3.0 - (double)(float)(1.0 / 3.0))};
+  // ---- forward (as rhs_ds) ----
+  const ds w = y[0];
+  const ds S1[3] = {y[1], y[2], y[3]}, S2[3] = {y[4], y[5], y[6]}, L[3] = {y[7], y[8], y[9]};
+  ds r = ds_inv_cbrt(w);
+  if ((__float_as_uint(w.hi) & 0x7fffffffu) - 0x00800000u >= 0x7f000000u) r = ds{__int_as_float(0x7fc00000), 0.0f};
+  const ds r2 = ds_mul(r, r);
+  const ds v = ds_mul(w, r2);
+  const ds v2 = ds_mul(v, v);
+  const ds lw = ds_log(w, tabf);
+  const ds LS1 = dot3_ds(L, S1), LS2 = dot3_ds(L, S2), S12 = dot3_ds(S1, S2);
+  const ds so = dfma(c.w1, LS1, dfma(c.w2, LS2, ds_neg(c.tail)));
+  const ds c2p = dfma(c.ss721, ds_mul(LS1, LS2), dfma(ds_neg(c.ss247), S12, c.c2));
+  const ds c3p = dfma(c.clog, lw, c.c3l);
+  const ds P6 = dfma(v, c.c35, c3p);
+  const ds P5 = dfma(v, P6, c.c25);
+  const ds P4 = dfma(v, P5, c2p);
+  const ds P3 = dfma(v, P4, ds_neg(so));
+  const ds P2 = dfma(v, P3, c.c1);
+  const ds P = dfma(v2, P2, ds_of(1.0f));
+  const ds w2 = ds_mul(w, w);
+  const ds Q = ds_mul(ds_mul(w2, w), v2);
+  ds A1[3], A2[3], C[3];
+  cross_ds(L, S1, A1);
+  cross_ds(L, S2, A2);
+  cross_ds(S1, S2, C);
+  const ds pre = ds_mul(c.prec, w2);
+  const ds al1 = dfma(c.a1, r, ds_mul_f(LS2, -3.0f)), al2 = dfma(c.a2, r, ds_mul_f(LS1, -3.0f));
+  const ds p1 = ds_mul(pre, al1), p2 = ds_mul(pre, al2);
+  ds d1[3], d2[3];
+  for (int k = 0; k < 3; k++) {
+    const ds pc = ds_mul(pre, C[k]);
+    d1[k] = ds_sub(ds_mul(p1, A1[k]), pc);
+    d2[k] = ds_add(ds_mul(p2, A2[k]), pc);
+  }
+  const ds lf = ds_mul(v, c.nie);
+  f[0] = ds_mul(ds_mul(Q, c.K), P);
+  for (int k = 0; k < 3; k++) {
+    f[1 + k] = d1[k];
+    f[4 + k] = d2[k];
+    f[7 + k] = ds_mul(lf, ds_add(d1[k], d2[k]));
+  }
+  // ---- reverse ----
+  ds S1b[3] = {dzero(), dzero(), dzero()}, S2b[3] = {dzero(), dzero(), dzero()}, Lb[3] = {dzero(), dzero(), dzero()};
+  ds d1b[3], d2b[3], A1b[3], A2b[3], Cb[3];
+  ds lfb = dzero();
+  for (int k = 0; k < 3; k++) lfb = dfma(fb[7 + k], ds_add(d1[k], d2[k]), lfb);  // f_L = lf (d1 + d2)
+  for (int k = 0; k < 3; k++) {
+    d1b[k] = dfma(lf, fb[7 + k], fb[1 + k]);
+    d2b[k] = dfma(lf, fb[7 + k], fb[4 + k]);
+  }
+  ds vb = ds_mul(lfb, c.nie);  // lf = v nie
+  cb.nie = dfma(lfb, v, cb.nie);
+  ds p1b = dzero(), p2b = dzero(), preb = dzero();  // d1 = p1 A1 - pre C, d2 = p2 A2 + pre C
+  for (int k = 0; k < 3; k++) {
+    p1b = dfma(d1b[k], A1[k], p1b);
+    p2b = dfma(d2b[k], A2[k], p2b);
+    A1b[k] = ds_mul(p1, d1b[k]);
+    A2b[k] = ds_mul(p2, d2b[k]);
+    const ds dd = ds_sub(d2b[k], d1b[k]);
+    Cb[k] = ds_mul(pre, dd);
+    preb = dfma(C[k], dd, preb);
+  }
+  preb = dfma(p1b, al1, dfma(p2b, al2, preb));  // p_i = pre al_i
+  const ds al1b = ds_mul(p1b, pre), al2b = ds_mul(p2b, pre);
+  cb.a1 = dfma(al1b, r, cb.a1);  // al1 = a1 r - 3 LS2, al2 = a2 r - 3 LS1
+  cb.a2 = dfma(al2b, r, cb.a2);
+  ds rb = dfma(al1b, c.a1, ds_mul(al2b, c.a2));
+  ds LS2b = ds_mul_f(al1b, -3.0f), LS1b = ds_mul_f(al2b, -3.0f);
+  ds w2b = ds_mul(preb, c.prec);  // pre = prec w2
+  cb.prec = dfma(preb, w2, cb.prec);
+  cross_vjp_ds(S1, S2, Cb, S1b, S2b);  // C = S1 x S2
+  cross_vjp_ds(L, S1, A1b, Lb, S1b);   // A1 = L x S1
+  cross_vjp_ds(L, S2, A2b, Lb, S2b);   // A2 = L x S2
+  const ds f0b = fb[0];  // f0 = Q K P
+  const ds Qb = ds_mul(ds_mul(f0b, c.K), P);
+  cb.K = dfma(ds_mul(f0b, Q), P, cb.K);
+  const ds Pb = ds_mul(ds_mul(f0b, Q), c.K);
+  w2b = dfma(ds_mul(Qb, w), v2, w2b);  // Q = w2 w v2
+  ds wb = ds_mul(ds_mul(Qb, w2), v2);
+  ds v2b = ds_mul(ds_mul(Qb, w2), w);
+  wb = dfma(ds_scale(w, 2.0f), w2b, wb);  // w2 = w^2
+  v2b = dfma(Pb, P2, v2b);                // P = v2 P2 + 1
+  const ds P2b = ds_mul(Pb, v2);
+  vb = dfma(P2b, P3, vb);  // P2 = v P3 + c1
+  const ds P3b = ds_mul(P2b, v);
+  cb.c1 = ds_add(cb.c1, P2b);
+  vb = dfma(P3b, P4, vb);  // P3 = v P4 - so
+  const ds P4b = ds_mul(P3b, v);
+  const ds sob = ds_neg(P3b);
+  vb = dfma(P4b, P5, vb);  // P4 = v P5 + c2p
+  const ds P5b = ds_mul(P4b, v);
+  const ds c2pb = P4b;
+  vb = dfma(P5b, P6, vb);  // P5 = v P6 + c25
+  const ds P6b = ds_mul(P5b, v);
+  cb.c25 = ds_add(cb.c25, P5b);
+  vb = dfma(P6b, c.c35, vb);  // P6 = v c35 + c3p
+  cb.c35 = dfma(P6b, v, cb.c35);
+  const ds c3pb = P6b;
+  cb.clog = dfma(c3pb, lw, cb.clog);  // c3p = clog lw + c3l
+  const ds lwb = ds_mul(c3pb, c.clog);
+  cb.c3l = ds_add(cb.c3l, c3pb);
+  cb.ss721 = dfma(ds_mul(c2pb, LS1), LS2, cb.ss721);  // c2p = ss721 LS1 LS2 - ss247 S12 + c2
+  LS1b = dfma(ds_mul(c2pb, c.ss721), LS2, LS1b);
+  LS2b = dfma(ds_mul(c2pb, c.ss721), LS1, LS2b);
+  cb.ss247 = ds_sub(cb.ss247, ds_mul(c2pb, S12));
+  const ds S12b = ds_neg(ds_mul(c2pb, c.ss247));
+  cb.c2 = ds_add(cb.c2, c2pb);
+  cb.w1 = dfma(sob, LS1, cb.w1);  // so = w1 LS1 + w2 LS2 - tail
+  LS1b = dfma(sob, c.w1, LS1b);
+  cb.w2 = dfma(sob, LS2, cb.w2);
+  LS2b = dfma(sob, c.w2, LS2b);
+  cb.tail = ds_sub(cb.tail, sob);
+  for (int k = 0; k < 3; k++) {  // LS1 = L.S1, LS2 = L.S2, S12 = S1.S2
+    Lb[k] = dfma(LS1b, S1[k], dfma(LS2b, S2[k], Lb[k]));
+    S1b[k] = dfma(LS1b, L[k], dfma(S12b, S2[k], S1b[k]));
+    S2b[k] = dfma(LS2b, L[k], dfma(S12b, S1[k], S2b[k]));
+  }
+  const ds r3 = ds_mul(r2, r);  // = 1/w
+  wb = dfma(lwb, r3, wb);       // lw = ln|w|
+  vb = dfma(ds_scale(v, 2.0f), v2b, vb);  // v2 = v^2
+  wb = dfma(vb, r2, wb);                  // v = w r^2
+  rb = dfma(ds_mul(vb, ds_scale(w, 2.0f)), r, rb);
+  wb = ds_sub(wb, ds_mul(ds_mul(ds_mul(rb, dconst(kThird)), r), r3));  // dr/dw = -r/(3w)
+  yb[0] = wb;
+  for (int k = 0; k < 3; k++) {
+    yb[1 + k] = S1b[k];
+    yb[4 + k] = S2b[k];
+    yb[7 + k] = Lb[k];
+  }
+}
+
+// One recomputed step in double-single: stage states Y_0..Y_5 (pairs) to
+// sp[(10 s + k) * ss], and when y5 != nullptr the step's result, accumulated in
+// FP64 from the double-single increment.
+__device__ __forceinline__ void dp5_stages_ds(const Coef<ds>& c, const float* __restrict__ tabf, const double* y,
+                                              double h, float2* sp, size_t ss, double* y5) {
+  ds K[6][10], yd[10];
+  const ds hd = split64(h);
+  for (int i = 0; i < 10; i++) {
+    yd[i] = split64(y[i]);
+    sp[(size_t)i * ss] = make_float2(yd[i].hi, yd[i].lo);
+  }
+  rhs_ds(c, tabf, yd, K[0]);
+#pragma unroll 1
+  for (int s = 1; s < 6; s++) {
+    ds ys[10];
+    for (int i = 0; i < 10; i++) {
+      dacc acc = dot_first(c_dp_a_ds[s - 1][0], K[0][i]);
+      for (int j = 1; j < s; j++) acc = dot_add(acc, c_dp_a_ds[s - 1][j], K[j][i]);
+      ys[i] = ds_add(yd[i], ds_mul(hd, dot_val(acc)));
+      sp[(size_t)(10 * s + i) * ss] = make_float2(ys[i].hi, ys[i].lo);
+    }
+    if (s < 5 || y5) rhs_ds(c, tabf, ys, K[s]);
+  }
+  if (!y5) return;
+  for (int i = 0; i < 10; i++) {
+    dacc acc = dot_first(c_dp_a_ds[5][0], K[0][i]);
+    for (int j = 2; j < 6; j++) acc = dot_add(acc, c_dp_a_ds[5][j], K[j][i]);
+    const ds inc = ds_mul(hd, dot_val(acc));
+    y5[i] = y[i] + (f32_to_f64(inc.hi) + f32_to_f64(inc.lo));
+  }
+}
+
+// Reverse mode of one step from its stored double-single stage states (the same
+// recurrences as dp5_step_vjp): lam in/out, cb accumulated, returns h's cotangent.
+__device__ double dp5_step_vjp_ds(const Coef<ds>& c, const float* __restrict__ tabf, const float2* sp, size_t ss,
+                                  double h, ds* lam, Coef<ds>& cb) {
+  ds kp[6][10], yb[10];
+  const ds hd = split64(h);
+  for (int j = 0; j < 6; j++)
+    for (int i = 0; i < 10; i++) kp[j][i] = ds_mul(dconst(c_dp_a_ds[5][j]), lam[i]);
+  for (int i = 0; i < 10; i++) yb[i] = lam[i];
+  ds hb = dzero();
+#pragma unroll 1
+  for (int s = 5; s >= 0; s--) {
+    ds Ys[10], fb[10], Yb[10], ks[10];
+    for (int i = 0; i < 10; i++) {
+      const float2 t = sp[(size_t)(10 * s + i) * ss];
+      Ys[i] = ds{t.x, t.y};
+      fb[i] = ds_mul(hd, kp[s][i]);
+    }
+    rhs_ds_vjp(c, tabf, Ys, fb, Yb, cb, ks);
+    for (int i = 0; i < 10; i++) {
+      hb = dfma(ks[i], kp[s][i], hb);
+      yb[i] = ds_add(yb[i], Yb[i]);
+    }
+    for (int j = 0; j < s; j++) {
+      const ds a = dconst(c_dp_a_ds[s - 1][j]);
+      if (a.hi != 0.0f)
+        for (int i = 0; i < 10; i++) kp[j][i] = dfma(a, Yb[i], kp[j][i]);
+    }
+  }
+  for (int i = 0; i < 10; i++) lam[i] = yb[i];
+  return ds_to_f64(hb);
+}
+
 __device__ __forceinline__ double gval(const double* p, int64_t i) { return p ? p[i] : 0.0; }
 
 // Sort key of binary i: its accepted-step count when the sweep walks its
@@ -369,7 +599,9 @@ __device__ __forceinline__ void angle_grads(const double* gv, const double* s, d
 }
 
 // Gradients of binary i; sp0 is the lane's segment buffer (stride ss).
-__device__ void adjoint_one(const AdjArgs& a, const double* __restrict__ tab, int64_t i, double* sp0, size_t ss) {
+template <bool DS>
+__device__ void adjoint_one(const AdjArgs& a, const double* __restrict__ tab, const float* __restrict__ tabf,
+                            int64_t i, double* sp0, size_t ss) {
   const pn_outputs& o = a.k.out;
   const pn_grads& g = a.grad;
   const int32_t N = o.n_acc[i];
@@ -428,9 +660,56 @@ __device__ void adjoint_one(const AdjArgs& a, const double* __restrict__ tab, in
   const int32_t every = a.every;
   const int32_t nseg = (N + every - 1) / every;
   const size_t step_words = (size_t)kAdjStageWords * ss;
+  if constexpr (DS) {
+    const Coef<ds> cd = to_ds(c);
+    Coef<ds> cbd;
+    ds* cbdv = &cbd.K;
+    for (int f = 0; f < 16; f++) cbdv[f] = dzero();
+    ds lamd[10];
+    for (int k = 0; k < 10; k++) lamd[k] = split64(lam[k]);
+    float2* sf0 = reinterpret_cast<float2*>(sp0);
 #pragma unroll 1
-  for (int32_t seg = nseg - 1; seg >= 0; seg--) {
-    const int32_t n0 = seg * every;
+    for (int32_t seg = nseg - 1; seg >= 0; seg--) {
+      const int32_t n0 = seg * every;
+      const int32_t n1s = (n0 + every < N) ? n0 + every : N;
+      double y[10];
+      for (int k = 0; k < 10; k++) y[k] = a.ck[((size_t)seg * 10 + k) * a.stride + i];
+#pragma unroll 1
+      for (int32_t n = n0; n < n1s; n++) {
+        double y5[10];
+        const bool more = n + 1 < n1s;
+        dp5_stages_ds(cd, tabf, y, a.h[(size_t)n * a.stride + i], sf0 + (size_t)(n - n0) * step_words, ss,
+                      more ? y5 : nullptr);
+        if (more)
+          for (int k = 0; k < 10; k++) y[k] = y5[k];
+      }
+#pragma unroll 1
+      for (int32_t n = n1s - 1; n >= n0; n--) {
+        const float2* sp = sf0 + (size_t)(n - n0) * step_words;
+        const double hn = a.h[(size_t)n * a.stride + i];
+        if (n == N - 1) {  // landing step: implicit h*
+          Coef<ds> cA, cB;
+          ds* av = &cA.K;
+          ds* bv = &cB.K;
+          for (int f = 0; f < 16; f++) { av[f] = dzero(); bv[f] = dzero(); }
+          ds lA[10];
+          for (int k = 0; k < 10; k++) lA[k] = dzero();
+          lA[0] = ds_of(1.0f);
+          const double nu = dp5_step_vjp_ds(cd, tabf, sp, ss, hn, lA, cA);
+          const double mu = dp5_step_vjp_ds(cd, tabf, sp, ss, hn, lamd, cB) + tbar;
+          const ds ratio = split64(mu / nu);
+          for (int k = 0; k < 10; k++) lamd[k] = ds_sub(lamd[k], ds_mul(ratio, lA[k]));
+          for (int f = 0; f < 16; f++) cbdv[f] = ds_add(cbdv[f], ds_sub(bv[f], ds_mul(ratio, av[f])));
+        } else {
+          (void)dp5_step_vjp_ds(cd, tabf, sp, ss, hn, lamd, cbd);
+        }
+      }
+    }
+    for (int k = 0; k < 10; k++) lam[k] = ds_to_f64(lamd[k]);
+    for (int f = 0; f < 16; f++) cbv[f] = ds_to_f64(cbdv[f]);
+  } else {
+#pragma unroll 1
+  for (int32_t seg = nseg - 1; seg >= 0; seg--) {    const int32_t n0 = seg * every;
     const int32_t n1s = (n0 + every < N) ? n0 + every : N;
     double y[10];
     for (int k = 0; k < 10; k++) y[k] = a.ck[((size_t)seg * 10 + k) * a.stride + i];
@@ -465,6 +744,7 @@ __device__ void adjoint_one(const AdjArgs& a, const double* __restrict__ tab, in
       }
     }
   }
+  }
   // Initial state S_i = chi_i m_i^2 S_i-hat, and the mass ratio q = m1/m2 (M = 1).
   const double s1[3] = {in.s1x[i], in.s1y[i], in.s1z[i]}, s2[3] = {in.s2x[i], in.s2y[i], in.s2z[i]};
   const double f1 = chi1 * (m1 * m1), f2 = chi2 * (m2 * m2);
@@ -492,10 +772,16 @@ __device__ void adjoint_one(const AdjArgs& a, const double* __restrict__ tab, in
 }
 
 // Persistent sweep: each warp claims 32 consecutive entries of the order.
-// blockDim.x must be a multiple of 32.
+// blockDim.x must be a multiple of 32.  DS: the double-single sweep.
+template <bool DS>
 __global__ void __launch_bounds__(128) k_adjoint(const AdjArgs a) {
   __shared__ double s_tab[256];
+  __shared__ float s_tabf[512];
   for (int q = threadIdx.x; q < 256; q += blockDim.x) s_tab[q] = a.k.tab[q];
+  if (DS) {
+    const float* gf = reinterpret_cast<const float*>(a.k.tab + 256);
+    for (int q = threadIdx.x; q < 512; q += blockDim.x) s_tabf[q] = gf[q];
+  }
   __syncthreads();
   const int64_t slot = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const unsigned lane = threadIdx.x & 31u;
@@ -506,7 +792,7 @@ __global__ void __launch_bounds__(128) k_adjoint(const AdjArgs a) {
     base = __shfl_sync(0xffffffffu, base, 0);
     if (base >= (unsigned long long)a.k.n) break;
     const int64_t p = (int64_t)base + lane;
-    if (p < a.k.n) adjoint_one(a, s_tab, a.order[p], sp0, (size_t)a.seg_stride);
+    if (p < a.k.n) adjoint_one<DS>(a, s_tab, s_tabf, a.order[p], sp0, (size_t)a.seg_stride);
   }
 }
 
@@ -523,12 +809,14 @@ cudaError_t launch_adjoint(const AdjArgs& a, int block, int grid, cudaStream_t s
   k_order_scatter<<<eg, 256, 0, s>>>(a.k.out, a.k.n, a.cap, a.bins, a.order);
   e = cudaMemsetAsync(a.k.queue, 0, sizeof(unsigned long long), s);
   if (e != cudaSuccess) return e;
-  k_adjoint<<<grid, block, 0, s>>>(a);
+  if (a.ds) k_adjoint<true><<<grid, block, 0, s>>>(a);
+  else k_adjoint<false><<<grid, block, 0, s>>>(a);
   return cudaGetLastError();
 }
 
-cudaError_t adjoint_occupancy(int block, int* blocks_per_sm) {
-  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, (const void*)k_adjoint, block, 0);
+cudaError_t adjoint_occupancy(bool ds, int block, int* blocks_per_sm) {
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+      blocks_per_sm, ds ? (const void*)k_adjoint<true> : (const void*)k_adjoint<false>, block, 0);
 }
 
 }  // namespace pn

@@ -559,8 +559,10 @@ extern "C" int pn_batch_adjoint(pn_batch* b, int64_t n, const pn_inputs* in, con
     if (set != 0 && set != 4) return fail(b, PN_E_ARG, "angle gradient pointers must be all set or all NULL");
   }
   if (out && !outputs_ok(out)) return fail(b, PN_E_ARG, "NULL output pointer");
-  if (b->p.precision != PN_FP64 || b->p.stop_mode != PN_STOP_LAND || b->p.fixed_step)
-    return fail(b, PN_E_UNIMPLEMENTED, "the adjoint needs precision PN_FP64, PN_STOP_LAND and adaptive steps");
+  if (b->p.precision == PN_MIXED || b->p.stop_mode != PN_STOP_LAND || b->p.fixed_step)
+    return fail(b, PN_E_UNIMPLEMENTED,
+                "the adjoint needs precision PN_FP64 or PN_MIXED_DS, PN_STOP_LAND and adaptive steps");
+  const bool ds_sweep = b->p.precision == PN_MIXED_DS;
   if (n == 0) return PN_OK;
   const size_t N = (size_t)b->n_max;
   pn_outputs o;
@@ -662,7 +664,7 @@ extern "C" int pn_batch_adjoint(pn_batch* b, int64_t n, const pn_inputs* in, con
   // claim, lane-private stage-state buffer.
   const int block = 128;
   int per_sm = 0;
-  PN_CUDA(b, pn::adjoint_occupancy(block, &per_sm));
+  PN_CUDA(b, pn::adjoint_occupancy(ds_sweep, block, &per_sm));
   const int64_t full = (n + block - 1) / block, capg = (int64_t)b->num_sms * (per_sm > 0 ? per_sm : 1);
   const int grid = (int)(full < capg ? full : capg);
   const int64_t lanes = (int64_t)grid * block;
@@ -706,6 +708,7 @@ extern "C" int pn_batch_adjoint(pn_batch* b, int64_t n, const pn_inputs* in, con
   aa.seg_stride = b->seg_lanes;
   aa.cap = b->rec_cap;
   aa.every = every;
+  aa.ds = ds_sweep ? 1 : 0;
   aa.gbar = *gbar;
   aa.grad = *grad;
   PN_CUDA(b, pn::launch_adjoint(aa, block, grid, b->stream));

@@ -55,6 +55,8 @@ struct AdjArgs {
   int64_t* order;    // n binary indices, longest record first
   int64_t stride, seg_stride;
   int32_t cap, every;
+  int32_t ds;        // 1: the reverse sweep in double-single arithmetic
+  int32_t pad_;
   pn_cotangents gbar;
   pn_grads grad;
 };
@@ -65,7 +67,7 @@ cudaError_t record_occupancy(int block, int* blocks_per_sm);
 // Orders the binaries by accepted-step count (bins, order), resets the queue
 // and launches the reverse sweep (pn_adjoint.cu).
 cudaError_t launch_adjoint(const AdjArgs& a, int block, int grid, cudaStream_t s);
-cudaError_t adjoint_occupancy(int block, int* blocks_per_sm);
+cudaError_t adjoint_occupancy(bool ds, int block, int* blocks_per_sm);
 
 // Set-up table: setup_fields() doubles per binary, field-major with the given stride (>= n).
 int setup_fields();

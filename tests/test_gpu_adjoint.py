@@ -158,6 +158,34 @@ def test_autograd_function_backward(pn):
     assert np.allclose(got, ref, rtol=1e-9, atol=1e-12)  # m1, m2 round-trip through q = m1/m2
 
 
+DS_GRAD_TOL = 1e-8  # double-single sweep: ~48-bit arithmetic through a few hundred steps
+
+
+@pytest.mark.parametrize("name", ["C4", "C2"])
+def test_double_single_sweep_matches_oracle(pn, orc, name):
+    """The reverse sweep in double-single arithmetic (precision PN_MIXED_DS) against the oracle's
+    forward-mode gradient of the FP64 map and against the FP64 sweep."""
+    ens = workloads.config(name, n=160, seed=300 + len(name))
+    g = cotangents(160, 17)
+    got = run_adjoint(pn, ens, g, precision=2)
+    ref = oracle_grads(orc, ens, g)
+    assert np.all(np.isfinite(got))
+    assert rel_err(got, ref) < DS_GRAD_TOL, rel_err(got, ref)
+    fp64 = run_adjoint(pn, ens, g)
+    assert rel_err(got, fp64) < DS_GRAD_TOL
+
+
+def test_double_single_sweep_full_size_subsample(pn, orc):
+    ens = workloads.config("C4")
+    n = ens["m1"].shape[0]
+    g = cotangents(n, 13)
+    got = run_adjoint(pn, ens, g, precision=2)
+    idx = workloads.subsample(n, 256, seed=workloads.SEED_BASE + 106)
+    ref = oracle_grads(orc, workloads.take(ens, idx), g[:, idx])
+    assert np.all(np.isfinite(got))
+    assert rel_err(got[:, idx], ref) < DS_GRAD_TOL
+
+
 def test_adjoint_refuses_other_modes(pn):
     import torch
     ens = workloads.config("C4", n=8)
