@@ -27,7 +27,7 @@
 //    hands back the stage rate for the step-size cotangent as well.
 
 #include "pn_device.cuh"
-#include "pn_internal.h"
+#include "pn_adjoint.h"
 
 namespace pn {
 namespace {

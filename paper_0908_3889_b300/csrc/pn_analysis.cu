@@ -10,7 +10,7 @@
 
 #include <cmath>
 
-#include "pn_internal.h"
+#include "pn_analysis.h"
 
 namespace pn {
 

@@ -10,6 +10,8 @@
 #include <cstring>
 #include <string>
 
+#include "pn_adjoint.h"
+#include "pn_analysis.h"
 #include "pn_internal.h"
 
 using pn::KArgs;

@@ -1,4 +1,6 @@
-// pn_internal.h -- declarations shared by the kernels (pn_kernels.cu) and the C ABI layer (pn_capi.cu).
+// pn_internal.h -- declarations shared by the integration kernels (pn_kernels.cu)
+// and the C ABI layer (pn_capi.cu).  The adjoint's and the analysis kernels'
+// own declarations are in pn_adjoint.h and pn_analysis.h.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -43,31 +45,10 @@ struct RecArgs {
   int32_t cap, every;
 };
 
-// Doubles the reverse sweep keeps per recomputed step: the six stage states.
-constexpr int kAdjStageWords = 60;
-
-struct AdjArgs {
-  KArgs k;           // inputs, forward outputs, n, queue, log table, controls
-  const double* h;   // recorded step sizes (RecArgs layout)
-  const double* ck;  // recorded checkpoints
-  double* seg;       // per-lane stage states: every x kAdjStageWords x seg_stride
-  unsigned long long* bins;  // cap + 1 counters for the ordering by step count
-  int64_t* order;    // n binary indices, longest record first
-  int64_t stride, seg_stride;
-  int32_t cap, every;
-  int32_t ds;        // 1: the reverse sweep in double-single arithmetic
-  int32_t pad_;
-  pn_cotangents gbar;
-  pn_grads grad;
-};
-
+// The recording forward pass of the adjoint (k_integrate<FP64, persistent, RECORD>).
 cudaError_t launch_integrate_record(const KArgs& a, const double* ws, int64_t stride, const RecArgs& rec, int block,
                                     int grid, cudaStream_t s);
 cudaError_t record_occupancy(int block, int* blocks_per_sm);
-// Orders the binaries by accepted-step count (bins, order), resets the queue
-// and launches the reverse sweep (pn_adjoint.cu).
-cudaError_t launch_adjoint(const AdjArgs& a, int block, int grid, cudaStream_t s);
-cudaError_t adjoint_occupancy(bool ds, int block, int* blocks_per_sm);
 
 // Set-up table: setup_fields() doubles per binary, field-major with the given stride (>= n).
 int setup_fields();
@@ -81,10 +62,10 @@ cudaError_t launch_integrate(int prec, bool persistent, int block, int grid, con
 // The integration kernel alone.
 cudaError_t launch_integrate_only(int prec, bool persistent, int block, int grid, const KArgs& a, const double* ws,
                                   int64_t stride, cudaStream_t s);
-// Resident blocks per SM of that kernel at this block size.
-// Allows the double-single integration kernels their shared-memory workspace
+// Allows the mixed-precision integration kernels their shared-memory workspace
 // (call once per device before launching them).
 cudaError_t prepare_integrate_kernels();
+// Resident blocks per SM of the integration kernel at this block size.
 cudaError_t integrate_occupancy(int prec, bool persistent, int block, int* blocks_per_sm);
 
 cudaError_t launch_sample(uint64_t seed, const pn_dist& d, int64_t n, const pn_inputs& in, cudaStream_t s);
@@ -94,16 +75,6 @@ constexpr int kStatWords = 40;
 constexpr int kStatGrid = 296;
 cudaError_t launch_stats(int64_t n, const pn_inputs& in, const pn_outputs& out, double* part, double* total,
                          cudaStream_t s);
-
-// Analysis (pn_analysis.cu).
-constexpr int kMaxHistBins = 8192;             // counts in shared memory up to this many bins
-constexpr int kMaxHistBinsGlobal = 1 << 22;  // counts in global memory beyond
-cudaError_t launch_histogram(const pn_inputs& in, const pn_outputs& out, int64_t n, const pn_hist_spec& sp,
-                             unsigned long long* counts, cudaStream_t s);
-cudaError_t launch_moments(const pn_inputs& in, const pn_outputs& out, int64_t n, int q, double* part, int blocks,
-                           cudaStream_t s);
-cudaError_t launch_kde(const pn_inputs& in, const pn_outputs& out, int64_t n, int q, const double* grid, int64_t m,
-                       double h, double count, double* density, cudaStream_t s);
 
 // Parameter and pointer checks shared by the C entry points (pn_capi.cu), and
 // the thread-local error message that pn_last_error(NULL) returns.
