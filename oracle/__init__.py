@@ -110,6 +110,7 @@ def lib():
         L.oracle_uniform.argtypes = [C.c_uint64, C.c_uint64, C.c_uint64]
         L.oracle_uniform.restype = C.c_double
         L.oracle_sample.argtypes = [C.c_uint64, C.POINTER(_Dist), C.c_int64] + [_DP] * 15
+        L.oracle_sample_at.argtypes = [C.c_uint64, C.POINTER(_Dist), C.POINTER(C.c_int64), C.c_int64] + [_DP] * 15
         _lib = L
     return _lib
 
@@ -263,15 +264,20 @@ class Dist:
     omega_f: float = 0.05
 
 
-def sample(seed: int, dist: Dist, n: int) -> dict:
-    """The paper's initial-data draw (Sec. V) from counter-based SplitMix64 uniforms."""
+def sample(seed: int, dist: Dist, n: int, idx=None) -> dict:
+    """The paper's initial-data draw (Sec. V) from counter-based SplitMix64 uniforms: binaries 0..n-1,
+    or the binaries with the given indices (each depends only on the seed and its own index)."""
     d = _Dist(**dist.__dict__)
+    if idx is not None:
+        idx = np.ascontiguousarray(np.asarray(idx, dtype=np.int64))
+        n = idx.shape[0]
     a = {k: np.empty(n) for k in ("m1", "m2", "chi1", "chi2", "omega0", "omega_f")}
     for k in ("s1hat", "s2hat", "lhat"):
         a[k] = np.empty((3, n))
-    lib().oracle_sample(seed, C.byref(d), n, _dp(a["m1"]), _dp(a["m2"]), _dp(a["chi1"]), _dp(a["chi2"]),
-                        _dp(a["s1hat"][0]), _dp(a["s1hat"][1]), _dp(a["s1hat"][2]),
-                        _dp(a["s2hat"][0]), _dp(a["s2hat"][1]), _dp(a["s2hat"][2]),
-                        _dp(a["lhat"][0]), _dp(a["lhat"][1]), _dp(a["lhat"][2]),
-                        _dp(a["omega0"]), _dp(a["omega_f"]))
+    ip = idx.ctypes.data_as(C.POINTER(C.c_int64)) if idx is not None else None
+    lib().oracle_sample_at(seed, C.byref(d), ip, n, _dp(a["m1"]), _dp(a["m2"]), _dp(a["chi1"]), _dp(a["chi2"]),
+                           _dp(a["s1hat"][0]), _dp(a["s1hat"][1]), _dp(a["s1hat"][2]),
+                           _dp(a["s2hat"][0]), _dp(a["s2hat"][1]), _dp(a["s2hat"][2]),
+                           _dp(a["lhat"][0]), _dp(a["lhat"][1]), _dp(a["lhat"][2]),
+                           _dp(a["omega0"]), _dp(a["omega_f"]))
     return a

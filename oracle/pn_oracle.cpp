@@ -827,11 +827,13 @@ double oracle_uniform(uint64_t seed, uint64_t i, uint64_t j) {
 
 // Draw slots: 0 q, 1 chi1, 2 chi2, 3 omega0, then pairs for Marsaglia's method
 // (S1-hat first, S2-hat continuing from the next unused slot; at most 64 pairs each).
-void oracle_sample(uint64_t seed, const ODist* d, int64_t n, double* m1, double* m2, double* chi1,
-                   double* chi2, double* s1x, double* s1y, double* s1z, double* s2x, double* s2y,
-                   double* s2z, double* lx, double* ly, double* lz, double* omega0, double* omega_f) {
+// Binary idx[k] of the draw (every binary's values depend only on the seed and
+// its own index) written to position k; idx == nullptr means idx[k] = k.
+void oracle_sample_at(uint64_t seed, const ODist* d, const int64_t* idx, int64_t n, double* m1, double* m2,
+                      double* chi1, double* chi2, double* s1x, double* s1y, double* s1z, double* s2x, double* s2y,
+                      double* s2z, double* lx, double* ly, double* lz, double* omega0, double* omega_f) {
   for (int64_t i = 0; i < n; i++) {
-    const uint64_t ui = (uint64_t)i;
+    const uint64_t ui = (uint64_t)(idx ? idx[i] : i);
     double q;
     const double u0 = oracle_uniform(seed, ui, 0);
     if (d->q_mode == 0) q = d->q_lo;
@@ -867,6 +869,13 @@ void oracle_sample(uint64_t seed, const ODist* d, int64_t n, double* m1, double*
     }
     lx[i] = 0.0; ly[i] = 0.0; lz[i] = 1.0;
   }
+}
+
+void oracle_sample(uint64_t seed, const ODist* d, int64_t n, double* m1, double* m2, double* chi1,
+                   double* chi2, double* s1x, double* s1y, double* s1z, double* s2x, double* s2y,
+                   double* s2z, double* lx, double* ly, double* lz, double* omega0, double* omega_f) {
+  oracle_sample_at(seed, d, nullptr, n, m1, m2, chi1, chi2, s1x, s1y, s1z, s2x, s2y, s2z, lx, ly, lz, omega0,
+                   omega_f);
 }
 
 }  // extern "C"

@@ -309,3 +309,25 @@ def test_degenerate_configurations(pn, orc):
         assert np.all(m["status"] == 0)
         assert np.all(m["Lhat"][:, zero | aligned] == z[:, None]) and np.all(m["S1"][:, zero] == 0.0)
         assert np.all(m["n_acc"][short] == 1)
+
+
+def test_largest_single_batch_64bit_indexing(pn, orc):
+    """2^26 binaries in one call (about 37 GB of device buffers: inputs, outputs and the set-up table
+    with 37 x 2^26 doubles), drawn on the device by pn_batch_sample; a subsample spread over the whole
+    index range, the last 32 binaries included, against the oracle fed by its own sampler."""
+    import torch
+    n = 1 << 26
+    seed = 0x0908_3889_64
+    with pn.Batch(n) as b:
+        inp = b.sample(seed, pn.dist(q=(1.0, 1.0), chi=(0.0, 1.0), chi_mode=1, omega0=(0.01, 0.01)), n)
+        out = b.integrate(inp)
+        torch.cuda.synchronize()
+        st = b.stats(inp, out)
+        idx = np.union1d(workloads.subsample(n, 2048, seed=workloads.SEED_BASE + 107), np.arange(n - 32, n))
+        it = torch.from_numpy(idx).cuda()
+        g = {k: v.index_select(-1, it).cpu().numpy() for k, v in out.items() if not k.startswith("_")}
+    assert st["count_by_status"][0] == n
+    ens = orc.sample(seed, orc.Dist(q_mode=0, q_lo=1.0, q_hi=1.0, chi_mode=1, chi_lo=0.0, chi_hi=1.0,
+                                    omega0_lo=0.01, omega0_hi=0.01, omega_f=0.05), 0, idx=idx)
+    o = orc.integrate(ens)
+    assert_fp64_parity(g, o, max_divergent=1)
