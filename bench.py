@@ -111,6 +111,26 @@ def aggregate_rate(world: int, n_per_rank: int, steps: int, max_ms: float) -> fl
     return world * n_per_rank * steps / (max_ms * 1e-3)
 
 
+def init_dist(backend: str, device_id=None, timeout_s: float | None = None):
+    """Join the process group with a bounded timeout.
+
+    A rank that never joins makes the others' rendezvous fail after timeout_s, and a
+    rank that leaves between steps makes the others' next barrier or reduction raise
+    (at once when its connection closes, else after timeout_s) instead of waiting
+    forever.  Default: PN_DIST_TIMEOUT_S from the environment, else 300 s.
+    """
+    import datetime
+
+    import torch.distributed as tdist
+    if timeout_s is None:
+        timeout_s = float(os.environ.get("PN_DIST_TIMEOUT_S", "300"))
+    kw = {"timeout": datetime.timedelta(seconds=timeout_s)}
+    if device_id is not None:
+        kw["device_id"] = device_id
+    tdist.init_process_group(backend, **kw)
+    return tdist
+
+
 def reduce_max(x: float, tdist, device) -> float:
     """Max over ranks (a timing reduction only; no data moves between ranks)."""
     if tdist is None:
@@ -279,9 +299,8 @@ def main():
     from paper_0908_3889_b300.build import build
 
     if world > 1:
-        import torch.distributed as tdist
         torch.cuda.set_device(local)
-        tdist.init_process_group("nccl", device_id=torch.device("cuda", local))
+        tdist = init_dist("nccl", device_id=torch.device("cuda", local))
     else:
         tdist = None
         torch.cuda.set_device(0)

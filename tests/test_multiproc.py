@@ -64,3 +64,71 @@ def test_two_gloo_ranks_shard_without_exchange():
     assert t0 != t1                                        # different binaries integrated
     assert mx0 == mx1 == pytest.approx(max(ms0, ms1))      # timing: max over ranks
     assert rate0 == rate1 == pytest.approx(2 * 64 / (mx0 * 1e-3))
+
+
+# ---------------------------------------------------------------------------
+# Failure detection on the host.  The ranks share nothing but the timing
+# reduction and the barriers, so a failed rank must surface on the others as an
+# error from their next collective (or from the rendezvous), not as a wait without
+# end.  The failures are made on the host: a rank that raises, one that never
+# joins, one that leaves between steps.
+
+def _fail_worker(rank, world, port, mode, q):
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank), WORLD_SIZE=str(world),
+                      LOCAL_RANK=str(rank))
+    import time
+
+    import torch
+
+    import bench
+    t0 = time.perf_counter()
+    try:
+        if mode == "never_joins" and rank == 1:
+            q.put((rank, "absent", 0.0))
+            return
+        tdist = bench.init_dist("gloo", timeout_s=4.0)
+        if mode == "raises" and rank == 1:
+            raise RuntimeError("injected failure before the timing reduction")
+        if mode == "leaves" and rank == 1:
+            bench.reduce_max(1.0, tdist, torch.device("cpu"))   # step 1 completes on both ranks
+            q.put((rank, "left", time.perf_counter() - t0))
+            q.close()
+            q.join_thread()                                     # flush the report before leaving
+            os._exit(0)                                         # leaves between steps, no teardown
+        bench.reduce_max(1.0, tdist, torch.device("cpu"))
+        if mode == "leaves":
+            time.sleep(0.5)
+            tdist.barrier()                                     # step 2: the peer is gone
+        q.put((rank, "ok", time.perf_counter() - t0))
+        tdist.destroy_process_group()
+    except RuntimeError as e:       # torch.distributed errors derive from RuntimeError
+        q.put((rank, "error:" + type(e).__name__, time.perf_counter() - t0))
+
+
+def _run_failure_case(mode):
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_fail_worker, args=(r, 2, port, mode, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    res = {}
+    for _ in procs:
+        r, what, dt = q.get(timeout=120)
+        res[r] = (what, dt)
+    for p in procs:
+        p.join(timeout=60)
+        if p.is_alive():            # only the process this test started
+            p.kill()
+            p.join()
+    return res
+
+
+@pytest.mark.parametrize("mode,peer", [("raises", "error:RuntimeError"), ("never_joins", "absent"),
+                                       ("leaves", "left")])
+def test_failed_rank_surfaces_as_an_error_on_the_other(mode, peer):
+    res = _run_failure_case(mode)
+    what0, dt0 = res[0]
+    assert what0.startswith("error:"), res       # rank 0 learns of the failure ...
+    assert dt0 < 60.0, res                       # ... within the bounded timeout, not never
+    assert res[1][0] == peer, res
