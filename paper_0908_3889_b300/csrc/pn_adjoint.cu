@@ -51,7 +51,7 @@ __device__ __forceinline__ void cross_vjp(const double* a, const double* b, cons
 
 __device__ __noinline__ void rhs64_vjp(const Coef<double>& c, const double* __restrict__ tab, const double* y,
                                        const double* fb, double* yb, Coef<double>& cb, double* f) {
-  // ---- forward (as rhs64) ----
+  // ---- forward (the function rhs64 computes, in the A_i, C form) ----
   const double w = y[0];
   const double S1[3] = {y[1], y[2], y[3]}, S2[3] = {y[4], y[5], y[6]}, L[3] = {y[7], y[8], y[9]};
   double r = inv_cbrt(w);
@@ -229,11 +229,12 @@ __constant__ double c_dp_B[6] = {DP_B1, 0.0, DP_B3, DP_B4, DP_B5, DP_B6};
 // apply; same FP64 arithmetic as the forward kernel's stages), writing the six
 // stage states Y_0 = y, ..., Y_5 to sp[(10 s + k) * ss].  With y5 == nullptr
 // only the stage states are made (the last rate k_6 is then not needed).
-__device__ __forceinline__ void dp5_stages(const Coef<double>& c, const double* __restrict__ tab, const double* y,
-                                           double h, double* sp, size_t ss, double* y5) {
+__device__ __forceinline__ void dp5_stages(const Coef<double>& c, const double* __restrict__ tab,
+                                           const float* __restrict__ tabf, const double* y, double h, double* sp,
+                                           size_t ss, double* y5) {
   double K[6][10], ys[10];
   for (int i = 0; i < 10; i++) sp[(size_t)i * ss] = y[i];
-  rhs64(c, tab, y, K[0]);
+  rhs64(c, tab, tabf, y, K[0]);
 #pragma unroll 1
   for (int s = 1; s < 6; s++) {
     for (int i = 0; i < 10; i++) ys[i] = y[i];
@@ -243,7 +244,7 @@ __device__ __forceinline__ void dp5_stages(const Coef<double>& c, const double* 
         for (int i = 0; i < 10; i++) ys[i] = fma(a, K[j][i], ys[i]);
     }
     for (int i = 0; i < 10; i++) sp[(size_t)(10 * s + i) * ss] = ys[i];
-    if (s < 5 || y5) rhs64(c, tab, ys, K[s]);
+    if (s < 5 || y5) rhs64(c, tab, tabf, ys, K[s]);
   }
   if (!y5) return;
   for (int i = 0; i < 10; i++) y5[i] = y[i];
@@ -717,7 +718,7 @@ __device__ void adjoint_one(const AdjArgs& a, const double* __restrict__ tab, co
     for (int32_t n = n0; n < n1s; n++) {  // recompute the segment, keeping the stage states
       double y5[10];
       const bool more = n + 1 < n1s;
-      dp5_stages(c, tab, y, a.h[(size_t)n * a.stride + i], sp0 + (size_t)(n - n0) * step_words, ss,
+      dp5_stages(c, tab, tabf, y, a.h[(size_t)n * a.stride + i], sp0 + (size_t)(n - n0) * step_words, ss,
                  more ? y5 : nullptr);
       if (more)
         for (int k = 0; k < 10; k++) y[k] = y5[k];
@@ -778,7 +779,7 @@ __global__ void __launch_bounds__(128) k_adjoint(const AdjArgs a) {
   __shared__ double s_tab[256];
   __shared__ float s_tabf[512];
   for (int q = threadIdx.x; q < 256; q += blockDim.x) s_tab[q] = a.k.tab[q];
-  if (DS) {
+  {
     const float* gf = reinterpret_cast<const float*>(a.k.tab + 256);
     for (int q = threadIdx.x; q < 512; q += blockDim.x) s_tabf[q] = gf[q];
   }

@@ -108,6 +108,15 @@ __device__ __forceinline__ double rcp_pos(double x) {
   return fma(r, fma(e, e, e), r);
 }
 
+// 1/x for positive normal x to within 3.3e-14 relative, for the error norm:
+// FP32 reciprocal seed r (|e| <= 1.8e-7), then r (1 + e), e = 1 - x r.  The
+// norm only feeds the accept test and the step-size factor, where a relative
+// change of 1e-13 moves the next step size by ~1e-14 of itself.
+__device__ __forceinline__ double rcp_norm(double x) {
+  const double r = seed_f64(__frcp_rn(seed_f32(x)));
+  return fma(r, fma(-x, r, 1.0), r);
+}
+
 // s^(-1/10) for s in [2^-126, 2^128): FP32 exp2/log2 seed, then
 // z (1 + e/10 + 11 e^2/200), e = 1 - s z^10 (the series of (1 - e)^(-1/10)).
 __device__ __forceinline__ double pow_m_tenth(double s) {
@@ -216,6 +225,8 @@ __device__ __forceinline__ Coef<float> to_f32(const Coef<double>& c) {
   return f;
 }
 
+__device__ __forceinline__ double log_w(double x, const double* __restrict__ tab, const float* __restrict__ tabf);
+
 // ---------------------------------------------------------------------------
 // Right-hand side f(y), y = (omega, S1, S2, L), M = 1, x = omega, v = x^{1/3}.
 //   Eq. (1): domega/dt = (96/5) eta omega^2 v^5 P, P = 1 + c1 v^2 - SO v^3
@@ -225,11 +236,13 @@ __device__ __forceinline__ Coef<float> to_f32(const Coef<double>& c) {
 //            with chi_i S_i-hat = S_i / m_i^2.
 //   Eq. (4): Omega_1 = (x^2/2) [eta v^{-1} (4 + 3 m2/m1) L + S2 - 3 (S2.L) L], 1<->2.
 //   Eq. (2): dS_i/dt = Omega_i x S_i.   Eq. (3): dL/dt = -(v/eta)(dS1/dt + dS2/dt).
-// Written with A_i = L x S_i and C = S1 x S2:
-//   dS1/dt = (x^2/2)[(a1/v - 3 L.S2) A1 - C],  dS2/dt = (x^2/2)[(a2/v - 3 L.S1) A2 + C].
+// With a_i = eta (4 + 3 m_j/m_i) and q_i = a_i/v - 3 L.S_j (j the other body):
+//   Omega_i = (x^2/2) U_i,  U_i = q_i L + S_j,  dS_i/dt = (x^2/2) (U_i x S_i).
+// The adjoint's rhs64_vjp differentiates the equivalent form with A_i = L x S_i
+// and C = S1 x S2: dS1/dt = (x^2/2)[q1 A1 - C], dS2/dt = (x^2/2)[q2 A2 + C].
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ void rhs64(const Coef<double>& c, const double* __restrict__ tab, const double* y,
-                                      double* f) {
+__device__ __forceinline__ void rhs64(const Coef<double>& c, const double* __restrict__ tab,
+                                      const float* __restrict__ tabf, const double* y, double* f) {
   const double w = y[0];
   const double S1x = y[1], S1y = y[2], S1z = y[3];
   const double S2x = y[4], S2y = y[5], S2z = y[6];
@@ -240,7 +253,7 @@ __device__ __forceinline__ void rhs64(const Coef<double>& c, const double* __res
   if ((hi32(w) & 0x7fffffffu) - (897u << 20) >= ((1151u - 897u) << 20)) r = dnan();
   const double v = w * (r * r);
   const double v2 = v * v;
-  const double lw = log_tang(w, tab);
+  const double lw = log_w(w, tab, tabf);
 
   const double LS1 = fma(Lz, S1z, fma(Ly, S1y, Lx * S1x));
   const double LS2 = fma(Lz, S2z, fma(Ly, S2y, Lx * S2x));
@@ -258,15 +271,17 @@ __device__ __forceinline__ void rhs64(const Coef<double>& c, const double* __res
   const double w2 = w * w;
   f[0] = (((w2 * w) * v2) * c.K) * P;
 
-  const double A1x = fma(Ly, S1z, -Lz * S1y), A1y = fma(Lz, S1x, -Lx * S1z), A1z = fma(Lx, S1y, -Ly * S1x);
-  const double A2x = fma(Ly, S2z, -Lz * S2y), A2y = fma(Lz, S2x, -Lx * S2z), A2z = fma(Lx, S2y, -Ly * S2x);
-  const double Cx = fma(S1y, S2z, -S1z * S2y), Cy = fma(S1z, S2x, -S1x * S2z), Cz = fma(S1x, S2y, -S1y * S2x);
+  // Eq. (4) as Omega_i = pre U_i with U_1 = q1 L + S2, q1 = a1/v - 3 L.S2 (1 <-> 2),
+  // and dS_i/dt = pre (U_i x S_i): 29 FP64 operations for both spins.
+  const double q1 = fma(c.a1, r, -3.0 * LS2);
+  const double q2 = fma(c.a2, r, -3.0 * LS1);
+  const double U1x = fma(q1, Lx, S2x), U1y = fma(q1, Ly, S2y), U1z = fma(q1, Lz, S2z);
+  const double U2x = fma(q2, Lx, S1x), U2y = fma(q2, Ly, S1y), U2z = fma(q2, Lz, S1z);
   const double pre = c.prec * w2;
-  const double p1 = pre * fma(c.a1, r, -3.0 * LS2);
-  const double p2 = pre * fma(c.a2, r, -3.0 * LS1);
-  const double pCx = pre * Cx, pCy = pre * Cy, pCz = pre * Cz;
-  const double d1x = fma(p1, A1x, -pCx), d1y = fma(p1, A1y, -pCy), d1z = fma(p1, A1z, -pCz);
-  const double d2x = fma(p2, A2x, pCx), d2y = fma(p2, A2y, pCy), d2z = fma(p2, A2z, pCz);
+  const double d1x = pre * fma(U1y, S1z, -U1z * S1y), d1y = pre * fma(U1z, S1x, -U1x * S1z),
+               d1z = pre * fma(U1x, S1y, -U1y * S1x);
+  const double d2x = pre * fma(U2y, S2z, -U2z * S2y), d2y = pre * fma(U2z, S2x, -U2x * S2z),
+               d2z = pre * fma(U2x, S2y, -U2y * S2x);
   f[1] = d1x; f[2] = d1y; f[3] = d1z;
   f[4] = d2x; f[5] = d2y; f[6] = d2z;
   const double lf = v * c.nie;
@@ -388,6 +403,35 @@ __device__ __forceinline__ ds split64(double d) {
 // double-single -> double (exact sum of the two parts).
 __device__ __forceinline__ double ds_to_f64(ds a) { return f32_to_f64(a.hi) + f32_to_f64(a.lo); }
 
+// ln|x| for the FP64 right-hand side, for |x| in the normal double range.
+// With |x| = 2^k m and F = 1 + (2j+1)/256 as in log_tang, f = m - F is exact
+// in FP64 and |f| <= 2^-8.  k ln2 + ln F is summed in FP64 (one FMA with the
+// double nearest ln 2, so |k| 2.3e-17 of representation error, 1.6e-16 for
+// the omegas of an inspiral); the remainder ln(1 + u), u = f/F, is evaluated
+// in double-single on the FP32 pipe: u, u^2/2 and u^3/3 as pairs and
+// u^4 (-1/4 + u/5 - u^2/6) in FP32 (below 1.1e-10, so its rounding is under
+// 1e-16 of it), truncation u^7/7 < 2.4e-18.  The remainder is thus within
+// ~1e-17 absolute, and the result carries only the FP64 roundings of the two
+// final sums, with five FP64 instructions instead of log_tang's thirteen.
+// tabf[4j..4j+3] = 1/F_j (hi, lo), ln F_j (hi, lo); tab[2j+1] = ln F_j.
+__device__ __forceinline__ double log_w(double x, const double* __restrict__ tab, const float* __restrict__ tabf) {
+  const uint32_t hx = hi32(x) & 0x7fffffffu;
+  const int k = (int)(hx >> 20) - 1023;
+  const uint32_t j = (hx >> 13) & 127u;
+  const double m = mk64((hx & 0x000fffffu) | 0x3ff00000u, lo32(x));
+  const double F = mk64(0x3ff00000u | ((2u * j + 1u) << 12), 0u);
+  const ds u = ds_mul(split64(m - F), ds{tabf[4 * j], tabf[4 * j + 1]});
+  const ds u2 = ds_mul(u, u);
+  const ds t3 = ds_mul(ds_mul(u2, u), ds{(float)(1.0 / 3.0), (float)(1.0 / 3.0 - (double)(float)(1.0 / 3.0))});
+  const float uh = u.hi;
+  float q = __fmaf_rn(uh, -1.0f / 6.0f, 0.2f);
+  q = __fmaf_rn(q, uh, -0.25f);
+  const float t4 = __fmul_rn(__fmul_rn(u2.hi, u2.hi), q);
+  const ds rem = ds_add(u, ds_add(ds_scale(u2, -0.5f), ds_add(t3, ds_of(t4))));
+  const double kd = mk64(0x43300000u, (uint32_t)k ^ 0x80000000u) - 4503601774854144.0;
+  return fma(kd, 0.6931471805599453, tab[2 * j + 1]) + ds_to_f64(rem);
+}
+
 // x^(-1/3) in double-single: FP32 seed r0 = rcbrtf(hi), then
 // r0 (1 + e/3 + 2e^2/9) with e = 1 - x r0^3 formed in double-single.
 __device__ __forceinline__ ds ds_inv_cbrt(ds x) {
@@ -495,8 +539,8 @@ struct Coefs {
   Coef<ds> cds;
 };
 struct Tabs {
-  const double* d;  // 256 doubles for log_tang
-  const float* f;   // 512 floats for ds_log
+  const double* d;  // 256 doubles: 1/F_j, ln F_j
+  const float* f;   // 512 floats: 1/F_j, ln F_j as FP32 pairs (ds_log, log_w)
 };
 
 // ---------------------------------------------------------------------------
@@ -546,7 +590,7 @@ struct Ctl {
 template <int PREC>
 __device__ __forceinline__ void eval_rhs(const Coefs& cf, const Tabs& tb, const double* y, double* k) {
   if constexpr (PREC == 0) {
-    rhs64(cf.c64, tb.d, y, k);
+    rhs64(cf.c64, tb.d, tb.f, y, k);
   } else if constexpr (PREC == 1) {
     float yf[10], kf[10];
 #pragma unroll
@@ -609,16 +653,17 @@ __device__ __forceinline__ double dp5_attempt(const Coefs& cf, const Tabs& tb, c
       y5[i] = fma(b6, k6[i], fma(b5, k5[i], fma(b4, k4[i], fma(b3, k3[i], fma(b1, k1[i], y[i])))));
   }
   eval_rhs<PREC>(cf, tb, y5, k7);
-  const double e1 = h * DP_E1, e3 = h * DP_E3, e4 = h * DP_E4, e5 = h * DP_E5, e6 = h * DP_E6, e7 = h * DP_E7;
+  // The error estimate without its factor h (applied to the sum as h^2).
   double sum = 0.0;
 #pragma unroll
   for (int i = 0; i < 10; i++) {
-    const double e = fma(e7, k7[i], fma(e6, k6[i], fma(e5, k5[i], fma(e4, k4[i], fma(e3, k3[i], e1 * k1[i])))));
+    const double e = fma(DP_E7, k7[i], fma(DP_E6, k6[i], fma(DP_E5, k5[i], fma(DP_E4, k4[i],
+                     fma(DP_E3, k3[i], DP_E1 * k1[i])))));
     const double sc = fma(ctl.rtol, max_abs(y[i], y5[i]), ctl.atol);
-    const double q = e * rcp_pos(sc);
+    const double q = e * rcp_norm(sc);
     sum = fma(q, q, sum);
   }
-  return sum * 0.1;
+  return sum * ((h * h) * 0.1);
 }
 
 // The mixed-precision attempt (FP32 right-hand side).  The stage inputs
@@ -687,18 +732,17 @@ __device__ __forceinline__ double dp5_attempt_f32(const Coef<float>& c, const Ct
       for (int i = 0; i < 10; i++) w.put(r + 1, i, kn[i]);
     }
   }
-  const double e1 = h * DP_E1, e3 = h * DP_E3, e4 = h * DP_E4, e5 = h * DP_E5, e6 = h * DP_E6, e7 = h * DP_E7;
   double sum = 0.0;
 #pragma unroll
   for (int i = 0; i < 10; i++) {
     k7[i] = f32_to_f64(kn[i]);
-    const double e = fma(e7, k7[i], fma(e6, f32_to_f64(w.get(5, i)), fma(e5, f32_to_f64(w.get(4, i)),
-                     fma(e4, f32_to_f64(w.get(3, i)), fma(e3, f32_to_f64(w.get(2, i)), e1 * k1[i])))));
+    const double e = fma(DP_E7, k7[i], fma(DP_E6, f32_to_f64(w.get(5, i)), fma(DP_E5, f32_to_f64(w.get(4, i)),
+                     fma(DP_E4, f32_to_f64(w.get(3, i)), fma(DP_E3, f32_to_f64(w.get(2, i)), DP_E1 * k1[i])))));
     const double sc = fma(ctl.rtol, max_abs(y[i], y5[i]), ctl.atol);
-    const double q = e * rcp_pos(sc);
+    const double q = e * rcp_norm(sc);
     sum = fma(q, q, sum);
   }
-  return sum * 0.1;
+  return sum * ((h * h) * 0.1);
 }
 
 // ---------------------------------------------------------------------------
@@ -823,7 +867,7 @@ __device__ __forceinline__ double dp5_attempt_ds(const Coefs& cf, const Tabs& tb
     k7[c] = ds_to_f64(kn[c]);
     const double e = ds_to_f64(w.get(1, c));
     const double sc = fma(ctl.rtol, max_abs(y[c], y5[c]), ctl.atol);
-    const double q = e * rcp_pos(sc);
+    const double q = e * rcp_norm(sc);
     sum = fma(q, q, sum);
   }
   return sum * 0.1;

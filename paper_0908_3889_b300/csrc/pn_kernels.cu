@@ -41,7 +41,8 @@ template <int PREC>
 __device__ __forceinline__ Tabs load_tabs(const double* __restrict__ g, double* s_tab, float* s_tabf) {
   if constexpr (PREC == 0) {
     for (int q = threadIdx.x; q < 256; q += blockDim.x) s_tab[q] = g[q];
-  } else if constexpr (PREC == 2) {
+  }
+  if constexpr (PREC == 0 || PREC == 2) {
     const float* gf = (const float*)(g + 256);
     for (int q = threadIdx.x; q < 512; q += blockDim.x) s_tabf[q] = gf[q];
   }
