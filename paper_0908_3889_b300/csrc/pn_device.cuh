@@ -314,15 +314,16 @@ __device__ __forceinline__ void rhs32(const Coef<float>& c, const float* y, floa
   P = fmaf(v2, P, 1.0f);
   const float w2 = w * w;
   f[0] = (((w2 * w) * v2) * c.K) * P;
-  const float A1x = fmaf(Ly, S1z, -Lz * S1y), A1y = fmaf(Lz, S1x, -Lx * S1z), A1z = fmaf(Lx, S1y, -Ly * S1x);
-  const float A2x = fmaf(Ly, S2z, -Lz * S2y), A2y = fmaf(Lz, S2x, -Lx * S2z), A2z = fmaf(Lx, S2y, -Ly * S2x);
-  const float Cx = fmaf(S1y, S2z, -S1z * S2y), Cy = fmaf(S1z, S2x, -S1x * S2z), Cz = fmaf(S1x, S2y, -S1y * S2x);
+  // Eq. (4) as in rhs64: dS_i/dt = pre (U_i x S_i), U_1 = q1 L + S2, q1 = a1/v - 3 L.S2.
+  const float q1 = fmaf(c.a1, r, -3.0f * LS2);
+  const float q2 = fmaf(c.a2, r, -3.0f * LS1);
+  const float U1x = fmaf(q1, Lx, S2x), U1y = fmaf(q1, Ly, S2y), U1z = fmaf(q1, Lz, S2z);
+  const float U2x = fmaf(q2, Lx, S1x), U2y = fmaf(q2, Ly, S1y), U2z = fmaf(q2, Lz, S1z);
   const float pre = c.prec * w2;
-  const float p1 = pre * fmaf(c.a1, r, -3.0f * LS2);
-  const float p2 = pre * fmaf(c.a2, r, -3.0f * LS1);
-  const float pCx = pre * Cx, pCy = pre * Cy, pCz = pre * Cz;
-  const float d1x = fmaf(p1, A1x, -pCx), d1y = fmaf(p1, A1y, -pCy), d1z = fmaf(p1, A1z, -pCz);
-  const float d2x = fmaf(p2, A2x, pCx), d2y = fmaf(p2, A2y, pCy), d2z = fmaf(p2, A2z, pCz);
+  const float d1x = pre * fmaf(U1y, S1z, -U1z * S1y), d1y = pre * fmaf(U1z, S1x, -U1x * S1z),
+              d1z = pre * fmaf(U1x, S1y, -U1y * S1x);
+  const float d2x = pre * fmaf(U2y, S2z, -U2z * S2y), d2y = pre * fmaf(U2z, S2x, -U2x * S2z),
+              d2z = pre * fmaf(U2x, S2y, -U2y * S2x);
   f[1] = d1x; f[2] = d1y; f[3] = d1z;
   f[4] = d2x; f[5] = d2y; f[6] = d2z;
   const float lf = v * c.nie;
@@ -503,18 +504,18 @@ __device__ __forceinline__ void rhs_ds(const Coef<ds>& c, const float* __restric
   P = ds_fma(v2, P, ds_of(1.0f));
   const ds w2 = ds_mul(w, w);
   f[0] = ds_mul(ds_mul(ds_mul(ds_mul(w2, w), v2), c.K), P);
-  const ds A1x = ds_sub(ds_mul(Ly, S1z), ds_mul(Lz, S1y)), A1y = ds_sub(ds_mul(Lz, S1x), ds_mul(Lx, S1z)),
-           A1z = ds_sub(ds_mul(Lx, S1y), ds_mul(Ly, S1x));
-  const ds A2x = ds_sub(ds_mul(Ly, S2z), ds_mul(Lz, S2y)), A2y = ds_sub(ds_mul(Lz, S2x), ds_mul(Lx, S2z)),
-           A2z = ds_sub(ds_mul(Lx, S2y), ds_mul(Ly, S2x));
-  const ds Cx = ds_sub(ds_mul(S1y, S2z), ds_mul(S1z, S2y)), Cy = ds_sub(ds_mul(S1z, S2x), ds_mul(S1x, S2z)),
-           Cz = ds_sub(ds_mul(S1x, S2y), ds_mul(S1y, S2x));
+  // Eq. (4) as in rhs64: dS_i/dt = pre (U_i x S_i), U_1 = q1 L + S2, q1 = a1/v - 3 L.S2.
+  const ds q1 = ds_fma(c.a1, r, ds_mul_f(LS2, -3.0f));
+  const ds q2 = ds_fma(c.a2, r, ds_mul_f(LS1, -3.0f));
+  const ds U1x = ds_fma(q1, Lx, S2x), U1y = ds_fma(q1, Ly, S2y), U1z = ds_fma(q1, Lz, S2z);
+  const ds U2x = ds_fma(q2, Lx, S1x), U2y = ds_fma(q2, Ly, S1y), U2z = ds_fma(q2, Lz, S1z);
   const ds pre = ds_mul(c.prec, w2);
-  const ds p1 = ds_mul(pre, ds_fma(c.a1, r, ds_mul_f(LS2, -3.0f)));
-  const ds p2 = ds_mul(pre, ds_fma(c.a2, r, ds_mul_f(LS1, -3.0f)));
-  const ds pCx = ds_mul(pre, Cx), pCy = ds_mul(pre, Cy), pCz = ds_mul(pre, Cz);
-  const ds d1x = ds_sub(ds_mul(p1, A1x), pCx), d1y = ds_sub(ds_mul(p1, A1y), pCy), d1z = ds_sub(ds_mul(p1, A1z), pCz);
-  const ds d2x = ds_fma(p2, A2x, pCx), d2y = ds_fma(p2, A2y, pCy), d2z = ds_fma(p2, A2z, pCz);
+  const ds d1x = ds_mul(pre, ds_sub(ds_mul(U1y, S1z), ds_mul(U1z, S1y)));
+  const ds d1y = ds_mul(pre, ds_sub(ds_mul(U1z, S1x), ds_mul(U1x, S1z)));
+  const ds d1z = ds_mul(pre, ds_sub(ds_mul(U1x, S1y), ds_mul(U1y, S1x)));
+  const ds d2x = ds_mul(pre, ds_sub(ds_mul(U2y, S2z), ds_mul(U2z, S2y)));
+  const ds d2y = ds_mul(pre, ds_sub(ds_mul(U2z, S2x), ds_mul(U2x, S2z)));
+  const ds d2z = ds_mul(pre, ds_sub(ds_mul(U2x, S2y), ds_mul(U2y, S2x)));
   f[1] = d1x; f[2] = d1y; f[3] = d1z;
   f[4] = d2x; f[5] = d2y; f[6] = d2z;
   const ds lf = ds_mul(v, c.nie);
