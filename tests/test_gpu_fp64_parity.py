@@ -184,17 +184,23 @@ def test_land_exactly_on_omega_f(pn):
     assert np.max(np.abs(g["omega"] / 0.05 - 1)) < 1e-15
 
 
-def test_host_buffer_entry_point_matches_device(pn):
-    import torch
-    ens = workloads.config("C1", n=5000)
-    dev = run_gpu(pn, ens)
-    hin = pn.to_device(ens, device="cpu", pin_memory=True)
-    hout = pn.alloc_outputs(5000, pin_memory=True)
-    with pn.Batch(5000) as b:
-        pn.pn_batch_integrate_host(b.handle, 5000, hin, hout)
-    h = pn.to_numpy(hout)
+@pytest.mark.parametrize("n,precision,pinned", [(5000, 0, True), (300_000, 0, True), (300_000, 2, True),
+                                                (300_000, 1, False), (1_048_576, 0, True)])
+def test_host_buffer_entry_point_matches_device(pn, n, precision, pinned):
+    """The host-buffer entry point against the device-buffer one: bit-identical outputs in every
+    precision, from pinned or pageable host memory, up to the bench's 1,048,576 binaries."""
+    ens = workloads.config("C1", n=n)
+    dev = run_gpu(pn, ens, precision=precision)
+    hin = pn.to_device(ens, device="cpu", pin_memory=pinned)
+    hout = pn.alloc_outputs(n, device="cpu", pin_memory=pinned)
+    with pn.Batch(n, pn.params(precision=precision)) as b:
+        pn.pn_batch_integrate_host(b.handle, n, hin, hout)
+        h1 = pn.to_numpy(hout)
+        pn.pn_batch_integrate_host(b.handle, n - 1000, hin, hout)   # a second, shorter call on the same batch
+        h2 = pn.to_numpy(hout)
     for k in dev:
-        assert np.array_equal(dev[k], h[k], equal_nan=True), k
+        assert np.array_equal(dev[k], h1[k], equal_nan=True), k
+        assert np.array_equal(dev[k][:n - 1000], h2[k][:n - 1000], equal_nan=True), k
 
 
 def test_repeat_calls_reuse_graph_and_agree(pn):
