@@ -669,10 +669,15 @@ __device__ __forceinline__ double dp5_attempt(const Coefs& cf, const Tabs& tb, c
 
 // The mixed-precision attempt (FP32 right-hand side).  The stage inputs
 // Y_2..Y_6 only feed the FP32 right-hand side, which rounds them to FP32 on
-// entry, so they are formed in FP32 from the FP32-rounded state; the new state
-// y5 = y + h sum_j b_j k_j (the state accumulation), the embedded error
-// estimate, its norm and the step control are FP64, with the FP32 rates widened
-// exactly.  Conversions between the two formats are integer operations.  The
+// entry, so they are formed in FP32 from the FP32-rounded state.  The rates are
+// FP32 values, so the sums over them that need more than FP32 -- the increment
+// sum_j b_j k_j of the new state and the embedded error estimate, which cancels
+// to ~tol of its terms -- are compensated double-single sums on the FP32 pipe
+// (~2^-48 relative).  The state accumulation y5 = y + h (increment) is one FP64
+// FMA per component; the error norm is taken in FP32 from the estimate's
+// leading float (the FP32 rates already perturb it by ~1e-3 of itself); the
+// accept test and the step-size update are FP64.  Conversions between the two
+// formats are integer operations.  The
 // six stages run as one loop so that the right-hand side is emitted once
 // (seven inlined copies overflow the instruction cache); the rates k1..k6 sit
 // in a per-thread shared-memory workspace (lane-interleaved: rate j, component
@@ -693,58 +698,6 @@ __constant__ float c_dp_a_f[5][5] = {
     {(float)DP_A51, (float)DP_A52, (float)DP_A53, (float)DP_A54, 0},
     {(float)DP_A61, (float)DP_A62, (float)DP_A63, (float)DP_A64, (float)DP_A65},
 };
-
-__device__ __forceinline__ double dp5_attempt_f32(const Coef<float>& c, const Ctl& ctl, const double* y,
-                                                  const double* k1, double h, double* y5, double* k7,
-                                                  const F32Work& w) {
-  float yf[10], ys[10], kn[10];
-  const float hf = f64_to_f32(h);
-#pragma unroll
-  for (int i = 0; i < 10; i++) {
-    yf[i] = f64_to_f32(y[i]);
-    w.put(0, i, f64_to_f32(k1[i]));  // k1 is an FP32 rate widened: exact
-  }
-#pragma unroll 1
-  for (int r = 0; r < 6; r++) {
-    if (r < 5) {
-      const float a0 = hf * c_dp_a_f[r][0], a1 = hf * c_dp_a_f[r][1], a2 = hf * c_dp_a_f[r][2],
-                  a3 = hf * c_dp_a_f[r][3], a4 = hf * c_dp_a_f[r][4];
-#pragma unroll
-      for (int i = 0; i < 10; i++) {
-        float acc = fmaf(a0, w.get(0, i), yf[i]);
-        if (r >= 1) acc = fmaf(a1, w.get(1, i), acc);
-        if (r >= 2) acc = fmaf(a2, w.get(2, i), acc);
-        if (r >= 3) acc = fmaf(a3, w.get(3, i), acc);
-        if (r >= 4) acc = fmaf(a4, w.get(4, i), acc);
-        ys[i] = acc;
-      }
-    } else {  // the 5th-order solution, accumulated in FP64
-      const double b1 = h * DP_B1, b3 = h * DP_B3, b4 = h * DP_B4, b5 = h * DP_B5, b6 = h * DP_B6;
-#pragma unroll
-      for (int i = 0; i < 10; i++) {
-        y5[i] = fma(b6, f32_to_f64(w.get(5, i)), fma(b5, f32_to_f64(w.get(4, i)), fma(b4, f32_to_f64(w.get(3, i)),
-                fma(b3, f32_to_f64(w.get(2, i)), fma(b1, k1[i], y[i])))));
-        ys[i] = f64_to_f32(y5[i]);
-      }
-    }
-    rhs32(c, ys, kn);  // k_{r+2}; for r = 5, k7 = f(y5)
-    if (r < 5) {
-#pragma unroll
-      for (int i = 0; i < 10; i++) w.put(r + 1, i, kn[i]);
-    }
-  }
-  double sum = 0.0;
-#pragma unroll
-  for (int i = 0; i < 10; i++) {
-    k7[i] = f32_to_f64(kn[i]);
-    const double e = fma(DP_E7, k7[i], fma(DP_E6, f32_to_f64(w.get(5, i)), fma(DP_E5, f32_to_f64(w.get(4, i)),
-                     fma(DP_E4, f32_to_f64(w.get(3, i)), fma(DP_E3, f32_to_f64(w.get(2, i)), DP_E1 * k1[i])))));
-    const double sc = fma(ctl.rtol, max_abs(y[i], y5[i]), ctl.atol);
-    const double q = e * rcp_norm(sc);
-    sum = fma(q, q, sum);
-  }
-  return sum * ((h * h) * 0.1);
-}
 
 // ---------------------------------------------------------------------------
 // The double-single attempt.  Its stage inputs feed the double-single
@@ -797,6 +750,84 @@ __device__ __forceinline__ dacc dot_add(dacc a, dsc c, ds x) {
   return dacc{t.hi, __fadd_rn(a.e, __fadd_rn(t.lo, e))};
 }
 __device__ __forceinline__ ds dot_val(dacc a) { return two_sum(a.s, a.e); }
+
+// The same for FP32 values x (exact floats: no low part).
+__device__ __forceinline__ dacc dot_first_f(dsc c, float x) {
+  const float p = __fmul_rn(c.hi, x);
+  return dacc{p, __fmaf_rn(c.lo, x, __fmaf_rn(c.hi, x, -p))};
+}
+__device__ __forceinline__ dacc dot_add_f(dacc a, dsc c, float x) {
+  const float p = __fmul_rn(c.hi, x);
+  const float e = __fmaf_rn(c.lo, x, __fmaf_rn(c.hi, x, -p));
+  const ds t = two_sum(a.s, p);
+  return dacc{t.hi, __fadd_rn(a.e, __fadd_rn(t.lo, e))};
+}
+
+// The FP32-RHS attempt (declared with its workspace above).
+__device__ __forceinline__ double dp5_attempt_f32(const Coef<float>& c, const Ctl& ctl, const double* y,
+                                                  const double* k1, double h, double* y5, double* k7,
+                                                  const F32Work& w) {
+  float yf[10], ys[10], kn[10];
+  const float hf = f64_to_f32(h);
+#pragma unroll
+  for (int i = 0; i < 10; i++) {
+    yf[i] = f64_to_f32(y[i]);
+    w.put(0, i, f64_to_f32(k1[i]));  // k1 is an FP32 rate widened: exact
+  }
+#pragma unroll 1
+  for (int r = 0; r < 6; r++) {
+    if (r < 5) {
+      const float a0 = hf * c_dp_a_f[r][0], a1 = hf * c_dp_a_f[r][1], a2 = hf * c_dp_a_f[r][2],
+                  a3 = hf * c_dp_a_f[r][3], a4 = hf * c_dp_a_f[r][4];
+#pragma unroll
+      for (int i = 0; i < 10; i++) {
+        float acc = fmaf(a0, w.get(0, i), yf[i]);
+        if (r >= 1) acc = fmaf(a1, w.get(1, i), acc);
+        if (r >= 2) acc = fmaf(a2, w.get(2, i), acc);
+        if (r >= 3) acc = fmaf(a3, w.get(3, i), acc);
+        if (r >= 4) acc = fmaf(a4, w.get(4, i), acc);
+        ys[i] = acc;
+      }
+    } else {  // the 5th-order solution y5 = y + h inc, inc = sum_j b_j k_j compensated, then one FP64 FMA
+#pragma unroll
+      for (int i = 0; i < 10; i++) {
+        dacc acc = dot_first_f(c_dp_a_ds[5][0], w.get(0, i));
+        acc = dot_add_f(acc, c_dp_a_ds[5][2], w.get(2, i));
+        acc = dot_add_f(acc, c_dp_a_ds[5][3], w.get(3, i));
+        acc = dot_add_f(acc, c_dp_a_ds[5][4], w.get(4, i));
+        acc = dot_add_f(acc, c_dp_a_ds[5][5], w.get(5, i));
+        const ds inc = dot_val(acc);
+        y5[i] = fma(h, f32_to_f64(inc.hi) + f32_to_f64(inc.lo), y[i]);
+        ys[i] = f64_to_f32(y5[i]);
+      }
+    }
+    rhs32(c, ys, kn);  // k_{r+2}; for r = 5, k7 = f(y5)
+    if (r < 5) {
+#pragma unroll
+      for (int i = 0; i < 10; i++) w.put(r + 1, i, kn[i]);
+    }
+  }
+  // Error estimate sum_j (b_j - bhat_j) k_j compensated (it cancels to ~tol of its terms), its
+  // scaled RMS norm in FP32 from the estimate's leading float; h enters once, in FP64.
+  const float rtf = f64_to_f32(ctl.rtol), atf = f64_to_f32(ctl.atol);
+  float sf = 0.0f;
+#pragma unroll
+  for (int i = 0; i < 10; i++) {
+    k7[i] = f32_to_f64(kn[i]);
+    dacc acc = dot_first_f(c_dp_e_ds[0], w.get(0, i));
+    acc = dot_add_f(acc, c_dp_e_ds[1], w.get(2, i));
+    acc = dot_add_f(acc, c_dp_e_ds[2], w.get(3, i));
+    acc = dot_add_f(acc, c_dp_e_ds[3], w.get(4, i));
+    acc = dot_add_f(acc, c_dp_e_ds[4], w.get(5, i));
+    acc = dot_add_f(acc, c_dp_e_ds[5], kn[i]);
+    const float e = __fadd_rn(acc.s, acc.e);
+    const float sc = __fmaf_rn(rtf, fmaxf(fabsf(yf[i]), fabsf(ys[i])), atf);
+    const float q = __fmul_rn(e, __frcp_rn(sc));
+    sf = __fmaf_rn(q, q, sf);
+  }
+  return f32_to_f64(sf) * ((h * h) * 0.1);
+}
+
 
 // Per-thread workspace of dp5_attempt_ds in shared memory, lane-interleaved so
 // that a warp's accesses are 32 consecutive 8-byte words: vector v, component
