@@ -683,7 +683,10 @@ __device__ __forceinline__ double dp5_attempt(const Coefs& cf, const Tabs& tb, c
 // in a per-thread shared-memory workspace (lane-interleaved: rate j, component
 // c of thread t at base[(j * 10 + c) * nthreads + t]) so no register queue has
 // to be shifted between stages.
-constexpr int kF32WorkBytes = 6 * 10 * 4;  // per thread
+// Slots 0..5 hold k1..k6; slot 1 takes k7 once k2 is spent (its weights in b and
+// in b - bhat are 0); slots 6 and 7 the increment of y5 (hi, lo), then slot 6
+// the error scale.
+constexpr int kF32WorkBytes = 8 * 10 * 4;  // per thread
 struct F32Work {
   float* base;
   int nt, t;
@@ -789,15 +792,20 @@ __device__ __forceinline__ double dp5_attempt_f32(const Coef<float>& c, const Ct
         ys[i] = acc;
       }
     } else {  // the 5th-order solution y5 = y + h inc, inc = sum_j b_j k_j compensated, then one FP64 FMA
-#pragma unroll
-      for (int i = 0; i < 10; i++) {
+#pragma unroll 1
+      for (int i = 0; i < 10; i++) {  // rolled: the compensated sums would not fit the instruction cache x10
         dacc acc = dot_first_f(c_dp_a_ds[5][0], w.get(0, i));
         acc = dot_add_f(acc, c_dp_a_ds[5][2], w.get(2, i));
         acc = dot_add_f(acc, c_dp_a_ds[5][3], w.get(3, i));
         acc = dot_add_f(acc, c_dp_a_ds[5][4], w.get(4, i));
         acc = dot_add_f(acc, c_dp_a_ds[5][5], w.get(5, i));
         const ds inc = dot_val(acc);
-        y5[i] = fma(h, f32_to_f64(inc.hi) + f32_to_f64(inc.lo), y[i]);
+        w.put(6, i, inc.hi);
+        w.put(7, i, inc.lo);
+      }
+#pragma unroll
+      for (int i = 0; i < 10; i++) {
+        y5[i] = fma(h, f32_to_f64(w.get(6, i)) + f32_to_f64(w.get(7, i)), y[i]);
         ys[i] = f64_to_f32(y5[i]);
       }
     }
@@ -810,19 +818,23 @@ __device__ __forceinline__ double dp5_attempt_f32(const Coef<float>& c, const Ct
   // Error estimate sum_j (b_j - bhat_j) k_j compensated (it cancels to ~tol of its terms), its
   // scaled RMS norm in FP32 from the estimate's leading float; h enters once, in FP64.
   const float rtf = f64_to_f32(ctl.rtol), atf = f64_to_f32(ctl.atol);
-  float sf = 0.0f;
 #pragma unroll
   for (int i = 0; i < 10; i++) {
     k7[i] = f32_to_f64(kn[i]);
+    w.put(1, i, kn[i]);
+    w.put(6, i, __fmaf_rn(rtf, fmaxf(fabsf(yf[i]), fabsf(ys[i])), atf));
+  }
+  float sf = 0.0f;
+#pragma unroll 1
+  for (int i = 0; i < 10; i++) {
     dacc acc = dot_first_f(c_dp_e_ds[0], w.get(0, i));
     acc = dot_add_f(acc, c_dp_e_ds[1], w.get(2, i));
     acc = dot_add_f(acc, c_dp_e_ds[2], w.get(3, i));
     acc = dot_add_f(acc, c_dp_e_ds[3], w.get(4, i));
     acc = dot_add_f(acc, c_dp_e_ds[4], w.get(5, i));
-    acc = dot_add_f(acc, c_dp_e_ds[5], kn[i]);
+    acc = dot_add_f(acc, c_dp_e_ds[5], w.get(1, i));
     const float e = __fadd_rn(acc.s, acc.e);
-    const float sc = __fmaf_rn(rtf, fmaxf(fabsf(yf[i]), fabsf(ys[i])), atf);
-    const float q = __fmul_rn(e, __frcp_rn(sc));
+    const float q = __fmul_rn(e, __frcp_rn(w.get(6, i)));
     sf = __fmaf_rn(q, q, sf);
   }
   return f32_to_f64(sf) * ((h * h) * 0.1);
