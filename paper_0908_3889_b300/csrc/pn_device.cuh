@@ -382,7 +382,46 @@ __device__ __forceinline__ ds ds_mul_f(ds a, float b) {
   e = __fmaf_rn(a.lo, b, e);
   return fast_two_sum(p, e);
 }
-__device__ __forceinline__ ds ds_fma(ds a, ds b, ds c) { return ds_add(ds_mul(a, b), c); }  // a b + c
+// a b + c: the product's exact leading part p = a.hi b.hi joins c through
+// two-sum, and its rounding and cross terms go straight into the low part
+// (no separate normalisation of the product).
+__device__ __forceinline__ ds ds_fma(ds a, ds b, ds c) {
+  const float p = __fmul_rn(a.hi, b.hi);
+  float e = __fmaf_rn(a.hi, b.hi, -p);
+  e = __fmaf_rn(a.hi, b.lo, e);
+  e = __fmaf_rn(a.lo, b.hi, e);
+  const ds s = two_sum(p, c.hi);
+  return fast_two_sum(s.hi, __fadd_rn(s.lo, __fadd_rn(e, c.lo)));
+}
+// a0 b0 + a1 b1 + a2 b2 in the same way: leading products summed by two-sum,
+// every rounding error and cross term collected in one FP32 correction.
+__device__ __forceinline__ ds ds_dot3(ds a0, ds b0, ds a1, ds b1, ds a2, ds b2) {
+  const float p0 = __fmul_rn(a0.hi, b0.hi), p1 = __fmul_rn(a1.hi, b1.hi), p2 = __fmul_rn(a2.hi, b2.hi);
+  float e = __fmaf_rn(a0.hi, b0.hi, -p0);
+  e = __fmaf_rn(a0.hi, b0.lo, e);
+  e = __fmaf_rn(a0.lo, b0.hi, e);
+  e = __fadd_rn(e, __fmaf_rn(a1.hi, b1.hi, -p1));
+  e = __fmaf_rn(a1.hi, b1.lo, e);
+  e = __fmaf_rn(a1.lo, b1.hi, e);
+  e = __fadd_rn(e, __fmaf_rn(a2.hi, b2.hi, -p2));
+  e = __fmaf_rn(a2.hi, b2.lo, e);
+  e = __fmaf_rn(a2.lo, b2.hi, e);
+  const ds s = two_sum(p0, p1);
+  const ds t = two_sum(s.hi, p2);
+  return fast_two_sum(t.hi, __fadd_rn(e, __fadd_rn(s.lo, t.lo)));
+}
+// a b - c d (one component of a cross product).
+__device__ __forceinline__ ds ds_diff_prod(ds a, ds b, ds c, ds d) {
+  const float p = __fmul_rn(a.hi, b.hi), q = __fmul_rn(c.hi, d.hi);
+  float e = __fmaf_rn(a.hi, b.hi, -p);
+  e = __fmaf_rn(a.hi, b.lo, e);
+  e = __fmaf_rn(a.lo, b.hi, e);
+  float f = __fmaf_rn(c.hi, d.hi, -q);
+  f = __fmaf_rn(c.hi, d.lo, f);
+  f = __fmaf_rn(c.lo, d.hi, f);
+  const ds s = two_sum(p, -q);
+  return fast_two_sum(s.hi, __fadd_rn(s.lo, __fsub_rn(e, f)));
+}
 // Exact scaling by a power of two given as a float.
 __device__ __forceinline__ ds ds_scale(ds a, float p2) { return ds{a.hi * p2, a.lo * p2}; }
 
@@ -490,9 +529,9 @@ __device__ __forceinline__ void rhs_ds(const Coef<ds>& c, const float* __restric
   const ds v = ds_mul(w, ds_mul(r, r));
   const ds v2 = ds_mul(v, v);
   const ds lw = ds_log(w, tabf);
-  const ds LS1 = ds_fma(Lz, S1z, ds_fma(Ly, S1y, ds_mul(Lx, S1x)));
-  const ds LS2 = ds_fma(Lz, S2z, ds_fma(Ly, S2y, ds_mul(Lx, S2x)));
-  const ds S12 = ds_fma(S1z, S2z, ds_fma(S1y, S2y, ds_mul(S1x, S2x)));
+  const ds LS1 = ds_dot3(Lx, S1x, Ly, S1y, Lz, S1z);
+  const ds LS2 = ds_dot3(Lx, S2x, Ly, S2y, Lz, S2z);
+  const ds S12 = ds_dot3(S1x, S2x, S1y, S2y, S1z, S2z);
   const ds so = ds_fma(c.w1, LS1, ds_fma(c.w2, LS2, ds_neg(c.tail)));
   const ds c2p = ds_fma(c.ss721, ds_mul(LS1, LS2), ds_fma(ds_neg(c.ss247), S12, c.c2));
   const ds c3p = ds_fma(c.clog, lw, c.c3l);
@@ -510,12 +549,12 @@ __device__ __forceinline__ void rhs_ds(const Coef<ds>& c, const float* __restric
   const ds U1x = ds_fma(q1, Lx, S2x), U1y = ds_fma(q1, Ly, S2y), U1z = ds_fma(q1, Lz, S2z);
   const ds U2x = ds_fma(q2, Lx, S1x), U2y = ds_fma(q2, Ly, S1y), U2z = ds_fma(q2, Lz, S1z);
   const ds pre = ds_mul(c.prec, w2);
-  const ds d1x = ds_mul(pre, ds_sub(ds_mul(U1y, S1z), ds_mul(U1z, S1y)));
-  const ds d1y = ds_mul(pre, ds_sub(ds_mul(U1z, S1x), ds_mul(U1x, S1z)));
-  const ds d1z = ds_mul(pre, ds_sub(ds_mul(U1x, S1y), ds_mul(U1y, S1x)));
-  const ds d2x = ds_mul(pre, ds_sub(ds_mul(U2y, S2z), ds_mul(U2z, S2y)));
-  const ds d2y = ds_mul(pre, ds_sub(ds_mul(U2z, S2x), ds_mul(U2x, S2z)));
-  const ds d2z = ds_mul(pre, ds_sub(ds_mul(U2x, S2y), ds_mul(U2y, S2x)));
+  const ds d1x = ds_mul(pre, ds_diff_prod(U1y, S1z, U1z, S1y));
+  const ds d1y = ds_mul(pre, ds_diff_prod(U1z, S1x, U1x, S1z));
+  const ds d1z = ds_mul(pre, ds_diff_prod(U1x, S1y, U1y, S1x));
+  const ds d2x = ds_mul(pre, ds_diff_prod(U2y, S2z, U2z, S2y));
+  const ds d2y = ds_mul(pre, ds_diff_prod(U2z, S2x, U2x, S2z));
+  const ds d2z = ds_mul(pre, ds_diff_prod(U2x, S2y, U2y, S2x));
   f[1] = d1x; f[2] = d1y; f[3] = d1z;
   f[4] = d2x; f[5] = d2y; f[6] = d2z;
   const ds lf = ds_mul(v, c.nie);
