@@ -49,9 +49,10 @@ __device__ __forceinline__ void cross_vjp(const double* a, const double* b, cons
   bb[2] += cb_[0] * a[1] - cb_[1] * a[0];
 }
 
-__device__ __noinline__ void rhs64_vjp(const Coef<double>& c, const double* __restrict__ tab, const double* y,
-                                       const double* fb, double* yb, Coef<double>& cb, double* f) {
-  // ---- forward (the function rhs64 computes, in the A_i, C form) ----
+__device__ __noinline__ void rhs64_vjp(const Coef<double>& c, const double* __restrict__ tab,
+                                       const float* __restrict__ tabf, const double* y, const double* fb, double* yb,
+                                       Coef<double>& cb, double* f) {
+  // ---- forward (as rhs64) ----
   const double w = y[0];
   const double S1[3] = {y[1], y[2], y[3]}, S2[3] = {y[4], y[5], y[6]}, L[3] = {y[7], y[8], y[9]};
   double r = inv_cbrt(w);
@@ -59,7 +60,7 @@ __device__ __noinline__ void rhs64_vjp(const Coef<double>& c, const double* __re
   const double r2 = r * r;
   const double v = w * r2;
   const double v2 = v * v;
-  const double lw = log_tang(w, tab);
+  const double lw = log_w(w, tab, tabf);
   const double LS1 = L[0] * S1[0] + L[1] * S1[1] + L[2] * S1[2];
   const double LS2 = L[0] * S2[0] + L[1] * S2[1] + L[2] * S2[2];
   const double S12 = S1[0] * S2[0] + S1[1] * S2[1] + S1[2] * S2[2];
@@ -74,17 +75,19 @@ __device__ __noinline__ void rhs64_vjp(const Coef<double>& c, const double* __re
   const double P = fma(v2, P2, 1.0);
   const double w2 = w * w;
   const double Q = (w2 * w) * v2;
-  double A1[3], A2[3], C[3];
-  A1[0] = L[1] * S1[2] - L[2] * S1[1]; A1[1] = L[2] * S1[0] - L[0] * S1[2]; A1[2] = L[0] * S1[1] - L[1] * S1[0];
-  A2[0] = L[1] * S2[2] - L[2] * S2[1]; A2[1] = L[2] * S2[0] - L[0] * S2[2]; A2[2] = L[0] * S2[1] - L[1] * S2[0];
-  C[0] = S1[1] * S2[2] - S1[2] * S2[1]; C[1] = S1[2] * S2[0] - S1[0] * S2[2]; C[2] = S1[0] * S2[1] - S1[1] * S2[0];
+  // Eq. (4): Omega_i = pre U_i, U_1 = q1 L + S2, q1 = a1 r - 3 LS2 (1 <-> 2); dS_i/dt = pre (U_i x S_i).
   const double pre = c.prec * w2;
-  const double al1 = fma(c.a1, r, -3.0 * LS2), al2 = fma(c.a2, r, -3.0 * LS1);
-  const double p1 = pre * al1, p2 = pre * al2;
-  double d1[3], d2[3];
+  const double q1 = fma(c.a1, r, -3.0 * LS2), q2 = fma(c.a2, r, -3.0 * LS1);
+  double U1[3], U2[3], X1[3], X2[3], d1[3], d2[3];
   for (int k = 0; k < 3; k++) {
-    d1[k] = p1 * A1[k] - pre * C[k];
-    d2[k] = p2 * A2[k] + pre * C[k];
+    U1[k] = fma(q1, L[k], S2[k]);
+    U2[k] = fma(q2, L[k], S1[k]);
+  }
+  X1[0] = U1[1] * S1[2] - U1[2] * S1[1]; X1[1] = U1[2] * S1[0] - U1[0] * S1[2]; X1[2] = U1[0] * S1[1] - U1[1] * S1[0];
+  X2[0] = U2[1] * S2[2] - U2[2] * S2[1]; X2[1] = U2[2] * S2[0] - U2[0] * S2[2]; X2[2] = U2[0] * S2[1] - U2[1] * S2[0];
+  for (int k = 0; k < 3; k++) {
+    d1[k] = pre * X1[k];
+    d2[k] = pre * X2[k];
   }
   const double lf = v * c.nie;
   f[0] = (Q * c.K) * P;
@@ -95,7 +98,7 @@ __device__ __noinline__ void rhs64_vjp(const Coef<double>& c, const double* __re
   }
   // ---- reverse ----
   double S1b[3] = {0, 0, 0}, S2b[3] = {0, 0, 0}, Lb[3] = {0, 0, 0};
-  double d1b[3], d2b[3], A1b[3], A2b[3], Cb[3];
+  double d1b[3], d2b[3], X1b[3], X2b[3], U1b[3] = {0, 0, 0}, U2b[3] = {0, 0, 0};
   double lfb = 0.0;
   for (int k = 0; k < 3; k++) lfb += fb[7 + k] * (d1[k] + d2[k]);  // f_L = lf (d1 + d2)
   for (int k = 0; k < 3; k++) {
@@ -104,26 +107,28 @@ __device__ __noinline__ void rhs64_vjp(const Coef<double>& c, const double* __re
   }
   double vb = lfb * c.nie;  // lf = v nie
   cb.nie += lfb * v;
-  double p1b = 0.0, p2b = 0.0, preb = 0.0;  // d1 = p1 A1 - pre C, d2 = p2 A2 + pre C
+  double preb = 0.0;  // d_i = pre X_i
   for (int k = 0; k < 3; k++) {
-    p1b += d1b[k] * A1[k];
-    p2b += d2b[k] * A2[k];
-    A1b[k] = p1 * d1b[k];
-    A2b[k] = p2 * d2b[k];
-    Cb[k] = pre * (d2b[k] - d1b[k]);
-    preb += C[k] * (d2b[k] - d1b[k]);
+    preb += X1[k] * d1b[k] + X2[k] * d2b[k];
+    X1b[k] = pre * d1b[k];
+    X2b[k] = pre * d2b[k];
   }
-  preb += p1b * al1 + p2b * al2;  // p_i = pre al_i
-  const double al1b = p1b * pre, al2b = p2b * pre;
-  cb.a1 += al1b * r;  // al1 = a1 r - 3 LS2, al2 = a2 r - 3 LS1
-  cb.a2 += al2b * r;
-  double rb = al1b * c.a1 + al2b * c.a2;
-  double LS2b = -3.0 * al1b, LS1b = -3.0 * al2b;
+  cross_vjp(U1, S1, X1b, U1b, S1b);  // X1 = U1 x S1
+  cross_vjp(U2, S2, X2b, U2b, S2b);  // X2 = U2 x S2
+  double q1b = 0.0, q2b = 0.0;       // U1 = q1 L + S2, U2 = q2 L + S1
+  for (int k = 0; k < 3; k++) {
+    q1b += U1b[k] * L[k];
+    q2b += U2b[k] * L[k];
+    Lb[k] += q1 * U1b[k] + q2 * U2b[k];
+    S2b[k] += U1b[k];
+    S1b[k] += U2b[k];
+  }
+  cb.a1 += q1b * r;  // q1 = a1 r - 3 LS2, q2 = a2 r - 3 LS1
+  cb.a2 += q2b * r;
+  double rb = q1b * c.a1 + q2b * c.a2;
+  double LS2b = -3.0 * q1b, LS1b = -3.0 * q2b;
   double w2b = preb * c.prec;  // pre = prec w2
   cb.prec += preb * w2;
-  cross_vjp(S1, S2, Cb, S1b, S2b);  // C = S1 x S2
-  cross_vjp(L, S1, A1b, Lb, S1b);   // A1 = L x S1
-  cross_vjp(L, S2, A2b, Lb, S2b);   // A2 = L x S2
   const double f0b = fb[0];  // f0 = Q K P
   const double Qb = f0b * c.K * P;
   cb.K += f0b * Q * P;
@@ -261,8 +266,8 @@ __device__ __forceinline__ void dp5_stages(const Coef<double>& c, const double* 
 //   y5 = y + h sum_j b_j k_j,  Y_s = y + h sum_{j<s} a_sj k_j,  k_s = f(Y_s)
 // and kp_j = b_j lam + sum_{s>j} a_sj Yb_s (the cotangent of k_j is h kp_j):
 //   Yb_s = J(Y_s)^T (h kp_s),  yb = lam + sum_s Yb_s,  hb = sum_j k_j . kp_j.
-__device__ double dp5_step_vjp(const Coef<double>& c, const double* __restrict__ tab, const double* sp, size_t ss,
-                               double h, double* lam, Coef<double>& cb) {
+__device__ double dp5_step_vjp(const Coef<double>& c, const double* __restrict__ tab, const float* __restrict__ tabf,
+                               const double* sp, size_t ss, double h, double* lam, Coef<double>& cb) {
   double kp[6][10], yb[10];
   for (int j = 0; j < 6; j++)
     for (int i = 0; i < 10; i++) kp[j][i] = c_dp_B[j] * lam[i];
@@ -275,7 +280,7 @@ __device__ double dp5_step_vjp(const Coef<double>& c, const double* __restrict__
       Ys[i] = sp[(size_t)(10 * s + i) * ss];
       fb[i] = h * kp[s][i];
     }
-    rhs64_vjp(c, tab, Ys, fb, Yb, cb, ks);
+    rhs64_vjp(c, tab, tabf, Ys, fb, Yb, cb, ks);
     for (int i = 0; i < 10; i++) {
       hb = fma(ks[i], kp[s][i], hb);
       yb[i] += Yb[i];
@@ -735,13 +740,13 @@ __device__ void adjoint_one(const AdjArgs& a, const double* __restrict__ tab, co
         double lA[10];
         for (int k = 0; k < 10; k++) lA[k] = 0.0;
         lA[0] = 1.0;
-        const double nu = dp5_step_vjp(c, tab, sp, ss, hn, lA, cA);
-        const double mu = dp5_step_vjp(c, tab, sp, ss, hn, lam, cB) + tbar;
+        const double nu = dp5_step_vjp(c, tab, tabf, sp, ss, hn, lA, cA);
+        const double mu = dp5_step_vjp(c, tab, tabf, sp, ss, hn, lam, cB) + tbar;
         const double ratio = mu / nu;
         for (int k = 0; k < 10; k++) lam[k] -= ratio * lA[k];
         for (int f = 0; f < 16; f++) cbv[f] += bv[f] - ratio * av[f];
       } else {
-        (void)dp5_step_vjp(c, tab, sp, ss, hn, lam, cb);
+        (void)dp5_step_vjp(c, tab, tabf, sp, ss, hn, lam, cb);
       }
     }
   }

@@ -238,8 +238,6 @@ __device__ __forceinline__ double log_w(double x, const double* __restrict__ tab
 //   Eq. (2): dS_i/dt = Omega_i x S_i.   Eq. (3): dL/dt = -(v/eta)(dS1/dt + dS2/dt).
 // With a_i = eta (4 + 3 m_j/m_i) and q_i = a_i/v - 3 L.S_j (j the other body):
 //   Omega_i = (x^2/2) U_i,  U_i = q_i L + S_j,  dS_i/dt = (x^2/2) (U_i x S_i).
-// The adjoint's rhs64_vjp differentiates the equivalent form with A_i = L x S_i
-// and C = S1 x S2: dS1/dt = (x^2/2)[q1 A1 - C], dS2/dt = (x^2/2)[q2 A2 + C].
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ void rhs64(const Coef<double>& c, const double* __restrict__ tab,
                                       const float* __restrict__ tabf, const double* y, double* f) {
