@@ -305,14 +305,14 @@ __device__ double dp5_step_vjp(const Coef<double>& c, const double* __restrict__
 // recomputed with double-single stage sums and FP64 state accumulation, so the
 // gradient is evaluated within ~1e-13 of the FP64 trajectory.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ ds dfma(ds a, ds b, ds c) { return ds_add(ds_mul(a, b), c); }
+__device__ __forceinline__ ds dfma(ds a, ds b, ds c) { return ds_fma(a, b, c); }
 __device__ __forceinline__ ds dzero() { return ds{0.0f, 0.0f}; }
 __device__ __forceinline__ ds dconst(dsc k) { return ds{k.hi, k.lo}; }
 
 __device__ __forceinline__ void cross_ds(const ds* a, const ds* b, ds* c) {
-  c[0] = ds_sub(ds_mul(a[1], b[2]), ds_mul(a[2], b[1]));
-  c[1] = ds_sub(ds_mul(a[2], b[0]), ds_mul(a[0], b[2]));
-  c[2] = ds_sub(ds_mul(a[0], b[1]), ds_mul(a[1], b[0]));
+  c[0] = ds_diff_prod(a[1], b[2], a[2], b[1]);
+  c[1] = ds_diff_prod(a[2], b[0], a[0], b[2]);
+  c[2] = ds_diff_prod(a[0], b[1], a[1], b[0]);
 }
 // c = a x b:  ab += b x cb,  bb += cb x a
 __device__ __forceinline__ void cross_vjp_ds(const ds* a, const ds* b, const ds* cb_, ds* ab, ds* bb) {
@@ -323,7 +323,7 @@ __device__ __forceinline__ void cross_vjp_ds(const ds* a, const ds* b, const ds*
   for (int k = 0; k < 3; k++) bb[k] = ds_add(bb[k], t[k]);
 }
 __device__ __forceinline__ ds dot3_ds(const ds* a, const ds* b) {
-  return dfma(a[2], b[2], dfma(a[1], b[1], ds_mul(a[0], b[0])));
+  return ds_dot3(a[0], b[0], a[1], b[1], a[2], b[2]);
 }
 
 __device__ __noinline__ void rhs_ds_vjp(const Coef<ds>& c, const float* __restrict__ tabf, const ds* y, const ds* fb,
@@ -350,18 +350,19 @@ __device__ __noinline__ void rhs_ds_vjp(const Coef<ds>& c, const float* __restri
   const ds P = dfma(v2, P2, ds_of(1.0f));
   const ds w2 = ds_mul(w, w);
   const ds Q = ds_mul(ds_mul(w2, w), v2);
-  ds A1[3], A2[3], C[3];
-  cross_ds(L, S1, A1);
-  cross_ds(L, S2, A2);
-  cross_ds(S1, S2, C);
+  // Eq. (4) as in rhs_ds: dS_i/dt = pre (U_i x S_i), U_1 = q1 L + S2, q1 = a1 r - 3 LS2 (1 <-> 2).
   const ds pre = ds_mul(c.prec, w2);
-  const ds al1 = dfma(c.a1, r, ds_mul_f(LS2, -3.0f)), al2 = dfma(c.a2, r, ds_mul_f(LS1, -3.0f));
-  const ds p1 = ds_mul(pre, al1), p2 = ds_mul(pre, al2);
-  ds d1[3], d2[3];
+  const ds q1 = dfma(c.a1, r, ds_mul_f(LS2, -3.0f)), q2 = dfma(c.a2, r, ds_mul_f(LS1, -3.0f));
+  ds U1[3], U2[3], X1[3], X2[3], d1[3], d2[3];
   for (int k = 0; k < 3; k++) {
-    const ds pc = ds_mul(pre, C[k]);
-    d1[k] = ds_sub(ds_mul(p1, A1[k]), pc);
-    d2[k] = ds_add(ds_mul(p2, A2[k]), pc);
+    U1[k] = dfma(q1, L[k], S2[k]);
+    U2[k] = dfma(q2, L[k], S1[k]);
+  }
+  cross_ds(U1, S1, X1);
+  cross_ds(U2, S2, X2);
+  for (int k = 0; k < 3; k++) {
+    d1[k] = ds_mul(pre, X1[k]);
+    d2[k] = ds_mul(pre, X2[k]);
   }
   const ds lf = ds_mul(v, c.nie);
   f[0] = ds_mul(ds_mul(Q, c.K), P);
@@ -372,7 +373,8 @@ __device__ __noinline__ void rhs_ds_vjp(const Coef<ds>& c, const float* __restri
   }
   // ---- reverse ----
   ds S1b[3] = {dzero(), dzero(), dzero()}, S2b[3] = {dzero(), dzero(), dzero()}, Lb[3] = {dzero(), dzero(), dzero()};
-  ds d1b[3], d2b[3], A1b[3], A2b[3], Cb[3];
+  ds d1b[3], d2b[3], X1b[3], X2b[3];
+  ds U1b[3] = {dzero(), dzero(), dzero()}, U2b[3] = {dzero(), dzero(), dzero()};
   ds lfb = dzero();
   for (int k = 0; k < 3; k++) lfb = dfma(fb[7 + k], ds_add(d1[k], d2[k]), lfb);  // f_L = lf (d1 + d2)
   for (int k = 0; k < 3; k++) {
@@ -381,27 +383,26 @@ __device__ __noinline__ void rhs_ds_vjp(const Coef<ds>& c, const float* __restri
   }
   ds vb = ds_mul(lfb, c.nie);  // lf = v nie
   cb.nie = dfma(lfb, v, cb.nie);
-  ds p1b = dzero(), p2b = dzero(), preb = dzero();  // d1 = p1 A1 - pre C, d2 = p2 A2 + pre C
+  ds preb = dzero();  // d_i = pre X_i
   for (int k = 0; k < 3; k++) {
-    p1b = dfma(d1b[k], A1[k], p1b);
-    p2b = dfma(d2b[k], A2[k], p2b);
-    A1b[k] = ds_mul(p1, d1b[k]);
-    A2b[k] = ds_mul(p2, d2b[k]);
-    const ds dd = ds_sub(d2b[k], d1b[k]);
-    Cb[k] = ds_mul(pre, dd);
-    preb = dfma(C[k], dd, preb);
+    preb = dfma(X1[k], d1b[k], dfma(X2[k], d2b[k], preb));
+    X1b[k] = ds_mul(pre, d1b[k]);
+    X2b[k] = ds_mul(pre, d2b[k]);
   }
-  preb = dfma(p1b, al1, dfma(p2b, al2, preb));  // p_i = pre al_i
-  const ds al1b = ds_mul(p1b, pre), al2b = ds_mul(p2b, pre);
-  cb.a1 = dfma(al1b, r, cb.a1);  // al1 = a1 r - 3 LS2, al2 = a2 r - 3 LS1
-  cb.a2 = dfma(al2b, r, cb.a2);
-  ds rb = dfma(al1b, c.a1, ds_mul(al2b, c.a2));
-  ds LS2b = ds_mul_f(al1b, -3.0f), LS1b = ds_mul_f(al2b, -3.0f);
+  cross_vjp_ds(U1, S1, X1b, U1b, S1b);  // X1 = U1 x S1
+  cross_vjp_ds(U2, S2, X2b, U2b, S2b);  // X2 = U2 x S2
+  const ds q1b = dot3_ds(U1b, L), q2b = dot3_ds(U2b, L);  // U1 = q1 L + S2, U2 = q2 L + S1
+  for (int k = 0; k < 3; k++) {
+    Lb[k] = dfma(q1, U1b[k], dfma(q2, U2b[k], Lb[k]));
+    S2b[k] = ds_add(S2b[k], U1b[k]);
+    S1b[k] = ds_add(S1b[k], U2b[k]);
+  }
+  cb.a1 = dfma(q1b, r, cb.a1);  // q1 = a1 r - 3 LS2, q2 = a2 r - 3 LS1
+  cb.a2 = dfma(q2b, r, cb.a2);
+  ds rb = dfma(q1b, c.a1, ds_mul(q2b, c.a2));
+  ds LS2b = ds_mul_f(q1b, -3.0f), LS1b = ds_mul_f(q2b, -3.0f);
   ds w2b = ds_mul(preb, c.prec);  // pre = prec w2
   cb.prec = dfma(preb, w2, cb.prec);
-  cross_vjp_ds(S1, S2, Cb, S1b, S2b);  // C = S1 x S2
-  cross_vjp_ds(L, S1, A1b, Lb, S1b);   // A1 = L x S1
-  cross_vjp_ds(L, S2, A2b, Lb, S2b);   // A2 = L x S2
   const ds f0b = fb[0];  // f0 = Q K P
   const ds Qb = ds_mul(ds_mul(f0b, c.K), P);
   cb.K = dfma(ds_mul(f0b, Q), P, cb.K);
