@@ -128,35 +128,6 @@ __device__ __forceinline__ double pow_m_tenth(double s) {
   return fma(z, e * fma(e, 11.0 / 200.0, 0.1), z);
 }
 
-// Cody-Waite split of ln 2: LN2_HI has 40 significant bits, so k * LN2_HI is
-// exact for |k| < 2^12; LN2_HI + LN2_LO = ln 2 to 2e-31.
-#define PN_LN2_HI 0.6931471805601177
-#define PN_LN2_LO (-1.7239444525614835e-13)
-
-// ln|x| for |x| in the normal double range by Tang's table-driven method
-// (P. T. P. Tang, ACM TOMS 16, 1990): |x| = 2^k m with m in [1, 2);
-// F = 1 + (2j + 1)/256 where j is the top 7 bits of m's fraction, so
-// |m - F| <= 2^-8 and f = m - F is exact; u = f / F; then
-// ln|x| = k ln2 + ln F + ln(1 + u), the last from its Taylor series to u^6
-// (truncation below u^7/7 < 2e-18).  tab[2j] = 1/F_j, tab[2j+1] = ln F_j
-// (computed on the host in extended precision, rounded to double).
-__device__ __forceinline__ double log_tang(double x, const double* __restrict__ tab) {
-  const uint32_t hx = hi32(x) & 0x7fffffffu;
-  const int k = (int)(hx >> 20) - 1023;
-  const uint32_t j = (hx >> 13) & 127u;
-  const double m = mk64((hx & 0x000fffffu) | 0x3ff00000u, lo32(x));
-  const double F = mk64(0x3ff00000u | ((2u * j + 1u) << 12), 0u);
-  const double u = (m - F) * tab[2 * j];
-  double q = fma(u, -1.0 / 6.0, 0.2);
-  q = fma(q, u, -0.25);
-  q = fma(q, u, 1.0 / 3.0);
-  q = fma(q, u, -0.5);
-  const double p = fma(q, u * u, u);
-  // (double)k from the bit pattern 2^52 + 2^31 + k, minus 2^52 + 2^31.
-  const double kd = mk64(0x43300000u, (uint32_t)k ^ 0x80000000u) - 4503601774854144.0;
-  return fma(kd, PN_LN2_HI, tab[2 * j + 1]) + fma(kd, PN_LN2_LO, p);
-}
-
 // ---------------------------------------------------------------------------
 // Per-binary coefficients of Eqs. (1) and (4) (M = m1 + m2 = 1, eta = m1 m2).
 // ---------------------------------------------------------------------------
@@ -441,17 +412,22 @@ __device__ __forceinline__ ds split64(double d) {
 // double-single -> double (exact sum of the two parts).
 __device__ __forceinline__ double ds_to_f64(ds a) { return f32_to_f64(a.hi) + f32_to_f64(a.lo); }
 
-// ln|x| for the FP64 right-hand side, for |x| in the normal double range.
-// With |x| = 2^k m and F = 1 + (2j+1)/256 as in log_tang, f = m - F is exact
-// in FP64 and |f| <= 2^-8.  k ln2 + ln F is summed in FP64 (one FMA with the
-// double nearest ln 2, so |k| 2.3e-17 of representation error, 1.6e-16 for
-// the omegas of an inspiral); the remainder ln(1 + u), u = f/F, is evaluated
-// in double-single on the FP32 pipe: u, u^2/2 and u^3/3 as pairs and
+// ln|x| for the FP64 right-hand side, for |x| in the normal double range, by
+// Tang's table-driven reduction (P. T. P. Tang, ACM TOMS 16, 1990): |x| = 2^k m
+// with m in [1, 2), F = 1 + (2j+1)/256 where j is the top 7 bits of m's
+// fraction, so f = m - F is exact in FP64 and |f| <= 2^-8; then
+// ln|x| = k ln2 + ln F + ln(1 + u), u = f/F.  k ln2 + ln F is summed in FP64
+// (one FMA with the double nearest ln 2, so |k| 2.3e-17 of representation
+// error, 1.6e-16 for the omegas of an inspiral); the remainder ln(1 + u) is
+// evaluated in double-single on the FP32 pipe: u, u^2/2 and u^3/3 as pairs and
 // u^4 (-1/4 + u/5 - u^2/6) in FP32 (below 1.1e-10, so its rounding is under
 // 1e-16 of it), truncation u^7/7 < 2.4e-18.  The remainder is thus within
 // ~1e-17 absolute, and the result carries only the FP64 roundings of the two
-// final sums, with five FP64 instructions instead of log_tang's thirteen.
-// tabf[4j..4j+3] = 1/F_j (hi, lo), ln F_j (hi, lo); tab[2j+1] = ln F_j.
+// final sums: five FP64 instructions (an all-FP64 evaluation with the series
+// to u^6 takes thirteen).  Within 1.1e-15 absolute of ln|x| for x in
+// [0.005, 0.1] (checked against a long-double logarithm on the host).
+// tabf[4j..4j+3] = 1/F_j (hi, lo), ln F_j (hi, lo); tab[2j+1] = ln F_j (both
+// computed on the host in extended precision).
 __device__ __forceinline__ double log_w(double x, const double* __restrict__ tab, const float* __restrict__ tabf) {
   const uint32_t hx = hi32(x) & 0x7fffffffu;
   const int k = (int)(hx >> 20) - 1023;

@@ -83,7 +83,7 @@ bool check_params(const pn_params* p, std::string* why);
 bool check_io(const pn_inputs* in, const pn_outputs* out);
 Ctl ctl_from(const pn_params& p);
 
-// Host-side logarithm tables (kLogTabBytes): tab[2j] = 1/F_j, tab[2j+1] = ln F_j for log_tang, then
+// Host-side logarithm tables (kLogTabBytes): tab[2j] = 1/F_j, tab[2j+1] = ln F_j (log_w), then
 // 512 floats for ds_log: (1/F_j hi, lo, ln F_j hi, lo), F_j = 1 + (2j+1)/256.
 constexpr size_t kLogTabBytes = 256 * sizeof(double) + 512 * sizeof(float);
 void fill_log_table(double* tab);
