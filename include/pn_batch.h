@@ -275,6 +275,19 @@ int pn_batch_resume(pn_batch *b, int64_t n, const pn_inputs *in, pn_outputs *out
  * PN_E_ARG, PN_E_NOMEM, PN_E_CUDA. */
 int pn_batch_integrate_host(pn_batch *b, int64_t n, const pn_inputs *host_in, pn_outputs *host_out);
 
+/* The right-hand side f(y) of Eqs. (1)-(4) (arXiv:0908.3889 Sec. II) at n
+ * given states, evaluated by the integration kernels' own device function in
+ * the batch's precision (PN_FP64, PN_MIXED: FP32, PN_MIXED_DS: double-single)
+ * and term mask / theta mode, with the coefficients formed from (m1[i], m2[i])
+ * (M = 1, so m1 + m2 = 1 is expected; nothing is validated).  y and f are
+ * DEVICE arrays of 10 x n doubles, component-major: component c of state i at
+ * [c * n + i], in the order omega, S1 (3), S2 (3), L-hat (3); m1, m2 hold n
+ * doubles.  The caller owns every array.  States with |omega| outside
+ * [2^-126, 2^128) (the FP32 normal range, in every precision) give
+ * non-finite rates.  Asynchronous on the batch's stream.  Errors: PN_E_ARG
+ * (NULL batch or pointer, n < 0), PN_E_CUDA. */
+int pn_batch_eval_rhs(pn_batch *b, int64_t n, const double *m1, const double *m2, const double *y, double *f);
+
 /* Time the candidate launch shapes of the current precision -- plain schedule x
  * {64, 128, 256} threads x {1, 2} binaries per thread, persistent schedule x
  * {64, 128, 256} threads -- on the first min(n, 262144) binaries of *in (writing

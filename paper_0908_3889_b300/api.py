@@ -222,6 +222,16 @@ def pn_batch_adjoint(h, n: int, inputs: dict, cotangents: dict, grads: dict, out
     _check(_lib().pn_batch_adjoint(h, int(n), C.byref(inputs_struct(inputs, n)), C.byref(cs), C.byref(gs), os_), h)
 
 
+def pn_batch_eval_rhs(h, n: int, m1: torch.Tensor, m2: torch.Tensor, y: torch.Tensor, f: torch.Tensor) -> None:
+    """f(y) of Eqs. (1)-(4) at n states in the batch's precision; y, f: (10, n) float64 CUDA tensors, contiguous."""
+    for t, rows in ((m1, None), (m2, None), (y, 10), (f, 10)):
+        if t.dtype != torch.float64 or not t.is_cuda or not t.is_contiguous():
+            raise PNError("pn_batch_eval_rhs needs contiguous float64 CUDA tensors")
+        if (rows is None and t.shape != (n,)) or (rows is not None and t.shape != (rows, n)):
+            raise PNError("pn_batch_eval_rhs: m1, m2 must be (n,), y and f (10, n)")
+    _check(_lib().pn_batch_eval_rhs(h, int(n), _dptr(m1), _dptr(m2), _dptr(y), _dptr(f)), h)
+
+
 def pn_batch_stats(h, n: int, inputs: dict, outputs: dict) -> dict:
     s = N.pn_stats()
     _check(_lib().pn_batch_stats(h, int(n), C.byref(inputs_struct(inputs, n)), C.byref(outputs_struct(outputs, n)),
@@ -319,6 +329,12 @@ class Batch:
         outputs = alloc_outputs(n, inputs["m1"].device) if outputs is None else outputs
         pn_batch_integrate(self.handle, n, inputs, outputs)
         return outputs
+
+    def eval_rhs(self, m1: torch.Tensor, m2: torch.Tensor, y: torch.Tensor) -> torch.Tensor:
+        """The right-hand side at the states y (10, n) in this batch's precision; returns f (10, n)."""
+        f = torch.empty_like(y)
+        pn_batch_eval_rhs(self.handle, int(y.shape[1]), m1, m2, y, f)
+        return f
 
     def integrate_budget(self, inputs: dict, outputs: dict | None = None, budget: int = 64,
                          n: int | None = None) -> dict:

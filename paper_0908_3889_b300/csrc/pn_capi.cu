@@ -486,6 +486,17 @@ extern "C" int pn_batch_integrate_host(pn_batch* b, int64_t n, const pn_inputs* 
   return PN_OK;
 }
 
+extern "C" int pn_batch_eval_rhs(pn_batch* b, int64_t n, const double* m1, const double* m2, const double* y,
+                                 double* f) {
+  if (!b) return fail(nullptr, PN_E_ARG, "batch is NULL");
+  if (n < 0) return fail(b, PN_E_ARG, "n must be >= 0");
+  if (!m1 || !m2 || !y || !f) return fail(b, PN_E_ARG, "NULL pointer");
+  if (n == 0) return PN_OK;
+  const cudaError_t e = pn::launch_eval_rhs(b->p.precision, n, m1, m2, y, f, b->d_tab, make_ctl(b->p).terms, b->stream);
+  if (e != cudaSuccess) return cuda_fail(b, e, "right-hand-side kernel launch");
+  return PN_OK;
+}
+
 extern "C" int pn_batch_autotune(pn_batch* b, int64_t n, const pn_inputs* in, pn_outputs* scratch,
                                  pn_tune_result* res) {
   if (!b) return fail(nullptr, PN_E_ARG, "batch is NULL");

@@ -68,6 +68,10 @@ cudaError_t prepare_integrate_kernels();
 // Resident blocks per SM of the integration kernel at this block size.
 cudaError_t integrate_occupancy(int prec, bool persistent, int block, int* blocks_per_sm);
 
+// f(y) at n states (component-major y[c * n + i], f likewise) in precision prec.
+cudaError_t launch_eval_rhs(int prec, int64_t n, const double* m1, const double* m2, const double* y, double* f,
+                            const double* tab, TermCfg tc, cudaStream_t s);
+
 cudaError_t launch_sample(uint64_t seed, const pn_dist& d, int64_t n, const pn_inputs& in, cudaStream_t s);
 
 // Statistics: partial sums per block into part (grid x kStatWords doubles), then one block reduces them.

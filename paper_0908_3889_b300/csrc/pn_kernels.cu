@@ -88,6 +88,29 @@ constexpr int kSetupFields = 37;
 
 __device__ __forceinline__ double* fld(double* ws, int64_t stride, int f) { return ws + (size_t)f * stride; }
 
+// f(y) of Eqs. (1)-(4) at n given states, in the precision PREC, with the
+// coefficients from (m1[i], m2[i]) (pn_batch_eval_rhs).
+template <int PREC>
+__global__ void __launch_bounds__(256) k_eval_rhs(int64_t n, const double* __restrict__ m1,
+                                                  const double* __restrict__ m2, const double* __restrict__ y,
+                                                  double* __restrict__ f, const double* __restrict__ tab, TermCfg tc) {
+  __shared__ double s_tab[256];
+  __shared__ float s_tabf[512];
+  const Tabs tb = load_tabs<PREC>(tab, s_tab, s_tabf);
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  Coefs cf;
+  cf.c64 = make_coef(m1[i], m2[i], tc);
+  if constexpr (PREC == 1) cf.c32 = to_f32(cf.c64);
+  if constexpr (PREC == 2) cf.cds = to_ds(cf.c64);
+  double yy[10], k[10];
+#pragma unroll
+  for (int c = 0; c < 10; c++) yy[c] = y[(size_t)c * n + i];
+  eval_rhs<PREC>(cf, tb, yy, k);
+#pragma unroll
+  for (int c = 0; c < 10; c++) f[(size_t)c * n + i] = k[c];
+}
+
 template <int PREC>
 __global__ void __launch_bounds__(256) k_setup(const KArgs a, double* __restrict__ ws, int64_t stride) {
   __shared__ double s_tab[256];
@@ -418,6 +441,18 @@ static const void* pick(int prec, bool persistent) {
 }
 
 int setup_fields() { return kSetupFields; }
+
+cudaError_t launch_eval_rhs(int prec, int64_t n, const double* m1, const double* m2, const double* y, double* f,
+                            const double* tab, TermCfg tc, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  const int block = 256;
+  const int64_t grid = (n + block - 1) / block;
+  if (grid > 0x7fffffff) return cudaErrorInvalidValue;
+  if (prec == PN_MIXED) k_eval_rhs<1><<<(unsigned)grid, block, 0, s>>>(n, m1, m2, y, f, tab, tc);
+  else if (prec == PN_MIXED_DS) k_eval_rhs<2><<<(unsigned)grid, block, 0, s>>>(n, m1, m2, y, f, tab, tc);
+  else k_eval_rhs<0><<<(unsigned)grid, block, 0, s>>>(n, m1, m2, y, f, tab, tc);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_setup(int prec, const KArgs& a, double* ws, int64_t stride, cudaStream_t s) {
   if (a.n <= 0) return cudaSuccess;
