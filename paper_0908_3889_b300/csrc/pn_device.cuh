@@ -948,15 +948,21 @@ __device__ __forceinline__ double step_factor(const Ctl& ctl, double s, double f
 // denominators in a monotone chirp); a non-positive one gives a value the
 // caller's bracket check rejects.
 __device__ __forceinline__ double hermite_root(double w0, double d0, double w1, double d1, double wf) {
-  double s = (wf - w0) * rcp_pos(w1 - w0);
+  // The interpolant in power form: p(s) - wf = a0 + s (a1 + s (a2 + s a3)) with
+  // a2 = 3 (w1 - w0) - 2 d0 - d1 and a3 = d0 + d1 - 2 (w1 - w0), so each Newton
+  // step is two Horner evaluations (this runs in a branch that usually holds
+  // one lane of the warp, so its FP64 instructions cost the whole warp).
+  const double dw = w1 - w0;
+  const double a0 = w0 - wf, a1 = d0;
+  const double a2 = fma(3.0, dw, -fma(2.0, d0, d1));
+  const double a3 = fma(-2.0, dw, d0 + d1);
+  const double b1 = 2.0 * a2, b2 = 3.0 * a3;
+  double s = -a0 * rcp_pos(dw);
 #pragma unroll
   for (int it = 0; it < 3; it++) {
-    const double s2 = s * s, s3 = s2 * s;
-    const double ps = (2.0 * s3 - 3.0 * s2 + 1.0) * w0 + (s3 - 2.0 * s2 + s) * d0 + (3.0 * s2 - 2.0 * s3) * w1 +
-                      (s3 - s2) * d1;
-    const double dps = (6.0 * s2 - 6.0 * s) * w0 + (3.0 * s2 - 4.0 * s + 1.0) * d0 + (6.0 * s - 6.0 * s2) * w1 +
-                       (3.0 * s2 - 2.0 * s) * d1;
-    s = s - (ps - wf) * rcp_pos(dps);
+    const double p = fma(fma(fma(a3, s, a2), s, a1), s, a0);
+    const double dp = fma(fma(b2, s, b1), s, a1);
+    s = fma(-p, rcp_pos(dp), s);
   }
   return s;
 }
