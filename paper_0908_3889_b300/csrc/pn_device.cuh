@@ -942,29 +942,41 @@ __device__ __forceinline__ double step_factor(const Ctl& ctl, double s, double f
   return fac;
 }
 
-// Root in (0, 1] of the cubic Hermite interpolant of omega over a step (end
-// values w0, w1; end slopes times h: d0, d1), three Newton steps from the
-// linear guess.  Once per binary.  Divisions use rcp_pos (positive normal
-// denominators in a monotone chirp); a non-positive one gives a value the
-// caller's bracket check rejects.
-__device__ __forceinline__ double hermite_root(double w0, double d0, double w1, double d1, double wf) {
-  // The interpolant in power form: p(s) - wf = a0 + s (a1 + s (a2 + s a3)) with
-  // a2 = 3 (w1 - w0) - 2 d0 - d1 and a3 = d0 + d1 - 2 (w1 - w0), so each Newton
-  // step is two Horner evaluations (this runs in a branch that usually holds
-  // one lane of the warp, so its FP64 instructions cost the whole warp).
-  const double dw = w1 - w0;
-  const double a0 = w0 - wf, a1 = d0;
-  const double a2 = fma(3.0, dw, -fma(2.0, d0, d1));
-  const double a3 = fma(-2.0, dw, d0 + d1);
-  const double b1 = 2.0 * a2, b2 = 3.0 * a3;
-  double s = -a0 * rcp_pos(dw);
-#pragma unroll
+// a / b in double-single: quotient of the leading parts, then one correction
+// from the double-single remainder a - q b (b.hi a normal FP32 value).
+__device__ __forceinline__ ds ds_div(ds a, ds b) {
+  const float q1 = __fdiv_rn(a.hi, b.hi);
+  const ds r = ds_sub(a, ds_mul_f(b, q1));
+  return fast_two_sum(q1, __fdiv_rn(r.hi, b.hi));
+}
+
+// The first retake of a step that crossed omega_f: h times the root in (0, 1]
+// of the step's cubic Hermite interpolant of omega (end values w0, w1, end
+// slopes dw0, dw1), by three Newton steps from the linear guess.  The
+// interpolant in power form is p(s) - wf = a0 + s (a1 + s (a2 + s a3)) with
+// d_i = h dw_i, a2 = 3 (w1 - w0) - 2 d0 - d1, a3 = d0 + d1 - 2 (w1 - w0).  This
+// runs once per binary in a branch that usually holds one lane of the warp,
+// where FP64 instructions would cost the whole warp the FP64 pipe's time, so it
+// is evaluated in double-single on the FP32 pipe from the two FP64 differences
+// w1 - w0 and w0 - wf: within ~1e-13 of the FP64 evaluation, a seed for the
+// landing iteration, which then converges to its own tolerance.  A
+// non-positive denominator gives a value the caller's bracket check rejects.
+__device__ __forceinline__ double hermite_step_ds(double h, double w0, double dw0, double w1, double dw1,
+                                                  double wf) {
+  const ds hd = split64(h);
+  const ds dw = split64(w1 - w0), a0 = split64(w0 - wf);
+  const ds d0 = ds_mul(hd, split64(dw0)), d1 = ds_mul(hd, split64(dw1));
+  const ds a2 = ds_sub(ds_mul_f(dw, 3.0f), ds_add(ds_scale(d0, 2.0f), d1));
+  const ds a3 = ds_add(ds_scale(dw, -2.0f), ds_add(d0, d1));
+  const ds b1 = ds_scale(a2, 2.0f), b2 = ds_mul_f(a3, 3.0f);
+  ds s = ds_div(ds_neg(a0), dw);
+#pragma unroll 1
   for (int it = 0; it < 3; it++) {
-    const double p = fma(fma(fma(a3, s, a2), s, a1), s, a0);
-    const double dp = fma(fma(b2, s, b1), s, a1);
-    s = fma(-p, rcp_pos(dp), s);
+    const ds p = ds_fma(ds_fma(ds_fma(a3, s, a2), s, d0), s, a0);
+    const ds dp = ds_fma(ds_fma(b2, s, b1), s, d0);
+    s = ds_sub(s, ds_div(p, dp));
   }
-  return s;
+  return ds_to_f64(ds_mul(hd, s));
 }
 
 }  // namespace pn

@@ -267,6 +267,15 @@ __device__ __forceinline__ void lane_commit(Lane& L, const double* y5, double hc
 
 // Decisions after one attempt (y5, k7 = f(y5), s = err^2).  Returns true when
 // the binary is finished, with its status in *status.
+// lo < h < hi for a bracket with 0 <= lo < hi (integer comparison of the bit
+// patterns, which order like the values there; a negative or NaN h is outside).
+__device__ __forceinline__ bool in_bracket(double h, double lo, double hi) {
+  const long long b = __double_as_longlong(h);
+  return b > __double_as_longlong(lo) && b < __double_as_longlong(hi);
+}
+
+// Comparisons of doubles below are integer comparisons of the bit patterns (the
+// operands are finite here, and the FP64 compare would take an FP64-pipe slot).
 template <bool RECORD>
 __device__ __forceinline__ bool lane_decide(Lane& L, const Ctl& ctl, double* y5, const double* k7, double s,
                                             int32_t* status, const RecArgs& rec) {
@@ -285,7 +294,7 @@ __device__ __forceinline__ bool lane_decide(Lane& L, const Ctl& ctl, double* y5,
     L.n_land++;
     L.land_it++;
     const double g = y5[0] - L.wf;
-    if (fabs(g) <= tolw) {  // converged: move onto omega_f along f
+    if (le_pos(dabs(g), tolw)) {  // converged: move onto omega_f along f
       const double dh = -g * rk7;
 #pragma unroll
       for (int c = 0; c < 10; c++) y5[c] = fma(dh, k7[c], y5[c]);
@@ -298,22 +307,22 @@ __device__ __forceinline__ bool lane_decide(Lane& L, const Ctl& ctl, double* y5,
       *status = (L.attempts >= ctl.max_steps) ? PN_ST_MAX_STEPS : PN_ST_LAND_MAXIT;
       return true;
     }
-    if (g > 0.0) L.h_hi = L.h; else L.h_lo = L.h;
+    if (__double_as_longlong(g) > 0) L.h_hi = L.h; else L.h_lo = L.h;
     double hn = fma(-g, rk7, L.h);
-    if (!(hn > L.h_lo && hn < L.h_hi)) hn = 0.5 * (L.h_lo + L.h_hi);
+    if (!in_bracket(hn, L.h_lo, L.h_hi)) hn = 0.5 * (L.h_lo + L.h_hi);
     L.h = hn;
     return false;
   }
 
   if (accepted) {
-    if (y5[0] >= L.wf) {
+    if (__double_as_longlong(y5[0]) >= __double_as_longlong(L.wf)) {
       const double g = y5[0] - L.wf;
       if (ctl.stop_mode == PN_STOP_FIRST_CROSS) {
         lane_commit<RECORD>(L, y5, L.h, rec);
         *status = PN_ST_OK;
         return true;
       }
-      if (fabs(g) <= tolw) {
+      if (le_pos(dabs(g), tolw)) {
         const double dh = -g * rk7;
 #pragma unroll
         for (int c = 0; c < 10; c++) y5[c] = fma(dh, k7[c], y5[c]);
@@ -326,8 +335,8 @@ __device__ __forceinline__ bool lane_decide(Lane& L, const Ctl& ctl, double* y5,
       L.land_it = 0;
       L.h_lo = 0.0;
       L.h_hi = L.h;
-      const double hn = L.h * hermite_root(L.y[0], L.h * L.k1[0], y5[0], L.h * k7[0], L.wf);
-      L.h = (hn > L.h_lo && hn < L.h_hi) ? hn : 0.5 * (L.h_lo + L.h_hi);
+      const double hn = hermite_step_ds(L.h, L.y[0], L.k1[0], y5[0], k7[0], L.wf);
+      L.h = in_bracket(hn, L.h_lo, L.h_hi) ? hn : 0.5 * (L.h_lo + L.h_hi);
     } else {
       lane_commit<RECORD>(L, y5, L.h, rec);
 #pragma unroll
@@ -339,7 +348,7 @@ __device__ __forceinline__ bool lane_decide(Lane& L, const Ctl& ctl, double* y5,
     L.n_rej++;
     L.h = L.h * fac;
     L.last_rej = true;
-    if (L.h < ctl.h_min) { *status = PN_ST_H_UNDERFLOW; return true; }
+    if (__double_as_longlong(L.h) < __double_as_longlong(ctl.h_min)) { *status = PN_ST_H_UNDERFLOW; return true; }
   }
   if (L.attempts >= ctl.max_steps) { *status = PN_ST_MAX_STEPS; return true; }
   return false;
