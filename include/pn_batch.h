@@ -361,7 +361,7 @@ void pn_batch_destroy(pn_batch *b);
  * budget and cannot have a library call cudaMalloc behind their back.  The
  * paper has no counterpart; it is a deployment variant of the same kernels.
  * Scratch (work-queue counter, logarithm table, per-binary set-up table) lives
- * in one fixed area of about 4.6 MiB inside the library's device image, held
+ * in one fixed area of about 6 MiB inside the library's device image, held
  * on every GPU that loads the library until exit, so n <= 16384 per call
  * (larger n: PN_E_ARG).  No pn_batch is needed: *p, *in and *out are as for
  * pn_batch_init / pn_batch_integrate, and the work is queued on cuda_stream

@@ -26,6 +26,7 @@ struct KArgs {
   double* rs;                 // saved integrator state, kResumeD doubles per binary (field-major, rs_stride)
   int32_t* ri;                // saved integrator state, kResumeI int32 per binary (field-major, rs_stride)
   int64_t rs_stride;
+  double* land;               // deferred landing moves (set by the launchers: the table's last kLandFields fields)
 };
 
 // Saved state of a binary between bounded calls: y[10], f(y)[10], t, h, h_lo,
@@ -50,7 +51,10 @@ cudaError_t launch_integrate_record(const KArgs& a, const double* ws, int64_t st
                                     int grid, cudaStream_t s);
 cudaError_t record_occupancy(int block, int* blocks_per_sm);
 
-// Set-up table: setup_fields() doubles per binary, field-major with the given stride (>= n).
+// Set-up table: setup_fields() doubles per binary, field-major with the given stride (>= n): the
+// set-up fields, then kLandFields fields for the final move of a binary that lands on omega_f
+// (f(y5) and dh, written by the integration kernel, applied and cleared by the output epilogue).
+constexpr int kLandFields = 11;
 int setup_fields();
 // Validate every binary, write BAD_INPUT results, and fill the set-up table.
 cudaError_t launch_setup(int prec, const KArgs& a, double* ws, int64_t stride, cudaStream_t s);

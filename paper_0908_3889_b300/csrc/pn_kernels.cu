@@ -63,11 +63,27 @@ __device__ __forceinline__ void write_result(const pn_outputs& o, int64_t i, con
   o.n_acc[i] = n_acc; o.n_rej[i] = n_rej; o.n_land[i] = n_land; o.status[i] = status;
 }
 
-// Sec. V's scalar products of the final unit vectors, S1-hat.S2-hat, L-hat.S1-hat,
-// L-hat.S2-hat (NaN for a zero spin: 0/0; NaN for BAD_INPUT binaries).
-__global__ void __launch_bounds__(256) k_dots(const pn_outputs o, int64_t n) {
+// The output epilogue, a converged pass over all binaries.  First the final move
+// of a binary that landed on omega_f: the integration kernel leaves the retaken
+// state y5 and t + h in the outputs and f(y5), dh = -(omega - omega_f)/(domega/dt)
+// in land (fields 0..9, 10); here y += dh f(y5), t += dh, and dh is cleared (so
+// a later bounded call's epilogue does not move it again).  Doing this here
+// rather than in the kernel's landing branch, which usually holds one lane of
+// the warp, keeps its eleven FP64 operations out of divergent code.
+// Then Sec. V's scalar products of the final unit vectors, S1-hat.S2-hat,
+// L-hat.S1-hat, L-hat.S2-hat (NaN for a zero spin: 0/0; NaN for BAD_INPUT binaries).
+__global__ void __launch_bounds__(256) k_dots(const pn_outputs o, int64_t n, double* __restrict__ land,
+                                              int64_t stride) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
+  const double dh = land[(size_t)10 * stride + i];
+  if (dh != 0.0) {
+    double* const yo[10] = {o.omega, o.S1x, o.S1y, o.S1z, o.S2x, o.S2y, o.S2z, o.Lx, o.Ly, o.Lz};
+#pragma unroll
+    for (int c = 0; c < 10; c++) yo[c][i] = fma(dh, land[(size_t)c * stride + i], yo[c][i]);
+    o.t[i] = o.t[i] + dh;
+    land[(size_t)10 * stride + i] = 0.0;
+  }
   const double a0 = o.S1x[i], a1 = o.S1y[i], a2 = o.S1z[i];
   const double b0 = o.S2x[i], b1 = o.S2y[i], b2 = o.S2z[i];
   const double l0 = o.Lx[i], l1 = o.Ly[i], l2 = o.Lz[i];
@@ -118,6 +134,7 @@ __global__ void __launch_bounds__(256) k_setup(const KArgs a, double* __restrict
   const Tabs tb = load_tabs<PREC>(a.tab, s_tab, s_tabf);
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= a.n) return;
+  ws[(size_t)(kSetupFields + 10) * stride + i] = 0.0;  // no deferred landing move yet
   const pn_inputs& in = a.in;
   const double m1 = in.m1[i], m2 = in.m2[i], chi1 = in.chi1[i], chi2 = in.chi2[i];
   const double s1x = in.s1x[i], s1y = in.s1y[i], s1z = in.s1z[i];
@@ -265,6 +282,22 @@ __device__ __forceinline__ void lane_commit(Lane& L, const double* y5, double hc
   if constexpr (RECORD) record_commit(rec, L, hc);
 }
 
+// The landing step: commit the retake (t advances by h) and leave its final move
+// dh along f(y5) to the output epilogue (k_dots); the recording pass records the
+// step as h + dh.
+template <bool RECORD>
+__device__ __forceinline__ void lane_land(Lane& L, const double* y5, const double* k7, double dh, double* land,
+                                          int64_t stride, const RecArgs& rec) {
+#pragma unroll
+  for (int c = 0; c < 10; c++) land[(size_t)c * stride + L.i] = k7[c];
+  land[(size_t)10 * stride + L.i] = dh;
+  L.t = L.t + L.h;
+#pragma unroll
+  for (int c = 0; c < 10; c++) L.y[c] = y5[c];
+  L.n_acc++;
+  if constexpr (RECORD) record_commit(rec, L, L.h + dh);
+}
+
 // Decisions after one attempt (y5, k7 = f(y5), s = err^2).  Returns true when
 // the binary is finished, with its status in *status.
 // lo < h < hi for a bracket with 0 <= lo < hi (integer comparison of the bit
@@ -278,7 +311,7 @@ __device__ __forceinline__ bool in_bracket(double h, double lo, double hi) {
 // operands are finite here, and the FP64 compare would take an FP64-pipe slot).
 template <bool RECORD>
 __device__ __forceinline__ bool lane_decide(Lane& L, const Ctl& ctl, double* y5, const double* k7, double s,
-                                            int32_t* status, const RecArgs& rec) {
+                                            int32_t* status, const RecArgs& rec, double* land, int64_t stride) {
   bool fin = ctl.fixed_step ? true : finite64(s);
 #pragma unroll
   for (int c = 0; c < 10; c++) fin = fin && finite64(y5[c]);
@@ -294,11 +327,8 @@ __device__ __forceinline__ bool lane_decide(Lane& L, const Ctl& ctl, double* y5,
     L.n_land++;
     L.land_it++;
     const double g = y5[0] - L.wf;
-    if (le_pos(dabs(g), tolw)) {  // converged: move onto omega_f along f
-      const double dh = -g * rk7;
-#pragma unroll
-      for (int c = 0; c < 10; c++) y5[c] = fma(dh, k7[c], y5[c]);
-      lane_commit<RECORD>(L, y5, L.h + dh, rec);
+    if (le_pos(dabs(g), tolw)) {  // converged: move onto omega_f along f (in the epilogue)
+      lane_land<RECORD>(L, y5, k7, -g * rk7, land, stride, rec);
       *status = PN_ST_OK;
       return true;
     }
@@ -323,10 +353,7 @@ __device__ __forceinline__ bool lane_decide(Lane& L, const Ctl& ctl, double* y5,
         return true;
       }
       if (le_pos(dabs(g), tolw)) {
-        const double dh = -g * rk7;
-#pragma unroll
-        for (int c = 0; c < 10; c++) y5[c] = fma(dh, k7[c], y5[c]);
-        lane_commit<RECORD>(L, y5, L.h + dh, rec);
+        lane_land<RECORD>(L, y5, k7, -g * rk7, land, stride, rec);
         *status = PN_ST_OK;
         return true;
       }
@@ -412,7 +439,7 @@ __device__ __forceinline__ void integrate_body(const KArgs& a, const double* __r
       else s = dp5_attempt<PREC>(L.cf, tb, a.ctl, L.y, L.k1, L.h, y5, k7);
       L.attempts++;
       int32_t st;
-      if (lane_decide<RECORD>(L, a.ctl, y5, k7, s, &st, rec)) {
+      if (lane_decide<RECORD>(L, a.ctl, y5, k7, s, &st, rec, a.land, stride)) {
         write_result(a.out, L.i, L.y, L.t, L.n_acc, L.n_rej, L.n_land, st);
         have = false;
       } else if (BOUNDED && L.attempts >= L.stop_at) {
@@ -449,7 +476,7 @@ static const void* pick(int prec, bool persistent) {
   return persistent ? integrate_fn<0, true>() : integrate_fn<0, false>();
 }
 
-int setup_fields() { return kSetupFields; }
+int setup_fields() { return kSetupFields + kLandFields; }
 
 cudaError_t launch_eval_rhs(int prec, int64_t n, const double* m1, const double* m2, const double* y, double* f,
                             const double* tab, TermCfg tc, cudaStream_t s) {
@@ -473,9 +500,20 @@ cudaError_t launch_setup(int prec, const KArgs& a, double* ws, int64_t stride, c
   return cudaGetLastError();
 }
 
-static cudaError_t launch_dots(const pn_outputs& o, int64_t n, cudaStream_t s) {
+// The deferred-landing fields of the set-up table ws (the same allocation,
+// past the set-up fields the integration kernels read).
+static double* land_fields(const double* ws, int64_t stride) {
+  return const_cast<double*>(ws) + (size_t)kSetupFields * (size_t)stride;
+}
+static KArgs with_land(const KArgs& a, const double* ws, int64_t stride) {
+  KArgs b = a;
+  b.land = land_fields(ws, stride);
+  return b;
+}
+
+static cudaError_t launch_dots(const pn_outputs& o, int64_t n, const double* ws, int64_t stride, cudaStream_t s) {
   if (n <= 0) return cudaSuccess;
-  k_dots<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(o, n);
+  k_dots<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(o, n, land_fields(ws, stride), stride);
   return cudaGetLastError();
 }
 
@@ -484,7 +522,7 @@ cudaError_t launch_integrate(int prec, bool persistent, int block, int grid, con
   if (grid <= 0) return cudaSuccess;
   const cudaError_t e = launch_integrate_only(prec, persistent, block, grid, a, ws, stride, s);
   if (e != cudaSuccess) return e;
-  return launch_dots(a.out, a.n, s);
+  return launch_dots(a.out, a.n, ws, stride, s);
 }
 
 // Dynamic shared memory of an integration launch: the double-single workspace.
@@ -528,8 +566,9 @@ static void launch_integrate_variant(int prec, bool persistent, int block, int g
   }
 }
 
-cudaError_t launch_integrate_only(int prec, bool persistent, int block, int grid, const KArgs& a, const double* ws,
+cudaError_t launch_integrate_only(int prec, bool persistent, int block, int grid, const KArgs& a_in, const double* ws,
                                   int64_t stride, cudaStream_t s) {
+  const KArgs a = with_land(a_in, ws, stride);
   if (a.budget > 0 || a.resume) {
     launch_integrate_variant<true>(prec, persistent, block, grid, a, ws, stride, s);
     return cudaGetLastError();
@@ -557,10 +596,10 @@ cudaError_t integrate_occupancy(int prec, bool persistent, int block, int* block
 cudaError_t launch_integrate_record(const KArgs& a, const double* ws, int64_t stride, const RecArgs& rec, int block,
                                     int grid, cudaStream_t s) {
   if (grid <= 0) return cudaSuccess;
-  k_integrate<0, true, true><<<grid, block, 0, s>>>(a, ws, stride, rec);
+  k_integrate<0, true, true><<<grid, block, 0, s>>>(with_land(a, ws, stride), ws, stride, rec);
   const cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  return launch_dots(a.out, a.n, s);
+  return launch_dots(a.out, a.n, ws, stride, s);
 }
 
 cudaError_t record_occupancy(int block, int* blocks_per_sm) {

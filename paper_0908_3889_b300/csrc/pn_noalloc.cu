@@ -7,10 +7,10 @@
 // entry point instead uses one fixed scratch area that lives in the library's
 // own device image, so a call allocates nothing.
 //
-// The scratch area is the file-scope array below (about 4.6 MiB).  Every GPU
+// The scratch area is the file-scope array below (about 6 MiB).  Every GPU
 // that loads the library keeps it until the process exits.  It holds the work
-// queue counter, the logarithm table and the per-binary set-up table for at
-// most kNoAllocMax binaries, which is why a call is limited to that many.
+// queue counter, the logarithm table and the per-binary set-up table (with its
+// deferred-landing fields) for at most kNoAllocMax binaries, which is why a call is limited to that many.
 //
 // The array is shared by all calls: each call resets the queue counter and
 // rewrites the set-up entries it uses, and calls whose GPU work overlaps (on
@@ -31,7 +31,7 @@ constexpr int64_t kNoAllocMax = 16384;  // binaries per call
 constexpr size_t kQueueOff = 0;         // unsigned long long work-queue counter
 constexpr size_t kTabOff = 256;         // the logarithm tables (pn::kLogTabBytes)
 constexpr size_t kSetupOff = 256 + 4096;
-constexpr size_t kNoAllocBytes = kSetupOff + (size_t)37 * kNoAllocMax * sizeof(double);
+constexpr size_t kNoAllocBytes = kSetupOff + (size_t)(37 + pn::kLandFields) * kNoAllocMax * sizeof(double);
 
 static __device__ __align__(256) unsigned char g_scratch[kNoAllocBytes];
 
