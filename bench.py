@@ -48,7 +48,7 @@ FP64_DATASHEET_TFLOPS = 1.25  # nominal dense FP64 of one B300
 # DRAM traffic of the integration kernel per binary from an ncu capture
 # (dram__bytes_read.sum + dram__bytes_write.sum, profiles/); valid only while
 # the kernel sources hash (kernel_sha) to the recorded value.
-PROFILED = {"kernel_sha": "84b92a58b2cda066", "dram_bytes_per_binary": (38.91968e6 + 0.13696e6) / 131072}
+PROFILED = {"kernel_sha": "d2b85e96973d4a76", "dram_bytes_per_binary": (39.513088e6 + 1.377792e6) / 131072}
 
 
 def kernel_sha() -> str:
