@@ -818,8 +818,10 @@ __device__ __forceinline__ double dp5_attempt_f32(const Coef<float>& c, const Ct
       }
 #pragma unroll
       for (int i = 0; i < 10; i++) {
+        // The FP32 right-hand side's input at y5 directly in FP32 (within an FP32 ulp of
+        // y5 rounded), so the FP64 accumulation below is off the path to k7.
+        ys[i] = fmaf(hf, w.get(6, i), yf[i]);
         y5[i] = fma(h, f32_to_f64(w.get(6, i)) + f32_to_f64(w.get(7, i)), y[i]);
-        ys[i] = f64_to_f32(y5[i]);
       }
     }
     rhs32(c, ys, kn);  // k_{r+2}; for r = 5, k7 = f(y5)
