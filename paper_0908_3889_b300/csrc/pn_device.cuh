@@ -680,6 +680,77 @@ __device__ __forceinline__ double dp5_attempt(const Coefs& cf, const Tabs& tb, c
   return sum * ((h * h) * 0.1);
 }
 
+// The FP64 attempt with the same arithmetic as dp5_attempt, bit for bit, for
+// the 168-register kernel: the rates k2..k6 sit in a per-thread shared-memory
+// workspace (lane-interleaved: rate j, component c of thread t at
+// base[((j - 2) * 10 + c) * nthreads + t]) and the six stages run as one loop,
+// so one copy of the right-hand side serves them all.  Each stage's sum keeps
+// exactly its own terms.
+constexpr int kF64WorkBytes = 5 * 10 * 8;  // per thread
+struct F64Work {
+  double* base;
+  int nt, t;
+  __device__ __forceinline__ double get(int j, int c) const { return base[((j - 2) * 10 + c) * nt + t]; }
+  __device__ __forceinline__ void put(int j, int c, double v) const { base[((j - 2) * 10 + c) * nt + t] = v; }
+};
+
+__device__ __forceinline__ double dp5_attempt_ws(const Coefs& cf, const Tabs& tb, const Ctl& ctl, const double* y,
+                                                 const double* k1, double h, double* y5, double* k7,
+                                                 const F64Work& w) {
+  double ys[10], kn[10];
+#pragma unroll 1
+  for (int r = 0; r < 6; r++) {
+    if (r == 0) {
+      const double a1 = h * DP_A21;
+#pragma unroll
+      for (int i = 0; i < 10; i++) ys[i] = fma(a1, k1[i], y[i]);
+    } else if (r == 1) {
+      const double a1 = h * DP_A31, a2 = h * DP_A32;
+#pragma unroll
+      for (int i = 0; i < 10; i++) ys[i] = fma(a2, w.get(2, i), fma(a1, k1[i], y[i]));
+    } else if (r == 2) {
+      const double a1 = h * DP_A41, a2 = h * DP_A42, a3 = h * DP_A43;
+#pragma unroll
+      for (int i = 0; i < 10; i++) ys[i] = fma(a3, w.get(3, i), fma(a2, w.get(2, i), fma(a1, k1[i], y[i])));
+    } else if (r == 3) {
+      const double a1 = h * DP_A51, a2 = h * DP_A52, a3 = h * DP_A53, a4 = h * DP_A54;
+#pragma unroll
+      for (int i = 0; i < 10; i++)
+        ys[i] = fma(a4, w.get(4, i), fma(a3, w.get(3, i), fma(a2, w.get(2, i), fma(a1, k1[i], y[i]))));
+    } else if (r == 4) {
+      const double a1 = h * DP_A61, a2 = h * DP_A62, a3 = h * DP_A63, a4 = h * DP_A64, a5 = h * DP_A65;
+#pragma unroll
+      for (int i = 0; i < 10; i++)
+        ys[i] = fma(a5, w.get(5, i), fma(a4, w.get(4, i), fma(a3, w.get(3, i), fma(a2, w.get(2, i),
+                fma(a1, k1[i], y[i])))));
+    } else {
+      const double b1 = h * DP_B1, b3 = h * DP_B3, b4 = h * DP_B4, b5 = h * DP_B5, b6 = h * DP_B6;
+#pragma unroll
+      for (int i = 0; i < 10; i++) {
+        y5[i] = fma(b6, w.get(6, i), fma(b5, w.get(5, i), fma(b4, w.get(4, i), fma(b3, w.get(3, i),
+                fma(b1, k1[i], y[i])))));
+        ys[i] = y5[i];
+      }
+    }
+    rhs64(cf.c64, tb.d, tb.f, ys, kn);  // k_{r+2}; for r = 5, k7 = f(y5)
+    if (r < 5) {
+#pragma unroll
+      for (int i = 0; i < 10; i++) w.put(r + 2, i, kn[i]);
+    }
+  }
+  double sum = 0.0;
+#pragma unroll
+  for (int i = 0; i < 10; i++) {
+    k7[i] = kn[i];
+    const double e = fma(DP_E7, k7[i], fma(DP_E6, w.get(6, i), fma(DP_E5, w.get(5, i), fma(DP_E4, w.get(4, i),
+                     fma(DP_E3, w.get(3, i), DP_E1 * k1[i])))));
+    const double sc = fma(ctl.rtol, max_abs(y[i], y5[i]), ctl.atol);
+    const double q = e * rcp_norm(sc);
+    sum = fma(q, q, sum);
+  }
+  return sum * ((h * h) * 0.1);
+}
+
 // The mixed-precision attempt (FP32 right-hand side).  The stage inputs
 // Y_2..Y_6 only feed the FP32 right-hand side, which rounds them to FP32 on
 // entry, so they are formed in FP32 from the FP32-rounded state.  The rates are

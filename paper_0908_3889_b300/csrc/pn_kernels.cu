@@ -384,7 +384,7 @@ __device__ __forceinline__ bool lane_decide(Lane& L, const Ctl& ctl, double* y5,
 // BOUNDED: the launch may stop binaries at a per-launch attempt budget and may
 // resume saved ones (pn_batch_integrate_budget / pn_batch_resume); the default
 // launches are compiled without that bookkeeping.
-template <int PREC, bool PERSIST, bool RECORD, bool BOUNDED>
+template <int PREC, bool PERSIST, bool RECORD, bool BOUNDED, bool WS = false>
 __device__ __forceinline__ void integrate_body(const KArgs& a, const double* __restrict__ ws, int64_t stride,
                                                const RecArgs& rec) {
   __shared__ double s_tab[256];
@@ -436,6 +436,9 @@ __device__ __forceinline__ void integrate_body(const KArgs& a, const double* __r
       else if constexpr (PREC == 1)
         s = dp5_attempt_f32(L.cf.c32, a.ctl, L.y, L.k1, L.h, y5, k7,
                             F32Work{reinterpret_cast<float*>(s_dsw), (int)blockDim.x, (int)threadIdx.x});
+      else if constexpr (WS)
+        s = dp5_attempt_ws(L.cf, tb, a.ctl, L.y, L.k1, L.h, y5, k7,
+                           F64Work{reinterpret_cast<double*>(s_dsw), (int)blockDim.x, (int)threadIdx.x});
       else s = dp5_attempt<PREC>(L.cf, tb, a.ctl, L.y, L.k1, L.h, y5, k7);
       L.attempts++;
       int32_t st;
@@ -461,13 +464,12 @@ __global__ void __launch_bounds__(kMaxBlock) k_integrate(const KArgs a, const do
 // that fits three warps per scheduler.
 template <int PREC, bool PERSIST, bool BOUNDED = false>
 __global__ void __maxnreg__(168) k_integrate_mx(const KArgs a, const double* __restrict__ ws, int64_t stride) {
-  integrate_body<PREC, PERSIST, false, BOUNDED>(a, ws, stride, RecArgs{});
+  integrate_body<PREC, PERSIST, false, BOUNDED, PREC == 0>(a, ws, stride, RecArgs{});
 }
 
 template <int PREC, bool PERSIST>
 static const void* integrate_fn() {
-  if constexpr (PREC != 0) return (const void*)k_integrate_mx<PREC, PERSIST>;
-  else return (const void*)k_integrate<PREC, PERSIST>;
+  return (const void*)k_integrate_mx<PREC, PERSIST>;
 }
 
 static const void* pick(int prec, bool persistent) {
@@ -529,7 +531,7 @@ cudaError_t launch_integrate(int prec, bool persistent, int block, int grid, con
 static size_t integrate_smem(int prec, int block) {
   if (prec == PN_MIXED_DS) return (size_t)kDsWorkBytes * (size_t)block;
   if (prec == PN_MIXED) return (size_t)kF32WorkBytes * (size_t)block;
-  return 0;
+  return (size_t)kF64WorkBytes * (size_t)block;
 }
 
 cudaError_t prepare_integrate_kernels() {
@@ -547,6 +549,13 @@ cudaError_t prepare_integrate_kernels() {
         cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, kF32WorkBytes * kMaxBlock);
     if (e != cudaSuccess) return e;
   }
+  const void* f64[4] = {(const void*)k_integrate_mx<0, true>, (const void*)k_integrate_mx<0, false>,
+                        (const void*)k_integrate_mx<0, true, true>, (const void*)k_integrate_mx<0, false, true>};
+  for (const void* f : f64) {
+    const cudaError_t e =
+        cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, kF64WorkBytes * kMaxBlock);
+    if (e != cudaSuccess) return e;
+  }
   return cudaSuccess;
 }
 
@@ -561,8 +570,8 @@ static void launch_integrate_variant(int prec, bool persistent, int block, int g
     if (persistent) k_integrate_mx<2, true, BOUNDED><<<grid, block, sm, s>>>(a, ws, stride);
     else k_integrate_mx<2, false, BOUNDED><<<grid, block, sm, s>>>(a, ws, stride);
   } else {
-    if (persistent) k_integrate<0, true, false, BOUNDED><<<grid, block, 0, s>>>(a, ws, stride);
-    else k_integrate<0, false, false, BOUNDED><<<grid, block, 0, s>>>(a, ws, stride);
+    if (persistent) k_integrate_mx<0, true, BOUNDED><<<grid, block, sm, s>>>(a, ws, stride);
+    else k_integrate_mx<0, false, BOUNDED><<<grid, block, sm, s>>>(a, ws, stride);
   }
 }
 
@@ -582,8 +591,9 @@ cudaError_t launch_integrate_only(int prec, bool persistent, int block, int grid
     if (persistent) k_integrate_mx<2, true><<<grid, block, sm, s>>>(a, ws, stride);
     else k_integrate_mx<2, false><<<grid, block, sm, s>>>(a, ws, stride);
   } else {
-    if (persistent) k_integrate<0, true><<<grid, block, 0, s>>>(a, ws, stride);
-    else k_integrate<0, false><<<grid, block, 0, s>>>(a, ws, stride);
+    const size_t sm = integrate_smem(prec, block);
+    if (persistent) k_integrate_mx<0, true><<<grid, block, sm, s>>>(a, ws, stride);
+    else k_integrate_mx<0, false><<<grid, block, sm, s>>>(a, ws, stride);
   }
   return cudaGetLastError();
 }
