@@ -48,7 +48,7 @@ FP64_DATASHEET_TFLOPS = 1.25  # nominal dense FP64 of one B300
 # DRAM traffic of the integration kernel per binary from an ncu capture
 # (dram__bytes_read.sum + dram__bytes_write.sum, profiles/); valid only while
 # the kernel sources hash (kernel_sha) to the recorded value.
-PROFILED = {"kernel_sha": "d2b85e96973d4a76", "dram_bytes_per_binary": (39.513088e6 + 1.377792e6) / 131072}
+PROFILED = {"kernel_sha": "3ddb04e726f5045d", "dram_bytes_per_binary": (39.494912e6 + 1.157632e6) / 131072}
 
 
 def kernel_sha() -> str:
@@ -406,7 +406,7 @@ def main():
             "pipe": "FP64", "peak_source": "FP64 FMA throughput measured live by the peak probe (2 flops per FMA)",
             "datasheet_peak": FP64_DATASHEET_TFLOPS, "frac_of_datasheet": achieved / 1e12 / FP64_DATASHEET_TFLOPS,
             "flops_per_attempt": FLOPS_ATTEMPT, "attempts_per_launch": attempts,
-            "kernel": "pn::k_integrate<FP64>"}
+            "kernel": "pn::k_integrate_mx<FP64>"}
 
     # Mixed precision on the same ensemble: FP32 right-hand side (PN_MIXED) and
     # double-single right-hand side on the FP32 pipe (PN_MIXED_DS).
