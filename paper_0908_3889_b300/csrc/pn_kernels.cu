@@ -463,7 +463,8 @@ __global__ void __launch_bounds__(kMaxBlock) k_integrate(const KArgs a, const do
 // double-single), held to 168 registers: with their rates in shared memory
 // that fits three warps per scheduler.
 template <int PREC, bool PERSIST, bool BOUNDED = false>
-__global__ void __maxnreg__(168) k_integrate_mx(const KArgs a, const double* __restrict__ ws, int64_t stride) {
+__global__ void __maxnreg__(PREC == 0 ? 255 : 168) k_integrate_mx(const KArgs a, const double* __restrict__ ws,
+                                                                 int64_t stride) {
   integrate_body<PREC, PERSIST, false, BOUNDED, PREC == 0>(a, ws, stride, RecArgs{});
 }
 
