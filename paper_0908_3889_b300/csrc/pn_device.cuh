@@ -622,70 +622,13 @@ __device__ __forceinline__ void eval_rhs(const Coefs& cf, const Tabs& tb, const 
   }
 }
 
-// One Dormand-Prince attempt of size h from y, with k1 = f(y) given.
+// One Dormand-Prince attempt of size h from y in FP64, with k1 = f(y) given.
 // Writes y5 (the 5th-order solution), k7 = f(y5) and returns the mean of the
-// squared scaled error components, s = err^2 (err = RMS norm).
-template <int PREC>
-__device__ __forceinline__ double dp5_attempt(const Coefs& cf, const Tabs& tb, const Ctl& ctl, const double* y,
-                                              const double* k1, double h, double* y5, double* k7) {
-  double k2[10], k3[10], k4[10], k5[10], k6[10], ys[10];
-  {
-    const double a1 = h * DP_A21;
-#pragma unroll
-    for (int i = 0; i < 10; i++) ys[i] = fma(a1, k1[i], y[i]);
-  }
-  eval_rhs<PREC>(cf, tb, ys, k2);
-  {
-    const double a1 = h * DP_A31, a2 = h * DP_A32;
-#pragma unroll
-    for (int i = 0; i < 10; i++) ys[i] = fma(a2, k2[i], fma(a1, k1[i], y[i]));
-  }
-  eval_rhs<PREC>(cf, tb, ys, k3);
-  {
-    const double a1 = h * DP_A41, a2 = h * DP_A42, a3 = h * DP_A43;
-#pragma unroll
-    for (int i = 0; i < 10; i++) ys[i] = fma(a3, k3[i], fma(a2, k2[i], fma(a1, k1[i], y[i])));
-  }
-  eval_rhs<PREC>(cf, tb, ys, k4);
-  {
-    const double a1 = h * DP_A51, a2 = h * DP_A52, a3 = h * DP_A53, a4 = h * DP_A54;
-#pragma unroll
-    for (int i = 0; i < 10; i++) ys[i] = fma(a4, k4[i], fma(a3, k3[i], fma(a2, k2[i], fma(a1, k1[i], y[i]))));
-  }
-  eval_rhs<PREC>(cf, tb, ys, k5);
-  {
-    const double a1 = h * DP_A61, a2 = h * DP_A62, a3 = h * DP_A63, a4 = h * DP_A64, a5 = h * DP_A65;
-#pragma unroll
-    for (int i = 0; i < 10; i++)
-      ys[i] = fma(a5, k5[i], fma(a4, k4[i], fma(a3, k3[i], fma(a2, k2[i], fma(a1, k1[i], y[i])))));
-  }
-  eval_rhs<PREC>(cf, tb, ys, k6);
-  {
-    const double b1 = h * DP_B1, b3 = h * DP_B3, b4 = h * DP_B4, b5 = h * DP_B5, b6 = h * DP_B6;
-#pragma unroll
-    for (int i = 0; i < 10; i++)
-      y5[i] = fma(b6, k6[i], fma(b5, k5[i], fma(b4, k4[i], fma(b3, k3[i], fma(b1, k1[i], y[i])))));
-  }
-  eval_rhs<PREC>(cf, tb, y5, k7);
-  // The error estimate without its factor h (applied to the sum as h^2).
-  double sum = 0.0;
-#pragma unroll
-  for (int i = 0; i < 10; i++) {
-    const double e = fma(DP_E7, k7[i], fma(DP_E6, k6[i], fma(DP_E5, k5[i], fma(DP_E4, k4[i],
-                     fma(DP_E3, k3[i], DP_E1 * k1[i])))));
-    const double sc = fma(ctl.rtol, max_abs(y[i], y5[i]), ctl.atol);
-    const double q = e * rcp_norm(sc);
-    sum = fma(q, q, sum);
-  }
-  return sum * ((h * h) * 0.1);
-}
-
-// The FP64 attempt with the same arithmetic as dp5_attempt, bit for bit, for
-// the 168-register kernel: the rates k2..k6 sit in a per-thread shared-memory
-// workspace (lane-interleaved: rate j, component c of thread t at
-// base[((j - 2) * 10 + c) * nthreads + t]) and the six stages run as one loop,
-// so one copy of the right-hand side serves them all.  Each stage's sum keeps
-// exactly its own terms.
+// squared scaled error components, s = err^2 (err = RMS norm).  The rates
+// k2..k6 sit in a per-thread shared-memory workspace (lane-interleaved: rate j,
+// component c of thread t at base[((j - 2) * 10 + c) * nthreads + t]) and the
+// six stages run as one loop, so one copy of the right-hand side serves them
+// all; each stage's sum keeps exactly its own terms.
 constexpr int kF64WorkBytes = 5 * 10 * 8;  // per thread
 struct F64Work {
   double* base;

@@ -384,7 +384,7 @@ __device__ __forceinline__ bool lane_decide(Lane& L, const Ctl& ctl, double* y5,
 // BOUNDED: the launch may stop binaries at a per-launch attempt budget and may
 // resume saved ones (pn_batch_integrate_budget / pn_batch_resume); the default
 // launches are compiled without that bookkeeping.
-template <int PREC, bool PERSIST, bool RECORD, bool BOUNDED, bool WS = false>
+template <int PREC, bool PERSIST, bool RECORD, bool BOUNDED, bool WS>
 __device__ __forceinline__ void integrate_body(const KArgs& a, const double* __restrict__ ws, int64_t stride,
                                                const RecArgs& rec) {
   __shared__ double s_tab[256];
@@ -436,10 +436,9 @@ __device__ __forceinline__ void integrate_body(const KArgs& a, const double* __r
       else if constexpr (PREC == 1)
         s = dp5_attempt_f32(L.cf.c32, a.ctl, L.y, L.k1, L.h, y5, k7,
                             F32Work{reinterpret_cast<float*>(s_dsw), (int)blockDim.x, (int)threadIdx.x});
-      else if constexpr (WS)
+      else
         s = dp5_attempt_ws(L.cf, tb, a.ctl, L.y, L.k1, L.h, y5, k7,
                            F64Work{reinterpret_cast<double*>(s_dsw), (int)blockDim.x, (int)threadIdx.x});
-      else s = dp5_attempt<PREC>(L.cf, tb, a.ctl, L.y, L.k1, L.h, y5, k7);
       L.attempts++;
       int32_t st;
       if (lane_decide<RECORD>(L, a.ctl, y5, k7, s, &st, rec, a.land, stride)) {
@@ -453,10 +452,13 @@ __device__ __forceinline__ void integrate_body(const KArgs& a, const double* __r
   }
 }
 
+// The recording pass of the adjoint (FP64, persistent, RECORD): the FP64
+// attempt with its rates in the dynamic shared-memory workspace, as in
+// k_integrate_mx<0>.
 template <int PREC, bool PERSIST, bool RECORD = false, bool BOUNDED = false>
 __global__ void __launch_bounds__(kMaxBlock) k_integrate(const KArgs a, const double* __restrict__ ws, int64_t stride,
                                                          const RecArgs rec = RecArgs{}) {
-  integrate_body<PREC, PERSIST, RECORD, BOUNDED>(a, ws, stride, rec);
+  integrate_body<PREC, PERSIST, RECORD, BOUNDED, true>(a, ws, stride, rec);
 }
 
 // The two mixed-precision kernels (PREC 1: FP32 right-hand side, PREC 2:
@@ -550,8 +552,9 @@ cudaError_t prepare_integrate_kernels() {
         cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, kF32WorkBytes * kMaxBlock);
     if (e != cudaSuccess) return e;
   }
-  const void* f64[4] = {(const void*)k_integrate_mx<0, true>, (const void*)k_integrate_mx<0, false>,
-                        (const void*)k_integrate_mx<0, true, true>, (const void*)k_integrate_mx<0, false, true>};
+  const void* f64[5] = {(const void*)k_integrate_mx<0, true>, (const void*)k_integrate_mx<0, false>,
+                        (const void*)k_integrate_mx<0, true, true>, (const void*)k_integrate_mx<0, false, true>,
+                        (const void*)k_integrate<0, true, true>};
   for (const void* f : f64) {
     const cudaError_t e =
         cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, kF64WorkBytes * kMaxBlock);
@@ -607,14 +610,16 @@ cudaError_t integrate_occupancy(int prec, bool persistent, int block, int* block
 cudaError_t launch_integrate_record(const KArgs& a, const double* ws, int64_t stride, const RecArgs& rec, int block,
                                     int grid, cudaStream_t s) {
   if (grid <= 0) return cudaSuccess;
-  k_integrate<0, true, true><<<grid, block, 0, s>>>(with_land(a, ws, stride), ws, stride, rec);
+  k_integrate<0, true, true><<<grid, block, integrate_smem(PN_FP64, block), s>>>(with_land(a, ws, stride), ws, stride,
+                                                                                 rec);
   const cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   return launch_dots(a.out, a.n, ws, stride, s);
 }
 
 cudaError_t record_occupancy(int block, int* blocks_per_sm) {
-  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, (const void*)k_integrate<0, true, true>, block, 0);
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, (const void*)k_integrate<0, true, true>, block,
+                                                       integrate_smem(PN_FP64, block));
 }
 
 // ---------------------------------------------------------------------------
