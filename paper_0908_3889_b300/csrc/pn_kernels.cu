@@ -14,10 +14,9 @@
 //               different lengths do not leave lanes idle.
 // Inputs and outputs are structure-of-arrays: lane i touches element i of
 // each array, so every load and store of a warp is one coalesced 256-byte
-// transaction.  The FP64 kernel keeps its stage rates in registers
-// (k_integrate); the two mixed-precision kernels keep theirs in a per-thread
-// shared-memory workspace and are held to 168 registers (k_integrate_mx), so
-// their stage loops stay small and three warps fit per scheduler.
+// transaction.  All three precisions keep their stage rates in a per-thread
+// shared-memory workspace (k_integrate_mx; k_integrate is the adjoint's FP64
+// recording pass), so their stage loops stay small: one right-hand-side copy.
 
 #include <cmath>
 
@@ -461,11 +460,13 @@ __global__ void __launch_bounds__(kMaxBlock) k_integrate(const KArgs a, const do
   integrate_body<PREC, PERSIST, RECORD, BOUNDED, true>(a, ws, stride, rec);
 }
 
-// The two mixed-precision kernels (PREC 1: FP32 right-hand side, PREC 2:
-// double-single), held to 168 registers: with their rates in shared memory
-// that fits three warps per scheduler.
+// The integration kernels with their rates in a per-thread shared-memory
+// workspace: PREC 0 FP64, PREC 1 FP32 right-hand side, PREC 2 double-single.
+// The FP32-RHS kernel is held to 168 registers, three warps per scheduler (it is
+// latency-bound, and measured faster so); the FP64 and double-single kernels
+// take up to 255 (two warps per scheduler), which measured faster for them.
 template <int PREC, bool PERSIST, bool BOUNDED = false>
-__global__ void __maxnreg__(PREC == 0 ? 255 : 168) k_integrate_mx(const KArgs a, const double* __restrict__ ws,
+__global__ void __maxnreg__(PREC == 1 ? 168 : 255) k_integrate_mx(const KArgs a, const double* __restrict__ ws,
                                                                  int64_t stride) {
   integrate_body<PREC, PERSIST, false, BOUNDED, PREC == 0>(a, ws, stride, RecArgs{});
 }
