@@ -1,6 +1,6 @@
 // pn_kernels.cu -- CUDA kernels of the batched PN inspiral integrator (sm_103a).
 //
-// k_integrate: one binary per lane, state in registers, one Dormand-Prince
+// k_integrate_mx / k_integrate: one binary per lane, state in registers, one Dormand-Prince
 // attempt per loop iteration for every lane that holds a binary, so a warp
 // stays converged on the RHS-heavy part whatever each lane's step history.
 // The per-lane control is a small state machine (STEP / LAND) that takes the
@@ -98,7 +98,8 @@ __global__ void __launch_bounds__(256) k_dots(const pn_outputs o, int64_t n, dou
 // fields 0..15 the coefficients, 16..25 the initial state y0, 26..35 k1 = f(y0)
 // in the kernel's precision, 36 omega_f (NaN marks a binary whose BAD_INPUT
 // result is already written).  k_setup fills it with one converged pass, so a
-// lane that picks up a new binary in k_integrate only loads.
+// lane that picks up a new binary in the integration kernel only loads.  The
+// kLandFields fields after them hold the deferred landing moves (k_dots).
 constexpr int kSetupFields = 37;
 
 __device__ __forceinline__ double* fld(double* ws, int64_t stride, int f) { return ws + (size_t)f * stride; }
