@@ -271,9 +271,27 @@ int pn_batch_resume(pn_batch *b, int64_t n, const pn_inputs *in, pn_outputs *out
 /* Same as pn_batch_integrate with HOST input and output arrays: copies the
  * inputs to the library's device staging buffers (allocated on first use,
  * n_max binaries), integrates, copies the outputs back and synchronises the
- * stream.  Page-locked host memory gives the fastest copies.  Errors:
- * PN_E_ARG, PN_E_NOMEM, PN_E_CUDA. */
+ * stream (it is pn_batch_integrate_host_async followed by pn_batch_host_wait).
+ * Page-locked host memory gives the fastest copies.  Errors: PN_E_ARG,
+ * PN_E_NOMEM, PN_E_CUDA. */
 int pn_batch_integrate_host(pn_batch *b, int64_t n, const pn_inputs *host_in, pn_outputs *host_out);
+
+/* The same as pn_batch_integrate_host without the final wait: enqueues the
+ * input copy (on a library copy-in stream), the integration (on the batch's
+ * stream) and the output copy (on a library copy-out stream) and returns.
+ * The call alternates between two device staging sets (each allocated on
+ * first use, n_max binaries), so consecutive calls overlap: a call's input
+ * copy runs during the previous call's integration and its output copy during
+ * the next call's.  Until pn_batch_host_wait returns, the caller must not
+ * change *host_in's arrays nor read *host_out's, for every call made since the
+ * last wait.  Results are those of pn_batch_integrate_host.  Errors: PN_E_ARG,
+ * PN_E_NOMEM, PN_E_CUDA. */
+int pn_batch_integrate_host_async(pn_batch *b, int64_t n, const pn_inputs *host_in, pn_outputs *host_out);
+
+/* Wait until every pn_batch_integrate_host_async call made on b has copied its
+ * outputs to the host (and the batch's stream is idle).  Errors: PN_E_ARG,
+ * PN_E_CUDA. */
+int pn_batch_host_wait(pn_batch *b);
 
 /* The right-hand side f(y) of Eqs. (1)-(4) (arXiv:0908.3889 Sec. II) at n
  * given states, evaluated by the integration kernels' own device function in

@@ -195,6 +195,18 @@ def pn_batch_integrate_host(h, n: int, host_inputs: dict, host_outputs: dict) ->
                                           C.byref(outputs_struct(host_outputs, n))), h)
 
 
+def pn_batch_integrate_host_async(h, n: int, host_inputs: dict, host_outputs: dict) -> None:
+    """Enqueue a host-buffer integration and return; consecutive calls overlap their copies with the
+    neighbouring integrations.  The host tensors must stay untouched until pn_batch_host_wait."""
+    _check(_lib().pn_batch_integrate_host_async(h, int(n), C.byref(_host_inputs_struct(host_inputs, n)),
+                                                C.byref(outputs_struct(host_outputs, n))), h)
+
+
+def pn_batch_host_wait(h) -> None:
+    """Wait for every pn_batch_integrate_host_async call on the batch to have copied its outputs back."""
+    _check(_lib().pn_batch_host_wait(h), h)
+
+
 def pn_batch_autotune(h, n: int, inputs: dict, scratch: dict) -> dict:
     r = N.pn_tune_result()
     _check(_lib().pn_batch_autotune(h, int(n), C.byref(inputs_struct(inputs, n)),

@@ -60,9 +60,15 @@ struct pn_batch {
   // saved integrator states between bounded calls (pn_batch_integrate_budget / pn_batch_resume)
   double* d_rs = nullptr;
   int32_t* d_ri = nullptr;
-  // staging for pn_batch_integrate_host
-  double* d_stage_d = nullptr;
-  int32_t* d_stage_i = nullptr;
+  // staging for pn_batch_integrate_host(_async): two sets used in turn, with a
+  // copy-in and a copy-out stream, so a call's copies overlap the integration of
+  // the call before or after it
+  double* d_stage_d[2] = {nullptr, nullptr};
+  int32_t* d_stage_i[2] = {nullptr, nullptr};
+  bool stage_used[2] = {false, false};
+  int stage_next = 0;
+  cudaStream_t s_in = nullptr, s_out = nullptr;
+  cudaEvent_t ev_in[2] = {}, ev_comp[2] = {}, ev_out[2] = {};
   std::string err;
 };
 
@@ -210,8 +216,16 @@ extern "C" void pn_batch_destroy(pn_batch* b) {
   cudaFree(b->d_adj_out_i);
   cudaFree(b->d_adj_order);
   cudaFree(b->d_adj_bins);
-  cudaFree(b->d_stage_d);
-  cudaFree(b->d_stage_i);
+  if (b->s_out) cudaStreamSynchronize(b->s_out);
+  for (int k = 0; k < 2; k++) {
+    cudaFree(b->d_stage_d[k]);
+    cudaFree(b->d_stage_i[k]);
+    if (b->ev_in[k]) cudaEventDestroy(b->ev_in[k]);
+    if (b->ev_comp[k]) cudaEventDestroy(b->ev_comp[k]);
+    if (b->ev_out[k]) cudaEventDestroy(b->ev_out[k]);
+  }
+  if (b->s_in) cudaStreamDestroy(b->s_in);
+  if (b->s_out) cudaStreamDestroy(b->s_out);
   cudaFree(b->d_rs);
   cudaFree(b->d_ri);
   delete b;
@@ -439,34 +453,42 @@ extern "C" int pn_batch_resume(pn_batch* b, int64_t n, const pn_inputs* in, pn_o
   return integrate_bounded(b, n, in, out, budget, 1);
 }
 
-extern "C" int pn_batch_integrate_host(pn_batch* b, int64_t n, const pn_inputs* hin, pn_outputs* hout) {
+extern "C" int pn_batch_integrate_host_async(pn_batch* b, int64_t n, const pn_inputs* hin, pn_outputs* hout) {
   if (!b) return fail(nullptr, PN_E_ARG, "batch is NULL");
   if (n < 0 || n > b->n_max) return fail(b, PN_E_ARG, "n must be in [0, n_max]");
   if (!inputs_ok(hin)) return fail(b, PN_E_ARG, "NULL input pointer");
   if (!outputs_ok(hout)) return fail(b, PN_E_ARG, "NULL output pointer");
+  if (n == 0) return PN_OK;
   const size_t N = (size_t)b->n_max;
-  if (!b->d_stage_d) {
-    cudaError_t e = cudaMalloc(&b->d_stage_d, 29 * N * sizeof(double));
-    if (e == cudaSuccess) e = cudaMalloc(&b->d_stage_i, 4 * N * sizeof(int32_t));
+  if (!b->s_in) {
+    PN_CUDA(b, cudaStreamCreateWithFlags(&b->s_in, cudaStreamNonBlocking));
+    PN_CUDA(b, cudaStreamCreateWithFlags(&b->s_out, cudaStreamNonBlocking));
+    for (int k = 0; k < 2; k++) {
+      PN_CUDA(b, cudaEventCreateWithFlags(&b->ev_in[k], cudaEventDisableTiming));
+      PN_CUDA(b, cudaEventCreateWithFlags(&b->ev_comp[k], cudaEventDisableTiming));
+      PN_CUDA(b, cudaEventCreateWithFlags(&b->ev_out[k], cudaEventDisableTiming));
+    }
+  }
+  const int st = b->stage_next;
+  if (!b->d_stage_d[st]) {
+    cudaError_t e = cudaMalloc(&b->d_stage_d[st], 29 * N * sizeof(double));
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_stage_i[st], 4 * N * sizeof(int32_t));
     if (e != cudaSuccess) {
-      cudaFree(b->d_stage_d);
-      b->d_stage_d = nullptr;
-      b->d_stage_i = nullptr;
+      cudaGetLastError();
+      cudaFree(b->d_stage_d[st]);
+      b->d_stage_d[st] = nullptr;
+      b->d_stage_i[st] = nullptr;
       return fail(b, PN_E_NOMEM, "staging allocation failed");
     }
   }
-  double* D = b->d_stage_d;
-  int32_t* I = b->d_stage_i;
+  double* D = b->d_stage_d[st];
+  int32_t* I = b->d_stage_i[st];
   pn_inputs din;
   double** dp[15] = {&din.m1, &din.m2, &din.chi1, &din.chi2, &din.s1x, &din.s1y, &din.s1z, &din.s2x,
                      &din.s2y, &din.s2z, &din.lx, &din.ly, &din.lz, &din.omega0, &din.omega_f};
   double* const hp[15] = {hin->m1, hin->m2, hin->chi1, hin->chi2, hin->s1x, hin->s1y, hin->s1z, hin->s2x,
                           hin->s2y, hin->s2z, hin->lx, hin->ly, hin->lz, hin->omega0, hin->omega_f};
-  const size_t bytes = (size_t)n * sizeof(double);
-  for (int k = 0; k < 15; k++) {
-    *dp[k] = D + (size_t)k * N;
-    if (n) PN_CUDA(b, cudaMemcpyAsync(*dp[k], hp[k], bytes, cudaMemcpyHostToDevice, b->stream));
-  }
+  for (int k = 0; k < 15; k++) *dp[k] = D + (size_t)k * N;
   pn_outputs dout;
   double** op[14] = {&dout.S1x, &dout.S1y, &dout.S1z, &dout.S2x, &dout.S2y, &dout.S2z, &dout.Lx,
                      &dout.Ly, &dout.Lz, &dout.omega, &dout.t, &dout.dot_s1s2, &dout.dot_ls1, &dout.dot_ls2};
@@ -476,14 +498,40 @@ extern "C" int pn_batch_integrate_host(pn_batch* b, int64_t n, const pn_inputs* 
   int32_t** ip[4] = {&dout.n_acc, &dout.n_rej, &dout.n_land, &dout.status};
   int32_t* const hi[4] = {hout->n_acc, hout->n_rej, hout->n_land, hout->status};
   for (int k = 0; k < 4; k++) *ip[k] = I + (size_t)k * N;
-  int rc = pn_batch_integrate(b, n, &din, &dout);
+  const size_t bytes = (size_t)n * sizeof(double);
+  // Inputs: after the last integration that read this staging set.
+  if (b->stage_used[st]) PN_CUDA(b, cudaStreamWaitEvent(b->s_in, b->ev_comp[st], 0));
+  for (int k = 0; k < 15; k++) PN_CUDA(b, cudaMemcpyAsync(*dp[k], hp[k], bytes, cudaMemcpyHostToDevice, b->s_in));
+  PN_CUDA(b, cudaEventRecord(b->ev_in[st], b->s_in));
+  // Integration on the batch's stream: after this call's inputs, and after the
+  // output copy of the last call that used this staging set.
+  PN_CUDA(b, cudaStreamWaitEvent(b->stream, b->ev_in[st], 0));
+  if (b->stage_used[st]) PN_CUDA(b, cudaStreamWaitEvent(b->stream, b->ev_out[st], 0));
+  const int rc = pn_batch_integrate(b, n, &din, &dout);
   if (rc != PN_OK) return rc;
-  for (int k = 0; k < 14 && n; k++)
-    PN_CUDA(b, cudaMemcpyAsync(ho[k], *op[k], bytes, cudaMemcpyDeviceToHost, b->stream));
-  for (int k = 0; k < 4 && n; k++)
-    PN_CUDA(b, cudaMemcpyAsync(hi[k], *ip[k], (size_t)n * sizeof(int32_t), cudaMemcpyDeviceToHost, b->stream));
+  PN_CUDA(b, cudaEventRecord(b->ev_comp[st], b->stream));
+  // Outputs: after the integration.
+  PN_CUDA(b, cudaStreamWaitEvent(b->s_out, b->ev_comp[st], 0));
+  for (int k = 0; k < 14; k++) PN_CUDA(b, cudaMemcpyAsync(ho[k], *op[k], bytes, cudaMemcpyDeviceToHost, b->s_out));
+  for (int k = 0; k < 4; k++)
+    PN_CUDA(b, cudaMemcpyAsync(hi[k], *ip[k], (size_t)n * sizeof(int32_t), cudaMemcpyDeviceToHost, b->s_out));
+  PN_CUDA(b, cudaEventRecord(b->ev_out[st], b->s_out));
+  b->stage_used[st] = true;
+  b->stage_next = st ^ 1;
+  return PN_OK;
+}
+
+extern "C" int pn_batch_host_wait(pn_batch* b) {
+  if (!b) return fail(nullptr, PN_E_ARG, "batch is NULL");
+  if (b->s_out) PN_CUDA(b, cudaStreamSynchronize(b->s_out));
   PN_CUDA(b, cudaStreamSynchronize(b->stream));
   return PN_OK;
+}
+
+extern "C" int pn_batch_integrate_host(pn_batch* b, int64_t n, const pn_inputs* hin, pn_outputs* hout) {
+  const int rc = pn_batch_integrate_host_async(b, n, hin, hout);
+  if (rc != PN_OK) return rc;
+  return pn_batch_host_wait(b);
 }
 
 extern "C" int pn_batch_eval_rhs(pn_batch* b, int64_t n, const double* m1, const double* m2, const double* y,

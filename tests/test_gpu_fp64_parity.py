@@ -200,7 +200,30 @@ def test_host_buffer_entry_point_matches_device(pn, n, precision, pinned):
         h2 = pn.to_numpy(hout)
     for k in dev:
         assert np.array_equal(dev[k], h1[k], equal_nan=True), k
-        assert np.array_equal(dev[k][:n - 1000], h2[k][:n - 1000], equal_nan=True), k
+        assert np.array_equal(dev[k][..., :n - 1000], h2[k][..., :n - 1000], equal_nan=True), k
+
+
+def test_host_async_calls_pipeline_and_match_device(pn):
+    """Three asynchronous host-buffer calls in a row (the two staging sets in turn, copies overlapping
+    the neighbouring integrations), each into its own output buffers, then one wait: every call's
+    outputs are bit-identical to the device-buffer entry point's for its own inputs."""
+    import torch
+    n = 40_000
+    ensa, ensb = workloads.config("C1", n=n), workloads.config("C2", n=n)
+    deva, devb = run_gpu(pn, ensa), run_gpu(pn, ensb)
+    hina = pn.to_device(ensa, device="cpu", pin_memory=True)
+    hinb = pn.to_device(ensb, device="cpu", pin_memory=True)
+    outs = [pn.alloc_outputs(n, pin_memory=True) for _ in range(3)]
+    with pn.Batch(n) as b:
+        pn.pn_batch_integrate_host_async(b.handle, n, hina, outs[0])
+        pn.pn_batch_integrate_host_async(b.handle, n, hinb, outs[1])
+        pn.pn_batch_integrate_host_async(b.handle, n - 5, hina, outs[2])
+        pn.pn_batch_host_wait(b.handle)
+    h = [pn.to_numpy(o) for o in outs]
+    for k in deva:
+        assert np.array_equal(deva[k], h[0][k], equal_nan=True), k
+        assert np.array_equal(devb[k], h[1][k], equal_nan=True), k
+        assert np.array_equal(deva[k][..., :n - 5], h[2][k][..., :n - 5], equal_nan=True), k
 
 
 def test_repeat_calls_reuse_graph_and_agree(pn):
