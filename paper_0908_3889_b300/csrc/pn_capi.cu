@@ -216,6 +216,7 @@ extern "C" void pn_batch_destroy(pn_batch* b) {
   cudaFree(b->d_adj_out_i);
   cudaFree(b->d_adj_order);
   cudaFree(b->d_adj_bins);
+  if (b->s_in) cudaStreamSynchronize(b->s_in);
   if (b->s_out) cudaStreamSynchronize(b->s_out);
   for (int k = 0; k < 2; k++) {
     cudaFree(b->d_stage_d[k]);
@@ -523,6 +524,7 @@ extern "C" int pn_batch_integrate_host_async(pn_batch* b, int64_t n, const pn_in
 
 extern "C" int pn_batch_host_wait(pn_batch* b) {
   if (!b) return fail(nullptr, PN_E_ARG, "batch is NULL");
+  if (b->s_in) PN_CUDA(b, cudaStreamSynchronize(b->s_in));
   if (b->s_out) PN_CUDA(b, cudaStreamSynchronize(b->s_out));
   PN_CUDA(b, cudaStreamSynchronize(b->stream));
   return PN_OK;
