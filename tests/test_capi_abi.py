@@ -91,6 +91,12 @@ def test_argument_errors_before_any_cuda_call(native):
         assert h.value is None
     assert lib.pn_batch_integrate(None, 1, None, None) == native.PN_E_ARG
     assert lib.pn_batch_stats(None, 1, None, None, None) == native.PN_E_ARG
+    assert lib.pn_batch_integrate_host(None, 1, None, None) == native.PN_E_ARG
+    assert lib.pn_batch_integrate_host_async(None, 1, None, None) == native.PN_E_ARG
+    assert lib.pn_batch_host_wait(None) == native.PN_E_ARG
+    assert lib.pn_batch_eval_rhs(None, 1, None, None, None, None) == native.PN_E_ARG
+    assert lib.pn_batch_integrate_budget(None, 1, None, None, 1) == native.PN_E_ARG
+    assert lib.pn_batch_resume(None, 1, None, None, 1) == native.PN_E_ARG
     lib.pn_batch_destroy(None)
 
 
