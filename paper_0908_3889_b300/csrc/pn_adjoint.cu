@@ -231,7 +231,8 @@ __constant__ double c_dp_A[6][6] = {
 __constant__ double c_dp_B[6] = {DP_B1, 0.0, DP_B3, DP_B4, DP_B5, DP_B6};
 
 // One Dormand-Prince step y -> y5 with a fixed h (the map the accepted steps
-// apply; same FP64 arithmetic as the forward kernel's stages), writing the six
+// apply; same FP64 arithmetic as the forward kernel's stages, so c holds the
+// coefficients with K folded in, as there), writing the six
 // stage states Y_0 = y, ..., Y_5 to sp[(10 s + k) * ss].  With y5 == nullptr
 // only the stage states are made (the last rate k_6 is then not needed).
 __device__ __forceinline__ void dp5_stages(const Coef<double>& c, const double* __restrict__ tab,
@@ -625,6 +626,7 @@ __device__ void adjoint_one(const AdjArgs& a, const double* __restrict__ tab, co
   const pn_inputs& in = a.k.in;
   const double m1 = in.m1[i], m2 = in.m2[i], chi1 = in.chi1[i], chi2 = in.chi2[i];
   const Coef<double> c = make_coef(m1, m2, a.k.ctl.terms);
+  const Coef<double> cf = fold_K(c);  // the forward kernel's coefficients, for a bitwise replay
   // Cotangent of the final state from the output cotangents.
   const double S1[3] = {o.S1x[i], o.S1y[i], o.S1z[i]}, S2[3] = {o.S2x[i], o.S2y[i], o.S2z[i]};
   const double L[3] = {o.Lx[i], o.Ly[i], o.Lz[i]};
@@ -724,7 +726,7 @@ __device__ void adjoint_one(const AdjArgs& a, const double* __restrict__ tab, co
     for (int32_t n = n0; n < n1s; n++) {  // recompute the segment, keeping the stage states
       double y5[10];
       const bool more = n + 1 < n1s;
-      dp5_stages(c, tab, tabf, y, a.h[(size_t)n * a.stride + i], sp0 + (size_t)(n - n0) * step_words, ss,
+      dp5_stages(cf, tab, tabf, y, a.h[(size_t)n * a.stride + i], sp0 + (size_t)(n - n0) * step_words, ss,
                  more ? y5 : nullptr);
       if (more)
         for (int k = 0; k < 10; k++) y[k] = y5[k];

@@ -186,6 +186,33 @@ __device__ __forceinline__ Coef<double> make_coef(double m1, double m2, TermCfg 
   return c;
 }
 
+// The coefficients of P multiplied by the prefactor K = (96/5) eta, once per
+// binary: P_K = K + v^2 (K c1 - K so v + ...), so the right-hand side skips one
+// FP64 multiplication (rhs64).  K itself stays as P_K's constant term.
+__device__ __forceinline__ Coef<double> fold_K(const Coef<double>& c) {
+  Coef<double> f = c;
+  f.w1 = c.K * c.w1;
+  f.w2 = c.K * c.w2;
+  f.tail = c.K * c.tail;
+  f.ss247 = c.K * c.ss247;
+  f.ss721 = c.K * c.ss721;
+  f.c1 = c.K * c.c1;
+  f.c2 = c.K * c.c2;
+  f.c25 = c.K * c.c25;
+  f.c35 = c.K * c.c35;
+  f.c3l = c.K * c.c3l;
+  f.clog = c.K * c.clog;
+  return f;
+}
+
+// prec * x for prec in {0, 1/2} (the precession switch of make_coef) and x = w^2,
+// with no FP64 instruction.  Where rhs64's r = w^{-1/3} is a number, x lies in
+// [2^-252, 2^256): normal, so halving is the exponent minus one, exact.  Outside
+// that range every rate that takes this factor is NaN through r, whatever it is.
+__device__ __forceinline__ double half_or_zero(double prec, double x) {
+  return (hi32(prec) & 0x7fffffffu) == 0u ? 0.0 : mk64(hi32(x) - (1u << 20), lo32(x));
+}
+
 // The FP32 coefficients, rounded with the same integer conversion the kernels use.
 __device__ __forceinline__ Coef<float> to_f32(const Coef<double>& c) {
   Coef<float> f;
@@ -210,6 +237,8 @@ __device__ __forceinline__ double log_w(double x, const double* __restrict__ tab
 // With a_i = eta (4 + 3 m_j/m_i) and q_i = a_i/v - 3 L.S_j (j the other body):
 //   Omega_i = (x^2/2) U_i,  U_i = q_i L + S_j,  dS_i/dt = (x^2/2) (U_i x S_i).
 // ---------------------------------------------------------------------------
+// c holds the coefficients of P with the prefactor K folded in (fold_K), so that
+// omega-dot = omega^2 v^5 P_K with P_K = K P.
 __device__ __forceinline__ void rhs64(const Coef<double>& c, const double* __restrict__ tab,
                                       const float* __restrict__ tabf, const double* y, double* f) {
   const double w = y[0];
@@ -236,9 +265,9 @@ __device__ __forceinline__ void rhs64(const Coef<double>& c, const double* __res
   P = fma(v, P, c2p);
   P = fma(v, P, -so);
   P = fma(v, P, c.c1);
-  P = fma(v2, P, 1.0);
   const double w2 = w * w;
-  f[0] = (((w2 * w) * v2) * c.K) * P;
+  P = fma(v2, P, c.K);
+  f[0] = ((w2 * w) * v2) * P;
 
   // Eq. (4) as Omega_i = pre U_i with U_1 = q1 L + S2, q1 = a1/v - 3 L.S2 (1 <-> 2),
   // and dS_i/dt = pre (U_i x S_i): 29 FP64 operations for both spins.
@@ -246,7 +275,7 @@ __device__ __forceinline__ void rhs64(const Coef<double>& c, const double* __res
   const double q2 = fma(c.a2, r, -3.0 * LS1);
   const double U1x = fma(q1, Lx, S2x), U1y = fma(q1, Ly, S2y), U1z = fma(q1, Lz, S2z);
   const double U2x = fma(q2, Lx, S1x), U2y = fma(q2, Ly, S1y), U2z = fma(q2, Lz, S1z);
-  const double pre = c.prec * w2;
+  const double pre = half_or_zero(c.prec, w2);
   const double d1x = pre * fma(U1y, S1z, -U1z * S1y), d1y = pre * fma(U1z, S1x, -U1x * S1z),
                d1z = pre * fma(U1x, S1y, -U1y * S1x);
   const double d2x = pre * fma(U2y, S2z, -U2z * S2y), d2y = pre * fma(U2z, S2x, -U2x * S2z),

@@ -117,6 +117,7 @@ __global__ void __launch_bounds__(256) k_eval_rhs(int64_t n, const double* __res
   if (i >= n) return;
   Coefs cf;
   cf.c64 = make_coef(m1[i], m2[i], tc);
+  if constexpr (PREC == 0) cf.c64 = fold_K(cf.c64);
   if constexpr (PREC == 1) cf.c32 = to_f32(cf.c64);
   if constexpr (PREC == 2) cf.cds = to_ds(cf.c64);
   double yy[10], k[10];
@@ -158,6 +159,7 @@ __global__ void __launch_bounds__(256) k_setup(const KArgs a, double* __restrict
   }
   Coefs cf;
   cf.c64 = make_coef(m1, m2, a.ctl.terms);
+  if constexpr (PREC == 0) cf.c64 = fold_K(cf.c64);  // the FP64 kernels' right-hand side takes P_K
   if constexpr (PREC == 1) cf.c32 = to_f32(cf.c64);
   if constexpr (PREC == 2) cf.cds = to_ds(cf.c64);
   const Coef<double>& c = cf.c64;
