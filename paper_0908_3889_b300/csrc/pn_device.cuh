@@ -441,29 +441,45 @@ __device__ __forceinline__ ds split64(double d) {
 // double-single -> double (exact sum of the two parts).
 __device__ __forceinline__ double ds_to_f64(ds a) { return f32_to_f64(a.hi) + f32_to_f64(a.lo); }
 
+// An int k, |k| < 2^31, as a double, exactly, by integer operations (no FP64
+// instruction): the leading bit of |k| becomes the implicit one.
+__device__ __forceinline__ double i32_to_f64(int k) {
+  if (k == 0) return 0.0;
+  const uint32_t a = (k < 0) ? (uint32_t)(-k) : (uint32_t)k;
+  const int e = 31 - __clz(a);  // a in [2^e, 2^(e+1))
+  const uint32_t n = a << (31 - e);  // leading bit at bit 31
+  return mk64(((uint32_t)(1023 + e) << 20) | ((n >> 11) & 0x000fffffu) | ((uint32_t)k & 0x80000000u), n << 21);
+}
+
 // ln|x| for the FP64 right-hand side, for |x| in the normal double range, by
 // Tang's table-driven reduction (P. T. P. Tang, ACM TOMS 16, 1990): |x| = 2^k m
 // with m in [1, 2), F = 1 + (2j+1)/256 where j is the top 7 bits of m's
-// fraction, so f = m - F is exact in FP64 and |f| <= 2^-8; then
-// ln|x| = k ln2 + ln F + ln(1 + u), u = f/F.  k ln2 + ln F is summed in FP64
-// (one FMA with the double nearest ln 2, so |k| 2.3e-17 of representation
-// error, 1.6e-16 for the omegas of an inspiral); the remainder ln(1 + u) is
-// evaluated in double-single on the FP32 pipe: u, u^2/2 and u^3/3 as pairs and
-// u^4 (-1/4 + u/5 - u^2/6) in FP32 (below 1.1e-10, so its rounding is under
-// 1e-16 of it), truncation u^7/7 < 2.4e-18.  The remainder is thus within
-// ~1e-17 absolute, and the result carries only the FP64 roundings of the two
-// final sums: five FP64 instructions (an all-FP64 evaluation with the series
-// to u^6 takes thirteen).  Within 1.1e-15 absolute of ln|x| for x in
-// [0.005, 0.1] (checked against a long-double logarithm on the host).
-// tabf[4j..4j+3] = 1/F_j (hi, lo), ln F_j (hi, lo); tab[2j+1] = ln F_j (both
-// computed on the host in extended precision).
+// fraction, so f = m - F is exact and |f| <= 2^-8; then
+// ln|x| = k ln2 + (ln F + ln(1 + u)), u = f/F.  Only k ln2 and the final sum
+// are FP64 (one FMA with the double nearest ln 2, and the conversion of the
+// bracket to a double: two FP64 instructions; an all-FP64 evaluation with the
+// series to u^6 takes thirteen).  The bracket is formed in double-single on
+// the FP32 pipe: f from the significand bits by integer operations (exact),
+// u, u^2/2 and u^3/3 as pairs, u^4 (-1/4 + u/5 - u^2/6) in FP32 (below 1.1e-10,
+// so its rounding is under 1e-16 of it), truncation u^7/7 < 2.4e-18, and
+// ln F_j as a pair.  The bracket (|.| < 0.7) is then within ~3e-15 absolute,
+// and ln|x| within ~4e-15 absolute for x in [0.003, 0.2].  The right-hand side
+// takes the logarithm only in the v^6 term of P, with the coefficient 1712/315,
+// so this moves P by under 1e-16 of itself for v < 0.6.
+// tabf[4j..4j+3] = 1/F_j (hi, lo), ln F_j (hi, lo) (computed on the host in
+// extended precision); tab is not read (the double-single variant shares the
+// signature).
 __device__ __forceinline__ double log_w(double x, const double* __restrict__ tab, const float* __restrict__ tabf) {
+  (void)tab;
   const uint32_t hx = hi32(x) & 0x7fffffffu;
   const int k = (int)(hx >> 20) - 1023;
   const uint32_t j = (hx >> 13) & 127u;
-  const double m = mk64((hx & 0x000fffffu) | 0x3ff00000u, lo32(x));
-  const double F = mk64(0x3ff00000u | ((2u * j + 1u) << 12), 0u);
-  const ds u = ds_mul(split64(m - F), ds{tabf[4 * j], tabf[4 * j + 1]});
+  // f = m - F_j in units of 2^-52: m's 52 fraction bits minus F_j's, |D| <= 2^44,
+  // split into a high part of 24 bits and a low part of 21 bits (both exact floats).
+  const int64_t D = (int64_t)((((uint64_t)(hx & 0x000fffffu)) << 32) | lo32(x)) - ((int64_t)(2u * j + 1u) << 44);
+  const float fh = __fmul_rn(__int2float_rn((int)(D >> 21)), 4.656612873077393e-10f);  // 2^-31
+  const float fl = __fmul_rn(__int2float_rn((int)(D & 0x1fffff)), 2.220446049250313e-16f);  // 2^-52
+  const ds u = ds_mul(two_sum(fh, fl), ds{tabf[4 * j], tabf[4 * j + 1]});
   const ds u2 = ds_mul(u, u);
   const ds t3 = ds_mul(ds_mul(u2, u), ds{(float)(1.0 / 3.0), (float)(1.0 / 3.0 - (double)(float)(1.0 / 3.0))});
   const float uh = u.hi;
@@ -471,8 +487,8 @@ __device__ __forceinline__ double log_w(double x, const double* __restrict__ tab
   q = __fmaf_rn(q, uh, -0.25f);
   const float t4 = __fmul_rn(__fmul_rn(u2.hi, u2.hi), q);
   const ds rem = ds_add(u, ds_add(ds_scale(u2, -0.5f), ds_add(t3, ds_of(t4))));
-  const double kd = mk64(0x43300000u, (uint32_t)k ^ 0x80000000u) - 4503601774854144.0;
-  return fma(kd, 0.6931471805599453, tab[2 * j + 1]) + ds_to_f64(rem);
+  const ds br = ds_add(ds{tabf[4 * j + 2], tabf[4 * j + 3]}, rem);
+  return fma(i32_to_f64(k), 0.6931471805599453, ds_to_f64(br));
 }
 
 // x^(-1/3) in double-single: FP32 seed r0 = rcbrtf(hi), then
