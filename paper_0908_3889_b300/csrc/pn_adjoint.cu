@@ -49,7 +49,7 @@ __device__ __forceinline__ void cross_vjp(const double* a, const double* b, cons
   bb[2] += cb_[0] * a[1] - cb_[1] * a[0];
 }
 
-__device__ __noinline__ void rhs64_vjp(const Coef<double>& c, const double* __restrict__ tab,
+__device__ __noinline__ void rhs64_vjp(const Coef<double>& c,
                                        const float* __restrict__ tabf, const double* y, const double* fb, double* yb,
                                        Coef<double>& cb, double* f) {
   // ---- forward (as rhs64) ----
@@ -60,7 +60,7 @@ __device__ __noinline__ void rhs64_vjp(const Coef<double>& c, const double* __re
   const double r2 = r * r;
   const double v = w * r2;
   const double v2 = v * v;
-  const double lw = log_w(w, tab, tabf);
+  const double lw = log_w(w, tabf);
   const double LS1 = L[0] * S1[0] + L[1] * S1[1] + L[2] * S1[2];
   const double LS2 = L[0] * S2[0] + L[1] * S2[1] + L[2] * S2[2];
   const double S12 = S1[0] * S2[0] + S1[1] * S2[1] + S1[2] * S2[2];
@@ -235,12 +235,12 @@ __constant__ double c_dp_B[6] = {DP_B1, 0.0, DP_B3, DP_B4, DP_B5, DP_B6};
 // coefficients with K folded in, as there), writing the six
 // stage states Y_0 = y, ..., Y_5 to sp[(10 s + k) * ss].  With y5 == nullptr
 // only the stage states are made (the last rate k_6 is then not needed).
-__device__ __forceinline__ void dp5_stages(const Coef<double>& c, const double* __restrict__ tab,
+__device__ __forceinline__ void dp5_stages(const Coef<double>& c,
                                            const float* __restrict__ tabf, const double* y, double h, double* sp,
                                            size_t ss, double* y5) {
   double K[6][10], ys[10];
   for (int i = 0; i < 10; i++) sp[(size_t)i * ss] = y[i];
-  rhs64(c, tab, tabf, y, K[0]);
+  rhs64(c, tabf, y, K[0]);
 #pragma unroll 1
   for (int s = 1; s < 6; s++) {
     for (int i = 0; i < 10; i++) ys[i] = y[i];
@@ -250,7 +250,7 @@ __device__ __forceinline__ void dp5_stages(const Coef<double>& c, const double* 
         for (int i = 0; i < 10; i++) ys[i] = fma(a, K[j][i], ys[i]);
     }
     for (int i = 0; i < 10; i++) sp[(size_t)(10 * s + i) * ss] = ys[i];
-    if (s < 5 || y5) rhs64(c, tab, tabf, ys, K[s]);
+    if (s < 5 || y5) rhs64(c, tabf, ys, K[s]);
   }
   if (!y5) return;
   for (int i = 0; i < 10; i++) y5[i] = y[i];
@@ -267,7 +267,7 @@ __device__ __forceinline__ void dp5_stages(const Coef<double>& c, const double* 
 //   y5 = y + h sum_j b_j k_j,  Y_s = y + h sum_{j<s} a_sj k_j,  k_s = f(Y_s)
 // and kp_j = b_j lam + sum_{s>j} a_sj Yb_s (the cotangent of k_j is h kp_j):
 //   Yb_s = J(Y_s)^T (h kp_s),  yb = lam + sum_s Yb_s,  hb = sum_j k_j . kp_j.
-__device__ double dp5_step_vjp(const Coef<double>& c, const double* __restrict__ tab, const float* __restrict__ tabf,
+__device__ double dp5_step_vjp(const Coef<double>& c, const float* __restrict__ tabf,
                                const double* sp, size_t ss, double h, double* lam, Coef<double>& cb) {
   double kp[6][10], yb[10];
   for (int j = 0; j < 6; j++)
@@ -281,7 +281,7 @@ __device__ double dp5_step_vjp(const Coef<double>& c, const double* __restrict__
       Ys[i] = sp[(size_t)(10 * s + i) * ss];
       fb[i] = h * kp[s][i];
     }
-    rhs64_vjp(c, tab, tabf, Ys, fb, Yb, cb, ks);
+    rhs64_vjp(c, tabf, Ys, fb, Yb, cb, ks);
     for (int i = 0; i < 10; i++) {
       hb = fma(ks[i], kp[s][i], hb);
       yb[i] += Yb[i];
@@ -608,7 +608,7 @@ __device__ __forceinline__ void angle_grads(const double* gv, const double* s, d
 
 // Gradients of binary i; sp0 is the lane's segment buffer (stride ss).
 template <bool DS>
-__device__ void adjoint_one(const AdjArgs& a, const double* __restrict__ tab, const float* __restrict__ tabf,
+__device__ void adjoint_one(const AdjArgs& a, const float* __restrict__ tabf,
                             int64_t i, double* sp0, size_t ss) {
   const pn_outputs& o = a.k.out;
   const pn_grads& g = a.grad;
@@ -726,7 +726,7 @@ __device__ void adjoint_one(const AdjArgs& a, const double* __restrict__ tab, co
     for (int32_t n = n0; n < n1s; n++) {  // recompute the segment, keeping the stage states
       double y5[10];
       const bool more = n + 1 < n1s;
-      dp5_stages(cf, tab, tabf, y, a.h[(size_t)n * a.stride + i], sp0 + (size_t)(n - n0) * step_words, ss,
+      dp5_stages(cf, tabf, y, a.h[(size_t)n * a.stride + i], sp0 + (size_t)(n - n0) * step_words, ss,
                  more ? y5 : nullptr);
       if (more)
         for (int k = 0; k < 10; k++) y[k] = y5[k];
@@ -743,13 +743,13 @@ __device__ void adjoint_one(const AdjArgs& a, const double* __restrict__ tab, co
         double lA[10];
         for (int k = 0; k < 10; k++) lA[k] = 0.0;
         lA[0] = 1.0;
-        const double nu = dp5_step_vjp(c, tab, tabf, sp, ss, hn, lA, cA);
-        const double mu = dp5_step_vjp(c, tab, tabf, sp, ss, hn, lam, cB) + tbar;
+        const double nu = dp5_step_vjp(c, tabf, sp, ss, hn, lA, cA);
+        const double mu = dp5_step_vjp(c, tabf, sp, ss, hn, lam, cB) + tbar;
         const double ratio = mu / nu;
         for (int k = 0; k < 10; k++) lam[k] -= ratio * lA[k];
         for (int f = 0; f < 16; f++) cbv[f] += bv[f] - ratio * av[f];
       } else {
-        (void)dp5_step_vjp(c, tab, tabf, sp, ss, hn, lam, cb);
+        (void)dp5_step_vjp(c, tabf, sp, ss, hn, lam, cb);
       }
     }
   }
@@ -784,13 +784,8 @@ __device__ void adjoint_one(const AdjArgs& a, const double* __restrict__ tab, co
 // blockDim.x must be a multiple of 32.  DS: the double-single sweep.
 template <bool DS>
 __global__ void __launch_bounds__(128) k_adjoint(const AdjArgs a) {
-  __shared__ double s_tab[256];
   __shared__ float s_tabf[512];
-  for (int q = threadIdx.x; q < 256; q += blockDim.x) s_tab[q] = a.k.tab[q];
-  {
-    const float* gf = reinterpret_cast<const float*>(a.k.tab + 256);
-    for (int q = threadIdx.x; q < 512; q += blockDim.x) s_tabf[q] = gf[q];
-  }
+  for (int q = threadIdx.x; q < 512; q += blockDim.x) s_tabf[q] = a.k.tabf[q];
   __syncthreads();
   const int64_t slot = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const unsigned lane = threadIdx.x & 31u;
@@ -801,7 +796,7 @@ __global__ void __launch_bounds__(128) k_adjoint(const AdjArgs a) {
     base = __shfl_sync(0xffffffffu, base, 0);
     if (base >= (unsigned long long)a.k.n) break;
     const int64_t p = (int64_t)base + lane;
-    if (p < a.k.n) adjoint_one<DS>(a, s_tab, s_tabf, a.order[p], sp0, (size_t)a.seg_stride);
+    if (p < a.k.n) adjoint_one<DS>(a, s_tabf, a.order[p], sp0, (size_t)a.seg_stride);
   }
 }
 

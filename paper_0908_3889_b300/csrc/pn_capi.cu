@@ -24,7 +24,7 @@ struct pn_batch {
   int device = 0;
   int num_sms = 0;
   unsigned long long* d_queue = nullptr;
-  double* d_tab = nullptr;
+  float* d_tab = nullptr;
   double* d_stat_part = nullptr;
   double* d_stat_total = nullptr;
   double* d_setup = nullptr;  // per-binary set-up table, setup_fields() x n_max doubles
@@ -254,7 +254,7 @@ extern "C" int pn_batch_init(pn_batch** out, int64_t n_max, const pn_params* p, 
   if (e == cudaSuccess) e = cudaMalloc(&b->d_stat_total, pn::kStatWords * sizeof(double));
   for (int k = 0; k < 6 && e == cudaSuccess; k++) e = cudaEventCreate(&b->ev[k]);
   if (e == cudaSuccess) {
-    double tab[pn::kLogTabBytes / sizeof(double)];
+    float tab[pn::kLogTabBytes / sizeof(float)];
     pn::fill_log_table(tab);
     e = cudaMemcpy(b->d_tab, tab, sizeof(tab), cudaMemcpyHostToDevice);
   }
@@ -327,7 +327,7 @@ int run_integrate(pn_batch* b, int64_t n, const pn_inputs* in, pn_outputs* out, 
   a.out = *out;
   a.n = n;
   a.queue = b->d_queue;
-  a.tab = b->d_tab;
+  a.tabf = b->d_tab;
   a.ctl = make_ctl(b->p);
   a.bpt = sh.bpt;
   a.budget = budget;
@@ -669,7 +669,7 @@ extern "C" int pn_batch_adjoint(pn_batch* b, int64_t n, const pn_inputs* in, con
   a.out = o;
   a.n = n;
   a.queue = b->d_queue;
-  a.tab = b->d_tab;
+  a.tabf = b->d_tab;
   a.ctl = make_ctl(b->p);
   PN_CUDA(b, cudaEventRecord(b->ev[4], b->stream));
 

@@ -223,7 +223,7 @@ __device__ __forceinline__ Coef<float> to_f32(const Coef<double>& c) {
   return f;
 }
 
-__device__ __forceinline__ double log_w(double x, const double* __restrict__ tab, const float* __restrict__ tabf);
+__device__ __forceinline__ double log_w(double x, const float* __restrict__ tabf);
 
 // ---------------------------------------------------------------------------
 // Right-hand side f(y), y = (omega, S1, S2, L), M = 1, x = omega, v = x^{1/3}.
@@ -239,7 +239,7 @@ __device__ __forceinline__ double log_w(double x, const double* __restrict__ tab
 // ---------------------------------------------------------------------------
 // c holds the coefficients of P with the prefactor K folded in (fold_K), so that
 // omega-dot = omega^2 v^5 P_K with P_K = K P.
-__device__ __forceinline__ void rhs64(const Coef<double>& c, const double* __restrict__ tab,
+__device__ __forceinline__ void rhs64(const Coef<double>& c,
                                       const float* __restrict__ tabf, const double* y, double* f) {
   const double w = y[0];
   const double S1x = y[1], S1y = y[2], S1z = y[3];
@@ -251,7 +251,7 @@ __device__ __forceinline__ void rhs64(const Coef<double>& c, const double* __res
   if ((hi32(w) & 0x7fffffffu) - (897u << 20) >= ((1151u - 897u) << 20)) r = dnan();
   const double v = w * (r * r);
   const double v2 = v * v;
-  const double lw = log_w(w, tab, tabf);
+  const double lw = log_w(w, tabf);
 
   const double LS1 = fma(Lz, S1z, fma(Ly, S1y, Lx * S1x));
   const double LS2 = fma(Lz, S2z, fma(Ly, S2y, Lx * S2x));
@@ -467,10 +467,8 @@ __device__ __forceinline__ double i32_to_f64(int k) {
 // takes the logarithm only in the v^6 term of P, with the coefficient 1712/315,
 // so this moves P by under 1e-16 of itself for v < 0.6.
 // tabf[4j..4j+3] = 1/F_j (hi, lo), ln F_j (hi, lo) (computed on the host in
-// extended precision); tab is not read (the double-single variant shares the
-// signature).
-__device__ __forceinline__ double log_w(double x, const double* __restrict__ tab, const float* __restrict__ tabf) {
-  (void)tab;
+// extended precision).
+__device__ __forceinline__ double log_w(double x, const float* __restrict__ tabf) {
   const uint32_t hx = hi32(x) & 0x7fffffffu;
   const int k = (int)(hx >> 20) - 1023;
   const uint32_t j = (hx >> 13) & 127u;
@@ -598,8 +596,7 @@ struct Coefs {
   Coef<ds> cds;
 };
 struct Tabs {
-  const double* d;  // 256 doubles: 1/F_j, ln F_j
-  const float* f;   // 512 floats: 1/F_j, ln F_j as FP32 pairs (ds_log, log_w)
+  const float* f;  // 512 floats: 1/F_j, ln F_j as FP32 pairs (ds_log, log_w)
 };
 
 // ---------------------------------------------------------------------------
@@ -649,7 +646,7 @@ struct Ctl {
 template <int PREC>
 __device__ __forceinline__ void eval_rhs(const Coefs& cf, const Tabs& tb, const double* y, double* k) {
   if constexpr (PREC == 0) {
-    rhs64(cf.c64, tb.d, tb.f, y, k);
+    rhs64(cf.c64, tb.f, y, k);
   } else if constexpr (PREC == 1) {
     float yf[10], kf[10];
 #pragma unroll
@@ -720,7 +717,7 @@ __device__ __forceinline__ double dp5_attempt_ws(const Coefs& cf, const Tabs& tb
         ys[i] = y5[i];
       }
     }
-    rhs64(cf.c64, tb.d, tb.f, ys, kn);  // k_{r+2}; for r = 5, k7 = f(y5)
+    rhs64(cf.c64, tb.f, ys, kn);  // k_{r+2}; for r = 5, k7 = f(y5)
     if (r < 5) {
 #pragma unroll
       for (int i = 0; i < 10; i++) w.put(r + 2, i, kn[i]);

@@ -17,7 +17,7 @@ struct KArgs {
   pn_outputs out;
   int64_t n;
   unsigned long long* queue;  // persistent schedule: next unclaimed binary index
-  const double* tab;          // logarithm tables: 256 doubles (1/F_j, ln F_j), then 512 floats (pairs)
+  const float* tabf;          // logarithm table: 512 floats, (1/F_j, ln F_j) as FP32 pairs
   Ctl ctl;
   int32_t bpt;                // plain schedule: binaries each thread integrates in turn (0 or 1: one)
   int32_t budget;             // attempts per binary in this launch (0: no limit)
@@ -74,7 +74,7 @@ cudaError_t integrate_occupancy(int prec, bool persistent, int block, int* block
 
 // f(y) at n states (component-major y[c * n + i], f likewise) in precision prec.
 cudaError_t launch_eval_rhs(int prec, int64_t n, const double* m1, const double* m2, const double* y, double* f,
-                            const double* tab, TermCfg tc, cudaStream_t s);
+                            const float* tab, TermCfg tc, cudaStream_t s);
 
 cudaError_t launch_sample(uint64_t seed, const pn_dist& d, int64_t n, const pn_inputs& in, cudaStream_t s);
 
@@ -91,9 +91,9 @@ bool check_params(const pn_params* p, std::string* why);
 bool check_io(const pn_inputs* in, const pn_outputs* out);
 Ctl ctl_from(const pn_params& p);
 
-// Host-side logarithm tables (kLogTabBytes): tab[2j] = 1/F_j, tab[2j+1] = ln F_j (log_w), then
-// 512 floats for ds_log: (1/F_j hi, lo, ln F_j hi, lo), F_j = 1 + (2j+1)/256.
-constexpr size_t kLogTabBytes = 256 * sizeof(double) + 512 * sizeof(float);
-void fill_log_table(double* tab);
+// Host-side logarithm table (kLogTabBytes) for log_w and ds_log: 512 floats,
+// (1/F_j hi, lo, ln F_j hi, lo), F_j = 1 + (2j+1)/256.
+constexpr size_t kLogTabBytes = 512 * sizeof(float);
+void fill_log_table(float* tabf);
 
 }  // namespace pn

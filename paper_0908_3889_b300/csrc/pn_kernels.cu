@@ -37,16 +37,12 @@ struct Lane {
 
 // Shared-memory copies of the logarithm tables the kernel's precision needs.
 template <int PREC>
-__device__ __forceinline__ Tabs load_tabs(const double* __restrict__ g, double* s_tab, float* s_tabf) {
-  if constexpr (PREC == 0) {
-    for (int q = threadIdx.x; q < 256; q += blockDim.x) s_tab[q] = g[q];
-  }
+__device__ __forceinline__ Tabs load_tabs(const float* __restrict__ g, float* s_tabf) {
   if constexpr (PREC == 0 || PREC == 2) {
-    const float* gf = (const float*)(g + 256);
-    for (int q = threadIdx.x; q < 512; q += blockDim.x) s_tabf[q] = gf[q];
+    for (int q = threadIdx.x; q < 512; q += blockDim.x) s_tabf[q] = g[q];
   }
   __syncthreads();
-  return Tabs{s_tab, s_tabf};
+  return Tabs{s_tabf};
 }
 
 // Final state, time, counters and status of binary i.  The scalar products are
@@ -109,10 +105,9 @@ __device__ __forceinline__ double* fld(double* ws, int64_t stride, int f) { retu
 template <int PREC>
 __global__ void __launch_bounds__(256) k_eval_rhs(int64_t n, const double* __restrict__ m1,
                                                   const double* __restrict__ m2, const double* __restrict__ y,
-                                                  double* __restrict__ f, const double* __restrict__ tab, TermCfg tc) {
-  __shared__ double s_tab[256];
+                                                  double* __restrict__ f, const float* __restrict__ tab, TermCfg tc) {
   __shared__ float s_tabf[512];
-  const Tabs tb = load_tabs<PREC>(tab, s_tab, s_tabf);
+  const Tabs tb = load_tabs<PREC>(tab, s_tabf);
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   Coefs cf;
@@ -130,9 +125,8 @@ __global__ void __launch_bounds__(256) k_eval_rhs(int64_t n, const double* __res
 
 template <int PREC>
 __global__ void __launch_bounds__(256) k_setup(const KArgs a, double* __restrict__ ws, int64_t stride) {
-  __shared__ double s_tab[256];
   __shared__ float s_tabf[512];
-  const Tabs tb = load_tabs<PREC>(a.tab, s_tab, s_tabf);
+  const Tabs tb = load_tabs<PREC>(a.tabf, s_tabf);
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= a.n) return;
   ws[(size_t)(kSetupFields + 10) * stride + i] = 0.0;  // no deferred landing move yet
@@ -389,10 +383,9 @@ __device__ __forceinline__ bool lane_decide(Lane& L, const Ctl& ctl, double* y5,
 template <int PREC, bool PERSIST, bool RECORD, bool BOUNDED, bool WS>
 __device__ __forceinline__ void integrate_body(const KArgs& a, const double* __restrict__ ws, int64_t stride,
                                                const RecArgs& rec) {
-  __shared__ double s_tab[256];
   __shared__ float s_tabf[512];
-  extern __shared__ float2 s_dsw[];  // per-thread stage workspace (PREC 1: kF32WorkBytes, PREC 2: kDsWorkBytes)
-  const Tabs tb = load_tabs<PREC>(a.tab, s_tab, s_tabf);
+  extern __shared__ float2 s_dsw[];  // per-thread stage workspace (PREC 0: kF64WorkBytes, 1: kF32WorkBytes, 2: kDsWorkBytes)
+  const Tabs tb = load_tabs<PREC>(a.tabf, s_tabf);
 
   const unsigned lane = threadIdx.x & 31u;
   Lane L;
@@ -488,7 +481,7 @@ static const void* pick(int prec, bool persistent) {
 int setup_fields() { return kSetupFields + kLandFields; }
 
 cudaError_t launch_eval_rhs(int prec, int64_t n, const double* m1, const double* m2, const double* y, double* f,
-                            const double* tab, TermCfg tc, cudaStream_t s) {
+                            const float* tab, TermCfg tc, cudaStream_t s) {
   if (n <= 0) return cudaSuccess;
   const int block = 256;
   const int64_t grid = (n + block - 1) / block;
@@ -803,13 +796,10 @@ cudaError_t launch_stats(int64_t n, const pn_inputs& in, const pn_outputs& out, 
   return cudaGetLastError();
 }
 
-void fill_log_table(double* tab) {
-  float* tabf = (float*)(tab + 256);
+void fill_log_table(float* tabf) {
   for (int j = 0; j < 128; j++) {
     const long double F = 1.0L + (long double)(2 * j + 1) / 256.0L;
     const long double inv = 1.0L / F, ln = logl(F);
-    tab[2 * j] = (double)inv;
-    tab[2 * j + 1] = (double)ln;
     const float ih = (float)inv, lh = (float)ln;
     tabf[4 * j] = ih;
     tabf[4 * j + 1] = (float)(inv - (long double)ih);

@@ -29,7 +29,7 @@ namespace {
 
 constexpr int64_t kNoAllocMax = 16384;  // binaries per call
 constexpr size_t kQueueOff = 0;         // unsigned long long work-queue counter
-constexpr size_t kTabOff = 256;         // the logarithm tables (pn::kLogTabBytes)
+constexpr size_t kTabOff = 256;         // the logarithm table (pn::kLogTabBytes)
 constexpr size_t kSetupOff = 256 + 4096;
 constexpr size_t kNoAllocBytes = kSetupOff + (size_t)(37 + pn::kLandFields) * kNoAllocMax * sizeof(double);
 
@@ -38,7 +38,7 @@ static __device__ __align__(256) unsigned char g_scratch[kNoAllocBytes];
 constexpr int kMaxDevices = 64;
 std::mutex g_mu;
 unsigned char* g_ptr[kMaxDevices] = {};  // device address of g_scratch per device, once looked up
-double g_host_tab[pn::kLogTabBytes / sizeof(double)];
+float g_host_tab[pn::kLogTabBytes / sizeof(float)];
 
 int scratch_for_current_device(unsigned char** out, std::string* why) {
   int dev = 0;
@@ -87,7 +87,7 @@ extern "C" int pn_integrate_noalloc(int64_t n, const pn_params* p, const pn_inpu
   a.out = *out;
   a.n = n;
   a.queue = (unsigned long long*)(base + kQueueOff);
-  a.tab = (const double*)(base + kTabOff);
+  a.tabf = (const float*)(base + kTabOff);
   a.ctl = pn::ctl_from(*p);
   double* table = (double*)(base + kSetupOff);
 
