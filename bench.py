@@ -48,7 +48,7 @@ FP64_DATASHEET_TFLOPS = 1.25  # nominal dense FP64 of one B300
 # DRAM traffic of the integration kernel per binary from an ncu capture
 # (dram__bytes_read.sum + dram__bytes_write.sum, profiles/); valid only while
 # the kernel sources hash (kernel_sha) to the recorded value.
-PROFILED = {"kernel_sha": "d1f86bcef30acdff", "dram_bytes_per_binary": (39.480576e6 + 1.135104e6) / 131072}
+PROFILED = {"kernel_sha": "4e915854aaac3794", "dram_bytes_per_binary": (39.478272e6 + 1.366784e6) / 131072}
 
 
 def kernel_sha() -> str:
