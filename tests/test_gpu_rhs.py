@@ -82,6 +82,21 @@ def test_rhs_fp64_term_mask_and_theta_mode(pn, orc):
             assert np.max(v) <= TOL[0], (kw, k, float(np.max(v)))
 
 
+def test_rhs_fp64_wide_omega_range(pn, orc):
+    """FP64 rates for M omega log-uniform in [2^-100, 2^100], far outside an inspiral: the logarithm's
+    exponent term k ln 2 (k converted to a double by integer operations) for every k in [-100, 99],
+    and its table reduction, against the oracle at the same tolerance as the inspiral range."""
+    st = workloads.states(2048, seed=workloads.SEED_BASE + 303, omega_range=(2.0 ** -100, 2.0 ** 100))
+    k = np.floor(np.log2(st["y"][0])).astype(int)
+    assert k.min() <= -95 and k.max() >= 94
+    ref = np.stack([orc.rhs(st["y"][:, i], st["m1"][i], st["m2"][i]) for i in range(2048)], axis=1)
+    got = device_rhs(pn, st, 0)
+    assert np.all(np.isfinite(got)) and np.all(np.isfinite(ref))
+    e = rel_errors(got, ref)
+    for name, v in e.items():
+        assert np.max(v) <= TOL[0], (name, float(np.max(v)))
+
+
 def test_rhs_out_of_range_omega_gives_non_finite_rates(pn):
     st = workloads.states(8, seed=workloads.SEED_BASE + 302)
     st["y"][0] = [0.0, -0.0, 1e-310, np.inf, np.nan, 1e300, 1e-40, 0.02]

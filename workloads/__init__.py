@@ -98,17 +98,18 @@ def config(name: str, n: int | None = None, seed: int | None = None) -> dict:
     raise KeyError(name)
 
 
-def states(n: int, seed: int) -> dict:
+def states(n: int, seed: int, omega_range: tuple = (0.003, 0.2)) -> dict:
     """n random points of the state space, for checking right-hand sides point by point: q = m1/m2
-    log-uniform in [1, 10], M omega log-uniform in [0.003, 0.2], spin vectors of isotropic direction and
-    magnitude uniform in [0, m_i^2], L-hat isotropic.  Returns m1, m2 (n,) and y (10, n), component-major
-    (omega, S1, S2, L-hat)."""
+    log-uniform in [1, 10], M omega log-uniform in omega_range (default [0.003, 0.2]), spin vectors of
+    isotropic direction and magnitude uniform in [0, m_i^2], L-hat isotropic.  Returns m1, m2 (n,) and
+    y (10, n), component-major (omega, S1, S2, L-hat)."""
     u = _uniforms(seed, (9, n))
     qv = np.exp(u[0] * np.log(10.0))
     m1 = qv / (1.0 + qv)
     m2 = 1.0 / (1.0 + qv)
     y = np.empty((10, n))
-    y[0] = 0.003 * np.exp(u[1] * np.log(0.2 / 0.003))
+    lo, hi = omega_range
+    y[0] = lo * np.exp(u[1] * np.log(hi / lo))
     y[1:4] = _isotropic(u[2], u[3]) * (u[4] * m1 * m1)
     y[4:7] = _isotropic(u[5], u[6]) * (u[7] * m2 * m2)
     y[7:10] = _isotropic(u[8], _uniforms(seed + 1, (n,)))
