@@ -7,10 +7,12 @@
 //
 // B300 shapes this file: the FP64 pipe issues ~2 lanes/clk/SM (64x below FP32),
 // and the CUDA FP64 cbrt / log / pow / divide cost roughly 17 / 37 / 100 / 8
-// FMA-equivalents there.  So every FP64 instruction counts.  The
-// transcendentals the RHS and the step control need are computed from FP32
-// seeds plus short FP64 corrections whose truncation error is below 1e-17
-// relative; comparisons, absolute values and maxima of doubles use integer
+// FMA-equivalents there.  So every FP64 instruction counts.  The inverse cube
+// root, reciprocals and the step control's power are computed from FP32 seeds
+// plus short FP64 corrections whose truncation error is below 1e-17 relative;
+// the logarithm, which enters only P's v^6 term, keeps only k ln 2 and the
+// final sum in FP64 and takes the rest in double-single on the FP32 pipe
+// (within ~4e-15 absolute); comparisons, absolute values and maxima of doubles use integer
 // instructions on the bit patterns; and in mixed precision the FP32<->FP64
 // conversions are done with integer instructions, not the FP64 pipe.
 #pragma once
