@@ -112,3 +112,22 @@ def test_ds_small_ensembles(pn, orc, schedule):
         assert np.array_equal(g["status"], o["status"])
         for k in ("dot_s1s2", "dot_ls1", "dot_ls2"):
             assert np.max(e[k]) <= DOT_TOL, (name, k, np.max(e[k]))
+
+
+@pytest.mark.parametrize("schedule", [1, 2])
+def test_ds_small_ensembles_meet_dot_bar(pn, orc, schedule):
+    """The double-single form on the other ensembles' shapes (C0 maximal spins, C2 uneven lengths
+    with q up to 10 and small spins, C4 q in [1, 4]): every binary within the 1e-6 bar on the final
+    scalar products, the oracle's statuses, and the oracle's step decisions for almost all."""
+    import torch
+    from gpu_util import decided_alike
+    for name in ("C0", "C2", "C4"):
+        ens = workloads.config(name, n=2000)
+        o = orc.integrate(ens)
+        g = pn.to_numpy(pn.integrate(pn.to_device(ens), precision=2, schedule=schedule))
+        torch.cuda.synchronize()
+        assert np.array_equal(g["status"], o["status"]), name
+        e = mixed_errors(g, o)
+        for k in ("dot_s1s2", "dot_ls1", "dot_ls2"):
+            assert np.max(e[k]) <= DOT_TOL, (name, k, float(np.max(e[k])))
+        assert np.mean(decided_alike(g, o)) >= 0.995, (name, float(np.mean(decided_alike(g, o))))
