@@ -225,7 +225,8 @@ void pn_params_default(pn_params *p);
 /* Create a batch context for up to n_max binaries per call on the current
  * CUDA device and the given stream (cudaStream_t, NULL = legacy default).
  * Allocates the small device workspace (queue head, reduction buffers, the
- * logarithm table) and records *p.  Errors: PN_E_ARG (NULL out/p, n_max < 1,
+ * logarithm table), uploads the table and waits for the device, and records
+ * *p.  Errors: PN_E_ARG (NULL out/p, n_max < 1,
  * bad parameters), PN_E_CUDA, PN_E_NOMEM.  *out is NULL on failure. */
 int pn_batch_init(pn_batch **out, int64_t n_max, const pn_params *p, void *cuda_stream);
 
@@ -385,8 +386,8 @@ void pn_batch_destroy(pn_batch *b);
  * pn_batch_init / pn_batch_integrate, and the work is queued on cuda_stream
  * (cudaStream_t, NULL = legacy default) without waiting.  All calls share the
  * area (each call resets what it reads), so calls whose GPU work overlaps race.
- * The first call on a device looks up the area's address and uploads the
- * logarithm table with a synchronous copy; make that first call before any
+ * The first call on a device looks up the area's address, uploads the
+ * logarithm table and waits for the device; make that first call before any
  * stream capture.  Errors: PN_E_ARG, PN_E_CUDA; message via pn_last_error(NULL). */
 int pn_integrate_noalloc(int64_t n, const pn_params *p, const pn_inputs *in, pn_outputs *out, void *cuda_stream);
 

@@ -13,6 +13,7 @@ where the paper is silent, and which functions are pinned by which tests.
 """
 from __future__ import annotations
 
+import contextlib
 import ctypes as C
 import os
 import subprocess
@@ -32,14 +33,46 @@ NEWTONIAN = T_PREC  # leading-order chirp, precession on
 ST_OK, ST_MAX_STEPS, ST_H_UNDERFLOW, ST_NONFINITE, ST_BAD_INPUT, ST_LAND_MAXIT = range(6)
 
 
+def _compile(src: str, out: str) -> None:
+    cmd = ["g++", "-std=c++17", "-O3", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared",
+           "-pthread", "-Wall", "-o", out + ".tmp", src]
+    subprocess.run(cmd, check=True)
+    os.replace(out + ".tmp", out)
+
+
 def build(force: bool = False) -> str:
     """Compile pn_oracle.cpp into libpn_oracle.so (portable -O3, no FMA contraction)."""
     if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
-        cmd = ["g++", "-std=c++17", "-O3", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared",
-               "-pthread", "-Wall", "-o", _LIB + ".tmp", _SRC]
-        subprocess.run(cmd, check=True)
-        os.replace(_LIB + ".tmp", _LIB)
+        _compile(_SRC, _LIB)
     return _LIB
+
+
+def source() -> str:
+    with open(_SRC) as fh:
+        return fh.read()
+
+
+def build_variant(src_text: str, directory: str, name: str) -> str:
+    """Compile a modified copy of the oracle's source (a planted mistake, for checking that the pins catch
+    it) into directory/name.so with the oracle's own flags; returns the library path."""
+    src = os.path.join(directory, name + ".cpp")
+    with open(src, "w") as fh:
+        fh.write(src_text)
+    out = os.path.join(directory, name + ".so")
+    _compile(src, out)
+    return out
+
+
+@contextlib.contextmanager
+def variant(path: str):
+    """Route every wrapper in this module through another build of the oracle while the block runs."""
+    global _lib
+    saved = lib()
+    _lib = _bind(C.CDLL(path))
+    try:
+        yield
+    finally:
+        _lib = saved
 
 
 class Params(C.Structure):
@@ -86,33 +119,37 @@ _lib = None
 def lib():
     global _lib
     if _lib is None:
-        L = C.CDLL(build())
-        L.oracle_abi_version.restype = C.c_int
-        assert L.oracle_abi_version() == ABI_VERSION
-        L.oracle_tableau.argtypes = [_DP, _DP, _DP, _DP]
-        L.oracle_rhs.argtypes = [C.POINTER(Params), C.c_double, C.c_double, _DP, _DP]
-        L.oracle_dp5_attempt.argtypes = [C.POINTER(Params), C.c_double, C.c_double, _DP, C.c_double, _DP]
-        L.oracle_dp5_attempt.restype = C.c_double
-        L.oracle_integrate_batch.argtypes = [C.c_int64, C.POINTER(_BatchIn), C.POINTER(Params),
-                                             C.POINTER(_BatchOut), C.c_int]
-        L.oracle_integrate_batch.restype = C.c_int
-        L.oracle_trace.argtypes = [C.POINTER(_BatchIn), C.c_int64, C.POINTER(Params), _DP, C.c_int64, _DP,
-                                   C.c_int64]
-        L.oracle_trace.restype = C.c_int64
-        L.oracle_replay.argtypes = [C.POINTER(_BatchIn), C.c_int64, C.POINTER(Params), _DP, C.c_int64, _DP, _DP]
-        L.oracle_replay.restype = C.c_int
-        L.oracle_grad.argtypes = [C.POINTER(_BatchIn), C.c_int64, C.POINTER(Params), _DP, _DP]
-        L.oracle_grad.restype = C.c_int64
-        L.oracle_count_ops.argtypes = [C.POINTER(Params), C.c_double, C.c_double, _DP,
-                                       C.POINTER(C.c_int64), C.POINTER(C.c_int64)]
-        L.oracle_splitmix64_next.argtypes = [C.POINTER(C.c_uint64)]
-        L.oracle_splitmix64_next.restype = C.c_uint64
-        L.oracle_uniform.argtypes = [C.c_uint64, C.c_uint64, C.c_uint64]
-        L.oracle_uniform.restype = C.c_double
-        L.oracle_sample.argtypes = [C.c_uint64, C.POINTER(_Dist), C.c_int64] + [_DP] * 15
-        L.oracle_sample_at.argtypes = [C.c_uint64, C.POINTER(_Dist), C.POINTER(C.c_int64), C.c_int64] + [_DP] * 15
-        _lib = L
+        _lib = _bind(C.CDLL(build()))
     return _lib
+
+
+def _bind(L):
+    """Declare the argument and result types of the oracle's extern "C" functions on a loaded library."""
+    L.oracle_abi_version.restype = C.c_int
+    assert L.oracle_abi_version() == ABI_VERSION
+    L.oracle_tableau.argtypes = [_DP, _DP, _DP, _DP]
+    L.oracle_rhs.argtypes = [C.POINTER(Params), C.c_double, C.c_double, _DP, _DP]
+    L.oracle_dp5_attempt.argtypes = [C.POINTER(Params), C.c_double, C.c_double, _DP, C.c_double, _DP]
+    L.oracle_dp5_attempt.restype = C.c_double
+    L.oracle_integrate_batch.argtypes = [C.c_int64, C.POINTER(_BatchIn), C.POINTER(Params),
+                                         C.POINTER(_BatchOut), C.c_int]
+    L.oracle_integrate_batch.restype = C.c_int
+    L.oracle_trace.argtypes = [C.POINTER(_BatchIn), C.c_int64, C.POINTER(Params), _DP, C.c_int64, _DP,
+                               C.c_int64]
+    L.oracle_trace.restype = C.c_int64
+    L.oracle_replay.argtypes = [C.POINTER(_BatchIn), C.c_int64, C.POINTER(Params), _DP, C.c_int64, _DP, _DP]
+    L.oracle_replay.restype = C.c_int
+    L.oracle_grad.argtypes = [C.POINTER(_BatchIn), C.c_int64, C.POINTER(Params), _DP, _DP]
+    L.oracle_grad.restype = C.c_int64
+    L.oracle_count_ops.argtypes = [C.POINTER(Params), C.c_double, C.c_double, _DP,
+                                   C.POINTER(C.c_int64), C.POINTER(C.c_int64)]
+    L.oracle_splitmix64_next.argtypes = [C.POINTER(C.c_uint64)]
+    L.oracle_splitmix64_next.restype = C.c_uint64
+    L.oracle_uniform.argtypes = [C.c_uint64, C.c_uint64, C.c_uint64]
+    L.oracle_uniform.restype = C.c_double
+    L.oracle_sample.argtypes = [C.c_uint64, C.POINTER(_Dist), C.c_int64] + [_DP] * 15
+    L.oracle_sample_at.argtypes = [C.c_uint64, C.POINTER(_Dist), C.POINTER(C.c_int64), C.c_int64] + [_DP] * 15
+    return L
 
 
 def _dp(a: np.ndarray):

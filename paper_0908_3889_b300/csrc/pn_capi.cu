@@ -257,6 +257,9 @@ extern "C" int pn_batch_init(pn_batch** out, int64_t n_max, const pn_params* p, 
     float tab[pn::kLogTabBytes / sizeof(float)];
     pn::fill_log_table(tab);
     e = cudaMemcpy(b->d_tab, tab, sizeof(tab), cudaMemcpyHostToDevice);
+    // The copy from pageable memory may return before its DMA lands, and the batch's stream may be a
+    // non-blocking one: wait for the table before the first kernel reads it.
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
   }
   if (e != cudaSuccess) {
     const int rc = (e == cudaErrorMemoryAllocation) ? PN_E_NOMEM : PN_E_CUDA;

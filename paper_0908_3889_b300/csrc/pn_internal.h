@@ -52,9 +52,12 @@ cudaError_t launch_integrate_record(const KArgs& a, const double* ws, int64_t st
 cudaError_t record_occupancy(int block, int* blocks_per_sm);
 
 // Set-up table: setup_fields() doubles per binary, field-major with the given stride (>= n): the
-// set-up fields, then kLandFields fields for the final move of a binary that lands on omega_f
-// (f(y5) and dh, written by the integration kernel, applied and cleared by the output epilogue).
+// kSetupFields set-up fields (16 coefficients, y0, k1 = f(y0), omega_f), then kLandFields fields for
+// the final move of a binary that lands on omega_f (f(y5) and dh, written by the integration kernel,
+// applied and cleared by the output epilogue).
+constexpr int kSetupFields = 37;
 constexpr int kLandFields = 11;
+constexpr int kTableFields = kSetupFields + kLandFields;
 int setup_fields();
 // Validate every binary, write BAD_INPUT results, and fill the set-up table.
 cudaError_t launch_setup(int prec, const KArgs& a, double* ws, int64_t stride, cudaStream_t s);

@@ -96,7 +96,7 @@ __global__ void __launch_bounds__(256) k_dots(const pn_outputs o, int64_t n, dou
 // result is already written).  k_setup fills it with one converged pass, so a
 // lane that picks up a new binary in the integration kernel only loads.  The
 // kLandFields fields after them hold the deferred landing moves (k_dots).
-constexpr int kSetupFields = 37;
+// kSetupFields (pn_internal.h) counts the fields before them.
 
 __device__ __forceinline__ double* fld(double* ws, int64_t stride, int f) { return ws + (size_t)f * stride; }
 
@@ -478,7 +478,7 @@ static const void* pick(int prec, bool persistent) {
   return persistent ? integrate_fn<0, true>() : integrate_fn<0, false>();
 }
 
-int setup_fields() { return kSetupFields + kLandFields; }
+int setup_fields() { return kTableFields; }
 
 cudaError_t launch_eval_rhs(int prec, int64_t n, const double* m1, const double* m2, const double* y, double* f,
                             const float* tab, TermCfg tc, cudaStream_t s) {

@@ -15,8 +15,8 @@
 // The array is shared by all calls: each call resets the queue counter and
 // rewrites the set-up entries it uses, and calls whose GPU work overlaps (on
 // different streams, or from different host threads) race on it.  The first
-// call on each device looks up the array's device address and uploads the
-// logarithm table with a synchronous copy, so that first call should come
+// call on each device looks up the array's device address, uploads the
+// logarithm table and waits for the device, so that first call should come
 // before any stream capture.
 
 #include <cstring>
@@ -31,7 +31,9 @@ constexpr int64_t kNoAllocMax = 16384;  // binaries per call
 constexpr size_t kQueueOff = 0;         // unsigned long long work-queue counter
 constexpr size_t kTabOff = 256;         // the logarithm table (pn::kLogTabBytes)
 constexpr size_t kSetupOff = 256 + 4096;
-constexpr size_t kNoAllocBytes = kSetupOff + (size_t)(37 + pn::kLandFields) * kNoAllocMax * sizeof(double);
+constexpr size_t kNoAllocBytes = kSetupOff + (size_t)pn::kTableFields * kNoAllocMax * sizeof(double);
+static_assert(kTabOff + pn::kLogTabBytes <= kSetupOff, "the logarithm table overlaps the set-up table");
+static_assert(kSetupOff % 256 == 0, "the set-up table must start on a 256-byte boundary");
 
 static __device__ __align__(256) unsigned char g_scratch[kNoAllocBytes];
 
@@ -50,13 +52,11 @@ int scratch_for_current_device(unsigned char** out, std::string* why) {
     void* p = nullptr;
     e = cudaGetSymbolAddress(&p, g_scratch);
     if (e != cudaSuccess) { *why = std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e); return PN_E_CUDA; }
-    if (pn::setup_fields() * (size_t)kNoAllocMax * sizeof(double) + kSetupOff > kNoAllocBytes ||
-        kTabOff + pn::kLogTabBytes > kSetupOff) {
-      *why = "set-up table does not fit the scratch area";
-      return PN_E_ARG;
-    }
     pn::fill_log_table(g_host_tab);
     e = cudaMemcpy((unsigned char*)p + kTabOff, g_host_tab, sizeof(g_host_tab), cudaMemcpyHostToDevice);
+    // A copy from pageable memory may return before its DMA lands, and a caller's non-blocking
+    // stream is not ordered after the legacy stream: wait for the table before any kernel reads it.
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
     if (e != cudaSuccess) { *why = std::string("log table upload: ") + cudaGetErrorString(e); return PN_E_CUDA; }
     g_ptr[dev] = (unsigned char*)p;
   }

@@ -5,7 +5,11 @@ FP32 rounding in the rates perturbs the embedded error estimate by ~1e-3 of
 its value, so a few step sizes (and, rarely, an accept/reject decision) differ
 from the FP64 run; the outputs then differ by the integration error itself,
 which for small spins at tolerance 5e-7 is up to ~1e-3.  The typical binary
-agrees to ~1e-7.  The bounds below state that behaviour."""
+agrees to ~1e-7.  The FP32 form's error is stated, not held to the 1e-6 bar:
+each bound below is about three times the error measured on the B300 for that
+ensemble (max, 99th percentile and median of |dot - oracle| over its binaries,
+largest of the three scalar products), so a regression in the FP32
+right-hand side fails."""
 import numpy as np
 import pytest
 
@@ -14,6 +18,21 @@ import workloads
 pytestmark = pytest.mark.gpu
 
 DOT_TOL = 1e-6  # bar on the final spin scalar products in mixed precision
+
+# FP32 form, bounds on |dot - oracle| as (max, p99, median).  Measured (max, p99, median):
+#   C1 4,096 subsample  2.7e-6, 1.1e-6, 1.3e-7  (all 1,048,576 binaries: max 6.4e-6, p99 1.0e-6)
+#   C0 2,000            9.4e-7, 3.8e-7, 6.0e-8
+#   C4 2,000            5.4e-6, 2.7e-6, 3.2e-7
+#   C2 2,000            3.6e-3, 9.0e-5, 4.3e-7  (q up to 10, spins down to 0: S2 far below the tolerance)
+FP32_STATED = {"C3": (1e-5, 1.5e-6, 3e-7), "C0": (3e-6, 1.2e-6, 2e-7), "C4": (1.6e-5, 8e-6, 1e-6),
+               "C2": (1.1e-2, 3e-4, 1.3e-6)}
+
+
+def assert_stated(e, name):
+    mx, p99, p50 = FP32_STATED[name]
+    for k in ("dot_s1s2", "dot_ls1", "dot_ls2"):
+        got = (float(np.max(e[k])), float(np.percentile(e[k], 99)), float(np.median(e[k])))
+        assert got[0] <= mx and got[1] <= p99 and got[2] <= p50, (name, k, got)
 
 
 @pytest.fixture(scope="module")
@@ -53,10 +72,9 @@ def test_c3_mixed_full_size_subsample(pn, orc):
     e = mixed_errors(g, o)
     report = {k: (float(np.max(v)), float(np.median(v))) for k, v in e.items()}
     print("mixed-vs-FP64 (max, median):", report)
+    assert_stated(e, "C3")
     for k in ("dot_s1s2", "dot_ls1", "dot_ls2"):
-        assert report[k][1] <= DOT_TOL / 3, (k, report[k])                 # median
-        assert np.mean(e[k] > DOT_TOL) < 0.02, (k, np.mean(e[k] > DOT_TOL))  # tail fraction
-        assert report[k][0] <= 5e-3, (k, report[k])
+        assert np.mean(e[k] > DOT_TOL) < 0.025, (k, np.mean(e[k] > DOT_TOL))  # tail fraction (measured 1.3 %)
     assert report["t"][1] < 1e-6
 
 
@@ -70,8 +88,7 @@ def test_mixed_small_ensembles(pn, orc, schedule):
         torch.cuda.synchronize()
         e = mixed_errors(g, o)
         assert np.array_equal(g["status"], o["status"])
-        for k in ("dot_s1s2", "dot_ls1", "dot_ls2"):
-            assert np.median(e[k]) <= DOT_TOL and np.max(e[k]) <= 5e-3, (name, k, np.median(e[k]), np.max(e[k]))
+        assert_stated(e, name)
 
 
 # ---------------------------------------------------------------------------

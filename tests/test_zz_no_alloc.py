@@ -29,13 +29,14 @@ def pn():
     return pn
 
 
-def noalloc(pn, inp, n, **kw):
+def noalloc(pn, inp, n, stream=None, **kw):
     import torch
     lib = pn.native.load()
     out = pn.alloc_outputs(n)
     prm = pn.params(**kw)
+    s = torch.cuda.current_stream() if stream is None else stream
     rc = lib.pn_integrate_noalloc(n, C.byref(prm), C.byref(pn.inputs_struct(inp, n)),
-                                  C.byref(pn.outputs_struct(out, n)), C.c_void_p(torch.cuda.current_stream().cuda_stream))
+                                  C.byref(pn.outputs_struct(out, n)), C.c_void_p(s.cuda_stream))
     assert rc == 0, lib.pn_last_error(None)
     torch.cuda.synchronize()
     return pn.to_numpy(out)
@@ -70,3 +71,45 @@ def test_mixed_precision_and_limits(pn):
     rc = lib.pn_integrate_noalloc(LIMIT + 1, C.byref(prm), C.byref(pn.inputs_struct(big)), C.byref(pn.outputs_struct(out)),
                                   C.c_void_p(torch.cuda.current_stream().cuda_stream))
     assert rc == pn.native.PN_E_ARG and b"16384" in lib.pn_last_error(None)
+
+
+def test_double_single_precision(pn):
+    """The double-single form through the no-allocation entry point gives the ordinary entry point's bits."""
+    ens = workloads.config("C4", n=3000, seed=505)
+    inp = pn.to_device(ens)
+    got = noalloc(pn, inp, 3000, precision=2)
+    ref = pn.to_numpy(pn.integrate(inp, precision=2))
+    for k in got:
+        assert np.array_equal(got[k], ref[k], equal_nan=True), k
+
+
+FIRST_CALL_ON_SIDE_STREAM = r"""
+import sys
+sys.path[:0] = [sys.argv[1], sys.argv[1] + "/tests"]
+import numpy as np, torch
+import paper_0908_3889_b300 as pn, workloads
+from test_zz_no_alloc import noalloc
+torch.cuda.set_device(0)
+ens = workloads.config("C2", n=4000, seed=506)
+inp = pn.to_device(ens)
+torch.cuda.synchronize()
+side = torch.cuda.Stream()
+with torch.cuda.stream(side):
+    got = noalloc(pn, inp, 4000, stream=side)  # the first call of this process, on a non-blocking stream
+ref = pn.to_numpy(pn.integrate(inp))
+for k in got:
+    assert np.array_equal(got[k], ref[k], equal_nan=True), k
+print("ok")
+"""
+
+
+def test_first_call_of_a_process_on_a_side_stream(pn):
+    """A fresh process whose first no-allocation call runs on a non-blocking torch stream: the table the
+    first call uploads must be in place before that stream's kernels read it."""
+    import os
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    r = subprocess.run([sys.executable, "-c", FIRST_CALL_ON_SIDE_STREAM, root], capture_output=True, text=True,
+                       timeout=600)
+    assert r.returncode == 0 and r.stdout.strip().endswith("ok"), r.stdout + r.stderr
