@@ -56,8 +56,18 @@
 //   integrate      pinned: Newtonian t_f closed form, quadrature of t_f for
 //                  non-spinning and aligned-spin binaries, 5th-order convergence,
 //                  tolerance scaling vs a tight run and an independent RK4.
-//   step control / landing / norm   parity unpinned (the paper states only the
-//                  tolerance and h0; constants are our reading, shared by both sides).
+//   err_norm and the step-size controller   pinned to the reading above (the
+//                  paper states only the tolerance and h0; the constants are
+//                  the reading's): on the leading-order chirp the norm of one
+//                  attempt equals the RMS of the embedded estimate from the
+//                  Butcher series of the tableau, for absolute, relative and
+//                  mixed scales; accepted steps settle at the 0.9^5 error fixed
+//                  point of safety 0.9 and exponent -1/5; the 0.2 / 10 clamps
+//                  and the no-growth rule after a rejection act where the series
+//                  says they must.  Planted mistakes in a copy of this file
+//                  (2-norm, dropped h, -1/4, safety 0.8, ...) fail these pins.
+//   landing        pinned: omega lands on omega_f; Newtonian t_f closed form
+//                  and quadrature of t_f for non-spinning and aligned spins.
 //   sample         pinned: SplitMix64 published output vectors; isotropy tests.
 //   grad           pinned: central finite differences of the replayed map.
 
