@@ -242,6 +242,16 @@ int pn_batch_set_params(pn_batch *b, const pn_params *p);
  * then S2-hat.  Errors: PN_E_ARG (NULL pointers, n > n_max, bad d), PN_E_CUDA. */
 int pn_batch_sample(pn_batch *b, uint64_t seed, const pn_dist *d, int64_t n, const pn_inputs *in);
 
+/* Masses from mass ratios, the first step of the per-binary set-up (Sec. II:
+ * M = m1 + m2 = 1): m1[i] = q[i]/(1 + q[i]), m2[i] = 1/(1 + q[i]) for
+ * i < n, each correctly rounded from the rounded 1 + q[i] (the rounding
+ * pn_batch_sample uses).  q, m1, m2: caller-owned device arrays of n doubles;
+ * m1 and m2 may be two rows of a pn_inputs block.  Asynchronous on b's
+ * stream.  q <= 0 or non-finite q gives masses that pn_batch_integrate then
+ * reports as PN_ST_BAD_INPUT.  Errors: PN_E_ARG (NULL b or, for n > 0, a NULL
+ * array; n outside [0, n_max]), PN_E_CUDA. */
+int pn_batch_masses(pn_batch *b, int64_t n, const double *q, double *m1, double *m2);
+
 /* Integrate binaries 0..n-1 of *in and write *out (asynchronous).
  * 0 <= n <= n_max (n = 0 does nothing).  Errors: PN_E_ARG (NULL pointers,
  * n out of range), PN_E_CUDA (launch failure).  Uses the schedule, block and

@@ -114,6 +114,8 @@ SIGNATURES = {
                                     C.POINTER(pn_tune_result)]),
     "pn_batch_adjoint": (C.c_int, [C.c_void_p, C.c_int64, C.POINTER(pn_inputs), C.POINTER(pn_cotangents),
                                    C.POINTER(pn_grads), C.POINTER(pn_outputs)]),
+    "pn_batch_masses": (C.c_int, [C.c_void_p, C.c_int64, C.POINTER(C.c_double), C.POINTER(C.c_double),
+                                  C.POINTER(C.c_double)]),
     "pn_batch_stats": (C.c_int, [C.c_void_p, C.c_int64, C.POINTER(pn_inputs), C.POINTER(pn_outputs),
                                  C.POINTER(pn_stats)]),
     "pn_batch_histogram": (C.c_int, [C.c_void_p, C.c_int64, C.POINTER(pn_inputs), C.POINTER(pn_outputs),

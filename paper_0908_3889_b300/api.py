@@ -1,7 +1,8 @@
 """Python binding of the C ABI (include/pn_batch.h): same names, torch tensors for memory and streams.
 
-Every function here only marshals arguments; all of the integration runs in
-the CUDA library.  Ensembles are dicts of float64 tensors on one CUDA device:
+Every function here only marshals arguments; all of the integration, the
+set-up included (masses from mass ratios: pn_batch_masses), runs in the CUDA
+library.  Ensembles are dicts of float64 tensors on one CUDA device:
 
   inputs   m1, m2, chi1, chi2, omega0, omega_f: shape (n,)
            s1hat, s2hat, lhat: shape (3, n), component-major (structure of arrays)
@@ -244,6 +245,14 @@ def pn_batch_eval_rhs(h, n: int, m1: torch.Tensor, m2: torch.Tensor, y: torch.Te
     _check(_lib().pn_batch_eval_rhs(h, int(n), _dptr(m1), _dptr(m2), _dptr(y), _dptr(f)), h)
 
 
+def pn_batch_masses(h, n: int, q: torch.Tensor, m1: torch.Tensor, m2: torch.Tensor) -> None:
+    """m1 = q/(1+q), m2 = 1/(1+q) on the device (the set-up's first step, M = 1)."""
+    dev = q.device
+    for t, name in ((q, "q"), (m1, "m1"), (m2, "m2")):
+        _check_tensor(t, n, torch.float64, name, None, dev)
+    _check(_lib().pn_batch_masses(h, int(n), _dptr(q), _dptr(m1), _dptr(m2)), h)
+
+
 def pn_batch_stats(h, n: int, inputs: dict, outputs: dict) -> dict:
     s = N.pn_stats()
     _check(_lib().pn_batch_stats(h, int(n), C.byref(inputs_struct(inputs, n)), C.byref(outputs_struct(outputs, n)),
@@ -401,8 +410,9 @@ class PNAdjointFn(torch.autograd.Function):
     """Final outputs as a differentiable function of the initial spin directions and the mass ratio.
 
     apply(s1hat (3, n), s2hat (3, n), q (n,), chi1, chi2, omega0, omega_f, lhat (3, n), prm=None)
-    returns (dot_s1s2, dot_ls1, dot_ls2, Lhat (3, n), S1 (3, n), S2 (3, n), t); m1 = q/(1+q),
-    m2 = 1/(1+q) (M = 1).  backward calls pn_batch_adjoint: reverse mode through the accepted
+    returns (dot_s1s2, dot_ls1, dot_ls2, Lhat (3, n), S1 (3, n), S2 (3, n), t); the library forms the
+    masses m1 = q/(1+q), m2 = 1/(1+q) (M = 1, pn_batch_masses).  backward calls pn_batch_adjoint:
+    reverse mode through the accepted
     Dormand-Prince steps with the step sizes held fixed and the stop at omega_f differentiated as an
     implicit function.  Needs PN_FP64 and PN_STOP_LAND.
     """
@@ -413,12 +423,10 @@ class PNAdjointFn(torch.autograd.Function):
         inp = alloc_inputs(n, q.device)
         inp["s1hat"].copy_(s1hat.detach())
         inp["s2hat"].copy_(s2hat.detach())
-        qd = q.detach()
-        inp["m1"].copy_(qd / (1.0 + qd))
-        inp["m2"].copy_(1.0 / (1.0 + qd))
         for k, v in (("chi1", chi1), ("chi2", chi2), ("omega0", omega0), ("omega_f", omega_f), ("lhat", lhat)):
             inp[k].copy_(v.detach())
         b = Batch(n, prm or params())
+        pn_batch_masses(b.handle, n, q.detach().contiguous(), inp["m1"], inp["m2"])
         out = b.integrate(inp)
         ctx.pn = (b, inp, n)
         return (out["dot_s1s2"].clone(), out["dot_ls1"].clone(), out["dot_ls2"].clone(), out["Lhat"].clone(),

@@ -798,6 +798,15 @@ extern "C" int pn_batch_sample(pn_batch* b, uint64_t seed, const pn_dist* d, int
   return PN_OK;
 }
 
+extern "C" int pn_batch_masses(pn_batch* b, int64_t n, const double* q, double* m1, double* m2) {
+  if (!b) return fail(nullptr, PN_E_ARG, "batch is NULL");
+  if (n < 0 || n > b->n_max) return fail(b, PN_E_ARG, "n must be in [0, n_max]");
+  if (n > 0 && (!q || !m1 || !m2)) return fail(b, PN_E_ARG, "NULL q, m1 or m2");
+  cudaError_t e = pn::launch_masses(n, q, m1, m2, b->stream);
+  if (e != cudaSuccess) return cuda_fail(b, e, "masses kernel launch");
+  return PN_OK;
+}
+
 extern "C" int pn_batch_stats(pn_batch* b, int64_t n, const pn_inputs* in, const pn_outputs* out, pn_stats* host) {
   if (!b) return fail(nullptr, PN_E_ARG, "batch is NULL");
   if (n < 0 || n > b->n_max) return fail(b, PN_E_ARG, "n must be in [0, n_max]");

@@ -80,6 +80,8 @@ cudaError_t launch_eval_rhs(int prec, int64_t n, const double* m1, const double*
                             const float* tab, TermCfg tc, cudaStream_t s);
 
 cudaError_t launch_sample(uint64_t seed, const pn_dist& d, int64_t n, const pn_inputs& in, cudaStream_t s);
+// m1 = q/(1+q), m2 = 1/(1+q) for n mass ratios (the sampler's own rounding).
+cudaError_t launch_masses(int64_t n, const double* q, double* m1, double* m2, cudaStream_t s);
 
 // Statistics: partial sums per block into part (grid x kStatWords doubles), then one block reduces them.
 constexpr int kStatWords = 40;

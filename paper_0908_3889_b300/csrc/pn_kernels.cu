@@ -642,6 +642,24 @@ __device__ __forceinline__ double uniform53(uint64_t seed, uint64_t i, uint64_t 
   return __dmul_rn((double)(z >> 11), 1.0 / 9007199254740992.0);
 }
 
+// Masses of a binary of mass ratio q = m1/m2 and total mass M = m1 + m2 = 1
+// (Sec. II sets M = 1): m1 = q/(1+q), m2 = 1/(1+q), each correctly rounded
+// from the rounded 1 + q.
+__device__ __forceinline__ void masses_of_q(double q, double* m1, double* m2) {
+  const double one_q = __dadd_rn(1.0, q);
+  *m1 = __ddiv_rn(q, one_q);
+  *m2 = __ddiv_rn(1.0, one_q);
+}
+
+__global__ void k_masses(int64_t n, const double* __restrict__ q, double* __restrict__ m1, double* __restrict__ m2) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  double a, b;
+  masses_of_q(q[i], &a, &b);
+  m1[i] = a;
+  m2[i] = b;
+}
+
 __global__ void k_sample(uint64_t seed, pn_dist d, int64_t n, pn_inputs o) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
@@ -651,9 +669,7 @@ __global__ void k_sample(uint64_t seed, pn_dist d, int64_t n, pn_inputs o) {
   if (d.q_mode == 0) q = d.q_lo;
   else if (d.q_mode == 1) q = __dadd_rn(d.q_lo, __dmul_rn(__dsub_rn(d.q_hi, d.q_lo), u0));
   else q = __dmul_rn(d.q_lo, exp(__dmul_rn(u0, log(__ddiv_rn(d.q_hi, d.q_lo)))));
-  const double one_q = __dadd_rn(1.0, q);
-  o.m1[i] = __ddiv_rn(q, one_q);
-  o.m2[i] = __ddiv_rn(1.0, one_q);
+  masses_of_q(q, &o.m1[i], &o.m2[i]);
   const double u1 = uniform53(seed, ui, 1), u2 = uniform53(seed, ui, 2);
   const double span = __dsub_rn(d.chi_hi, d.chi_lo);
   o.chi1[i] = d.chi_mode == 0 ? d.chi_lo : __dadd_rn(d.chi_lo, __dmul_rn(span, u1));
@@ -680,6 +696,14 @@ __global__ void k_sample(uint64_t seed, pn_dist d, int64_t n, pn_inputs o) {
     else { o.s2x[i] = vx; o.s2y[i] = vy; o.s2z[i] = vz; }
   }
   o.lx[i] = 0.0; o.ly[i] = 0.0; o.lz[i] = 1.0;
+}
+
+cudaError_t launch_masses(int64_t n, const double* q, double* m1, double* m2, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  const int block = 256;
+  const int64_t grid = (n + block - 1) / block;
+  k_masses<<<(unsigned)grid, block, 0, s>>>(n, q, m1, m2);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_sample(uint64_t seed, const pn_dist& d, int64_t n, const pn_inputs& in, cudaStream_t s) {

@@ -179,6 +179,26 @@ def test_autograd_function_backward(pn):
     assert np.allclose(got, ref, rtol=1e-9, atol=1e-12)  # m1, m2 round-trip through q = m1/m2
 
 
+def test_masses_from_mass_ratio_on_the_device(pn):
+    """pn_batch_masses: m1 = q/(1+q), m2 = 1/(1+q), bit for bit the IEEE divisions of the rounded 1 + q,
+    over the ratios the workloads use and the extremes of the sampler's range; a ragged n leaves the
+    elements beyond n untouched."""
+    import torch
+    rng = np.random.default_rng(7)
+    q = np.concatenate([np.exp(rng.uniform(0.0, np.log(10.0), 1000)), rng.uniform(1.0, 4.0, 1000),
+                        [1.0, 10.0, 0.4 / 0.6, 1e-300, 1e300]])
+    n = q.shape[0]
+    qd = torch.tensor(q, dtype=torch.float64, device="cuda")
+    m = torch.full((2, n + 3), -7.0, dtype=torch.float64, device="cuda")
+    with pn.Batch(n + 3) as b:
+        pn.pn_batch_masses(b.handle, n, qd, m[0], m[1])
+        torch.cuda.synchronize()
+    got = m.cpu().numpy()
+    one_q = 1.0 + q
+    assert np.array_equal(got[0, :n], q / one_q) and np.array_equal(got[1, :n], 1.0 / one_q)
+    assert np.all(got[:, n:] == -7.0)
+
+
 DS_GRAD_TOL = 1e-8  # double-single sweep: ~48-bit arithmetic through a few hundred steps
 
 
