@@ -348,6 +348,19 @@ int pn_batch_adjoint(pn_batch *b, int64_t n, const pn_inputs *in, const pn_cotan
  * Errors: PN_E_ARG, PN_E_CUDA. */
 int pn_batch_stats(pn_batch *b, int64_t n, const pn_inputs *in, const pn_outputs *out, pn_stats *host);
 
+/* pn_batch_stats for several ensembles integrated together in one call (the
+ * parameter sweeps of Sec. V B-D: one ensemble per mass ratio, spin magnitude
+ * or omega_0, concatenated along the binary index): segment k is binaries
+ * host_offsets[k] .. host_offsets[k + 1] - 1 and its statistics go to
+ * host[k].  host_offsets: n_seg + 1 non-decreasing host int64 values in
+ * [0, n_max] (an empty segment gives n = 0 and NaN Pearson r); host: n_seg
+ * caller-owned records.  One reduction launch covers every segment.
+ * n_seg = 0 does nothing.  Synchronises.  Errors: PN_E_ARG (NULL pointers,
+ * n_seg outside [0, 65535], bad offsets), PN_E_NOMEM (the scratch for the
+ * partial records, grown on demand and kept by the batch), PN_E_CUDA. */
+int pn_batch_stats_segments(pn_batch *b, int32_t n_seg, const int64_t *host_offsets, const pn_inputs *in,
+                            const pn_outputs *out, pn_stats *host);
+
 /* Histogram of outputs 0..n-1 (Sec. V A: 20 and 100 bins of the final
  * S1-hat.S2-hat; 79 x 79 bins of initial vs final; Sec. V B's KS test uses
  * fine 1-D bins).  nx * ny <= 4,194,304 bins.  Only binaries with status OK

@@ -118,6 +118,8 @@ SIGNATURES = {
                                   C.POINTER(C.c_double)]),
     "pn_batch_stats": (C.c_int, [C.c_void_p, C.c_int64, C.POINTER(pn_inputs), C.POINTER(pn_outputs),
                                  C.POINTER(pn_stats)]),
+    "pn_batch_stats_segments": (C.c_int, [C.c_void_p, C.c_int32, C.POINTER(C.c_int64), C.POINTER(pn_inputs),
+                                          C.POINTER(pn_outputs), C.POINTER(pn_stats)]),
     "pn_batch_histogram": (C.c_int, [C.c_void_p, C.c_int64, C.POINTER(pn_inputs), C.POINTER(pn_outputs),
                                      C.POINTER(pn_hist_spec), C.POINTER(C.c_int64)]),
     "pn_batch_kde": (C.c_int, [C.c_void_p, C.c_int64, C.POINTER(pn_inputs), C.POINTER(pn_outputs), C.c_int32,

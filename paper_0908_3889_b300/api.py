@@ -140,6 +140,12 @@ def to_device(ens: dict, device="cuda", pin_memory: bool = False) -> dict:
     return d
 
 
+def segment(tensors: dict, lo: int, hi: int) -> dict:
+    """Views of binaries lo .. hi - 1 of an input or output dict (pointers offset by lo, no copy), for
+    calling any entry point on one ensemble of a concatenated batch."""
+    return {k: v[..., lo:hi] for k, v in tensors.items() if not k.startswith("_")}
+
+
 def to_numpy(out: dict) -> dict:
     return {k: out[k].cpu().numpy() for k in OUTPUT_KEYS if k in out}
 
@@ -253,13 +259,31 @@ def pn_batch_masses(h, n: int, q: torch.Tensor, m1: torch.Tensor, m2: torch.Tens
     _check(_lib().pn_batch_masses(h, int(n), _dptr(q), _dptr(m1), _dptr(m2)), h)
 
 
+def _stats_dict(s: N.pn_stats) -> dict:
+    d = {f: getattr(s, f) for f, _ in N.pn_stats._fields_}
+    d["count_by_status"] = list(s.count_by_status)
+    return d
+
+
 def pn_batch_stats(h, n: int, inputs: dict, outputs: dict) -> dict:
     s = N.pn_stats()
     _check(_lib().pn_batch_stats(h, int(n), C.byref(inputs_struct(inputs, n)), C.byref(outputs_struct(outputs, n)),
                                  C.byref(s)), h)
-    d = {f: getattr(s, f) for f, _ in N.pn_stats._fields_}
-    d["count_by_status"] = list(s.count_by_status)
-    return d
+    return _stats_dict(s)
+
+
+def pn_batch_stats_segments(h, offsets, inputs: dict, outputs: dict) -> list:
+    """Statistics of each segment [offsets[k], offsets[k + 1]) of one batch, one dict per segment."""
+    off = np.ascontiguousarray(np.asarray(offsets, dtype=np.int64))
+    n_seg = int(off.shape[0]) - 1
+    if n_seg < 0:
+        raise ValueError("offsets needs at least one entry")
+    n = int(off[-1])
+    recs = (N.pn_stats * max(n_seg, 1))()
+    _check(_lib().pn_batch_stats_segments(h, n_seg, off.ctypes.data_as(C.POINTER(C.c_int64)),
+                                          C.byref(inputs_struct(inputs, n)), C.byref(outputs_struct(outputs, n)),
+                                          recs), h)
+    return [_stats_dict(recs[k]) for k in range(n_seg)]
 
 
 def pn_batch_histogram(h, n: int, inputs: dict, outputs: dict, quantity_x: int, nx: int, x_range=(-1.0, 1.0),
@@ -380,6 +404,9 @@ class Batch:
         n = int(inputs["m1"].shape[0]) if n is None else n
         return pn_batch_stats(self.handle, n, inputs, outputs)
 
+    def stats_segments(self, inputs: dict, outputs: dict, offsets) -> list:
+        return pn_batch_stats_segments(self.handle, offsets, inputs, outputs)
+
     def histogram(self, inputs: dict, outputs: dict, quantity_x: int, nx: int, **kw) -> np.ndarray:
         return pn_batch_histogram(self.handle, int(inputs["m1"].shape[0]), inputs, outputs, quantity_x, nx, **kw)
 
@@ -404,6 +431,22 @@ def integrate(inputs: dict, **kw) -> dict:
     n = int(inputs["m1"].shape[0])
     with Batch(max(n, 1), params(**kw)) as b:
         return b.integrate(inputs)
+
+
+def sweep(ensembles: list, device="cuda", **kw):
+    """Several NumPy ensembles (workloads layout) integrated in ONE pn_batch_integrate call, concatenated
+    along the binary index, with per-ensemble statistics from one pn_batch_stats_segments reduction.
+    Returns (inputs, outputs, offsets, stats): device tensors of the whole batch, the segment offsets and
+    one statistics dict per ensemble."""
+    sizes = [int(np.asarray(e["m1"]).shape[0]) for e in ensembles]
+    offsets = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int64)
+    n = int(offsets[-1])
+    cat = {k: np.concatenate([np.asarray(e[k], dtype=np.float64) for e in ensembles], axis=-1) for k in INPUT_KEYS}
+    inputs = to_device(cat, device=device)
+    with Batch(max(n, 1), params(**kw)) as b:
+        outputs = b.integrate(inputs)
+        stats = pn_batch_stats_segments(b.handle, offsets, inputs, outputs)
+    return inputs, outputs, offsets, stats
 
 
 class PNAdjointFn(torch.autograd.Function):

@@ -8,6 +8,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <vector>
 #include <string>
 
 #include "pn_adjoint.h"
@@ -27,6 +28,8 @@ struct pn_batch {
   float* d_tab = nullptr;
   double* d_stat_part = nullptr;
   double* d_stat_total = nullptr;
+  double* d_segstat = nullptr;  // pn_batch_stats_segments: offsets, partial and total records
+  size_t segstat_cap = 0;       // bytes
   double* d_setup = nullptr;  // per-binary set-up table, setup_fields() x n_max doubles
   cudaEvent_t ev[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};  // integrate, autotune, adjoint
   bool timed_integrate = false, timed_adjoint = false;
@@ -205,6 +208,7 @@ extern "C" void pn_batch_destroy(pn_batch* b) {
   cudaFree(b->d_tab);
   cudaFree(b->d_stat_part);
   cudaFree(b->d_stat_total);
+  cudaFree(b->d_segstat);
   cudaFree(b->d_setup);
   cudaFree(b->d_rec_h);
   cudaFree(b->d_rec_ck);
@@ -807,6 +811,8 @@ extern "C" int pn_batch_masses(pn_batch* b, int64_t n, const double* q, double* 
   return PN_OK;
 }
 
+static void stats_from_record(pn_batch* b, int64_t n, const double* t, pn_stats* host);
+
 extern "C" int pn_batch_stats(pn_batch* b, int64_t n, const pn_inputs* in, const pn_outputs* out, pn_stats* host) {
   if (!b) return fail(nullptr, PN_E_ARG, "batch is NULL");
   if (n < 0 || n > b->n_max) return fail(b, PN_E_ARG, "n must be in [0, n_max]");
@@ -818,6 +824,55 @@ extern "C" int pn_batch_stats(pn_batch* b, int64_t n, const pn_inputs* in, const
   if (e != cudaSuccess) return cuda_fail(b, e, "stats kernel launch");
   PN_CUDA(b, cudaMemcpyAsync(t, b->d_stat_total, sizeof(t), cudaMemcpyDeviceToHost, b->stream));
   PN_CUDA(b, cudaStreamSynchronize(b->stream));
+  stats_from_record(b, n, t, host);
+  return PN_OK;
+}
+
+extern "C" int pn_batch_stats_segments(pn_batch* b, int32_t n_seg, const int64_t* host_offsets, const pn_inputs* in,
+                                       const pn_outputs* out, pn_stats* host) {
+  if (!b) return fail(nullptr, PN_E_ARG, "batch is NULL");
+  if (n_seg < 0 || n_seg > pn::kMaxSegments) return fail(b, PN_E_ARG, "n_seg must be in [0, 65535]");
+  if (n_seg == 0) return PN_OK;
+  if (!host_offsets || !host) return fail(b, PN_E_ARG, "NULL offsets or host stats");
+  if (!inputs_ok(in)) return fail(b, PN_E_ARG, "NULL input pointer");
+  if (!outputs_ok(out)) return fail(b, PN_E_ARG, "NULL output pointer");
+  if (host_offsets[0] < 0 || host_offsets[n_seg] > b->n_max)
+    return fail(b, PN_E_ARG, "segment offsets must lie in [0, n_max]");
+  for (int32_t k = 0; k < n_seg; k++)
+    if (host_offsets[k + 1] < host_offsets[k]) return fail(b, PN_E_ARG, "segment offsets must not decrease");
+  const int bps = pn::stats_seg_blocks(n_seg);
+  const size_t off_bytes = ((size_t)(n_seg + 1) * sizeof(int64_t) + 255) / 256 * 256;
+  const size_t part_doubles = (size_t)n_seg * bps * pn::kStatWords, tot_doubles = (size_t)n_seg * pn::kStatWords;
+  const size_t need = off_bytes + (part_doubles + tot_doubles) * sizeof(double);
+  if (b->segstat_cap < need) {
+    PN_CUDA(b, cudaStreamSynchronize(b->stream));  // the old scratch may still be read by queued work
+    cudaFree(b->d_segstat);
+    b->d_segstat = nullptr;
+    b->segstat_cap = 0;
+    if (cudaMalloc(&b->d_segstat, need) != cudaSuccess) {
+      cudaGetLastError();
+      b->d_segstat = nullptr;
+      return fail(b, PN_E_NOMEM, "segment statistics scratch allocation failed");
+    }
+    b->segstat_cap = need;
+  }
+  int64_t* d_off = reinterpret_cast<int64_t*>(b->d_segstat);
+  double* d_part = reinterpret_cast<double*>(reinterpret_cast<char*>(b->d_segstat) + off_bytes);
+  double* d_tot = d_part + part_doubles;
+  std::vector<double> t(tot_doubles);
+  PN_CUDA(b, cudaMemcpyAsync(d_off, host_offsets, (size_t)(n_seg + 1) * sizeof(int64_t), cudaMemcpyHostToDevice,
+                             b->stream));
+  cudaError_t e = pn::launch_stats_segments(n_seg, d_off, *in, *out, d_part, d_tot, b->stream);
+  if (e != cudaSuccess) return cuda_fail(b, e, "segment stats kernel launch");
+  PN_CUDA(b, cudaMemcpyAsync(t.data(), d_tot, tot_doubles * sizeof(double), cudaMemcpyDeviceToHost, b->stream));
+  PN_CUDA(b, cudaStreamSynchronize(b->stream));
+  for (int32_t k = 0; k < n_seg; k++)
+    stats_from_record(b, host_offsets[k + 1] - host_offsets[k], t.data() + (size_t)k * pn::kStatWords, &host[k]);
+  return PN_OK;
+}
+
+// pn_stats of n binaries from one reduced record t (layout in pn_kernels.cu).
+static void stats_from_record(pn_batch* b, int64_t n, const double* t, pn_stats* host) {
   std::memset(host, 0, sizeof(*host));
   host->n = n;
   for (int k = 0; k < 8; k++) host->count_by_status[k] = (int64_t)t[k];
@@ -844,7 +899,6 @@ extern "C" int pn_batch_stats(pn_batch* b, int64_t n, const pn_inputs* in, const
   host->ms_last_integrate = (b->timed_integrate && cudaEventElapsedTime(&ms, b->ev[0], b->ev[1]) == cudaSuccess) ? ms : NAN;
   host->ms_last_adjoint = (b->timed_adjoint && cudaEventElapsedTime(&ms, b->ev[4], b->ev[5]) == cudaSuccess) ? ms : NAN;
   cudaGetLastError();
-  return PN_OK;
 }
 
 extern "C" int pn_batch_histogram(pn_batch* b, int64_t n, const pn_inputs* in, const pn_outputs* out,

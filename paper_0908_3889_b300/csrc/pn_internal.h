@@ -88,6 +88,12 @@ constexpr int kStatWords = 40;
 constexpr int kStatGrid = 296;
 cudaError_t launch_stats(int64_t n, const pn_inputs& in, const pn_outputs& out, double* part, double* total,
                          cudaStream_t s);
+// The same per segment [off[k], off[k + 1]), k < n_seg (off: n_seg + 1 device int64): partial
+// records into part (n_seg x stats_seg_blocks(n_seg) records), one total record per segment.
+constexpr int32_t kMaxSegments = 65535;
+int stats_seg_blocks(int32_t n_seg);
+cudaError_t launch_stats_segments(int32_t n_seg, const int64_t* off, const pn_inputs& in, const pn_outputs& out,
+                                  double* part, double* total, cudaStream_t s);
 
 // Parameter and pointer checks shared by the C entry points (pn_capi.cu), and
 // the thread-local error message that pn_last_error(NULL) returns.

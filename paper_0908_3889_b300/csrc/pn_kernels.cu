@@ -763,13 +763,14 @@ __device__ __forceinline__ double unit_dot(double ax, double ay, double az, doub
   return (ax * bx + ay * by + az * bz) / (na * nb);
 }
 
-__global__ void __launch_bounds__(256) k_stats_part(int64_t n, pn_inputs in, pn_outputs out, double* part) {
-  __shared__ double acc[32][kStatWords];
-  double v[kStatWords];
+__device__ __forceinline__ void stat_init(double* v) {
   for (int w = 0; w < kStatWords; w++) v[w] = 0.0;
   v[11] = v[13] = 1e300;
   v[12] = v[14] = -1e300;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+}
+
+// Adds binary i to the record v.
+__device__ __forceinline__ void stat_add(double* v, int64_t i, const pn_inputs& in, const pn_outputs& out) {
     const int st = out.status[i];
     v[(st >= 0 && st < 8) ? st : 7] += 1.0;
     const double a = out.n_acc[i], r = out.n_rej[i], l = out.n_land[i];
@@ -795,20 +796,42 @@ __global__ void __launch_bounds__(256) k_stats_part(int64_t n, pn_inputs in, pn_
         v[32] += y0 * y0;
       }
     }
-  }
+}
+
+__global__ void __launch_bounds__(256) k_stats_part(int64_t n, pn_inputs in, pn_outputs out, double* part) {
+  __shared__ double acc[32][kStatWords];
+  double v[kStatWords];
+  stat_init(v);
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    stat_add(v, i, in, out);
   block_reduce_store(acc, v, part + (size_t)blockIdx.x * kStatWords);
 }
 
+// Segmented records: block (x, k) covers binaries [off[k], off[k + 1]) with stride
+// gridDim.x * blockDim.x and writes partial record k * gridDim.x + x.
+__global__ void __launch_bounds__(256) k_stats_seg_part(const int64_t* __restrict__ off, pn_inputs in,
+                                                        pn_outputs out, double* part) {
+  __shared__ double acc[32][kStatWords];
+  double v[kStatWords];
+  stat_init(v);
+  const int64_t lo = off[blockIdx.y], hi = off[blockIdx.y + 1];
+  for (int64_t i = lo + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < hi; i += (int64_t)gridDim.x * blockDim.x)
+    stat_add(v, i, in, out);
+  block_reduce_store(acc, v, part + ((size_t)blockIdx.y * gridDim.x + blockIdx.x) * kStatWords);
+}
+
+// Block k reduces the nparts partial records starting at part + k * nparts records into total record k.
 __global__ void __launch_bounds__(256) k_stats_total(const double* part, int nparts, double* total) {
   __shared__ double acc[32][kStatWords];
   double v[kStatWords];
+  part += (size_t)blockIdx.x * nparts * kStatWords;
   for (int w = 0; w < kStatWords; w++) v[w] = is_minmax(w) ? (is_min(w) ? 1e300 : -1e300) : 0.0;
   for (int p = threadIdx.x; p < nparts; p += blockDim.x)
     for (int w = 0; w < kStatWords; w++) {
       const double z = part[(size_t)p * kStatWords + w];
       v[w] = is_minmax(w) ? (is_min(w) ? fmin(v[w], z) : fmax(v[w], z)) : v[w] + z;
     }
-  block_reduce_store(acc, v, total);
+  block_reduce_store(acc, v, total + (size_t)blockIdx.x * kStatWords);
 }
 
 cudaError_t launch_stats(int64_t n, const pn_inputs& in, const pn_outputs& out, double* part, double* total,
@@ -817,6 +840,22 @@ cudaError_t launch_stats(int64_t n, const pn_inputs& in, const pn_outputs& out, 
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   k_stats_total<<<1, 256, 0, s>>>(part, kStatGrid, total);
+  return cudaGetLastError();
+}
+
+int stats_seg_blocks(int32_t n_seg) {
+  const int b = (2 * kStatGrid + n_seg - 1) / n_seg;
+  return b < 1 ? 1 : (b > 64 ? 64 : b);
+}
+
+cudaError_t launch_stats_segments(int32_t n_seg, const int64_t* off, const pn_inputs& in, const pn_outputs& out,
+                                  double* part, double* total, cudaStream_t s) {
+  if (n_seg <= 0) return cudaSuccess;
+  const int bps = stats_seg_blocks(n_seg);
+  k_stats_seg_part<<<dim3((unsigned)bps, (unsigned)n_seg), 256, 0, s>>>(off, in, out, part);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  k_stats_total<<<(unsigned)n_seg, 256, 0, s>>>(part, bps, total);
   return cudaGetLastError();
 }
 

@@ -105,29 +105,75 @@ def test_paper_statistics_at_paper_size(pn):
     b.close()
 
 
-def test_paper_correlation_vs_chi_and_mass(pn):
-    """Sec. V C: r(S1.S2) > 0.98 for equal masses at every chi; Sec. V D: m1 = 0.4, chi = 0.05 gives r = -0.14;
-    Sec. V B (Fig. 5): r falls quickly as the masses become unequal."""
-    pv = paper_values()
-    lo = pv["pearson_s1s2_min_over_chi"][0]
+def paper_sweep_ensembles():
+    """Sec. V C (r vs chi at equal mass), Sec. V D (the m1 = 0.4, chi = 0.05 ring) and Sec. V B / Fig. 5
+    (r vs m1 at chi = 1), each N = 100,000, omega 0.00395 -> 0.05."""
+    ens = []
     for chi in (0.1, 0.3, 0.5, 0.7, 0.9):
-        ens = workloads.ensemble(100_000, 600 + int(chi * 10), chi=(chi, chi), omega0=(0.00395, 0.00395))
-        b, inp, out = run(pn, ens)
-        assert b.stats(inp, out)["pearson_s1s2"] > lo, chi
-        b.close()
-    v, tol = pv["pearson_s1s2_m04_chi005"]
-    ens = workloads.ensemble(100_000, 77, q=(0.4 / 0.6, 0.4 / 0.6), chi=(0.05, 0.05), omega0=(0.00395, 0.00395))
-    b, inp, out = run(pn, ens)
-    assert abs(b.stats(inp, out)["pearson_s1s2"] - v) <= tol
-    b.close()
-    rs = []
+        ens.append(("chi", chi, workloads.ensemble(100_000, 600 + int(chi * 10), chi=(chi, chi),
+                                                   omega0=(0.00395, 0.00395))))
+    ens.append(("ring", 0.4, workloads.ensemble(100_000, 77, q=(0.4 / 0.6, 0.4 / 0.6), chi=(0.05, 0.05),
+                                                omega0=(0.00395, 0.00395))))
     for m1 in (0.5, 0.45, 0.4, 0.3):
         q = m1 / (1 - m1)
-        ens = workloads.ensemble(100_000, 700 + int(m1 * 100), q=(q, q), omega0=(0.00395, 0.00395))
-        b, inp, out = run(pn, ens)
-        rs.append(b.stats(inp, out)["pearson_s1s2"])
-        b.close()
+        ens.append(("m1", m1, workloads.ensemble(100_000, 700 + int(m1 * 100), q=(q, q),
+                                                 omega0=(0.00395, 0.00395))))
+    return ens
+
+
+def test_paper_sweeps_in_one_launch(pn):
+    """The three parameter sweeps of Sec. V B-D as ONE integrate launch over 10 concatenated ensembles
+    (1,000,000 binaries) with per-ensemble statistics from one segmented reduction.  Each ensemble's
+    outputs are bit-identical to its own separate launch, its Pearson r agrees with that launch's
+    pn_batch_stats to 1e-12 (only the summation order differs), its histogram through segment views
+    equals the separate one, and the paper's printed values hold: r > 0.98 across chi (Sec. V C),
+    r = -0.14 on the ring (Sec. V D), r falling with m1 (Fig. 5)."""
+    import torch
+    pv = paper_values()
+    ens = paper_sweep_ensembles()
+    inp, out, off, st = pn.sweep([e for _, _, e in ens])
+    g = pn.to_numpy(out)
+    assert len(st) == len(ens) and off[-1] == 1_000_000
+    with pn.Batch(1_000_000) as b:
+        hist_all = [b.histogram(pn.segment(inp, off[k], off[k + 1]), pn.segment(out, off[k], off[k + 1]),
+                                pn.native.PN_Q_FINAL_S1S2, 20) for k in range(len(ens))]
+    for k, (kind, val, e) in enumerate(ens):
+        ref_b, ref_in, ref_out = run(pn, e)
+        ref = ref_b.stats(ref_in, ref_out)
+        assert np.array_equal(hist_all[k], ref_b.histogram(ref_in, ref_out, pn.native.PN_Q_FINAL_S1S2, 20))
+        ref_b.close()
+        r_np = pn.to_numpy(ref_out)
+        for key in ("dot_s1s2", "dot_ls1", "dot_ls2", "t", "n_acc", "status"):
+            assert np.array_equal(g[key][..., off[k]:off[k + 1]], r_np[key]), (kind, val, key)
+        assert st[k]["n"] == 100_000 and st[k]["count_by_status"] == ref["count_by_status"]
+        assert (st[k]["acc_total"], st[k]["acc_min"], st[k]["attempts_max"]) == \
+            (ref["acc_total"], ref["acc_min"], ref["attempts_max"])
+        for key in ("pearson_s1s2", "pearson_ls1", "pearson_ls2", "mean_final_s1s2", "std_final_s1s2"):
+            assert abs(st[k][key] - ref[key]) <= 1e-12, (kind, val, key, st[k][key], ref[key])
+    r_chi = [s["pearson_s1s2"] for (kind, _, _), s in zip(ens, st) if kind == "chi"]
+    assert min(r_chi) > pv["pearson_s1s2_min_over_chi"][0], r_chi
+    v, tol = pv["pearson_s1s2_m04_chi005"]
+    assert abs(st[5]["pearson_s1s2"] - v) <= tol
+    rs = [s["pearson_s1s2"] for (kind, _, _), s in zip(ens, st) if kind == "m1"]
     assert rs[0] > 0.98 and all(a > c for a, c in zip(rs, rs[1:])) and rs[-1] < 0.6, rs
+    torch.cuda.synchronize()
+
+
+def test_segment_statistics_edge_cases(pn):
+    """Empty segments give n = 0 and NaN r; one segment equals pn_batch_stats; zero segments do nothing;
+    decreasing or out-of-range offsets are argument errors."""
+    ens = workloads.config("C0", n=300)
+    b, inp, out = run(pn, ens)
+    whole = b.stats(inp, out)
+    st = b.stats_segments(inp, out, [0, 0, 300, 300])
+    assert st[0]["n"] == 0 and np.isnan(st[0]["pearson_s1s2"]) and st[2]["n"] == 0
+    assert st[1]["count_by_status"] == whole["count_by_status"] and st[1]["acc_total"] == whole["acc_total"]
+    assert abs(st[1]["pearson_s1s2"] - whole["pearson_s1s2"]) <= 1e-13
+    assert b.stats_segments(inp, out, [0]) == []
+    for bad in ([0, 200, 100], [-1, 10], [0, 301]):
+        with pytest.raises(pn.PNError):
+            b.stats_segments(inp, out, bad)
+    b.close()
 
 
 def test_analysis_argument_errors(pn):
