@@ -51,6 +51,25 @@ FP64_DATASHEET_TFLOPS = 1.25  # nominal dense FP64 of one B300
 PROFILED = {"kernel_sha": "4e915854aaac3794", "dram_bytes_per_binary": (39.478272e6 + 1.366784e6) / 131072}
 
 
+# Executed floating-point thread instructions per attempt of each integration kernel
+# k_integrate_mx<PREC> (PREC 0 FP64, 1 FP32 right-hand side, 2 double-single), from one ncu capture
+# of the 131,072-binary case (profiles/k_integrate_pipes_C1_131072.md): sums of
+# smsp__sass_thread_inst_executed_op_{ffma,fadd,fmul,ffma2,fadd2,fmul2,dfma,dadd,dmul}_pred_on over
+# the launch divided by its attempts.  Valid only while the kernel sources hash to kernel_sha.
+EXECUTED = {"kernel_sha": None, "per_attempt": {}}
+
+
+def executed_flops(prec: int):
+    """(FP32, FP64) flops one attempt executes (an FMA is 2, a packed pair instruction 2 lanes), or None
+    when no capture of the current kernel sources is recorded."""
+    if EXECUTED["kernel_sha"] != kernel_sha() or prec not in EXECUTED["per_attempt"]:
+        return None
+    c = EXECUTED["per_attempt"][prec]
+    f32 = 2 * c["ffma"] + c["fadd"] + c["fmul"] + 2 * (2 * c.get("ffma2", 0) + c.get("fadd2", 0) + c.get("fmul2", 0))
+    f64 = 2 * c["dfma"] + c["dadd"] + c["dmul"]
+    return f32, f64
+
+
 def kernel_sha() -> str:
     """Hash of the integration kernel's sources with comments and blank space removed (so an edit to a
     comment does not count as a kernel change)."""
@@ -178,14 +197,19 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def peak_probe():
+def peak_probe(index: int = 0):
+    """FP64 and FP32 FMA throughput (flop/s) measured live, and the clocks sampled while the probe ran."""
     from paper_0908_3889_b300.build import PEAK_LIB
     lib = C.CDLL(PEAK_LIB)
     lib.pn_peak_probe.argtypes = [C.POINTER(C.c_double), C.POINTER(C.c_double)]
     f64, f32 = C.c_double(), C.c_double()
-    if lib.pn_peak_probe(C.byref(f64), C.byref(f32)) != 0:
-        return None, None
-    return f64.value, f32.value
+    clocks = ClockSampler(index)
+    time.sleep(0.3)  # the sampler's first reading
+    rc = lib.pn_peak_probe(C.byref(f64), C.byref(f32))
+    ck = clocks.stop()
+    if rc != 0:
+        return None, None, ck
+    return f64.value, f32.value, ck
 
 
 def cpu_oracle_rate(ens, target_s: float = 10.0, threads: int = 0):
@@ -345,7 +369,7 @@ def main():
         return
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)  # 256 MB > L2 (126 MB)
 
-    f64_peak, f32_peak = peak_probe()
+    f64_peak, f32_peak, probe_clocks = peak_probe(torch.cuda.current_device())
 
     def timed_run(b, steps, warmup):
         for _ in range(warmup):
@@ -407,6 +431,10 @@ def main():
             "datasheet_peak": FP64_DATASHEET_TFLOPS, "frac_of_datasheet": achieved / 1e12 / FP64_DATASHEET_TFLOPS,
             "flops_per_attempt": FLOPS_ATTEMPT, "attempts_per_launch": attempts,
             "kernel": "pn::k_integrate_mx<FP64>"}
+    ex64 = executed_flops(0)
+    if ex64 is not None and f64_peak:
+        roof["fp64_flops_per_attempt_executed"] = ex64[1]
+        roof["fp64_pipe_executed_frac"] = ex64[1] * attempts / (ms_step * 1e-3) / f64_peak
 
     # Mixed precision on the same ensemble: FP32 right-hand side (PN_MIXED) and
     # double-single right-hand side on the FP32 pipe (PN_MIXED_DS).
@@ -433,12 +461,26 @@ def main():
             d = ((out[k] - fp64_out[k]).abs().amax(dim=0) / torch.where(mag > 0, mag, 1.0))[keep]
             errs[k] = {"max": float(d.max()), "p50": float(d.median())}
         m_attempts = mst["acc_total"] + mst["rej_total"] + mst["land_total"]
+        sec = mix_ms / args.steps * 1e-3
+        ex = executed_flops(prec)
+        roof_m = None
+        if ex is not None and f32_peak and f64_peak:
+            a32, a64 = ex[0] * m_attempts / sec, ex[1] * m_attempts / sec
+            roof_m = {"bound": "issue/latency", "pipe": "FP32", "achieved": a32 / 1e12, "peak": f32_peak / 1e12,
+                      "unit": "TFLOP/s", "frac": a32 / f32_peak,
+                      "peak_source": "FP32 FMA throughput measured live by the peak probe (2 flops per FMA)",
+                      "fp32_flops_per_attempt_executed": ex[0],
+                      "fp64_pipe": {"achieved": a64 / 1e12, "peak": f64_peak / 1e12, "frac": a64 / f64_peak,
+                                    "fp64_flops_per_attempt_executed": ex[1]},
+                      "counts": "executed instructions per attempt from ncu (profiles/), scaled by this run's attempts",
+                      "kernel": f"pn::k_integrate_mx<{prec}>"}
         return {"value": aggregate_rate(world, n, args.steps, mix_ms), "unit": "inspirals/s",
                 "ms_per_step": mix_ms / args.steps, "speedup_vs_fp64": total_ms / mix_ms,
                 "dot_err_vs_fp64": {k: errs[k] for k in ("dot_s1s2", "dot_ls1", "dot_ls2")},
-                "other_err_vs_fp64": {k: errs[k] for k in ("t", "omega", "S1", "S2", "Lhat")}, "schedule": {1: "plain", 2: "persistent"}.get(tn["schedule"]),
-                "block": tn["block"], "fp64_pipe_achieved_tflops": (FLOPS_STEP * m_attempts) /
-                (mix_ms / args.steps * 1e-3) / 1e12}
+                "other_err_vs_fp64": {k: errs[k] for k in ("t", "omega", "S1", "S2", "Lhat")},
+                "schedule": {1: "plain", 2: "persistent"}.get(tn["schedule"]), "block": tn["block"],
+                "attempts_per_binary": m_attempts / n,
+                "algorithmic_tflops": FLOPS_ATTEMPT * m_attempts / sec / 1e12, "roofline": roof_m}
 
     nvtx.range_pop()
     nvtx.range_push("mixed precision")
@@ -547,6 +589,33 @@ def main():
             "workload": "one seeded inspiral, omega 0.004 -> 0.1, 1,048,576 copies (Sec. IV lock-step test)",
             "paper_gpu_2009": {"value": 2700.0, "unit": "inspirals/s", "hardware": "1 GPU of a Tesla S1070, FP32"}}
         del inpp, outp
+        # Sec. V B-D's parameter sweeps: ten 100,000-binary ensembles (omega 0.00395 -> 0.05) in one
+        # integrate launch, per-ensemble statistics from one segmented reduction.
+        sw = workloads.paper_sweeps()
+        sizes = [e["m1"].shape[0] for _, _, e in sw]
+        off = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int64)
+        cat = {k: np.concatenate([e[k] for _, _, e in sw], axis=-1) for k in sw[0][2]}
+        inps = pn.to_device(cat, device=dev)
+        outs = pn.alloc_outputs(int(off[-1]), dev)
+        with pn.Batch(int(off[-1]), pn.params(precision=0)) as b:
+            b.integrate(inps, outs)
+            torch.cuda.synchronize()
+            e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+            e0.record()
+            b.integrate(inps, outs)
+            e1.record()
+            sst = b.stats_segments(inps, outs, off)
+            e2.record()
+            e2.synchronize()
+            mss = max_over_ranks(e0.elapsed_time(e1))
+        extras["paper_sweeps_one_launch"] = {
+            "value": aggregate_rate(world, int(off[-1]), 1, mss), "unit": "inspirals/s", "ms": mss,
+            "stats_ms": e1.elapsed_time(e2),
+            "workload": "Sec. V B-D sweeps: r vs chi (0.1..0.9), the m1 = 0.4 chi = 0.05 ring, r vs m1 (0.5..0.3); "
+                        "10 x 100,000 binaries, omega 0.00395 -> 0.05, one pn_batch_integrate + one "
+                        "pn_batch_stats_segments",
+            "pearson_s1s2": {f"{kind}={val}": s_["pearson_s1s2"] for (kind, val, _), s_ in zip(sw, sst)}}
+        del inps, outs
         extras["adjoint_C4"] = {"value": aggregate_rate(world, n4, 1, ms4), "unit": "gradients/s", "ms": ms4,
                                 "workload": "65,536 binaries, q ~ U[1,4], chi = 1, omega 0.01 -> 0.05; "
                                             "d(S1-hat.S2-hat final)/d(S1-hat, S2-hat, q), checkpoint every 64"}
@@ -584,7 +653,8 @@ def main():
                 # per step: k_setup + k_integrate + k_dots (the queue reset is a memset node)
                 "gpu_launches": 3 * args.steps,
                 "clocks": clocks, "mixed": mixed, "mixed_ds": mixed_ds, "extras": extras,
-                "fp32_fma_peak_tflops": (f32_peak or 0) / 1e12, "fp64_fma_peak_tflops": (f64_peak or 0) / 1e12}
+                "fp32_fma_peak_tflops": (f32_peak or 0) / 1e12, "fp64_fma_peak_tflops": (f64_peak or 0) / 1e12,
+                "peak_probe_clocks": probe_clocks}
         print(json.dumps(line), flush=True)
     if tdist:
         tdist.barrier()

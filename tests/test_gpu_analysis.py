@@ -105,22 +105,6 @@ def test_paper_statistics_at_paper_size(pn):
     b.close()
 
 
-def paper_sweep_ensembles():
-    """Sec. V C (r vs chi at equal mass), Sec. V D (the m1 = 0.4, chi = 0.05 ring) and Sec. V B / Fig. 5
-    (r vs m1 at chi = 1), each N = 100,000, omega 0.00395 -> 0.05."""
-    ens = []
-    for chi in (0.1, 0.3, 0.5, 0.7, 0.9):
-        ens.append(("chi", chi, workloads.ensemble(100_000, 600 + int(chi * 10), chi=(chi, chi),
-                                                   omega0=(0.00395, 0.00395))))
-    ens.append(("ring", 0.4, workloads.ensemble(100_000, 77, q=(0.4 / 0.6, 0.4 / 0.6), chi=(0.05, 0.05),
-                                                omega0=(0.00395, 0.00395))))
-    for m1 in (0.5, 0.45, 0.4, 0.3):
-        q = m1 / (1 - m1)
-        ens.append(("m1", m1, workloads.ensemble(100_000, 700 + int(m1 * 100), q=(q, q),
-                                                 omega0=(0.00395, 0.00395))))
-    return ens
-
-
 def test_paper_sweeps_in_one_launch(pn):
     """The three parameter sweeps of Sec. V B-D as ONE integrate launch over 10 concatenated ensembles
     (1,000,000 binaries) with per-ensemble statistics from one segmented reduction.  Each ensemble's
@@ -130,7 +114,7 @@ def test_paper_sweeps_in_one_launch(pn):
     r = -0.14 on the ring (Sec. V D), r falling with m1 (Fig. 5)."""
     import torch
     pv = paper_values()
-    ens = paper_sweep_ensembles()
+    ens = workloads.paper_sweeps()
     inp, out, off, st = pn.sweep([e for _, _, e in ens])
     g = pn.to_numpy(out)
     assert len(st) == len(ens) and off[-1] == 1_000_000
@@ -170,10 +154,15 @@ def test_segment_statistics_edge_cases(pn):
     assert st[1]["count_by_status"] == whole["count_by_status"] and st[1]["acc_total"] == whole["acc_total"]
     assert abs(st[1]["pearson_s1s2"] - whole["pearson_s1s2"]) <= 1e-13
     assert b.stats_segments(inp, out, [0]) == []
-    for bad in ([0, 200, 100], [-1, 10], [0, 301]):
+    for bad in ([0, 200, 100], [-1, 10]):
         with pytest.raises(pn.PNError):
             b.stats_segments(inp, out, bad)
+    with pytest.raises(ValueError):  # the binding: the tensors hold 300 binaries
+        b.stats_segments(inp, out, [0, 301])
     b.close()
+    with pn.Batch(200) as small:  # the library: offsets beyond the batch's n_max
+        with pytest.raises(pn.PNError):
+            small.stats_segments(inp, out, [0, 250])
 
 
 def test_analysis_argument_errors(pn):

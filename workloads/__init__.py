@@ -98,6 +98,20 @@ def config(name: str, n: int | None = None, seed: int | None = None) -> dict:
     raise KeyError(name)
 
 
+def paper_sweeps(n: int = 100_000) -> list:
+    """The parameter sweeps of Sec. V, each ensemble n binaries, isotropic spins, omega 0.00395 -> 0.05:
+    r vs chi at equal mass (Sec. V C: chi = 0.1 .. 0.9), the m1 = 0.4, chi = 0.05 ring (Sec. V D) and
+    r vs m1 at chi = 1 (Sec. V B, Fig. 5: m1 = 0.5 .. 0.3).  Returns (kind, value, ensemble) triples."""
+    out = []
+    for chi in (0.1, 0.3, 0.5, 0.7, 0.9):
+        out.append(("chi", chi, ensemble(n, 600 + int(chi * 10), chi=(chi, chi), omega0=(0.00395, 0.00395))))
+    out.append(("ring", 0.4, ensemble(n, 77, q=(0.4 / 0.6, 0.4 / 0.6), chi=(0.05, 0.05), omega0=(0.00395, 0.00395))))
+    for m1 in (0.5, 0.45, 0.4, 0.3):
+        q = m1 / (1 - m1)
+        out.append(("m1", m1, ensemble(n, 700 + int(m1 * 100), q=(q, q), omega0=(0.00395, 0.00395))))
+    return out
+
+
 def states(n: int, seed: int, omega_range: tuple = (0.003, 0.2)) -> dict:
     """n random points of the state space, for checking right-hand sides point by point: q = m1/m2
     log-uniform in [1, 10], M omega log-uniform in omega_range (default [0.003, 0.2]), spin vectors of
