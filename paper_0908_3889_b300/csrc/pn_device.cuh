@@ -914,78 +914,195 @@ __device__ __forceinline__ double dp5_attempt_f32(const Coef<float>& c, const Ct
 }
 
 
-// Per-thread workspace of dp5_attempt_ds in shared memory, lane-interleaved so
-// that a warp's accesses are 32 consecutive 8-byte words: vector v, component
-// c of thread t at base[(v * 10 + c) * nthreads + t].  Vectors 0..5 hold the
-// rates k1..k6, 6 the state split into pairs (then the increment of y5), 7 the
-// stage input (then k7); the error estimate goes to vector 1 once k2 is no
-// longer needed (its weight in b and in b - bhat is 0).
+// ---------------------------------------------------------------------------
+// Packed pairs of FP32 values (the f32x2 instructions of sm_100 and later): two
+// independent FP32 values in one 64-bit register, one instruction for both.
+// Each half of a packed instruction rounds exactly as the scalar instruction
+// does (round to nearest even, subnormals kept), so packed pair arithmetic
+// gives the same bits as two scalar evaluations in the same order.  On B300 a
+// packed instruction takes one issue slot and the FMA pipe for two cycles, at
+// the scalar latency: packing two independent chains halves their issue slots
+// and doubles the independent work a rolled loop body carries, without
+// growing the code (the double-single attempt is bound by dependency latency
+// and instruction-cache size, not by the FMA pipe).
+// ---------------------------------------------------------------------------
+typedef unsigned long long f2;  // .x in bits 0..31, .y in bits 32..63
+
+__device__ __forceinline__ f2 f2_of(float x, float y) {
+  f2 d;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(d) : "f"(x), "f"(y));
+  return d;
+}
+__device__ __forceinline__ f2 f2_dup(float x) { return f2_of(x, x); }
+__device__ __forceinline__ float f2_x(f2 a) { return __uint_as_float((uint32_t)a); }
+__device__ __forceinline__ float f2_y(f2 a) { return __uint_as_float((uint32_t)(a >> 32)); }
+__device__ __forceinline__ f2 add2(f2 a, f2 b) {
+  f2 d;
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+__device__ __forceinline__ f2 sub2(f2 a, f2 b) {
+  f2 d;
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+__device__ __forceinline__ f2 mul2(f2 a, f2 b) {
+  f2 d;
+  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+__device__ __forceinline__ f2 fma2(f2 a, f2 b, f2 c) {
+  f2 d;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+  return d;
+}
+// -a in both halves (sign bits flipped: exact, like the scalar negation).
+__device__ __forceinline__ f2 neg2(f2 a) { return a ^ 0x8000000080000000ull; }
+
+// Two double-single values, halves .x and .y: hi = (x.hi, y.hi), lo = (x.lo, y.lo).
+struct ds2 {
+  f2 hi, lo;
+};
+__device__ __forceinline__ ds2 ds2_of(ds x, ds y) { return ds2{f2_of(x.hi, y.hi), f2_of(x.lo, y.lo)}; }
+__device__ __forceinline__ ds ds2_x(ds2 a) { return ds{f2_x(a.hi), f2_x(a.lo)}; }
+__device__ __forceinline__ ds ds2_y(ds2 a) { return ds{f2_y(a.hi), f2_y(a.lo)}; }
+
+// The pair versions of two_sum, fast_two_sum and the double-single operations
+// above, operation for operation.
+__device__ __forceinline__ ds2 two_sum2(f2 a, f2 b) {
+  const f2 s = add2(a, b);
+  const f2 v = sub2(s, a);
+  return ds2{s, add2(sub2(a, sub2(s, v)), sub2(b, v))};
+}
+__device__ __forceinline__ ds2 fast_two_sum2(f2 a, f2 b) {
+  const f2 s = add2(a, b);
+  return ds2{s, sub2(b, sub2(s, a))};
+}
+__device__ __forceinline__ ds2 ds2_add(ds2 a, ds2 b) {
+  const ds2 s = two_sum2(a.hi, b.hi);
+  return fast_two_sum2(s.hi, add2(s.lo, add2(a.lo, b.lo)));
+}
+__device__ __forceinline__ ds2 ds2_mul(ds2 a, ds2 b) {
+  const f2 p = mul2(a.hi, b.hi);
+  f2 e = fma2(a.hi, b.hi, neg2(p));
+  e = fma2(a.hi, b.lo, e);
+  e = fma2(a.lo, b.hi, e);
+  return fast_two_sum2(p, e);
+}
+
+// Per-thread workspace of dp5_attempt_ds in shared memory: vector v of ten
+// double-single components as five packed pairs of components (2p, 2p + 1),
+// pair p of thread t at base[(v * 5 + p) * nthreads + t] as 16 bytes
+// (hi_2p, hi_2p+1, lo_2p, lo_2p+1), lane-interleaved so that a warp's accesses
+// are 32 consecutive 16-byte words.  Vectors 0..5 hold the rates k1..k6, 6 the
+// state split into pairs (then the increment of y5), 7 the stage input (then
+// k7); the error estimate goes to vector 1 once k2 is no longer needed (its
+// weight in b and in b - bhat is 0).
 constexpr int kDsVectors = 8;
 constexpr int kDsWorkBytes = kDsVectors * 10 * 8;  // per thread
 struct DsWork {
-  float2* base;
+  ulonglong2* base;
   int nt, t;
-  __device__ __forceinline__ ds get(int v, int c) const {
-    const float2 x = base[(v * 10 + c) * nt + t];
-    return ds{x.x, x.y};
+  __device__ __forceinline__ ds2 get2(int v, int p) const {
+    const ulonglong2 x = base[(v * 5 + p) * nt + t];
+    return ds2{x.x, x.y};
   }
-  __device__ __forceinline__ void put(int v, int c, ds a) const { base[(v * 10 + c) * nt + t] = make_float2(a.hi, a.lo); }
+  __device__ __forceinline__ void put2(int v, int p, ds2 a) const { base[(v * 5 + p) * nt + t] = make_ulonglong2(a.hi, a.lo); }
+  __device__ __forceinline__ void put_vec(int v, const ds* a) const {
+#pragma unroll
+    for (int p = 0; p < 5; p++) put2(v, p, ds2_of(a[2 * p], a[2 * p + 1]));
+  }
+  __device__ __forceinline__ void get_vec(int v, ds* a) const {
+#pragma unroll
+    for (int p = 0; p < 5; p++) {
+      const ds2 x = get2(v, p);
+      a[2 * p] = ds2_x(x);
+      a[2 * p + 1] = ds2_y(x);
+    }
+  }
 };
+
+// Compensated sums of products c_j x_j (dot_first / dot_add / dot_val) for a
+// pair of components with the same coefficients.
+struct dacc2 {
+  f2 s, e;
+};
+__device__ __forceinline__ dacc2 dot_first2(dsc c, ds2 x) {
+  const f2 ch = f2_dup(c.hi), cl = f2_dup(c.lo);
+  const f2 p = mul2(ch, x.hi);
+  f2 e = fma2(ch, x.hi, neg2(p));
+  e = fma2(ch, x.lo, e);
+  e = fma2(cl, x.hi, e);
+  return dacc2{p, e};
+}
+__device__ __forceinline__ dacc2 dot_add2(dacc2 a, dsc c, ds2 x) {
+  const f2 ch = f2_dup(c.hi), cl = f2_dup(c.lo);
+  const f2 p = mul2(ch, x.hi);
+  f2 e = fma2(ch, x.hi, neg2(p));
+  e = fma2(ch, x.lo, e);
+  e = fma2(cl, x.hi, e);
+  const ds2 t = two_sum2(a.s, p);
+  return dacc2{t.hi, add2(a.e, add2(t.lo, e))};
+}
+__device__ __forceinline__ ds2 dot_val2(dacc2 a) { return two_sum2(a.s, a.e); }
 
 __device__ __forceinline__ double dp5_attempt_ds(const Coefs& cf, const Tabs& tb, const Ctl& ctl, const double* y,
                                                  const double* k1, double h, double* y5, double* k7,
                                                  const DsWork& w) {
   const ds hd = split64(h);
+  const ds2 hd2 = ds2{f2_dup(hd.hi), f2_dup(hd.lo)};
 #pragma unroll
-  for (int c = 0; c < 10; c++) {
-    w.put(6, c, split64(y[c]));
-    w.put(0, c, split64(k1[c]));
+  for (int p = 0; p < 5; p++) {
+    w.put2(6, p, ds2_of(split64(y[2 * p]), split64(y[2 * p + 1])));
+    w.put2(0, p, ds2_of(split64(k1[2 * p]), split64(k1[2 * p + 1])));
   }
   ds kn[10];
 #pragma unroll 1
   for (int r = 0; r < 6; r++) {
     const dsc a0 = c_dp_a_ds[r][0], a1 = c_dp_a_ds[r][1], a2 = c_dp_a_ds[r][2], a3 = c_dp_a_ds[r][3],
               a4 = c_dp_a_ds[r][4], a5 = c_dp_a_ds[r][5];
-#pragma unroll 2
-    for (int c = 0; c < 10; c++) {
-      dacc acc = dot_first(a0, w.get(0, c));
-      if (r >= 1 && r < 5) acc = dot_add(acc, a1, w.get(1, c));  // b2 = 0
-      if (r >= 2) acc = dot_add(acc, a2, w.get(2, c));
-      if (r >= 3) acc = dot_add(acc, a3, w.get(3, c));
-      if (r >= 4) acc = dot_add(acc, a4, w.get(4, c));
-      if (r >= 5) acc = dot_add(acc, a5, w.get(5, c));
-      const ds inc = ds_mul(hd, dot_val(acc));  // h sum_j a_sj k_j
-      w.put(7, c, ds_add(w.get(6, c), inc));
-      if (r == 5) w.put(6, c, inc);
+#pragma unroll 1
+    for (int p = 0; p < 5; p++) {
+      dacc2 acc = dot_first2(a0, w.get2(0, p));
+      if (r >= 1 && r < 5) acc = dot_add2(acc, a1, w.get2(1, p));  // b2 = 0
+      if (r >= 2) acc = dot_add2(acc, a2, w.get2(2, p));
+      if (r >= 3) acc = dot_add2(acc, a3, w.get2(3, p));
+      if (r >= 4) acc = dot_add2(acc, a4, w.get2(4, p));
+      if (r >= 5) acc = dot_add2(acc, a5, w.get2(5, p));
+      const ds2 inc = ds2_mul(hd2, dot_val2(acc));  // h sum_j a_sj k_j
+      w.put2(7, p, ds2_add(w.get2(6, p), inc));
+      if (r == 5) w.put2(6, p, inc);
     }
     ds yin[10];
-#pragma unroll
-    for (int c = 0; c < 10; c++) yin[c] = w.get(7, c);
+    w.get_vec(7, yin);
     rhs_ds(cf.cds, tb.f, yin, kn);  // k_{r+2}; for r = 5, k7 at the double-single y5
-    const int slot = (r < 5) ? r + 1 : 7;
-#pragma unroll
-    for (int c = 0; c < 10; c++) w.put(slot, c, kn[c]);
+    w.put_vec((r < 5) ? r + 1 : 7, kn);
   }
-#pragma unroll 2
-  for (int c = 0; c < 10; c++) {  // embedded error estimate h sum_j (b_j - bhat_j) k_j
-    dacc acc = dot_first(c_dp_e_ds[0], w.get(0, c));
-    acc = dot_add(acc, c_dp_e_ds[1], w.get(2, c));
-    acc = dot_add(acc, c_dp_e_ds[2], w.get(3, c));
-    acc = dot_add(acc, c_dp_e_ds[3], w.get(4, c));
-    acc = dot_add(acc, c_dp_e_ds[4], w.get(5, c));
-    acc = dot_add(acc, c_dp_e_ds[5], w.get(7, c));
-    w.put(1, c, ds_mul(hd, dot_val(acc)));
+#pragma unroll 1
+  for (int p = 0; p < 5; p++) {  // embedded error estimate h sum_j (b_j - bhat_j) k_j
+    dacc2 acc = dot_first2(c_dp_e_ds[0], w.get2(0, p));
+    acc = dot_add2(acc, c_dp_e_ds[1], w.get2(2, p));
+    acc = dot_add2(acc, c_dp_e_ds[2], w.get2(3, p));
+    acc = dot_add2(acc, c_dp_e_ds[3], w.get2(4, p));
+    acc = dot_add2(acc, c_dp_e_ds[4], w.get2(5, p));
+    acc = dot_add2(acc, c_dp_e_ds[5], w.get2(7, p));
+    w.put2(1, p, ds2_mul(hd2, dot_val2(acc)));
   }
   double sum = 0.0;
 #pragma unroll
-  for (int c = 0; c < 10; c++) {
-    const ds inc = w.get(6, c);
-    y5[c] = y[c] + (f32_to_f64(inc.hi) + f32_to_f64(inc.lo));
-    k7[c] = ds_to_f64(kn[c]);
-    const double e = ds_to_f64(w.get(1, c));
-    const double sc = fma(ctl.rtol, max_abs(y[c], y5[c]), ctl.atol);
-    const double q = e * rcp_norm(sc);
-    sum = fma(q, q, sum);
+  for (int p = 0; p < 5; p++) {
+    const ds2 inc = w.get2(6, p), err = w.get2(1, p);
+#pragma unroll
+    for (int h2 = 0; h2 < 2; h2++) {
+      const int c = 2 * p + h2;
+      const ds i1 = h2 ? ds2_y(inc) : ds2_x(inc);
+      y5[c] = y[c] + (f32_to_f64(i1.hi) + f32_to_f64(i1.lo));
+      k7[c] = ds_to_f64(kn[c]);
+      const double e = ds_to_f64(h2 ? ds2_y(err) : ds2_x(err));
+      const double sc = fma(ctl.rtol, max_abs(y[c], y5[c]), ctl.atol);
+      const double q = e * rcp_norm(sc);
+      sum = fma(q, q, sum);
+    }
   }
   return sum * 0.1;
 }

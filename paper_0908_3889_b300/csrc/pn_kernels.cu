@@ -384,7 +384,7 @@ template <int PREC, bool PERSIST, bool RECORD, bool BOUNDED, bool WS>
 __device__ __forceinline__ void integrate_body(const KArgs& a, const double* __restrict__ ws, int64_t stride,
                                                const RecArgs& rec) {
   __shared__ float s_tabf[512];
-  extern __shared__ float2 s_dsw[];  // per-thread stage workspace (PREC 0: kF64WorkBytes, 1: kF32WorkBytes, 2: kDsWorkBytes)
+  extern __shared__ __align__(16) float2 s_dsw[];  // per-thread stage workspace (PREC 0: kF64WorkBytes, 1: kF32WorkBytes, 2: kDsWorkBytes)
   const Tabs tb = load_tabs<PREC>(a.tabf, s_tabf);
 
   const unsigned lane = threadIdx.x & 31u;
@@ -427,7 +427,7 @@ __device__ __forceinline__ void integrate_body(const KArgs& a, const double* __r
       double s;
       if constexpr (PREC == 2)
         s = dp5_attempt_ds(L.cf, tb, a.ctl, L.y, L.k1, L.h, y5, k7,
-                           DsWork{s_dsw, (int)blockDim.x, (int)threadIdx.x});
+                           DsWork{reinterpret_cast<ulonglong2*>(s_dsw), (int)blockDim.x, (int)threadIdx.x});
       else if constexpr (PREC == 1)
         s = dp5_attempt_f32(L.cf.c32, a.ctl, L.y, L.k1, L.h, y5, k7,
                             F32Work{reinterpret_cast<float*>(s_dsw), (int)blockDim.x, (int)threadIdx.x});
