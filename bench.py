@@ -361,11 +361,14 @@ def main():
         print(json.dumps({"profile_case": "C4 " + args.profile_case, "n": n4}))
         return
     if args.profile_case == "integrate":
+        attempts = {}
         for prec in (pn.native.PN_FP64, pn.native.PN_MIXED, pn.native.PN_MIXED_DS):
             with pn.Batch(n, pn.params(precision=prec, schedule=pn.native.PN_SCHED_PERSISTENT, block=256)) as b:
                 b.integrate(inp, out)
                 torch.cuda.synchronize()
-        print(json.dumps({"profile_case": "C1", "n": n, "precisions": [0, 1, 2]}))
+                st = b.stats(inp, out)
+                attempts[prec] = st["acc_total"] + st["rej_total"] + st["land_total"]
+        print(json.dumps({"profile_case": "C1", "n": n, "precisions": [0, 1, 2], "attempts": attempts}))
         return
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)  # 256 MB > L2 (126 MB)
 
