@@ -738,182 +738,6 @@ __device__ __forceinline__ double dp5_attempt_ws(const Coefs& cf, const Tabs& tb
   return sum * ((h * h) * 0.1);
 }
 
-// The mixed-precision attempt (FP32 right-hand side).  The stage inputs
-// Y_2..Y_6 only feed the FP32 right-hand side, which rounds them to FP32 on
-// entry, so they are formed in FP32 from the FP32-rounded state.  The rates are
-// FP32 values, so the sums over them that need more than FP32 -- the increment
-// sum_j b_j k_j of the new state and the embedded error estimate, which cancels
-// to ~tol of its terms -- are compensated double-single sums on the FP32 pipe
-// (~2^-48 relative).  The state accumulation y5 = y + h (increment) is one FP64
-// FMA per component; the error norm is taken in FP32 from the estimate's
-// leading float (the FP32 rates already perturb it by ~1e-3 of itself); the
-// accept test and the step-size update are FP64.  Conversions between the two
-// formats are integer operations.  The
-// six stages run as one loop so that the right-hand side is emitted once
-// (seven inlined copies overflow the instruction cache); the rates k1..k6 sit
-// in a per-thread shared-memory workspace (lane-interleaved: rate j, component
-// c of thread t at base[(j * 10 + c) * nthreads + t]) so no register queue has
-// to be shifted between stages.
-// Slots 0..5 hold k1..k6; slot 1 takes k7 once k2 is spent (its weights in b and
-// in b - bhat are 0); slots 6 and 7 the increment of y5 (hi, lo), then slot 6
-// the error scale.
-constexpr int kF32WorkBytes = 8 * 10 * 4;  // per thread
-struct F32Work {
-  float* base;
-  int nt, t;
-  __device__ __forceinline__ float get(int j, int c) const { return base[(j * 10 + c) * nt + t]; }
-  __device__ __forceinline__ void put(int j, int c, float v) const { base[(j * 10 + c) * nt + t] = v; }
-};
-// Rows of the stage tableau in FP32: coefficients of k1..k_{r+1} for stage r + 2.
-__constant__ float c_dp_a_f[5][5] = {
-    {(float)DP_A21, 0, 0, 0, 0},
-    {(float)DP_A31, (float)DP_A32, 0, 0, 0},
-    {(float)DP_A41, (float)DP_A42, (float)DP_A43, 0, 0},
-    {(float)DP_A51, (float)DP_A52, (float)DP_A53, (float)DP_A54, 0},
-    {(float)DP_A61, (float)DP_A62, (float)DP_A63, (float)DP_A64, (float)DP_A65},
-};
-
-// ---------------------------------------------------------------------------
-// The double-single attempt.  Its stage inputs feed the double-single
-// right-hand side and so need ~48-bit accuracy: they are formed on the FP32
-// pipe by compensated sums (Dot2 of Ogita, Rump & Oishi 2005) of double-single
-// rates, not by FP64 sums.  The state accumulation y5 = y + h sum_j b_j k_j, the
-// error norm and the step control stay FP64.  The rates and stage vectors live
-// in a per-thread shared-memory workspace so that the loops over the ten
-// components can stay rolled: with them unrolled (or with the vectors in
-// registers) the stage loop no longer fits the instruction cache.
-// ---------------------------------------------------------------------------
-struct dsc {  // a double-single constant: hi the nearest float, lo the nearest float to the rest
-  float hi, lo;
-};
-#define PN_DSC(x) {(float)(x), (float)((x) - (double)(float)(x))}
-// Row r: coefficients of k1..k_{r+1} for stage r + 2; row 5 is b (first same as last).
-__constant__ dsc c_dp_a_ds[6][6] = {
-    {PN_DSC(DP_A21), {0, 0}, {0, 0}, {0, 0}, {0, 0}, {0, 0}},
-    {PN_DSC(DP_A31), PN_DSC(DP_A32), {0, 0}, {0, 0}, {0, 0}, {0, 0}},
-    {PN_DSC(DP_A41), PN_DSC(DP_A42), PN_DSC(DP_A43), {0, 0}, {0, 0}, {0, 0}},
-    {PN_DSC(DP_A51), PN_DSC(DP_A52), PN_DSC(DP_A53), PN_DSC(DP_A54), {0, 0}, {0, 0}},
-    {PN_DSC(DP_A61), PN_DSC(DP_A62), PN_DSC(DP_A63), PN_DSC(DP_A64), PN_DSC(DP_A65), {0, 0}},
-    {PN_DSC(DP_B1), {0, 0}, PN_DSC(DP_B3), PN_DSC(DP_B4), PN_DSC(DP_B5), PN_DSC(DP_B6)},
-};
-// b - bhat for k1, k3, k4, k5, k6, k7 (the k2 weight is 0).
-__constant__ dsc c_dp_e_ds[6] = {PN_DSC(DP_E1), PN_DSC(DP_E3), PN_DSC(DP_E4),
-                                 PN_DSC(DP_E5), PN_DSC(DP_E6), PN_DSC(DP_E7)};
-#undef PN_DSC
-
-// Compensated sum of products c_j x_j: s collects the rounded leading products
-// exactly through two_sum, e the rounding errors of those sums, the products'
-// own errors and the cross terms c.hi x.lo + c.lo x.hi.  dot_val(s, e) carries
-// ~2^-48 relative error unless the sum cancels.
-struct dacc {
-  float s, e;
-};
-__device__ __forceinline__ dacc dot_first(dsc c, ds x) {
-  const float p = __fmul_rn(c.hi, x.hi);
-  float e = __fmaf_rn(c.hi, x.hi, -p);
-  e = __fmaf_rn(c.hi, x.lo, e);
-  e = __fmaf_rn(c.lo, x.hi, e);
-  return dacc{p, e};
-}
-__device__ __forceinline__ dacc dot_add(dacc a, dsc c, ds x) {
-  const float p = __fmul_rn(c.hi, x.hi);
-  float e = __fmaf_rn(c.hi, x.hi, -p);
-  e = __fmaf_rn(c.hi, x.lo, e);
-  e = __fmaf_rn(c.lo, x.hi, e);
-  const ds t = two_sum(a.s, p);
-  return dacc{t.hi, __fadd_rn(a.e, __fadd_rn(t.lo, e))};
-}
-__device__ __forceinline__ ds dot_val(dacc a) { return two_sum(a.s, a.e); }
-
-// The same for FP32 values x (exact floats: no low part).
-__device__ __forceinline__ dacc dot_first_f(dsc c, float x) {
-  const float p = __fmul_rn(c.hi, x);
-  return dacc{p, __fmaf_rn(c.lo, x, __fmaf_rn(c.hi, x, -p))};
-}
-__device__ __forceinline__ dacc dot_add_f(dacc a, dsc c, float x) {
-  const float p = __fmul_rn(c.hi, x);
-  const float e = __fmaf_rn(c.lo, x, __fmaf_rn(c.hi, x, -p));
-  const ds t = two_sum(a.s, p);
-  return dacc{t.hi, __fadd_rn(a.e, __fadd_rn(t.lo, e))};
-}
-
-// The FP32-RHS attempt (declared with its workspace above).
-__device__ __forceinline__ double dp5_attempt_f32(const Coef<float>& c, const Ctl& ctl, const double* y,
-                                                  const double* k1, double h, double* y5, double* k7,
-                                                  const F32Work& w) {
-  float yf[10], ys[10], kn[10];
-  const float hf = f64_to_f32(h);
-#pragma unroll
-  for (int i = 0; i < 10; i++) {
-    yf[i] = f64_to_f32(y[i]);
-    w.put(0, i, f64_to_f32(k1[i]));  // k1 is an FP32 rate widened: exact
-  }
-#pragma unroll 1
-  for (int r = 0; r < 6; r++) {
-    if (r < 5) {
-      const float a0 = hf * c_dp_a_f[r][0], a1 = hf * c_dp_a_f[r][1], a2 = hf * c_dp_a_f[r][2],
-                  a3 = hf * c_dp_a_f[r][3], a4 = hf * c_dp_a_f[r][4];
-#pragma unroll
-      for (int i = 0; i < 10; i++) {
-        float acc = fmaf(a0, w.get(0, i), yf[i]);
-        if (r >= 1) acc = fmaf(a1, w.get(1, i), acc);
-        if (r >= 2) acc = fmaf(a2, w.get(2, i), acc);
-        if (r >= 3) acc = fmaf(a3, w.get(3, i), acc);
-        if (r >= 4) acc = fmaf(a4, w.get(4, i), acc);
-        ys[i] = acc;
-      }
-    } else {  // the 5th-order solution y5 = y + h inc, inc = sum_j b_j k_j compensated, then one FP64 FMA
-#pragma unroll 1
-      for (int i = 0; i < 10; i++) {  // rolled: the compensated sums would not fit the instruction cache x10
-        dacc acc = dot_first_f(c_dp_a_ds[5][0], w.get(0, i));
-        acc = dot_add_f(acc, c_dp_a_ds[5][2], w.get(2, i));
-        acc = dot_add_f(acc, c_dp_a_ds[5][3], w.get(3, i));
-        acc = dot_add_f(acc, c_dp_a_ds[5][4], w.get(4, i));
-        acc = dot_add_f(acc, c_dp_a_ds[5][5], w.get(5, i));
-        const ds inc = dot_val(acc);
-        w.put(6, i, inc.hi);
-        w.put(7, i, inc.lo);
-      }
-#pragma unroll
-      for (int i = 0; i < 10; i++) {
-        // The FP32 right-hand side's input at y5 directly in FP32 (within an FP32 ulp of
-        // y5 rounded), so the FP64 accumulation below is off the path to k7.
-        ys[i] = fmaf(hf, w.get(6, i), yf[i]);
-        y5[i] = fma(h, f32_to_f64(w.get(6, i)) + f32_to_f64(w.get(7, i)), y[i]);
-      }
-    }
-    rhs32(c, ys, kn);  // k_{r+2}; for r = 5, k7 = f(y5)
-    if (r < 5) {
-#pragma unroll
-      for (int i = 0; i < 10; i++) w.put(r + 1, i, kn[i]);
-    }
-  }
-  // Error estimate sum_j (b_j - bhat_j) k_j compensated (it cancels to ~tol of its terms), its
-  // scaled RMS norm in FP32 from the estimate's leading float; h enters once, in FP64.
-  const float rtf = f64_to_f32(ctl.rtol), atf = f64_to_f32(ctl.atol);
-#pragma unroll
-  for (int i = 0; i < 10; i++) {
-    k7[i] = f32_to_f64(kn[i]);
-    w.put(1, i, kn[i]);
-    w.put(6, i, __fmaf_rn(rtf, fmaxf(fabsf(yf[i]), fabsf(ys[i])), atf));
-  }
-  float sf = 0.0f;
-#pragma unroll 1
-  for (int i = 0; i < 10; i++) {
-    dacc acc = dot_first_f(c_dp_e_ds[0], w.get(0, i));
-    acc = dot_add_f(acc, c_dp_e_ds[1], w.get(2, i));
-    acc = dot_add_f(acc, c_dp_e_ds[2], w.get(3, i));
-    acc = dot_add_f(acc, c_dp_e_ds[3], w.get(4, i));
-    acc = dot_add_f(acc, c_dp_e_ds[4], w.get(5, i));
-    acc = dot_add_f(acc, c_dp_e_ds[5], w.get(1, i));
-    const float e = __fadd_rn(acc.s, acc.e);
-    const float q = __fmul_rn(e, __frcp_rn(w.get(6, i)));
-    sf = __fmaf_rn(q, q, sf);
-  }
-  return f32_to_f64(sf) * ((h * h) * 0.1);
-}
-
-
 // ---------------------------------------------------------------------------
 // Packed pairs of FP32 values (the f32x2 instructions of sm_100 and later): two
 // independent FP32 values in one 64-bit register, one instruction for both.
@@ -990,6 +814,234 @@ __device__ __forceinline__ ds2 ds2_mul(ds2 a, ds2 b) {
   return fast_two_sum2(p, e);
 }
 
+// The mixed-precision attempt (FP32 right-hand side).  The stage inputs
+// Y_2..Y_6 only feed the FP32 right-hand side, which rounds them to FP32 on
+// entry, so they are formed in FP32 from the FP32-rounded state.  The rates are
+// FP32 values, so the sums over them that need more than FP32 -- the increment
+// sum_j b_j k_j of the new state and the embedded error estimate, which cancels
+// to ~tol of its terms -- are compensated double-single sums on the FP32 pipe
+// (~2^-48 relative).  The state accumulation y5 = y + h (increment) is one FP64
+// FMA per component; the error norm is taken in FP32 from the estimate's
+// leading float (the FP32 rates already perturb it by ~1e-3 of itself); the
+// accept test and the step-size update are FP64.  Conversions between the two
+// formats are integer operations.  The
+// six stages run as one loop so that the right-hand side is emitted once
+// (seven inlined copies overflow the instruction cache); the rates k1..k6 sit
+// in a per-thread shared-memory workspace so no register queue has to be
+// shifted between stages.  The workspace holds packed pairs of components
+// (2p, 2p + 1), and every sum over the components runs on the pairs with the
+// packed FP32 instructions (the same bits as the scalar sums, half the issue
+// slots): slot j, pair p of thread t at base[(j * 5 + p) * nthreads + t] as 8
+// bytes, lane-interleaved.
+// Slots 0..5 hold k1..k6; slot 1 takes k7 once k2 is spent (its weights in b and
+// in b - bhat are 0); slots 6 and 7 the increment of y5 (hi, lo), then slot 6
+// the error scale.
+constexpr int kF32WorkBytes = 8 * 10 * 4;  // per thread
+struct F32Work {
+  f2* base;
+  int nt, t;
+  __device__ __forceinline__ f2 get2(int j, int p) const { return base[(j * 5 + p) * nt + t]; }
+  __device__ __forceinline__ void put2(int j, int p, f2 v) const { base[(j * 5 + p) * nt + t] = v; }
+};
+// Rows of the stage tableau in FP32: coefficients of k1..k_{r+1} for stage r + 2.
+__constant__ float c_dp_a_f[5][5] = {
+    {(float)DP_A21, 0, 0, 0, 0},
+    {(float)DP_A31, (float)DP_A32, 0, 0, 0},
+    {(float)DP_A41, (float)DP_A42, (float)DP_A43, 0, 0},
+    {(float)DP_A51, (float)DP_A52, (float)DP_A53, (float)DP_A54, 0},
+    {(float)DP_A61, (float)DP_A62, (float)DP_A63, (float)DP_A64, (float)DP_A65},
+};
+
+// ---------------------------------------------------------------------------
+// The double-single attempt.  Its stage inputs feed the double-single
+// right-hand side and so need ~48-bit accuracy: they are formed on the FP32
+// pipe by compensated sums (Dot2 of Ogita, Rump & Oishi 2005) of double-single
+// rates, not by FP64 sums.  The state accumulation y5 = y + h sum_j b_j k_j, the
+// error norm and the step control stay FP64.  The rates and stage vectors live
+// in a per-thread shared-memory workspace so that the loops over the ten
+// components can stay rolled: with them unrolled (or with the vectors in
+// registers) the stage loop no longer fits the instruction cache.
+// ---------------------------------------------------------------------------
+struct dsc {  // a double-single constant: hi the nearest float, lo the nearest float to the rest
+  float hi, lo;
+};
+#define PN_DSC(x) {(float)(x), (float)((x) - (double)(float)(x))}
+// Row r: coefficients of k1..k_{r+1} for stage r + 2; row 5 is b (first same as last).
+__constant__ dsc c_dp_a_ds[6][6] = {
+    {PN_DSC(DP_A21), {0, 0}, {0, 0}, {0, 0}, {0, 0}, {0, 0}},
+    {PN_DSC(DP_A31), PN_DSC(DP_A32), {0, 0}, {0, 0}, {0, 0}, {0, 0}},
+    {PN_DSC(DP_A41), PN_DSC(DP_A42), PN_DSC(DP_A43), {0, 0}, {0, 0}, {0, 0}},
+    {PN_DSC(DP_A51), PN_DSC(DP_A52), PN_DSC(DP_A53), PN_DSC(DP_A54), {0, 0}, {0, 0}},
+    {PN_DSC(DP_A61), PN_DSC(DP_A62), PN_DSC(DP_A63), PN_DSC(DP_A64), PN_DSC(DP_A65), {0, 0}},
+    {PN_DSC(DP_B1), {0, 0}, PN_DSC(DP_B3), PN_DSC(DP_B4), PN_DSC(DP_B5), PN_DSC(DP_B6)},
+};
+// b - bhat for k1, k3, k4, k5, k6, k7 (the k2 weight is 0).
+__constant__ dsc c_dp_e_ds[6] = {PN_DSC(DP_E1), PN_DSC(DP_E3), PN_DSC(DP_E4),
+                                 PN_DSC(DP_E5), PN_DSC(DP_E6), PN_DSC(DP_E7)};
+#undef PN_DSC
+
+// Compensated sum of products c_j x_j: s collects the rounded leading products
+// exactly through two_sum, e the rounding errors of those sums, the products'
+// own errors and the cross terms c.hi x.lo + c.lo x.hi.  dot_val(s, e) carries
+// ~2^-48 relative error unless the sum cancels.
+struct dacc {
+  float s, e;
+};
+__device__ __forceinline__ dacc dot_first(dsc c, ds x) {
+  const float p = __fmul_rn(c.hi, x.hi);
+  float e = __fmaf_rn(c.hi, x.hi, -p);
+  e = __fmaf_rn(c.hi, x.lo, e);
+  e = __fmaf_rn(c.lo, x.hi, e);
+  return dacc{p, e};
+}
+__device__ __forceinline__ dacc dot_add(dacc a, dsc c, ds x) {
+  const float p = __fmul_rn(c.hi, x.hi);
+  float e = __fmaf_rn(c.hi, x.hi, -p);
+  e = __fmaf_rn(c.hi, x.lo, e);
+  e = __fmaf_rn(c.lo, x.hi, e);
+  const ds t = two_sum(a.s, p);
+  return dacc{t.hi, __fadd_rn(a.e, __fadd_rn(t.lo, e))};
+}
+__device__ __forceinline__ ds dot_val(dacc a) { return two_sum(a.s, a.e); }
+
+// The same for FP32 values x (exact floats: no low part).
+__device__ __forceinline__ dacc dot_first_f(dsc c, float x) {
+  const float p = __fmul_rn(c.hi, x);
+  return dacc{p, __fmaf_rn(c.lo, x, __fmaf_rn(c.hi, x, -p))};
+}
+__device__ __forceinline__ dacc dot_add_f(dacc a, dsc c, float x) {
+  const float p = __fmul_rn(c.hi, x);
+  const float e = __fmaf_rn(c.lo, x, __fmaf_rn(c.hi, x, -p));
+  const ds t = two_sum(a.s, p);
+  return dacc{t.hi, __fadd_rn(a.e, __fadd_rn(t.lo, e))};
+}
+
+// Compensated sums of products c_j x_j (dot_first / dot_add / dot_val) for a
+// pair of components with the same coefficients.
+struct dacc2 {
+  f2 s, e;
+};
+__device__ __forceinline__ dacc2 dot_first2(dsc c, ds2 x) {
+  const f2 ch = f2_dup(c.hi), cl = f2_dup(c.lo);
+  const f2 p = mul2(ch, x.hi);
+  f2 e = fma2(ch, x.hi, neg2(p));
+  e = fma2(ch, x.lo, e);
+  e = fma2(cl, x.hi, e);
+  return dacc2{p, e};
+}
+__device__ __forceinline__ dacc2 dot_add2(dacc2 a, dsc c, ds2 x) {
+  const f2 ch = f2_dup(c.hi), cl = f2_dup(c.lo);
+  const f2 p = mul2(ch, x.hi);
+  f2 e = fma2(ch, x.hi, neg2(p));
+  e = fma2(ch, x.lo, e);
+  e = fma2(cl, x.hi, e);
+  const ds2 t = two_sum2(a.s, p);
+  return dacc2{t.hi, add2(a.e, add2(t.lo, e))};
+}
+__device__ __forceinline__ ds2 dot_val2(dacc2 a) { return two_sum2(a.s, a.e); }
+
+// dot_first_f / dot_add_f for a pair of components with the same coefficients.
+__device__ __forceinline__ dacc2 dot_first_f2(dsc c, f2 x) {
+  const f2 ch = f2_dup(c.hi), cl = f2_dup(c.lo);
+  const f2 p = mul2(ch, x);
+  return dacc2{p, fma2(cl, x, fma2(ch, x, neg2(p)))};
+}
+__device__ __forceinline__ dacc2 dot_add_f2(dacc2 a, dsc c, f2 x) {
+  const f2 ch = f2_dup(c.hi), cl = f2_dup(c.lo);
+  const f2 p = mul2(ch, x);
+  const f2 e = fma2(cl, x, fma2(ch, x, neg2(p)));
+  const ds2 t = two_sum2(a.s, p);
+  return dacc2{t.hi, add2(a.e, add2(t.lo, e))};
+}
+
+// The FP32-RHS attempt (declared with its workspace above).
+__device__ __forceinline__ double dp5_attempt_f32(const Coef<float>& c, const Ctl& ctl, const double* y,
+                                                  const double* k1, double h, double* y5, double* k7,
+                                                  const F32Work& w) {
+  f2 yf[5];
+  float ys[10], kn[10];
+  const float hf = f64_to_f32(h);
+  const f2 hf2 = f2_dup(hf);
+#pragma unroll
+  for (int p = 0; p < 5; p++) {
+    yf[p] = f2_of(f64_to_f32(y[2 * p]), f64_to_f32(y[2 * p + 1]));
+    w.put2(0, p, f2_of(f64_to_f32(k1[2 * p]), f64_to_f32(k1[2 * p + 1])));  // k1 is an FP32 rate widened: exact
+  }
+#pragma unroll 1
+  for (int r = 0; r < 6; r++) {
+    if (r < 5) {
+      const f2 a0 = f2_dup(hf * c_dp_a_f[r][0]), a1 = f2_dup(hf * c_dp_a_f[r][1]), a2 = f2_dup(hf * c_dp_a_f[r][2]),
+               a3 = f2_dup(hf * c_dp_a_f[r][3]), a4 = f2_dup(hf * c_dp_a_f[r][4]);
+#pragma unroll
+      for (int p = 0; p < 5; p++) {
+        f2 acc = fma2(a0, w.get2(0, p), yf[p]);
+        if (r >= 1) acc = fma2(a1, w.get2(1, p), acc);
+        if (r >= 2) acc = fma2(a2, w.get2(2, p), acc);
+        if (r >= 3) acc = fma2(a3, w.get2(3, p), acc);
+        if (r >= 4) acc = fma2(a4, w.get2(4, p), acc);
+        ys[2 * p] = f2_x(acc);
+        ys[2 * p + 1] = f2_y(acc);
+      }
+    } else {  // the 5th-order solution y5 = y + h inc, inc = sum_j b_j k_j compensated, then one FP64 FMA
+#pragma unroll 1
+      for (int p = 0; p < 5; p++) {  // rolled: the compensated sums would not fit the instruction cache x5
+        dacc2 acc = dot_first_f2(c_dp_a_ds[5][0], w.get2(0, p));
+        acc = dot_add_f2(acc, c_dp_a_ds[5][2], w.get2(2, p));
+        acc = dot_add_f2(acc, c_dp_a_ds[5][3], w.get2(3, p));
+        acc = dot_add_f2(acc, c_dp_a_ds[5][4], w.get2(4, p));
+        acc = dot_add_f2(acc, c_dp_a_ds[5][5], w.get2(5, p));
+        const ds2 inc = dot_val2(acc);
+        w.put2(6, p, inc.hi);
+        w.put2(7, p, inc.lo);
+      }
+#pragma unroll
+      for (int p = 0; p < 5; p++) {
+        // The FP32 right-hand side's input at y5 directly in FP32 (within an FP32 ulp of
+        // y5 rounded), so the FP64 accumulation below is off the path to k7.
+        const f2 ih = w.get2(6, p), il = w.get2(7, p);
+        const f2 yy = fma2(hf2, ih, yf[p]);
+        ys[2 * p] = f2_x(yy);
+        ys[2 * p + 1] = f2_y(yy);
+        y5[2 * p] = fma(h, f32_to_f64(f2_x(ih)) + f32_to_f64(f2_x(il)), y[2 * p]);
+        y5[2 * p + 1] = fma(h, f32_to_f64(f2_y(ih)) + f32_to_f64(f2_y(il)), y[2 * p + 1]);
+      }
+    }
+    rhs32(c, ys, kn);  // k_{r+2}; for r = 5, k7 = f(y5)
+    if (r < 5) {
+#pragma unroll
+      for (int p = 0; p < 5; p++) w.put2(r + 1, p, f2_of(kn[2 * p], kn[2 * p + 1]));
+    }
+  }
+  // Error estimate sum_j (b_j - bhat_j) k_j compensated (it cancels to ~tol of its terms), its
+  // scaled RMS norm in FP32 from the estimate's leading float; h enters once, in FP64.
+  const float rtf = f64_to_f32(ctl.rtol), atf = f64_to_f32(ctl.atol);
+#pragma unroll
+  for (int p = 0; p < 5; p++) {
+    k7[2 * p] = f32_to_f64(kn[2 * p]);
+    k7[2 * p + 1] = f32_to_f64(kn[2 * p + 1]);
+    w.put2(1, p, f2_of(kn[2 * p], kn[2 * p + 1]));
+    w.put2(6, p, f2_of(__fmaf_rn(rtf, fmaxf(fabsf(f2_x(yf[p])), fabsf(ys[2 * p])), atf),
+                       __fmaf_rn(rtf, fmaxf(fabsf(f2_y(yf[p])), fabsf(ys[2 * p + 1])), atf)));
+  }
+  float sf = 0.0f;
+#pragma unroll 1
+  for (int p = 0; p < 5; p++) {
+    dacc2 acc = dot_first_f2(c_dp_e_ds[0], w.get2(0, p));
+    acc = dot_add_f2(acc, c_dp_e_ds[1], w.get2(2, p));
+    acc = dot_add_f2(acc, c_dp_e_ds[2], w.get2(3, p));
+    acc = dot_add_f2(acc, c_dp_e_ds[3], w.get2(4, p));
+    acc = dot_add_f2(acc, c_dp_e_ds[4], w.get2(5, p));
+    acc = dot_add_f2(acc, c_dp_e_ds[5], w.get2(1, p));
+    const f2 e = add2(acc.s, acc.e);
+    const f2 sc = w.get2(6, p);
+    const float q0 = __fmul_rn(f2_x(e), __frcp_rn(f2_x(sc))), q1 = __fmul_rn(f2_y(e), __frcp_rn(f2_y(sc)));
+    sf = __fmaf_rn(q0, q0, sf);
+    sf = __fmaf_rn(q1, q1, sf);
+  }
+  return f32_to_f64(sf) * ((h * h) * 0.1);
+}
+
+
 // Per-thread workspace of dp5_attempt_ds in shared memory: vector v of ten
 // double-single components as five packed pairs of components (2p, 2p + 1),
 // pair p of thread t at base[(v * 5 + p) * nthreads + t] as 16 bytes
@@ -1021,30 +1073,6 @@ struct DsWork {
     }
   }
 };
-
-// Compensated sums of products c_j x_j (dot_first / dot_add / dot_val) for a
-// pair of components with the same coefficients.
-struct dacc2 {
-  f2 s, e;
-};
-__device__ __forceinline__ dacc2 dot_first2(dsc c, ds2 x) {
-  const f2 ch = f2_dup(c.hi), cl = f2_dup(c.lo);
-  const f2 p = mul2(ch, x.hi);
-  f2 e = fma2(ch, x.hi, neg2(p));
-  e = fma2(ch, x.lo, e);
-  e = fma2(cl, x.hi, e);
-  return dacc2{p, e};
-}
-__device__ __forceinline__ dacc2 dot_add2(dacc2 a, dsc c, ds2 x) {
-  const f2 ch = f2_dup(c.hi), cl = f2_dup(c.lo);
-  const f2 p = mul2(ch, x.hi);
-  f2 e = fma2(ch, x.hi, neg2(p));
-  e = fma2(ch, x.lo, e);
-  e = fma2(cl, x.hi, e);
-  const ds2 t = two_sum2(a.s, p);
-  return dacc2{t.hi, add2(a.e, add2(t.lo, e))};
-}
-__device__ __forceinline__ ds2 dot_val2(dacc2 a) { return two_sum2(a.s, a.e); }
 
 __device__ __forceinline__ double dp5_attempt_ds(const Coefs& cf, const Tabs& tb, const Ctl& ctl, const double* y,
                                                  const double* k1, double h, double* y5, double* k7,

@@ -430,7 +430,7 @@ __device__ __forceinline__ void integrate_body(const KArgs& a, const double* __r
                            DsWork{reinterpret_cast<ulonglong2*>(s_dsw), (int)blockDim.x, (int)threadIdx.x});
       else if constexpr (PREC == 1)
         s = dp5_attempt_f32(L.cf.c32, a.ctl, L.y, L.k1, L.h, y5, k7,
-                            F32Work{reinterpret_cast<float*>(s_dsw), (int)blockDim.x, (int)threadIdx.x});
+                            F32Work{reinterpret_cast<f2*>(s_dsw), (int)blockDim.x, (int)threadIdx.x});
       else
         s = dp5_attempt_ws(L.cf, tb, a.ctl, L.y, L.k1, L.h, y5, k7,
                            F64Work{reinterpret_cast<double*>(s_dsw), (int)blockDim.x, (int)threadIdx.x});
