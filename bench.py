@@ -48,7 +48,7 @@ FP64_DATASHEET_TFLOPS = 1.25  # nominal dense FP64 of one B300
 # DRAM traffic of the integration kernel per binary from an ncu capture
 # (dram__bytes_read.sum + dram__bytes_write.sum, profiles/); valid only while
 # the kernel sources hash (kernel_sha) to the recorded value.
-PROFILED = {"kernel_sha": "4e915854aaac3794", "dram_bytes_per_binary": (39.478272e6 + 1.366784e6) / 131072}
+PROFILED = {"kernel_sha": "a6b073c3c891f87b", "dram_bytes_per_binary": (39.471872e6 + 0.862208e6) / 131072}
 
 
 # Executed floating-point thread instructions per attempt of each integration kernel
@@ -56,7 +56,13 @@ PROFILED = {"kernel_sha": "4e915854aaac3794", "dram_bytes_per_binary": (39.47827
 # of the 131,072-binary case (profiles/k_integrate_pipes_C1_131072.md): sums of
 # smsp__sass_thread_inst_executed_op_{ffma,fadd,fmul,ffma2,fadd2,fmul2,dfma,dadd,dmul}_pred_on over
 # the launch divided by its attempts.  Valid only while the kernel sources hash to kernel_sha.
-EXECUTED = {"kernel_sha": None, "per_attempt": {}}
+EXECUTED = {"kernel_sha": "a6b073c3c891f87b", "per_attempt": {
+    0: {"ffma": 130.84, "fadd": 397.54, "fmul": 93.55, "ffma2": 0.0, "fadd2": 0.0, "fmul2": 0.0,
+        "dfma": 505.94, "dadd": 44.96, "dmul": 242.83},
+    1: {"ffma": 318.97, "fadd": 51.53, "fmul": 263.58, "ffma2": 190.0, "fadd2": 395.0, "fmul2": 55.0,
+        "dfma": 15.97, "dadd": 10.96, "dmul": 10.91},
+    2: {"ffma": 1252.84, "fadd": 3213.46, "fmul": 516.83, "ffma2": 495.0, "fadd2": 1405.0, "fmul2": 165.0,
+        "dfma": 45.94, "dadd": 60.96, "dmul": 18.83}}}
 
 
 def executed_flops(prec: int):
@@ -207,6 +213,11 @@ def peak_probe(index: int = 0):
     time.sleep(0.3)  # the sampler's first reading
     rc = lib.pn_peak_probe(C.byref(f64), C.byref(f32))
     ck = clocks.stop()
+    lib.pn_peak_probe_packed.argtypes = [C.POINTER(C.c_double)] * 4
+    f2, l32, l2, l64 = C.c_double(), C.c_double(), C.c_double(), C.c_double()
+    if lib.pn_peak_probe_packed(C.byref(f2), C.byref(l32), C.byref(l2), C.byref(l64)) == 0:
+        ck["packed_f32x2_fma_tflops"] = f2.value / 1e12
+        ck["fma_latency_cycles"] = {"f32": l32.value, "f32x2": l2.value, "f64": l64.value}
     if rc != 0:
         return None, None, ck
     return f64.value, f32.value, ck
