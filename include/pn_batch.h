@@ -252,6 +252,14 @@ int pn_batch_sample(pn_batch *b, uint64_t seed, const pn_dist *d, int64_t n, con
  * array; n outside [0, n_max]), PN_E_CUDA. */
 int pn_batch_masses(pn_batch *b, int64_t n, const double *q, double *m1, double *m2);
 
+/* Device time of the last pn_batch_integrate / _integrate_budget / _resume /
+ * _integrate_host call on b (ms, CUDA events on the batch's stream): *ms_call
+ * the whole call (set-up, integration kernel, output epilogue), *ms_kernel the
+ * integration kernel alone (either pointer may be NULL).  Waits for that call
+ * to finish.  A call with n = 0 launches nothing and leaves the times of the
+ * call before it.  Errors: PN_E_ARG (NULL b, or no integration yet), PN_E_CUDA. */
+int pn_batch_timing(pn_batch *b, double *ms_call, double *ms_kernel);
+
 /* Integrate binaries 0..n-1 of *in and write *out (asynchronous).
  * 0 <= n <= n_max (n = 0 does nothing).  Errors: PN_E_ARG (NULL pointers,
  * n out of range), PN_E_CUDA (launch failure).  Uses the schedule, block and

@@ -105,6 +105,7 @@ SIGNATURES = {
     "pn_batch_integrate_host": (C.c_int, [C.c_void_p, C.c_int64, C.POINTER(pn_inputs), C.POINTER(pn_outputs)]),
     "pn_batch_integrate_host_async": (C.c_int, [C.c_void_p, C.c_int64, C.POINTER(pn_inputs), C.POINTER(pn_outputs)]),
     "pn_batch_host_wait": (C.c_int, [C.c_void_p]),
+    "pn_batch_timing": (C.c_int, [C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_double)]),
     "pn_batch_integrate_budget": (C.c_int, [C.c_void_p, C.c_int64, C.POINTER(pn_inputs), C.POINTER(pn_outputs),
                                             C.c_int32]),
     "pn_batch_resume": (C.c_int, [C.c_void_p, C.c_int64, C.POINTER(pn_inputs), C.POINTER(pn_outputs), C.c_int32]),

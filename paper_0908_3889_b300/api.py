@@ -209,6 +209,13 @@ def pn_batch_integrate_host_async(h, n: int, host_inputs: dict, host_outputs: di
                                                 C.byref(outputs_struct(host_outputs, n))), h)
 
 
+def pn_batch_timing(h) -> tuple:
+    """(ms of the last integration call, ms of its integration kernel alone), CUDA events; waits for it."""
+    mc, mk = C.c_double(), C.c_double()
+    _check(_lib().pn_batch_timing(h, C.byref(mc), C.byref(mk)), h)
+    return mc.value, mk.value
+
+
 def pn_batch_host_wait(h) -> None:
     """Wait for every pn_batch_integrate_host_async call on the batch to have copied its outputs back."""
     _check(_lib().pn_batch_host_wait(h), h)
@@ -403,6 +410,9 @@ class Batch:
     def stats(self, inputs: dict, outputs: dict, n: int | None = None) -> dict:
         n = int(inputs["m1"].shape[0]) if n is None else n
         return pn_batch_stats(self.handle, n, inputs, outputs)
+
+    def timing(self) -> tuple:
+        return pn_batch_timing(self.handle)
 
     def stats_segments(self, inputs: dict, outputs: dict, offsets) -> list:
         return pn_batch_stats_segments(self.handle, offsets, inputs, outputs)

@@ -32,6 +32,7 @@ struct pn_batch {
   size_t segstat_cap = 0;       // bytes
   double* d_setup = nullptr;  // per-binary set-up table, setup_fields() x n_max doubles
   cudaEvent_t ev[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};  // integrate, autotune, adjoint
+  cudaEvent_t kev[2] = {nullptr, nullptr};  // around the integration kernel alone (in the graph too)
   bool timed_integrate = false, timed_adjoint = false;
   // graph of the last persistent launch
   cudaGraphExec_t gexec = nullptr;
@@ -204,6 +205,8 @@ extern "C" void pn_batch_destroy(pn_batch* b) {
   if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
   for (auto& e : b->ev)
     if (e) cudaEventDestroy(e);
+  for (auto& e : b->kev)
+    if (e) cudaEventDestroy(e);
   cudaFree(b->d_queue);
   cudaFree(b->d_tab);
   cudaFree(b->d_stat_part);
@@ -257,6 +260,7 @@ extern "C" int pn_batch_init(pn_batch** out, int64_t n_max, const pn_params* p, 
   if (e == cudaSuccess) e = cudaMalloc(&b->d_stat_part, (size_t)pn::kStatGrid * pn::kStatWords * sizeof(double));
   if (e == cudaSuccess) e = cudaMalloc(&b->d_stat_total, pn::kStatWords * sizeof(double));
   for (int k = 0; k < 6 && e == cudaSuccess; k++) e = cudaEventCreate(&b->ev[k]);
+  for (int k = 0; k < 2 && e == cudaSuccess; k++) e = cudaEventCreate(&b->kev[k]);
   if (e == cudaSuccess) {
     float tab[pn::kLogTabBytes / sizeof(float)];
     pn::fill_log_table(tab);
@@ -320,6 +324,17 @@ Shape choose_shape(pn_batch* b, int64_t n, int prec, int sched_override = -1, in
   return s;
 }
 
+// The integration kernel between the batch's kernel events, then the output epilogue.
+static int launch_timed_kernel(pn_batch* b, int prec, const Shape& sh, const KArgs& a, int64_t stride, cudaStream_t s) {
+  PN_CUDA(b, cudaEventRecord(b->kev[0], s));
+  cudaError_t e = pn::launch_integrate_only(prec, sh.persistent, sh.block, sh.grid, a, b->d_setup, stride, s);
+  if (e != cudaSuccess) return cuda_fail(b, e, "integrate kernel launch");
+  PN_CUDA(b, cudaEventRecord(b->kev[1], s));
+  e = pn::launch_dots(a.out, a.n, b->d_setup, stride, s);
+  if (e != cudaSuccess) return cuda_fail(b, e, "output epilogue launch");
+  return PN_OK;
+}
+
 // Launch one integration of n binaries with the given shape on b->stream.
 // The persistent shape goes through a CUDA graph (queue reset + kernel),
 // captured on a private stream and re-used while the arguments repeat.
@@ -370,16 +385,12 @@ int run_integrate(pn_batch* b, int64_t n, const pn_inputs* in, pn_outputs* out, 
       cudaError_t e = pn::launch_setup(prec, a, b->d_setup, stride, b->stream);
       if (e != cudaSuccess) return cuda_fail(b, e, "set-up kernel launch");
     }
-    cudaError_t e = pn::launch_integrate(prec, sh.persistent, sh.block, sh.grid, a, b->d_setup, stride, b->stream);
-    if (e != cudaSuccess) return cuda_fail(b, e, "integrate kernel launch");
-    return PN_OK;
+    return launch_timed_kernel(b, prec, sh, a, stride, b->stream);
   }
   if (!sh.persistent) {
     cudaError_t e = pn::launch_setup(prec, a, b->d_setup, stride, b->stream);
     if (e != cudaSuccess) return cuda_fail(b, e, "set-up kernel launch");
-    e = pn::launch_integrate(prec, false, sh.block, sh.grid, a, b->d_setup, stride, b->stream);
-    if (e != cudaSuccess) return cuda_fail(b, e, "integrate kernel launch");
-    return PN_OK;
+    return launch_timed_kernel(b, prec, sh, a, stride, b->stream);
   }
   const bool same = b->gexec && b->have_key && b->key_prec == prec && b->key_block == sh.block &&
                     b->key_grid == sh.grid && std::memcmp(&b->key_args, &a, sizeof(a)) == 0;
@@ -388,7 +399,10 @@ int run_integrate(pn_batch* b, int64_t n, const pn_inputs* in, pn_outputs* out, 
     PN_CUDA(b, cudaStreamBeginCapture(b->cap_stream, cudaStreamCaptureModeThreadLocal));
     cudaError_t e1 = cudaMemsetAsync(b->d_queue, 0, sizeof(unsigned long long), b->cap_stream);
     cudaError_t e2 = pn::launch_setup(prec, a, b->d_setup, stride, b->cap_stream);
-    if (e2 == cudaSuccess) e2 = pn::launch_integrate(prec, true, sh.block, sh.grid, a, b->d_setup, stride, b->cap_stream);
+    if (e2 == cudaSuccess) e2 = cudaEventRecord(b->kev[0], b->cap_stream);
+    if (e2 == cudaSuccess) e2 = pn::launch_integrate_only(prec, true, sh.block, sh.grid, a, b->d_setup, stride, b->cap_stream);
+    if (e2 == cudaSuccess) e2 = cudaEventRecord(b->kev[1], b->cap_stream);
+    if (e2 == cudaSuccess) e2 = pn::launch_dots(a.out, a.n, b->d_setup, stride, b->cap_stream);
     cudaError_t e3 = cudaStreamEndCapture(b->cap_stream, &g);
     if (e1 != cudaSuccess) { if (g) cudaGraphDestroy(g); return cuda_fail(b, e1, "graph capture (memset)"); }
     if (e2 != cudaSuccess) { if (g) cudaGraphDestroy(g); return cuda_fail(b, e2, "graph capture (kernel)"); }
@@ -432,6 +446,18 @@ extern "C" int pn_batch_integrate(pn_batch* b, int64_t n, const pn_inputs* in, p
   if (rc != PN_OK) return rc;
   PN_CUDA(b, cudaEventRecord(b->ev[1], b->stream));
   b->timed_integrate = true;
+  return PN_OK;
+}
+
+extern "C" int pn_batch_timing(pn_batch* b, double* ms_call, double* ms_kernel) {
+  if (!b) return fail(nullptr, PN_E_ARG, "batch is NULL");
+  if (!b->timed_integrate) return fail(b, PN_E_ARG, "no integration call on this batch yet");
+  PN_CUDA(b, cudaEventSynchronize(b->ev[1]));
+  float mc = 0.f, mk = 0.f;
+  PN_CUDA(b, cudaEventElapsedTime(&mc, b->ev[0], b->ev[1]));
+  PN_CUDA(b, cudaEventElapsedTime(&mk, b->kev[0], b->kev[1]));
+  if (ms_call) *ms_call = mc;
+  if (ms_kernel) *ms_kernel = mk;
   return PN_OK;
 }
 

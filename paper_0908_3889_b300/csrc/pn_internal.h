@@ -66,6 +66,8 @@ cudaError_t launch_setup(int prec, const KArgs& a, double* ws, int64_t stride, c
 // persistent: work-queue schedule.
 cudaError_t launch_integrate(int prec, bool persistent, int block, int grid, const KArgs& a, const double* ws,
                              int64_t stride, cudaStream_t s);
+// The output epilogue alone: deferred landing moves and the output scalar products (k_dots).
+cudaError_t launch_dots(const pn_outputs& o, int64_t n, const double* ws, int64_t stride, cudaStream_t s);
 // The integration kernel alone.
 cudaError_t launch_integrate_only(int prec, bool persistent, int block, int grid, const KArgs& a, const double* ws,
                                   int64_t stride, cudaStream_t s);

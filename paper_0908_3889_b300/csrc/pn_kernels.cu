@@ -513,7 +513,7 @@ static KArgs with_land(const KArgs& a, const double* ws, int64_t stride) {
   return b;
 }
 
-static cudaError_t launch_dots(const pn_outputs& o, int64_t n, const double* ws, int64_t stride, cudaStream_t s) {
+cudaError_t launch_dots(const pn_outputs& o, int64_t n, const double* ws, int64_t stride, cudaStream_t s) {
   if (n <= 0) return cudaSuccess;
   k_dots<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(o, n, land_fields(ws, stride), stride);
   return cudaGetLastError();

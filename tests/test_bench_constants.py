@@ -16,3 +16,32 @@ def test_flop_constants_match_oracle_count(orc):
 
 def test_kernel_sha_is_stable():
     assert bench.kernel_sha() == bench.kernel_sha() and len(bench.kernel_sha()) == 16
+
+
+def test_executed_counts_are_consistent(monkeypatch):
+    """The recorded ncu counts and traffic come from one capture of one kernel version (bench.py reports
+    them only while the sources hash to it), and the FP64 kernel executes close to the oracle's
+    algorithmic count (each FMA two flops): the kernel does the method's work, not more."""
+    assert bench.EXECUTED["kernel_sha"] == bench.PROFILED["kernel_sha"]
+    monkeypatch.setattr(bench, "kernel_sha", lambda: bench.EXECUTED["kernel_sha"])
+    f32_0, f64_0 = bench.executed_flops(0)
+    assert 0.9 * bench.FLOPS_ATTEMPT < f64_0 < 1.0 * bench.FLOPS_ATTEMPT
+    f32_2, f64_2 = bench.executed_flops(2)
+    assert f64_2 < 0.2 * f64_0 and f32_2 > 5 * bench.FLOPS_ATTEMPT  # double-single: the FP32 pipe does the work
+    assert 250 < bench.PROFILED["dram_bytes_per_binary"] < 400
+
+
+def test_paper_sweep_ensembles():
+    """Sec. V's sweeps: ten ensembles, the masses and spins each one names, omega 0.00395 -> 0.05."""
+    import workloads
+    sw = workloads.paper_sweeps(n=64)
+    assert [k for k, _, _ in sw] == ["chi"] * 5 + ["ring"] + ["m1"] * 4
+    for kind, val, e in sw:
+        assert np.all(e["omega0"] == 0.00395) and np.all(e["omega_f"] == 0.05)
+        assert np.allclose(e["m1"] + e["m2"], 1.0, rtol=0, atol=1e-15)
+        if kind == "chi":
+            assert np.all(e["chi1"] == val) and np.allclose(e["m1"], 0.5)
+        elif kind == "ring":
+            assert np.allclose(e["m1"], 0.4) and np.all(e["chi1"] == 0.05)
+        else:
+            assert np.allclose(e["m1"], val) and np.all(e["chi1"] == 1.0)

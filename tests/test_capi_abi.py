@@ -98,6 +98,8 @@ def test_argument_errors_before_any_cuda_call(native):
     assert lib.pn_batch_integrate_budget(None, 1, None, None, 1) == native.PN_E_ARG
     assert lib.pn_batch_resume(None, 1, None, None, 1) == native.PN_E_ARG
     assert lib.pn_batch_masses(None, 1, None, None, None) == native.PN_E_ARG
+    assert lib.pn_batch_timing(None, None, None) == native.PN_E_ARG
+    assert lib.pn_batch_stats_segments(None, 1, None, None, None, None) == native.PN_E_ARG
     lib.pn_batch_destroy(None)
 
 

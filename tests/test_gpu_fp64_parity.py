@@ -232,6 +232,29 @@ def test_repeat_calls_reuse_graph_and_agree(pn):
         assert np.array_equal(o1[k][..., :7000], o3[k][..., :7000], equal_nan=True)
 
 
+@pytest.mark.parametrize("schedule", [1, 2])
+def test_kernel_timing_events(pn, schedule):
+    """pn_batch_timing: the integration kernel's own time (events around it, inside the graph on the
+    persistent schedule) is positive, below the whole call's, and most of it on a large batch; the
+    times follow the last call (a bounded call included); no call yet is an argument error."""
+    import torch
+    ens = workloads.config("C1", n=200_000)
+    inp = pn.to_device(ens)
+    with pn.Batch(200_000, pn.params(schedule=schedule)) as b:
+        with pytest.raises(pn.PNError):
+            b.timing()
+        for _ in range(2):  # the second persistent call replays the captured graph
+            b.integrate(inp)
+            call, kern = b.timing()
+            assert 0.0 < kern < call and kern > 0.9 * call, (call, kern)
+        out = b.integrate_budget(inp, budget=5)
+        call5, kern5 = b.timing()
+        assert 0.0 < kern5 < call5 and kern5 < 0.5 * kern, (kern5, kern)
+        b.resume(inp, out)
+        torch.cuda.synchronize()
+        assert b.timing()[1] > 0.0
+
+
 def test_autotune_choice_gives_same_results(pn):
     import torch
     ens = workloads.config("C2", n=40000)
