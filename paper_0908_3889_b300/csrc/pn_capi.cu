@@ -399,9 +399,10 @@ int run_integrate(pn_batch* b, int64_t n, const pn_inputs* in, pn_outputs* out, 
     PN_CUDA(b, cudaStreamBeginCapture(b->cap_stream, cudaStreamCaptureModeThreadLocal));
     cudaError_t e1 = cudaMemsetAsync(b->d_queue, 0, sizeof(unsigned long long), b->cap_stream);
     cudaError_t e2 = pn::launch_setup(prec, a, b->d_setup, stride, b->cap_stream);
-    if (e2 == cudaSuccess) e2 = cudaEventRecord(b->kev[0], b->cap_stream);
+    // External event record nodes: the events are recorded (and timed) each time the graph runs.
+    if (e2 == cudaSuccess) e2 = cudaEventRecordWithFlags(b->kev[0], b->cap_stream, cudaEventRecordExternal);
     if (e2 == cudaSuccess) e2 = pn::launch_integrate_only(prec, true, sh.block, sh.grid, a, b->d_setup, stride, b->cap_stream);
-    if (e2 == cudaSuccess) e2 = cudaEventRecord(b->kev[1], b->cap_stream);
+    if (e2 == cudaSuccess) e2 = cudaEventRecordWithFlags(b->kev[1], b->cap_stream, cudaEventRecordExternal);
     if (e2 == cudaSuccess) e2 = pn::launch_dots(a.out, a.n, b->d_setup, stride, b->cap_stream);
     cudaError_t e3 = cudaStreamEndCapture(b->cap_stream, &g);
     if (e1 != cudaSuccess) { if (g) cudaGraphDestroy(g); return cuda_fail(b, e1, "graph capture (memset)"); }
