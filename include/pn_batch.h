@@ -283,7 +283,8 @@ int pn_batch_integrate(pn_batch *b, int64_t n, const pn_inputs *in, pn_outputs *
  * copying the state between calls).  Asynchronous; count the binaries still
  * running with pn_batch_stats (count_by_status[PN_ST_RUNNING]).
  * Errors: PN_E_ARG (NULL pointers, n out of range, budget < 1 for the first
- * call or < 0 for resume), PN_E_NOMEM, PN_E_CUDA. */
+ * call or < 0 for resume, a resume whose params.precision differs from the
+ * bounded run's), PN_E_NOMEM, PN_E_CUDA. */
 int pn_batch_integrate_budget(pn_batch *b, int64_t n, const pn_inputs *in, pn_outputs *out, int32_t budget);
 int pn_batch_resume(pn_batch *b, int64_t n, const pn_inputs *in, pn_outputs *out, int32_t budget);
 

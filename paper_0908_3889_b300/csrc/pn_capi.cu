@@ -64,6 +64,7 @@ struct pn_batch {
   // saved integrator states between bounded calls (pn_batch_integrate_budget / pn_batch_resume)
   double* d_rs = nullptr;
   int32_t* d_ri = nullptr;
+  int32_t bounded_prec = -1;  // precision of the bounded run the saved states belong to
   // staging for pn_batch_integrate_host(_async): two sets used in turn, with a
   // copy-in and a copy-out stream, so a call's copies overlap the integration of
   // the call before or after it
@@ -470,12 +471,16 @@ static int integrate_bounded(pn_batch* b, int64_t n, const pn_inputs* in, pn_out
   if (!outputs_ok(out)) return fail(b, PN_E_ARG, "NULL output pointer");
   if (resume ? budget < 0 : budget < 1) return fail(b, PN_E_ARG, resume ? "budget must be >= 0" : "budget must be >= 1");
   const int prec = b->p.precision;
+  // The saved states are kept in the form the run's precision carries them: a resume must use it.
+  if (resume && b->bounded_prec >= 0 && b->bounded_prec != prec)
+    return fail(b, PN_E_ARG, "resume: the precision differs from the bounded run's");
   const Shape sh = choose_shape(b, n, prec);
   PN_CUDA(b, cudaEventRecord(b->ev[0], b->stream));
   const int rc = run_integrate(b, n, in, out, prec, sh, budget, resume);
   if (rc != PN_OK) return rc;
   PN_CUDA(b, cudaEventRecord(b->ev[1], b->stream));
   b->timed_integrate = true;
+  if (!resume) b->bounded_prec = prec;
   return PN_OK;
 }
 

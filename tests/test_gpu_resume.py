@@ -97,3 +97,23 @@ def test_bounded_call_argument_errors(pn):
             b.resume(inp, out)
         with pytest.raises(pn.PNError, match="budget"):
             pn.pn_batch_resume(b.handle, 8, inp, out, -1)
+
+
+def test_resume_refuses_a_changed_precision(pn):
+    """The saved states are kept as the run's precision carries them, so a resume under another
+    precision is an argument error, and the run then still continues under its own."""
+    import torch
+    ens = workloads.config("C1", n=256, seed=7)
+    inp = pn.to_device(ens)
+    with pn.Batch(256, pn.params(precision=2)) as b:
+        ref = pn.to_numpy(b.integrate(inp))
+        out = b.integrate_budget(inp, budget=10)
+        b.set_params(pn.params(precision=0))
+        with pytest.raises(pn.PNError, match="precision"):
+            b.resume(inp, out)
+        b.set_params(pn.params(precision=2))
+        b.resume(inp, out)
+        torch.cuda.synchronize()
+        done = pn.to_numpy(out)
+    for k in ref:
+        assert np.array_equal(ref[k], done[k], equal_nan=True), k
