@@ -327,19 +327,79 @@ __device__ __forceinline__ ds dot3_ds(const ds* a, const ds* b) {
   return ds_dot3(a[0], b[0], a[1], b[1], a[2], b[2]);
 }
 
+// Packed pair forms (f32x2) of the double-single operations, operation for
+// operation as the scalar ones (the same bits): the two spins' terms of the
+// VJP below -- (L.S1, L.S2), (q1, q2), (U1, U2), the cross products and their
+// cotangents -- go through them, which shortens the sweep's straight-line body.
+__device__ __forceinline__ ds2 ds2_mul_f(ds2 a, f2 b) {
+  const f2 p = mul2(a.hi, b);
+  f2 e = fma2(a.hi, b, neg2(p));
+  e = fma2(a.lo, b, e);
+  return fast_two_sum2(p, e);
+}
+__device__ __forceinline__ ds2 ds2_fma(ds2 a, ds2 b, ds2 c) {
+  const f2 p = mul2(a.hi, b.hi);
+  f2 e = fma2(a.hi, b.hi, neg2(p));
+  e = fma2(a.hi, b.lo, e);
+  e = fma2(a.lo, b.hi, e);
+  const ds2 s = two_sum2(p, c.hi);
+  return fast_two_sum2(s.hi, add2(s.lo, add2(e, c.lo)));
+}
+__device__ __forceinline__ ds2 ds2_dot3(ds2 a0, ds2 b0, ds2 a1, ds2 b1, ds2 a2, ds2 b2) {
+  const f2 p0 = mul2(a0.hi, b0.hi), p1 = mul2(a1.hi, b1.hi), p2 = mul2(a2.hi, b2.hi);
+  f2 e = fma2(a0.hi, b0.hi, neg2(p0));
+  e = fma2(a0.hi, b0.lo, e);
+  e = fma2(a0.lo, b0.hi, e);
+  e = add2(e, fma2(a1.hi, b1.hi, neg2(p1)));
+  e = fma2(a1.hi, b1.lo, e);
+  e = fma2(a1.lo, b1.hi, e);
+  e = add2(e, fma2(a2.hi, b2.hi, neg2(p2)));
+  e = fma2(a2.hi, b2.lo, e);
+  e = fma2(a2.lo, b2.hi, e);
+  const ds2 s = two_sum2(p0, p1);
+  const ds2 t = two_sum2(s.hi, p2);
+  return fast_two_sum2(t.hi, add2(e, add2(s.lo, t.lo)));
+}
+__device__ __forceinline__ ds2 ds2_diff_prod(ds2 a, ds2 b, ds2 c, ds2 d) {
+  const f2 p = mul2(a.hi, b.hi), q = mul2(c.hi, d.hi);
+  f2 e = fma2(a.hi, b.hi, neg2(p));
+  e = fma2(a.hi, b.lo, e);
+  e = fma2(a.lo, b.hi, e);
+  f2 f = fma2(c.hi, d.hi, neg2(q));
+  f = fma2(c.hi, d.lo, f);
+  f = fma2(c.lo, d.hi, f);
+  const ds2 s = two_sum2(p, neg2(q));
+  return fast_two_sum2(s.hi, add2(s.lo, sub2(e, f)));
+}
+__device__ __forceinline__ ds2 ds2_swap(ds2 a) {
+  return ds2{(a.hi >> 32) | (a.hi << 32), (a.lo >> 32) | (a.lo << 32)};
+}
+__device__ __forceinline__ ds2 ds2_dup(ds a) { return ds2{f2_dup(a.hi), f2_dup(a.lo)}; }
+__device__ __forceinline__ ds2 ds2_zero() { return ds2{0ull, 0ull}; }
+// c = a x b for pairs of vectors (one per spin)
+__device__ __forceinline__ void cross2(const ds2* a, const ds2* b, ds2* c) {
+  c[0] = ds2_diff_prod(a[1], b[2], a[2], b[1]);
+  c[1] = ds2_diff_prod(a[2], b[0], a[0], b[2]);
+  c[2] = ds2_diff_prod(a[0], b[1], a[1], b[0]);
+}
+
 __device__ __noinline__ void rhs_ds_vjp(const Coef<ds>& c, const float* __restrict__ tabf, const ds* y, const ds* fb,
                                         ds* yb, Coef<ds>& cb, ds* f) {
   const dsc kThird = {(float)(1.0 / 3.0), (float)(1.0 / 3.0 - (double)(float)(1.0 / 3.0))};
-  // ---- forward (as rhs_ds) ----
+  // ---- forward (as rhs_ds) ----  S[k] = (S1_k, S2_k); pairs carry the two spins' terms
   const ds w = y[0];
-  const ds S1[3] = {y[1], y[2], y[3]}, S2[3] = {y[4], y[5], y[6]}, L[3] = {y[7], y[8], y[9]};
+  const ds L[3] = {y[7], y[8], y[9]};
+  const ds2 S[3] = {ds2_of(y[1], y[4]), ds2_of(y[2], y[5]), ds2_of(y[3], y[6])};
+  const ds2 Ld[3] = {ds2_dup(L[0]), ds2_dup(L[1]), ds2_dup(L[2])};
   ds r = ds_inv_cbrt(w);
   if ((__float_as_uint(w.hi) & 0x7fffffffu) - 0x00800000u >= 0x7f000000u) r = ds{__int_as_float(0x7fc00000), 0.0f};
   const ds r2 = ds_mul(r, r);
   const ds v = ds_mul(w, r2);
   const ds v2 = ds_mul(v, v);
   const ds lw = ds_log(w, tabf);
-  const ds LS1 = dot3_ds(L, S1), LS2 = dot3_ds(L, S2), S12 = dot3_ds(S1, S2);
+  const ds2 LS = ds2_dot3(Ld[0], S[0], Ld[1], S[1], Ld[2], S[2]);  // (L.S1, L.S2)
+  const ds LS1 = ds2_x(LS), LS2 = ds2_y(LS);
+  const ds S12 = ds_dot3(ds2_x(S[0]), ds2_y(S[0]), ds2_x(S[1]), ds2_y(S[1]), ds2_x(S[2]), ds2_y(S[2]));
   const ds so = dfma(c.w1, LS1, dfma(c.w2, LS2, ds_neg(c.tail)));
   const ds c2p = dfma(c.ss721, ds_mul(LS1, LS2), dfma(ds_neg(c.ss247), S12, c.c2));
   const ds c3p = dfma(c.clog, lw, c.c3l);
@@ -353,50 +413,50 @@ __device__ __noinline__ void rhs_ds_vjp(const Coef<ds>& c, const float* __restri
   const ds Q = ds_mul(ds_mul(w2, w), v2);
   // Eq. (4) as in rhs_ds: dS_i/dt = pre (U_i x S_i), U_1 = q1 L + S2, q1 = a1 r - 3 LS2 (1 <-> 2).
   const ds pre = ds_mul(c.prec, w2);
-  const ds q1 = dfma(c.a1, r, ds_mul_f(LS2, -3.0f)), q2 = dfma(c.a2, r, ds_mul_f(LS1, -3.0f));
-  ds U1[3], U2[3], X1[3], X2[3], d1[3], d2[3];
-  for (int k = 0; k < 3; k++) {
-    U1[k] = dfma(q1, L[k], S2[k]);
-    U2[k] = dfma(q2, L[k], S1[k]);
-  }
-  cross_ds(U1, S1, X1);
-  cross_ds(U2, S2, X2);
-  for (int k = 0; k < 3; k++) {
-    d1[k] = ds_mul(pre, X1[k]);
-    d2[k] = ds_mul(pre, X2[k]);
-  }
+  const ds2 pre2 = ds2_dup(pre);
+  const ds2 q = ds2_fma(ds2_of(c.a1, c.a2), ds2_dup(r), ds2_mul_f(ds2_swap(LS), f2_dup(-3.0f)));  // (q1, q2)
+  const ds q1 = ds2_x(q), q2 = ds2_y(q);
+  ds2 U[3], X[3], D[3];
+  for (int k = 0; k < 3; k++) U[k] = ds2_fma(q, Ld[k], ds2_swap(S[k]));  // (U1_k, U2_k)
+  cross2(U, S, X);                                                       // (X1, X2) = (U1 x S1, U2 x S2)
+  for (int k = 0; k < 3; k++) D[k] = ds2_mul(pre2, X[k]);                // (d1, d2)
   const ds lf = ds_mul(v, c.nie);
   f[0] = ds_mul(ds_mul(Q, c.K), P);
+  ds dsum[3];
   for (int k = 0; k < 3; k++) {
-    f[1 + k] = d1[k];
-    f[4 + k] = d2[k];
-    f[7 + k] = ds_mul(lf, ds_add(d1[k], d2[k]));
+    f[1 + k] = ds2_x(D[k]);
+    f[4 + k] = ds2_y(D[k]);
+    dsum[k] = ds_add(ds2_x(D[k]), ds2_y(D[k]));
+    f[7 + k] = ds_mul(lf, dsum[k]);
   }
   // ---- reverse ----
-  ds S1b[3] = {dzero(), dzero(), dzero()}, S2b[3] = {dzero(), dzero(), dzero()}, Lb[3] = {dzero(), dzero(), dzero()};
-  ds d1b[3], d2b[3], X1b[3], X2b[3];
-  ds U1b[3] = {dzero(), dzero(), dzero()}, U2b[3] = {dzero(), dzero(), dzero()};
+  ds2 Sb[3] = {ds2_zero(), ds2_zero(), ds2_zero()};  // (S1b_k, S2b_k)
+  ds Lb[3] = {dzero(), dzero(), dzero()};
+  ds2 Db[3], Xb[3];
+  ds2 Ub[3] = {ds2_zero(), ds2_zero(), ds2_zero()};
   ds lfb = dzero();
-  for (int k = 0; k < 3; k++) lfb = dfma(fb[7 + k], ds_add(d1[k], d2[k]), lfb);  // f_L = lf (d1 + d2)
-  for (int k = 0; k < 3; k++) {
-    d1b[k] = dfma(lf, fb[7 + k], fb[1 + k]);
-    d2b[k] = dfma(lf, fb[7 + k], fb[4 + k]);
-  }
+  for (int k = 0; k < 3; k++) lfb = dfma(fb[7 + k], dsum[k], lfb);  // f_L = lf (d1 + d2)
+  const ds2 lf2 = ds2_dup(lf);
+  for (int k = 0; k < 3; k++) Db[k] = ds2_fma(lf2, ds2_dup(fb[7 + k]), ds2_of(fb[1 + k], fb[4 + k]));
   ds vb = ds_mul(lfb, c.nie);  // lf = v nie
   cb.nie = dfma(lfb, v, cb.nie);
   ds preb = dzero();  // d_i = pre X_i
   for (int k = 0; k < 3; k++) {
-    preb = dfma(X1[k], d1b[k], dfma(X2[k], d2b[k], preb));
-    X1b[k] = ds_mul(pre, d1b[k]);
-    X2b[k] = ds_mul(pre, d2b[k]);
+    preb = dfma(ds2_x(X[k]), ds2_x(Db[k]), dfma(ds2_y(X[k]), ds2_y(Db[k]), preb));
+    Xb[k] = ds2_mul(pre2, Db[k]);
   }
-  cross_vjp_ds(U1, S1, X1b, U1b, S1b);  // X1 = U1 x S1
-  cross_vjp_ds(U2, S2, X2b, U2b, S2b);  // X2 = U2 x S2
-  const ds q1b = dot3_ds(U1b, L), q2b = dot3_ds(U2b, L);  // U1 = q1 L + S2, U2 = q2 L + S1
+  {  // X_i = U_i x S_i:  Ub_i += S_i x Xb_i,  Sb_i += Xb_i x U_i
+    ds2 t[3];
+    cross2(S, Xb, t);
+    for (int k = 0; k < 3; k++) Ub[k] = ds2_add(Ub[k], t[k]);
+    cross2(Xb, U, t);
+    for (int k = 0; k < 3; k++) Sb[k] = ds2_add(Sb[k], t[k]);
+  }
+  const ds2 qb = ds2_dot3(Ub[0], Ld[0], Ub[1], Ld[1], Ub[2], Ld[2]);  // U1 = q1 L + S2, U2 = q2 L + S1
+  const ds q1b = ds2_x(qb), q2b = ds2_y(qb);
   for (int k = 0; k < 3; k++) {
-    Lb[k] = dfma(q1, U1b[k], dfma(q2, U2b[k], Lb[k]));
-    S2b[k] = ds_add(S2b[k], U1b[k]);
-    S1b[k] = ds_add(S1b[k], U2b[k]);
+    Lb[k] = dfma(q1, ds2_x(Ub[k]), dfma(q2, ds2_y(Ub[k]), Lb[k]));
+    Sb[k] = ds2_add(Sb[k], ds2_swap(Ub[k]));
   }
   cb.a1 = dfma(q1b, r, cb.a1);  // q1 = a1 r - 3 LS2, q2 = a2 r - 3 LS1
   cb.a2 = dfma(q2b, r, cb.a2);
@@ -443,10 +503,10 @@ __device__ __noinline__ void rhs_ds_vjp(const Coef<ds>& c, const float* __restri
   cb.w2 = dfma(sob, LS2, cb.w2);
   LS2b = dfma(sob, c.w2, LS2b);
   cb.tail = ds_sub(cb.tail, sob);
+  const ds2 LSb = ds2_of(LS1b, LS2b), S12b2 = ds2_dup(S12b);
   for (int k = 0; k < 3; k++) {  // LS1 = L.S1, LS2 = L.S2, S12 = S1.S2
-    Lb[k] = dfma(LS1b, S1[k], dfma(LS2b, S2[k], Lb[k]));
-    S1b[k] = dfma(LS1b, L[k], dfma(S12b, S2[k], S1b[k]));
-    S2b[k] = dfma(LS2b, L[k], dfma(S12b, S1[k], S2b[k]));
+    Lb[k] = dfma(LS1b, ds2_x(S[k]), dfma(LS2b, ds2_y(S[k]), Lb[k]));
+    Sb[k] = ds2_fma(LSb, Ld[k], ds2_fma(S12b2, ds2_swap(S[k]), Sb[k]));
   }
   const ds r3 = ds_mul(r2, r);  // = 1/w
   wb = dfma(lwb, r3, wb);       // lw = ln|w|
@@ -456,53 +516,67 @@ __device__ __noinline__ void rhs_ds_vjp(const Coef<ds>& c, const float* __restri
   wb = ds_sub(wb, ds_mul(ds_mul(ds_mul(rb, dconst(kThird)), r), r3));  // dr/dw = -r/(3w)
   yb[0] = wb;
   for (int k = 0; k < 3; k++) {
-    yb[1 + k] = S1b[k];
-    yb[4 + k] = S2b[k];
+    yb[1 + k] = ds2_x(Sb[k]);
+    yb[4 + k] = ds2_y(Sb[k]);
     yb[7 + k] = Lb[k];
   }
 }
 
 // One recomputed step in double-single: stage states Y_0..Y_5 (pairs) to
 // sp[(10 s + k) * ss], and when y5 != nullptr the step's result, accumulated in
-// FP64 from the double-single increment.
+// FP64 from the double-single increment.  The stage sums run on packed pairs of
+// components (2p, 2p + 1), operation for operation as the scalar sums.
 __device__ __forceinline__ void dp5_stages_ds(const Coef<ds>& c, const float* __restrict__ tabf, const double* y,
                                               double h, float2* sp, size_t ss, double* y5) {
-  ds K[6][10], yd[10];
+  ds2 K[6][5];
+  ds yd[10], kn[10];
   const ds hd = split64(h);
+  const ds2 hd2 = ds2_dup(hd);
   for (int i = 0; i < 10; i++) {
     yd[i] = split64(y[i]);
     sp[(size_t)i * ss] = make_float2(yd[i].hi, yd[i].lo);
   }
-  rhs_ds(c, tabf, yd, K[0]);
+  rhs_ds(c, tabf, yd, kn);
+  for (int p = 0; p < 5; p++) K[0][p] = ds2_of(kn[2 * p], kn[2 * p + 1]);
 #pragma unroll 1
   for (int s = 1; s < 6; s++) {
     ds ys[10];
-    for (int i = 0; i < 10; i++) {
-      dacc acc = dot_first(c_dp_a_ds[s - 1][0], K[0][i]);
-      for (int j = 1; j < s; j++) acc = dot_add(acc, c_dp_a_ds[s - 1][j], K[j][i]);
-      ys[i] = ds_add(yd[i], ds_mul(hd, dot_val(acc)));
-      sp[(size_t)(10 * s + i) * ss] = make_float2(ys[i].hi, ys[i].lo);
+    for (int p = 0; p < 5; p++) {
+      dacc2 acc = dot_first2(c_dp_a_ds[s - 1][0], K[0][p]);
+      for (int j = 1; j < s; j++) acc = dot_add2(acc, c_dp_a_ds[s - 1][j], K[j][p]);
+      const ds2 yy = ds2_add(ds2_of(yd[2 * p], yd[2 * p + 1]), ds2_mul(hd2, dot_val2(acc)));
+      ys[2 * p] = ds2_x(yy);
+      ys[2 * p + 1] = ds2_y(yy);
+      sp[(size_t)(10 * s + 2 * p) * ss] = make_float2(ys[2 * p].hi, ys[2 * p].lo);
+      sp[(size_t)(10 * s + 2 * p + 1) * ss] = make_float2(ys[2 * p + 1].hi, ys[2 * p + 1].lo);
     }
-    if (s < 5 || y5) rhs_ds(c, tabf, ys, K[s]);
+    if (s < 5 || y5) {
+      rhs_ds(c, tabf, ys, kn);
+      for (int p = 0; p < 5; p++) K[s][p] = ds2_of(kn[2 * p], kn[2 * p + 1]);
+    }
   }
   if (!y5) return;
-  for (int i = 0; i < 10; i++) {
-    dacc acc = dot_first(c_dp_a_ds[5][0], K[0][i]);
-    for (int j = 2; j < 6; j++) acc = dot_add(acc, c_dp_a_ds[5][j], K[j][i]);
-    const ds inc = ds_mul(hd, dot_val(acc));
-    y5[i] = y[i] + (f32_to_f64(inc.hi) + f32_to_f64(inc.lo));
+  for (int p = 0; p < 5; p++) {
+    dacc2 acc = dot_first2(c_dp_a_ds[5][0], K[0][p]);
+    for (int j = 2; j < 6; j++) acc = dot_add2(acc, c_dp_a_ds[5][j], K[j][p]);
+    const ds2 inc = ds2_mul(hd2, dot_val2(acc));
+    const ds i0 = ds2_x(inc), i1 = ds2_y(inc);
+    y5[2 * p] = y[2 * p] + (f32_to_f64(i0.hi) + f32_to_f64(i0.lo));
+    y5[2 * p + 1] = y[2 * p + 1] + (f32_to_f64(i1.hi) + f32_to_f64(i1.lo));
   }
 }
 
 // Reverse mode of one step from its stored double-single stage states (the same
 // recurrences as dp5_step_vjp): lam in/out, cb accumulated, returns h's cotangent.
+// The component sums run on packed pairs of components; hb keeps its scalar order.
 __device__ double dp5_step_vjp_ds(const Coef<ds>& c, const float* __restrict__ tabf, const float2* sp, size_t ss,
                                   double h, ds* lam, Coef<ds>& cb) {
-  ds kp[6][10], yb[10];
+  ds2 kp[6][5], yb[5];
   const ds hd = split64(h);
+  const ds2 hd2 = ds2_dup(hd);
   for (int j = 0; j < 6; j++)
-    for (int i = 0; i < 10; i++) kp[j][i] = ds_mul(dconst(c_dp_a_ds[5][j]), lam[i]);
-  for (int i = 0; i < 10; i++) yb[i] = lam[i];
+    for (int p = 0; p < 5; p++) kp[j][p] = ds2_mul(ds2_dup(dconst(c_dp_a_ds[5][j])), ds2_of(lam[2 * p], lam[2 * p + 1]));
+  for (int p = 0; p < 5; p++) yb[p] = ds2_of(lam[2 * p], lam[2 * p + 1]);
   ds hb = dzero();
 #pragma unroll 1
   for (int s = 5; s >= 0; s--) {
@@ -510,20 +584,32 @@ __device__ double dp5_step_vjp_ds(const Coef<ds>& c, const float* __restrict__ t
     for (int i = 0; i < 10; i++) {
       const float2 t = sp[(size_t)(10 * s + i) * ss];
       Ys[i] = ds{t.x, t.y};
-      fb[i] = ds_mul(hd, kp[s][i]);
+    }
+    for (int p = 0; p < 5; p++) {
+      const ds2 f = ds2_mul(hd2, kp[s][p]);
+      fb[2 * p] = ds2_x(f);
+      fb[2 * p + 1] = ds2_y(f);
     }
     rhs_ds_vjp(c, tabf, Ys, fb, Yb, cb, ks);
-    for (int i = 0; i < 10; i++) {
-      hb = dfma(ks[i], kp[s][i], hb);
-      yb[i] = ds_add(yb[i], Yb[i]);
+    ds2 Yb2[5];
+    for (int p = 0; p < 5; p++) {
+      hb = dfma(ks[2 * p], ds2_x(kp[s][p]), hb);
+      hb = dfma(ks[2 * p + 1], ds2_y(kp[s][p]), hb);
+      Yb2[p] = ds2_of(Yb[2 * p], Yb[2 * p + 1]);
+      yb[p] = ds2_add(yb[p], Yb2[p]);
     }
     for (int j = 0; j < s; j++) {
       const ds a = dconst(c_dp_a_ds[s - 1][j]);
-      if (a.hi != 0.0f)
-        for (int i = 0; i < 10; i++) kp[j][i] = dfma(a, Yb[i], kp[j][i]);
+      if (a.hi != 0.0f) {
+        const ds2 a2 = ds2_dup(a);
+        for (int p = 0; p < 5; p++) kp[j][p] = ds2_fma(a2, Yb2[p], kp[j][p]);
+      }
     }
   }
-  for (int i = 0; i < 10; i++) lam[i] = yb[i];
+  for (int p = 0; p < 5; p++) {
+    lam[2 * p] = ds2_x(yb[p]);
+    lam[2 * p + 1] = ds2_y(yb[p]);
+  }
   return ds_to_f64(hb);
 }
 
