@@ -256,8 +256,9 @@ int pn_batch_masses(pn_batch *b, int64_t n, const double *q, double *m1, double 
  * _integrate_host call on b (ms, CUDA events on the batch's stream): *ms_call
  * the whole call (set-up, integration kernel, output epilogue), *ms_kernel the
  * integration kernel alone (either pointer may be NULL).  Waits for that call
- * to finish.  A call with n = 0 launches nothing and leaves the times of the
- * call before it.  Errors: PN_E_ARG (NULL b, or no integration yet), PN_E_CUDA. */
+ * to finish.  A call with n = 0 launches no kernel: *ms_kernel is then the
+ * kernel time of the last call that did, or NaN if none has.  Errors: PN_E_ARG
+ * (NULL b, or no integration call yet), PN_E_CUDA. */
 int pn_batch_timing(pn_batch *b, double *ms_call, double *ms_kernel);
 
 /* Integrate binaries 0..n-1 of *in and write *out (asynchronous).

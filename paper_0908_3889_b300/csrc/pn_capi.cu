@@ -34,6 +34,7 @@ struct pn_batch {
   cudaEvent_t ev[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};  // integrate, autotune, adjoint
   cudaEvent_t kev[2] = {nullptr, nullptr};  // around the integration kernel alone (in the graph too)
   bool timed_integrate = false, timed_adjoint = false;
+  bool kernel_timed = false;  // kev hold a kernel of the last integration call that launched one
   // graph of the last persistent launch
   cudaGraphExec_t gexec = nullptr;
   bool have_key = false;
@@ -327,6 +328,7 @@ Shape choose_shape(pn_batch* b, int64_t n, int prec, int sched_override = -1, in
 
 // The integration kernel between the batch's kernel events, then the output epilogue.
 static int launch_timed_kernel(pn_batch* b, int prec, const Shape& sh, const KArgs& a, int64_t stride, cudaStream_t s) {
+  b->kernel_timed = true;
   PN_CUDA(b, cudaEventRecord(b->kev[0], s));
   cudaError_t e = pn::launch_integrate_only(prec, sh.persistent, sh.block, sh.grid, a, b->d_setup, stride, s);
   if (e != cudaSuccess) return cuda_fail(b, e, "integrate kernel launch");
@@ -431,6 +433,7 @@ int run_integrate(pn_batch* b, int64_t n, const pn_inputs* in, pn_outputs* out, 
     b->key_grid = sh.grid;
   }
   PN_CUDA(b, cudaGraphLaunch(b->gexec, b->stream));
+  b->kernel_timed = true;
   return PN_OK;
 }
 
@@ -457,9 +460,9 @@ extern "C" int pn_batch_timing(pn_batch* b, double* ms_call, double* ms_kernel) 
   PN_CUDA(b, cudaEventSynchronize(b->ev[1]));
   float mc = 0.f, mk = 0.f;
   PN_CUDA(b, cudaEventElapsedTime(&mc, b->ev[0], b->ev[1]));
-  PN_CUDA(b, cudaEventElapsedTime(&mk, b->kev[0], b->kev[1]));
+  if (b->kernel_timed) PN_CUDA(b, cudaEventElapsedTime(&mk, b->kev[0], b->kev[1]));
   if (ms_call) *ms_call = mc;
-  if (ms_kernel) *ms_kernel = mk;
+  if (ms_kernel) *ms_kernel = b->kernel_timed ? (double)mk : NAN;
   return PN_OK;
 }
 

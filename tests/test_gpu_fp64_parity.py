@@ -243,6 +243,9 @@ def test_kernel_timing_events(pn, schedule):
     with pn.Batch(200_000, pn.params(schedule=schedule)) as b:
         with pytest.raises(pn.PNError):
             b.timing()
+        out0 = pn.alloc_outputs(8)
+        pn.pn_batch_integrate(b.handle, 0, inp, out0)  # n = 0: no kernel, so no kernel time yet
+        assert np.isnan(b.timing()[1])
         for _ in range(2):  # the second persistent call replays the captured graph
             b.integrate(inp)
             call, kern = b.timing()
