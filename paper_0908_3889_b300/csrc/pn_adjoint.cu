@@ -310,23 +310,6 @@ __device__ __forceinline__ ds dfma(ds a, ds b, ds c) { return ds_fma(a, b, c); }
 __device__ __forceinline__ ds dzero() { return ds{0.0f, 0.0f}; }
 __device__ __forceinline__ ds dconst(dsc k) { return ds{k.hi, k.lo}; }
 
-__device__ __forceinline__ void cross_ds(const ds* a, const ds* b, ds* c) {
-  c[0] = ds_diff_prod(a[1], b[2], a[2], b[1]);
-  c[1] = ds_diff_prod(a[2], b[0], a[0], b[2]);
-  c[2] = ds_diff_prod(a[0], b[1], a[1], b[0]);
-}
-// c = a x b:  ab += b x cb,  bb += cb x a
-__device__ __forceinline__ void cross_vjp_ds(const ds* a, const ds* b, const ds* cb_, ds* ab, ds* bb) {
-  ds t[3];
-  cross_ds(b, cb_, t);
-  for (int k = 0; k < 3; k++) ab[k] = ds_add(ab[k], t[k]);
-  cross_ds(cb_, a, t);
-  for (int k = 0; k < 3; k++) bb[k] = ds_add(bb[k], t[k]);
-}
-__device__ __forceinline__ ds dot3_ds(const ds* a, const ds* b) {
-  return ds_dot3(a[0], b[0], a[1], b[1], a[2], b[2]);
-}
-
 // Packed pair forms (f32x2) of the double-single operations, operation for
 // operation as the scalar ones (the same bits): the two spins' terms of the
 // VJP below -- (L.S1, L.S2), (q1, q2), (U1, U2), the cross products and their

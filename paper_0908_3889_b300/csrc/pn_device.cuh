@@ -425,6 +425,31 @@ __device__ __forceinline__ ds ds_diff_prod(ds a, ds b, ds c, ds d) {
 // Exact scaling by a power of two given as a float.
 __device__ __forceinline__ ds ds_scale(ds a, float p2) { return ds{a.hi * p2, a.lo * p2}; }
 
+// Lazy forms of the products: the same arithmetic as ds_mul / ds_mul_f without
+// the final renormalization of the result (fast_two_sum), so lo may reach a few
+// ulp of hi instead of half an ulp.  The pair still carries the product to
+// ~2^-46 and every later operation takes both parts; a product cannot cancel, so
+// lo stays within a few ulp of hi.  Three dependent FP32 operations per product
+// leave the critical path of the double-single right-hand side.  The sum-type
+// operations (ds_add, ds_fma, ds_dot3, ds_diff_prod) keep their
+// renormalization: after a cancellation an unnormalized result would carry a
+// low part as large as its high part into the next product, which drops lo*lo
+// (lazy sums were measured to raise the right-hand side's error ~6x, and lazy
+// plain additions to change step decisions).
+__device__ __forceinline__ ds ds_mul_l(ds a, ds b) {
+  const float p = __fmul_rn(a.hi, b.hi);
+  float e = __fmaf_rn(a.hi, b.hi, -p);
+  e = __fmaf_rn(a.hi, b.lo, e);
+  e = __fmaf_rn(a.lo, b.hi, e);
+  return ds{p, e};
+}
+__device__ __forceinline__ ds ds_mul_f_l(ds a, float b) {
+  const float p = __fmul_rn(a.hi, b);
+  float e = __fmaf_rn(a.hi, b, -p);
+  e = __fmaf_rn(a.lo, b, e);
+  return ds{p, e};
+}
+
 // double -> double-single: hi is d rounded to FP32 (f64_to_f32); the residual
 // d - hi is the low 29 significand bits of d (minus 2^29 when hi was rounded
 // up), an integer R with |R| <= 2^28, so lo = R * 2^(E - 1075) rounded to FP32.
@@ -495,8 +520,8 @@ __device__ __forceinline__ double log_w(double x, const float* __restrict__ tabf
 // r0 (1 + e/3 + 2e^2/9) with e = 1 - x r0^3 formed in double-single.
 __device__ __forceinline__ ds ds_inv_cbrt(ds x) {
   const float r0 = rcbrtf(x.hi);
-  const ds r3 = ds_mul_f(two_prod(r0, r0), r0);
-  const ds e = ds_sub(ds_of(1.0f), ds_mul(x, r3));
+  const ds r3 = ds_mul_f_l(two_prod(r0, r0), r0);
+  const ds e = ds_sub(ds_of(1.0f), ds_mul_l(x, r3));
   const float t = __fmul_rn(e.hi, __fmaf_rn(e.hi, 2.0f / 9.0f, 1.0f / 3.0f));
   return two_sum(r0, __fmul_rn(r0, t));
 }
@@ -522,8 +547,8 @@ __device__ __forceinline__ ds ds_log(ds x, const float* __restrict__ tabf) {
   const float F = __uint_as_float(0x3f800000u | ((2u * j + 1u) << 15));
   const float l_scaled = __fmul_rn(l, __uint_as_float((uint32_t)(127 - k) << 23));
   const ds f = two_sum(__fsub_rn(m, F), l_scaled);
-  const ds u = ds_mul(f, ds{tabf[4 * j], tabf[4 * j + 1]});
-  const ds u2h = ds_scale(ds_mul(u, u), -0.5f);
+  const ds u = ds_mul_l(f, ds{tabf[4 * j], tabf[4 * j + 1]});
+  const ds u2h = ds_scale(ds_mul_l(u, u), -0.5f);
   const float uh = u.hi;
   float q = __fmaf_rn(uh, -1.0f / 6.0f, 0.2f);
   q = __fmaf_rn(q, uh, -0.25f);
@@ -537,7 +562,8 @@ __device__ __forceinline__ ds ds_log(ds x, const float* __restrict__ tabf) {
 }
 
 // The right-hand side of Eqs. (1)-(4) in double-single arithmetic, the same
-// formulation as rhs64.  |omega| outside the FP32 normal range gives NaN.
+// formulation as rhs64, with the lazy products (ds_mul_l).  |omega| outside
+// the FP32 normal range gives NaN.
 __device__ __forceinline__ void rhs_ds(const Coef<ds>& c, const float* __restrict__ tabf, const ds* y, ds* f) {
   const ds w = y[0];
   const ds S1x = y[1], S1y = y[2], S1z = y[3];
@@ -545,14 +571,14 @@ __device__ __forceinline__ void rhs_ds(const Coef<ds>& c, const float* __restric
   const ds Lx = y[7], Ly = y[8], Lz = y[9];
   ds r = ds_inv_cbrt(w);
   if ((__float_as_uint(w.hi) & 0x7fffffffu) - 0x00800000u >= 0x7f000000u) r = ds{__int_as_float(0x7fc00000), 0.0f};
-  const ds v = ds_mul(w, ds_mul(r, r));
-  const ds v2 = ds_mul(v, v);
+  const ds v = ds_mul_l(w, ds_mul_l(r, r));
+  const ds v2 = ds_mul_l(v, v);
   const ds lw = ds_log(w, tabf);
   const ds LS1 = ds_dot3(Lx, S1x, Ly, S1y, Lz, S1z);
   const ds LS2 = ds_dot3(Lx, S2x, Ly, S2y, Lz, S2z);
   const ds S12 = ds_dot3(S1x, S2x, S1y, S2y, S1z, S2z);
   const ds so = ds_fma(c.w1, LS1, ds_fma(c.w2, LS2, ds_neg(c.tail)));
-  const ds c2p = ds_fma(c.ss721, ds_mul(LS1, LS2), ds_fma(ds_neg(c.ss247), S12, c.c2));
+  const ds c2p = ds_fma(c.ss721, ds_mul_l(LS1, LS2), ds_fma(ds_neg(c.ss247), S12, c.c2));
   const ds c3p = ds_fma(c.clog, lw, c.c3l);
   ds P = ds_fma(v, c.c35, c3p);
   P = ds_fma(v, P, c.c25);
@@ -560,26 +586,26 @@ __device__ __forceinline__ void rhs_ds(const Coef<ds>& c, const float* __restric
   P = ds_fma(v, P, ds_neg(so));
   P = ds_fma(v, P, c.c1);
   P = ds_fma(v2, P, ds_of(1.0f));
-  const ds w2 = ds_mul(w, w);
-  f[0] = ds_mul(ds_mul(ds_mul(ds_mul(w2, w), v2), c.K), P);
+  const ds w2 = ds_mul_l(w, w);
+  f[0] = ds_mul_l(ds_mul_l(ds_mul_l(ds_mul_l(w2, w), v2), c.K), P);
   // Eq. (4) as in rhs64: dS_i/dt = pre (U_i x S_i), U_1 = q1 L + S2, q1 = a1/v - 3 L.S2.
-  const ds q1 = ds_fma(c.a1, r, ds_mul_f(LS2, -3.0f));
-  const ds q2 = ds_fma(c.a2, r, ds_mul_f(LS1, -3.0f));
+  const ds q1 = ds_fma(c.a1, r, ds_mul_f_l(LS2, -3.0f));
+  const ds q2 = ds_fma(c.a2, r, ds_mul_f_l(LS1, -3.0f));
   const ds U1x = ds_fma(q1, Lx, S2x), U1y = ds_fma(q1, Ly, S2y), U1z = ds_fma(q1, Lz, S2z);
   const ds U2x = ds_fma(q2, Lx, S1x), U2y = ds_fma(q2, Ly, S1y), U2z = ds_fma(q2, Lz, S1z);
-  const ds pre = ds_mul(c.prec, w2);
-  const ds d1x = ds_mul(pre, ds_diff_prod(U1y, S1z, U1z, S1y));
-  const ds d1y = ds_mul(pre, ds_diff_prod(U1z, S1x, U1x, S1z));
-  const ds d1z = ds_mul(pre, ds_diff_prod(U1x, S1y, U1y, S1x));
-  const ds d2x = ds_mul(pre, ds_diff_prod(U2y, S2z, U2z, S2y));
-  const ds d2y = ds_mul(pre, ds_diff_prod(U2z, S2x, U2x, S2z));
-  const ds d2z = ds_mul(pre, ds_diff_prod(U2x, S2y, U2y, S2x));
+  const ds pre = ds_mul_l(c.prec, w2);
+  const ds d1x = ds_mul_l(pre, ds_diff_prod(U1y, S1z, U1z, S1y));
+  const ds d1y = ds_mul_l(pre, ds_diff_prod(U1z, S1x, U1x, S1z));
+  const ds d1z = ds_mul_l(pre, ds_diff_prod(U1x, S1y, U1y, S1x));
+  const ds d2x = ds_mul_l(pre, ds_diff_prod(U2y, S2z, U2z, S2y));
+  const ds d2y = ds_mul_l(pre, ds_diff_prod(U2z, S2x, U2x, S2z));
+  const ds d2z = ds_mul_l(pre, ds_diff_prod(U2x, S2y, U2y, S2x));
   f[1] = d1x; f[2] = d1y; f[3] = d1z;
   f[4] = d2x; f[5] = d2y; f[6] = d2z;
-  const ds lf = ds_mul(v, c.nie);
-  f[7] = ds_mul(lf, ds_add(d1x, d2x));
-  f[8] = ds_mul(lf, ds_add(d1y, d2y));
-  f[9] = ds_mul(lf, ds_add(d1z, d2z));
+  const ds lf = ds_mul_l(v, c.nie);
+  f[7] = ds_mul_l(lf, ds_add(d1x, d2x));
+  f[8] = ds_mul_l(lf, ds_add(d1y, d2y));
+  f[9] = ds_mul_l(lf, ds_add(d1z, d2z));
 }
 
 __device__ __forceinline__ Coef<ds> to_ds(const Coef<double>& c) {
@@ -939,6 +965,11 @@ __device__ __forceinline__ dacc2 dot_add2(dacc2 a, dsc c, ds2 x) {
   return dacc2{t.hi, add2(a.e, add2(t.lo, e))};
 }
 __device__ __forceinline__ ds2 dot_val2(dacc2 a) { return two_sum2(a.s, a.e); }
+// The sum unnormalized, for the product by h that follows in the double-single
+// attempt: there h times the sum is added to y (or is the error estimate), so
+// only its absolute error matters, and the lo*lo term the lazy product drops is
+// ~2^-24 |lo| of a sum that is itself small beside y.
+__device__ __forceinline__ ds2 dot_val2_l(dacc2 a) { return ds2{a.s, a.e}; }
 
 // dot_first_f / dot_add_f for a pair of components with the same coefficients.
 __device__ __forceinline__ dacc2 dot_first_f2(dsc c, f2 x) {
@@ -1042,6 +1073,15 @@ __device__ __forceinline__ double dp5_attempt_f32(const Coef<float>& c, const Ct
 }
 
 
+// Lazy forms (see ds_mul_l) for the double-single attempt's stage and error sums.
+__device__ __forceinline__ ds2 ds2_mul_l(ds2 a, ds2 b) {
+  const f2 p = mul2(a.hi, b.hi);
+  f2 e = fma2(a.hi, b.hi, neg2(p));
+  e = fma2(a.hi, b.lo, e);
+  e = fma2(a.lo, b.hi, e);
+  return ds2{p, e};
+}
+
 // Per-thread workspace of dp5_attempt_ds in shared memory: vector v of ten
 // double-single components as five packed pairs of components (2p, 2p + 1),
 // pair p of thread t at base[(v * 5 + p) * nthreads + t] as 16 bytes
@@ -1097,7 +1137,7 @@ __device__ __forceinline__ double dp5_attempt_ds(const Coefs& cf, const Tabs& tb
       if (r >= 3) acc = dot_add2(acc, a3, w.get2(3, p));
       if (r >= 4) acc = dot_add2(acc, a4, w.get2(4, p));
       if (r >= 5) acc = dot_add2(acc, a5, w.get2(5, p));
-      const ds2 inc = ds2_mul(hd2, dot_val2(acc));  // h sum_j a_sj k_j
+      const ds2 inc = ds2_mul_l(hd2, dot_val2_l(acc));  // h sum_j a_sj k_j
       w.put2(7, p, ds2_add(w.get2(6, p), inc));
       if (r == 5) w.put2(6, p, inc);
     }
@@ -1114,7 +1154,7 @@ __device__ __forceinline__ double dp5_attempt_ds(const Coefs& cf, const Tabs& tb
     acc = dot_add2(acc, c_dp_e_ds[3], w.get2(4, p));
     acc = dot_add2(acc, c_dp_e_ds[4], w.get2(5, p));
     acc = dot_add2(acc, c_dp_e_ds[5], w.get2(7, p));
-    w.put2(1, p, ds2_mul(hd2, dot_val2(acc)));
+    w.put2(1, p, ds2_mul_l(hd2, dot_val2_l(acc)));
   }
   double sum = 0.0;
 #pragma unroll
