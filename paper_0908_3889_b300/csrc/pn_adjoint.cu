@@ -304,7 +304,9 @@ __device__ double dp5_step_vjp(const Coef<double>& c, const float* __restrict__ 
 // exact in FP32 enter as double-single pairs.  The recorded step sizes and
 // checkpoints are the FP64 forward run's; the states between checkpoints are
 // recomputed with double-single stage sums and FP64 state accumulation, so the
-// gradient is evaluated within ~1e-13 of the FP64 trajectory.
+// gradient is evaluated within ~1e-13 of the FP64 trajectory.  Products are the
+// lazy (unnormalized) ones of the forward kernel; sums keep their
+// renormalization.
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ ds dfma(ds a, ds b, ds c) { return ds_fma(a, b, c); }
 __device__ __forceinline__ ds dzero() { return ds{0.0f, 0.0f}; }
@@ -376,15 +378,15 @@ __device__ __noinline__ void rhs_ds_vjp(const Coef<ds>& c, const float* __restri
   const ds2 Ld[3] = {ds2_dup(L[0]), ds2_dup(L[1]), ds2_dup(L[2])};
   ds r = ds_inv_cbrt(w);
   if ((__float_as_uint(w.hi) & 0x7fffffffu) - 0x00800000u >= 0x7f000000u) r = ds{__int_as_float(0x7fc00000), 0.0f};
-  const ds r2 = ds_mul(r, r);
-  const ds v = ds_mul(w, r2);
-  const ds v2 = ds_mul(v, v);
+  const ds r2 = ds_mul_l(r, r);
+  const ds v = ds_mul_l(w, r2);
+  const ds v2 = ds_mul_l(v, v);
   const ds lw = ds_log(w, tabf);
   const ds2 LS = ds2_dot3(Ld[0], S[0], Ld[1], S[1], Ld[2], S[2]);  // (L.S1, L.S2)
   const ds LS1 = ds2_x(LS), LS2 = ds2_y(LS);
   const ds S12 = ds_dot3(ds2_x(S[0]), ds2_y(S[0]), ds2_x(S[1]), ds2_y(S[1]), ds2_x(S[2]), ds2_y(S[2]));
   const ds so = dfma(c.w1, LS1, dfma(c.w2, LS2, ds_neg(c.tail)));
-  const ds c2p = dfma(c.ss721, ds_mul(LS1, LS2), dfma(ds_neg(c.ss247), S12, c.c2));
+  const ds c2p = dfma(c.ss721, ds_mul_l(LS1, LS2), dfma(ds_neg(c.ss247), S12, c.c2));
   const ds c3p = dfma(c.clog, lw, c.c3l);
   const ds P6 = dfma(v, c.c35, c3p);
   const ds P5 = dfma(v, P6, c.c25);
@@ -392,25 +394,25 @@ __device__ __noinline__ void rhs_ds_vjp(const Coef<ds>& c, const float* __restri
   const ds P3 = dfma(v, P4, ds_neg(so));
   const ds P2 = dfma(v, P3, c.c1);
   const ds P = dfma(v2, P2, ds_of(1.0f));
-  const ds w2 = ds_mul(w, w);
-  const ds Q = ds_mul(ds_mul(w2, w), v2);
+  const ds w2 = ds_mul_l(w, w);
+  const ds Q = ds_mul_l(ds_mul_l(w2, w), v2);
   // Eq. (4) as in rhs_ds: dS_i/dt = pre (U_i x S_i), U_1 = q1 L + S2, q1 = a1 r - 3 LS2 (1 <-> 2).
-  const ds pre = ds_mul(c.prec, w2);
+  const ds pre = ds_mul_l(c.prec, w2);
   const ds2 pre2 = ds2_dup(pre);
   const ds2 q = ds2_fma(ds2_of(c.a1, c.a2), ds2_dup(r), ds2_mul_f(ds2_swap(LS), f2_dup(-3.0f)));  // (q1, q2)
   const ds q1 = ds2_x(q), q2 = ds2_y(q);
   ds2 U[3], X[3], D[3];
   for (int k = 0; k < 3; k++) U[k] = ds2_fma(q, Ld[k], ds2_swap(S[k]));  // (U1_k, U2_k)
   cross2(U, S, X);                                                       // (X1, X2) = (U1 x S1, U2 x S2)
-  for (int k = 0; k < 3; k++) D[k] = ds2_mul(pre2, X[k]);                // (d1, d2)
-  const ds lf = ds_mul(v, c.nie);
-  f[0] = ds_mul(ds_mul(Q, c.K), P);
+  for (int k = 0; k < 3; k++) D[k] = ds2_mul_l(pre2, X[k]);                // (d1, d2)
+  const ds lf = ds_mul_l(v, c.nie);
+  f[0] = ds_mul_l(ds_mul_l(Q, c.K), P);
   ds dsum[3];
   for (int k = 0; k < 3; k++) {
     f[1 + k] = ds2_x(D[k]);
     f[4 + k] = ds2_y(D[k]);
     dsum[k] = ds_add(ds2_x(D[k]), ds2_y(D[k]));
-    f[7 + k] = ds_mul(lf, dsum[k]);
+    f[7 + k] = ds_mul_l(lf, dsum[k]);
   }
   // ---- reverse ----
   ds2 Sb[3] = {ds2_zero(), ds2_zero(), ds2_zero()};  // (S1b_k, S2b_k)
@@ -421,12 +423,12 @@ __device__ __noinline__ void rhs_ds_vjp(const Coef<ds>& c, const float* __restri
   for (int k = 0; k < 3; k++) lfb = dfma(fb[7 + k], dsum[k], lfb);  // f_L = lf (d1 + d2)
   const ds2 lf2 = ds2_dup(lf);
   for (int k = 0; k < 3; k++) Db[k] = ds2_fma(lf2, ds2_dup(fb[7 + k]), ds2_of(fb[1 + k], fb[4 + k]));
-  ds vb = ds_mul(lfb, c.nie);  // lf = v nie
+  ds vb = ds_mul_l(lfb, c.nie);  // lf = v nie
   cb.nie = dfma(lfb, v, cb.nie);
   ds preb = dzero();  // d_i = pre X_i
   for (int k = 0; k < 3; k++) {
     preb = dfma(ds2_x(X[k]), ds2_x(Db[k]), dfma(ds2_y(X[k]), ds2_y(Db[k]), preb));
-    Xb[k] = ds2_mul(pre2, Db[k]);
+    Xb[k] = ds2_mul_l(pre2, Db[k]);
   }
   {  // X_i = U_i x S_i:  Ub_i += S_i x Xb_i,  Sb_i += Xb_i x U_i
     ds2 t[3];
@@ -443,43 +445,43 @@ __device__ __noinline__ void rhs_ds_vjp(const Coef<ds>& c, const float* __restri
   }
   cb.a1 = dfma(q1b, r, cb.a1);  // q1 = a1 r - 3 LS2, q2 = a2 r - 3 LS1
   cb.a2 = dfma(q2b, r, cb.a2);
-  ds rb = dfma(q1b, c.a1, ds_mul(q2b, c.a2));
-  ds LS2b = ds_mul_f(q1b, -3.0f), LS1b = ds_mul_f(q2b, -3.0f);
-  ds w2b = ds_mul(preb, c.prec);  // pre = prec w2
+  ds rb = dfma(q1b, c.a1, ds_mul_l(q2b, c.a2));
+  ds LS2b = ds_mul_f_l(q1b, -3.0f), LS1b = ds_mul_f_l(q2b, -3.0f);
+  ds w2b = ds_mul_l(preb, c.prec);  // pre = prec w2
   cb.prec = dfma(preb, w2, cb.prec);
   const ds f0b = fb[0];  // f0 = Q K P
-  const ds Qb = ds_mul(ds_mul(f0b, c.K), P);
-  cb.K = dfma(ds_mul(f0b, Q), P, cb.K);
-  const ds Pb = ds_mul(ds_mul(f0b, Q), c.K);
-  w2b = dfma(ds_mul(Qb, w), v2, w2b);  // Q = w2 w v2
-  ds wb = ds_mul(ds_mul(Qb, w2), v2);
-  ds v2b = ds_mul(ds_mul(Qb, w2), w);
+  const ds Qb = ds_mul_l(ds_mul_l(f0b, c.K), P);
+  cb.K = dfma(ds_mul_l(f0b, Q), P, cb.K);
+  const ds Pb = ds_mul_l(ds_mul_l(f0b, Q), c.K);
+  w2b = dfma(ds_mul_l(Qb, w), v2, w2b);  // Q = w2 w v2
+  ds wb = ds_mul_l(ds_mul_l(Qb, w2), v2);
+  ds v2b = ds_mul_l(ds_mul_l(Qb, w2), w);
   wb = dfma(ds_scale(w, 2.0f), w2b, wb);  // w2 = w^2
   v2b = dfma(Pb, P2, v2b);                // P = v2 P2 + 1
-  const ds P2b = ds_mul(Pb, v2);
+  const ds P2b = ds_mul_l(Pb, v2);
   vb = dfma(P2b, P3, vb);  // P2 = v P3 + c1
-  const ds P3b = ds_mul(P2b, v);
+  const ds P3b = ds_mul_l(P2b, v);
   cb.c1 = ds_add(cb.c1, P2b);
   vb = dfma(P3b, P4, vb);  // P3 = v P4 - so
-  const ds P4b = ds_mul(P3b, v);
+  const ds P4b = ds_mul_l(P3b, v);
   const ds sob = ds_neg(P3b);
   vb = dfma(P4b, P5, vb);  // P4 = v P5 + c2p
-  const ds P5b = ds_mul(P4b, v);
+  const ds P5b = ds_mul_l(P4b, v);
   const ds c2pb = P4b;
   vb = dfma(P5b, P6, vb);  // P5 = v P6 + c25
-  const ds P6b = ds_mul(P5b, v);
+  const ds P6b = ds_mul_l(P5b, v);
   cb.c25 = ds_add(cb.c25, P5b);
   vb = dfma(P6b, c.c35, vb);  // P6 = v c35 + c3p
   cb.c35 = dfma(P6b, v, cb.c35);
   const ds c3pb = P6b;
   cb.clog = dfma(c3pb, lw, cb.clog);  // c3p = clog lw + c3l
-  const ds lwb = ds_mul(c3pb, c.clog);
+  const ds lwb = ds_mul_l(c3pb, c.clog);
   cb.c3l = ds_add(cb.c3l, c3pb);
-  cb.ss721 = dfma(ds_mul(c2pb, LS1), LS2, cb.ss721);  // c2p = ss721 LS1 LS2 - ss247 S12 + c2
-  LS1b = dfma(ds_mul(c2pb, c.ss721), LS2, LS1b);
-  LS2b = dfma(ds_mul(c2pb, c.ss721), LS1, LS2b);
-  cb.ss247 = ds_sub(cb.ss247, ds_mul(c2pb, S12));
-  const ds S12b = ds_neg(ds_mul(c2pb, c.ss247));
+  cb.ss721 = dfma(ds_mul_l(c2pb, LS1), LS2, cb.ss721);  // c2p = ss721 LS1 LS2 - ss247 S12 + c2
+  LS1b = dfma(ds_mul_l(c2pb, c.ss721), LS2, LS1b);
+  LS2b = dfma(ds_mul_l(c2pb, c.ss721), LS1, LS2b);
+  cb.ss247 = ds_sub(cb.ss247, ds_mul_l(c2pb, S12));
+  const ds S12b = ds_neg(ds_mul_l(c2pb, c.ss247));
   cb.c2 = ds_add(cb.c2, c2pb);
   cb.w1 = dfma(sob, LS1, cb.w1);  // so = w1 LS1 + w2 LS2 - tail
   LS1b = dfma(sob, c.w1, LS1b);
@@ -491,12 +493,12 @@ __device__ __noinline__ void rhs_ds_vjp(const Coef<ds>& c, const float* __restri
     Lb[k] = dfma(LS1b, ds2_x(S[k]), dfma(LS2b, ds2_y(S[k]), Lb[k]));
     Sb[k] = ds2_fma(LSb, Ld[k], ds2_fma(S12b2, ds2_swap(S[k]), Sb[k]));
   }
-  const ds r3 = ds_mul(r2, r);  // = 1/w
+  const ds r3 = ds_mul_l(r2, r);  // = 1/w
   wb = dfma(lwb, r3, wb);       // lw = ln|w|
   vb = dfma(ds_scale(v, 2.0f), v2b, vb);  // v2 = v^2
   wb = dfma(vb, r2, wb);                  // v = w r^2
-  rb = dfma(ds_mul(vb, ds_scale(w, 2.0f)), r, rb);
-  wb = ds_sub(wb, ds_mul(ds_mul(ds_mul(rb, dconst(kThird)), r), r3));  // dr/dw = -r/(3w)
+  rb = dfma(ds_mul_l(vb, ds_scale(w, 2.0f)), r, rb);
+  wb = ds_sub(wb, ds_mul_l(ds_mul_l(ds_mul_l(rb, dconst(kThird)), r), r3));  // dr/dw = -r/(3w)
   yb[0] = wb;
   for (int k = 0; k < 3; k++) {
     yb[1 + k] = ds2_x(Sb[k]);
@@ -527,7 +529,7 @@ __device__ __forceinline__ void dp5_stages_ds(const Coef<ds>& c, const float* __
     for (int p = 0; p < 5; p++) {
       dacc2 acc = dot_first2(c_dp_a_ds[s - 1][0], K[0][p]);
       for (int j = 1; j < s; j++) acc = dot_add2(acc, c_dp_a_ds[s - 1][j], K[j][p]);
-      const ds2 yy = ds2_add(ds2_of(yd[2 * p], yd[2 * p + 1]), ds2_mul(hd2, dot_val2(acc)));
+      const ds2 yy = ds2_add(ds2_of(yd[2 * p], yd[2 * p + 1]), ds2_mul_l(hd2, dot_val2_l(acc)));
       ys[2 * p] = ds2_x(yy);
       ys[2 * p + 1] = ds2_y(yy);
       sp[(size_t)(10 * s + 2 * p) * ss] = make_float2(ys[2 * p].hi, ys[2 * p].lo);
@@ -542,7 +544,7 @@ __device__ __forceinline__ void dp5_stages_ds(const Coef<ds>& c, const float* __
   for (int p = 0; p < 5; p++) {
     dacc2 acc = dot_first2(c_dp_a_ds[5][0], K[0][p]);
     for (int j = 2; j < 6; j++) acc = dot_add2(acc, c_dp_a_ds[5][j], K[j][p]);
-    const ds2 inc = ds2_mul(hd2, dot_val2(acc));
+    const ds2 inc = ds2_mul_l(hd2, dot_val2_l(acc));
     const ds i0 = ds2_x(inc), i1 = ds2_y(inc);
     y5[2 * p] = y[2 * p] + (f32_to_f64(i0.hi) + f32_to_f64(i0.lo));
     y5[2 * p + 1] = y[2 * p + 1] + (f32_to_f64(i1.hi) + f32_to_f64(i1.lo));
@@ -558,7 +560,7 @@ __device__ double dp5_step_vjp_ds(const Coef<ds>& c, const float* __restrict__ t
   const ds hd = split64(h);
   const ds2 hd2 = ds2_dup(hd);
   for (int j = 0; j < 6; j++)
-    for (int p = 0; p < 5; p++) kp[j][p] = ds2_mul(ds2_dup(dconst(c_dp_a_ds[5][j])), ds2_of(lam[2 * p], lam[2 * p + 1]));
+    for (int p = 0; p < 5; p++) kp[j][p] = ds2_mul_l(ds2_dup(dconst(c_dp_a_ds[5][j])), ds2_of(lam[2 * p], lam[2 * p + 1]));
   for (int p = 0; p < 5; p++) yb[p] = ds2_of(lam[2 * p], lam[2 * p + 1]);
   ds hb = dzero();
 #pragma unroll 1
@@ -569,7 +571,7 @@ __device__ double dp5_step_vjp_ds(const Coef<ds>& c, const float* __restrict__ t
       Ys[i] = ds{t.x, t.y};
     }
     for (int p = 0; p < 5; p++) {
-      const ds2 f = ds2_mul(hd2, kp[s][p]);
+      const ds2 f = ds2_mul_l(hd2, kp[s][p]);
       fb[2 * p] = ds2_x(f);
       fb[2 * p + 1] = ds2_y(f);
     }
