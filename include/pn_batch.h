@@ -55,9 +55,12 @@ extern "C" {
 
 /* ---- parameter enums ---- */
 #define PN_FP64 0  /* everything in FP64 */
-#define PN_MIXED 1 /* right-hand side in FP32; stages, state, error estimate and step control in FP64 */
-#define PN_MIXED_DS 2 /* right-hand side in double-single (pairs of FP32, ~48-bit significand) on the FP32
-                         pipe; stages, state, error estimate and step control in FP64 */
+#define PN_MIXED 1 /* right-hand side and its stage inputs in FP32; the state increment and the error
+                      estimate as compensated FP32 sums, the error norm in FP32; state and step
+                      control in FP64 */
+#define PN_MIXED_DS 2 /* right-hand side, its stage inputs and the error estimate in double-single
+                         (pairs of FP32, ~48-bit significand) on the FP32 pipe; state accumulation,
+                         error norm and step control in FP64 */
 
 #define PN_STOP_LAND 0        /* stop exactly on omega_f (default) */
 #define PN_STOP_FIRST_CROSS 1 /* stop at the first accepted state with omega >= omega_f */
