@@ -110,11 +110,12 @@ def parse_args():
                          "one-sample KS test against U[-1, 1]")
     ap.add_argument("--science-n", type=int, default=362_799_815)
     ap.add_argument("--science-precision", type=int, default=0, help="0 FP64, 1 FP32 RHS, 2 double-single")
-    ap.add_argument("--profile-case", choices=("integrate", "adjoint", "adjoint_ds"), default=None,
+    ap.add_argument("--profile-case", choices=("integrate", "stops", "adjoint", "adjoint_ds"), default=None,
                     help="no timing, the small cases the ncu section captures run: 'integrate' integrates the "
                          "first --n binaries of the workload once per precision (persistent schedule, 256 "
-                         "threads); 'adjoint' runs one pn_batch_adjoint over the 65,536-binary adjoint ensemble, "
-                         "'adjoint_ds' the same with the double-single reverse sweep")
+                         "threads); 'stops' integrates them in FP64 once with the landing stop and once with "
+                         "the first-crossing stop; 'adjoint' runs one pn_batch_adjoint over the 65,536-binary "
+                         "adjoint ensemble, 'adjoint_ds' the same with the double-single reverse sweep")
     return ap.parse_args()
 
 
@@ -380,6 +381,17 @@ def main():
                 st = b.stats(inp, out)
                 attempts[prec] = st["acc_total"] + st["rej_total"] + st["land_total"]
         print(json.dumps({"profile_case": "C1", "n": n, "precisions": [0, 1, 2], "attempts": attempts}))
+        return
+    if args.profile_case == "stops":
+        attempts = {}
+        for mode in (pn.native.PN_STOP_LAND, pn.native.PN_STOP_FIRST_CROSS):
+            with pn.Batch(n, pn.params(precision=pn.native.PN_FP64, schedule=pn.native.PN_SCHED_PERSISTENT,
+                                       block=256, stop_mode=mode)) as b:
+                b.integrate(inp, out)
+                torch.cuda.synchronize()
+                st = b.stats(inp, out)
+                attempts[mode] = st["acc_total"] + st["rej_total"] + st["land_total"]
+        print(json.dumps({"profile_case": "C1 stops", "n": n, "stop_modes": [0, 1], "attempts": attempts}))
         return
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)  # 256 MB > L2 (126 MB)
 
