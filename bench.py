@@ -48,29 +48,35 @@ FP64_DATASHEET_TFLOPS = 1.25  # nominal dense FP64 of one B300
 # DRAM traffic of the integration kernel per binary from an ncu capture
 # (dram__bytes_read.sum + dram__bytes_write.sum, profiles/); valid only while
 # the kernel sources hash (kernel_sha) to the recorded value.
-PROFILED = {"kernel_sha": "8320d4adeff4fd91", "dram_bytes_per_binary": (39.485696e6 + 0.897024e6) / 131072}
+PROFILED = {"kernel_sha": "9d898a1d093bdc42", "dram_bytes_per_binary": (39.510016e6 + 0.897024e6) / 131072}
 
 
 # Executed floating-point thread instructions per attempt of each integration kernel
-# k_integrate_mx<PREC> (PREC 0 FP64, 1 FP32 right-hand side, 2 double-single), from one ncu capture
-# of the 131,072-binary case (profiles/k_integrate_pipes_C1_131072.md): sums of
+# k_integrate_mx<PREC> (PREC 0 FP64, 1 FP32 right-hand side, 2 double-single) at the persistent
+# schedule, and of the double-single kernel at the plain schedule (its own register budget), from one
+# ncu capture of the 131,072-binary case (profiles/k_integrate_pipes_C1_131072.md): sums of
 # smsp__sass_thread_inst_executed_op_{ffma,fadd,fmul,ffma2,fadd2,fmul2,dfma,dadd,dmul}_pred_on over
 # the launch divided by its attempts.  Valid only while the kernel sources hash to kernel_sha.
-EXECUTED = {"kernel_sha": "8320d4adeff4fd91", "per_attempt": {
+EXECUTED = {"kernel_sha": "9d898a1d093bdc42", "per_attempt": {
     0: {"ffma": 130.84, "fadd": 397.54, "fmul": 93.55, "ffma2": 0.0, "fadd2": 0.0, "fmul2": 0.0,
         "dfma": 505.94, "dadd": 44.96, "dmul": 242.83},
     1: {"ffma": 318.97, "fadd": 51.53, "fmul": 263.58, "ffma2": 190.0, "fadd2": 395.0, "fmul2": 55.0,
         "dfma": 15.97, "dadd": 10.96, "dmul": 10.91},
     2: {"ffma": 1252.84, "fadd": 2745.46, "fmul": 516.83, "ffma2": 495.0, "fadd2": 1090.0, "fmul2": 165.0,
-        "dfma": 45.94, "dadd": 60.96, "dmul": 18.83}}}
+        "dfma": 45.94, "dadd": 60.96, "dmul": 18.83}},
+    "per_attempt_plain": {
+    2: {"ffma": 1252.84, "fadd": 2745.46, "fmul": 516.83, "ffma2": 495.0, "fadd2": 1090.0, "fmul2": 165.0,
+        "dfma": 45.94, "dadd": 60.96, "dmul": 17.89}}}
 
 
-def executed_flops(prec: int):
-    """(FP32, FP64) flops one attempt executes (an FMA is 2, a packed pair instruction 2 lanes), or None
-    when no capture of the current kernel sources is recorded."""
-    if EXECUTED["kernel_sha"] != kernel_sha() or prec not in EXECUTED["per_attempt"]:
+def executed_flops(prec: int, plain: bool = False):
+    """(FP32, FP64) flops one attempt executes (an FMA is 2, a packed pair instruction 2 lanes) in the
+    kernel of that precision at the persistent schedule (or at the plain one, where it was captured), or
+    None when no capture of the current kernel sources is recorded."""
+    table = EXECUTED["per_attempt_plain"] if plain and prec in EXECUTED["per_attempt_plain"] else EXECUTED["per_attempt"]
+    if EXECUTED["kernel_sha"] != kernel_sha() or prec not in table:
         return None
-    c = EXECUTED["per_attempt"][prec]
+    c = table[prec]
     f32 = 2 * c["ffma"] + c["fadd"] + c["fmul"] + 2 * (2 * c.get("ffma2", 0) + c.get("fadd2", 0) + c.get("fmul2", 0))
     f64 = 2 * c["dfma"] + c["dadd"] + c["dmul"]
     return f32, f64
@@ -113,7 +119,7 @@ def parse_args():
     ap.add_argument("--profile-case", choices=("integrate", "stops", "adjoint", "adjoint_ds"), default=None,
                     help="no timing, the small cases the ncu section captures run: 'integrate' integrates the "
                          "first --n binaries of the workload once per precision (persistent schedule, 256 "
-                         "threads); 'stops' integrates them in FP64 once with the landing stop and once with "
+                         "threads), then in double-single at the plain schedule (128 threads); 'stops' integrates them in FP64 once with the landing stop and once with "
                          "the first-crossing stop; 'adjoint' runs one pn_batch_adjoint over the 65,536-binary "
                          "adjoint ensemble, 'adjoint_ds' the same with the double-single reverse sweep")
     return ap.parse_args()
@@ -374,13 +380,19 @@ def main():
         return
     if args.profile_case == "integrate":
         attempts = {}
-        for prec in (pn.native.PN_FP64, pn.native.PN_MIXED, pn.native.PN_MIXED_DS):
-            with pn.Batch(n, pn.params(precision=prec, schedule=pn.native.PN_SCHED_PERSISTENT, block=256)) as b:
+        persist, plain = pn.native.PN_SCHED_PERSISTENT, pn.native.PN_SCHED_PLAIN
+        runs = [(pn.native.PN_FP64, persist, 256), (pn.native.PN_MIXED, persist, 256),
+                (pn.native.PN_MIXED_DS, persist, 256), (pn.native.PN_MIXED_DS, plain, 128)]
+        for prec, sched, block in runs:
+            with pn.Batch(n, pn.params(precision=prec, schedule=sched, block=block, bpt=1)) as b:
                 b.integrate(inp, out)
                 torch.cuda.synchronize()
                 st = b.stats(inp, out)
-                attempts[prec] = st["acc_total"] + st["rej_total"] + st["land_total"]
-        print(json.dumps({"profile_case": "C1", "n": n, "precisions": [0, 1, 2], "attempts": attempts}))
+                key = str(prec) + ("" if sched == persist else " plain")
+                attempts[key] = st["acc_total"] + st["rej_total"] + st["land_total"]
+        print(json.dumps({"profile_case": "C1", "n": n, "launches": ["fp64", "fp32 rhs", "double-single",
+                                                                     "double-single plain 128"],
+                          "attempts": attempts}))
         return
     if args.profile_case == "stops":
         attempts = {}
@@ -495,7 +507,8 @@ def main():
             errs[k] = {"max": float(d.max()), "p50": float(d.median())}
         m_attempts = mst["acc_total"] + mst["rej_total"] + mst["land_total"]
         sec = mix_kernel_ms * 1e-3  # the integration kernel alone
-        ex = executed_flops(prec)
+        plain = tn["schedule"] == pn.native.PN_SCHED_PLAIN
+        ex = executed_flops(prec, plain=plain)
         roof_m = None
         if ex is not None and f32_peak and f64_peak:
             a32, a64 = ex[0] * m_attempts / sec, ex[1] * m_attempts / sec
@@ -506,7 +519,8 @@ def main():
                       "fp64_pipe": {"achieved": a64 / 1e12, "peak": f64_peak / 1e12, "frac": a64 / f64_peak,
                                     "fp64_flops_per_attempt_executed": ex[1]},
                       "counts": "executed instructions per attempt from ncu (profiles/), scaled by this run's attempts",
-                      "kernel": f"pn::k_integrate_mx<{prec}>", "kernel_ms_per_launch": mix_kernel_ms}
+                      "kernel": f"pn::k_integrate_mx<{prec}, {'plain' if plain else 'persistent'}>",
+                      "kernel_ms_per_launch": mix_kernel_ms}
         return {"value": aggregate_rate(world, n, args.steps, mix_ms), "unit": "inspirals/s",
                 "ms_per_step": mix_ms / args.steps, "speedup_vs_fp64": total_ms / mix_ms,
                 "dot_err_vs_fp64": {k: errs[k] for k in ("dot_s1s2", "dot_ls1", "dot_ls2")},

@@ -1086,11 +1086,13 @@ __device__ __forceinline__ ds2 ds2_mul_l(ds2 a, ds2 b) {
 // double-single components as five packed pairs of components (2p, 2p + 1),
 // pair p of thread t at base[(v * 5 + p) * nthreads + t] as 16 bytes
 // (hi_2p, hi_2p+1, lo_2p, lo_2p+1), lane-interleaved so that a warp's accesses
-// are 32 consecutive 16-byte words.  Vectors 0..5 hold the rates k1..k6, 6 the
-// state split into pairs (then the increment of y5), 7 the stage input (then
-// k7); the error estimate goes to vector 1 once k2 is no longer needed (its
-// weight in b and in b - bhat is 0).
-constexpr int kDsVectors = 8;
+// are 32 consecutive 16-byte words.  Vectors 0..5 hold the rates k1..k6 and 6
+// the state split into pairs (then the increment of y5).  Stage s's input is
+// formed in the vector its rate k_{s+1} will take (no sum of that stage reads
+// it); the last stage's input, then k7, then the error estimate take vector 1,
+// k2's, whose weight in b and in b - bhat is 0.  Seven vectors rather than
+// eight let three 128-thread blocks share an SM's shared memory.
+constexpr int kDsVectors = 7;
 constexpr int kDsWorkBytes = kDsVectors * 10 * 8;  // per thread
 struct DsWork {
   ulonglong2* base;
@@ -1138,13 +1140,14 @@ __device__ __forceinline__ double dp5_attempt_ds(const Coefs& cf, const Tabs& tb
       if (r >= 4) acc = dot_add2(acc, a4, w.get2(4, p));
       if (r >= 5) acc = dot_add2(acc, a5, w.get2(5, p));
       const ds2 inc = ds2_mul_l(hd2, dot_val2_l(acc));  // h sum_j a_sj k_j
-      w.put2(7, p, ds2_add(w.get2(6, p), inc));
+      w.put2(r < 5 ? r + 1 : 1, p, ds2_add(w.get2(6, p), inc));
       if (r == 5) w.put2(6, p, inc);
     }
+    const int vs = r < 5 ? r + 1 : 1;  // the stage input, then its rate
     ds yin[10];
-    w.get_vec(7, yin);
+    w.get_vec(vs, yin);
     rhs_ds(cf.cds, tb.f, yin, kn);  // k_{r+2}; for r = 5, k7 at the double-single y5
-    w.put_vec((r < 5) ? r + 1 : 7, kn);
+    w.put_vec(vs, kn);
   }
 #pragma unroll 1
   for (int p = 0; p < 5; p++) {  // embedded error estimate h sum_j (b_j - bhat_j) k_j
@@ -1153,7 +1156,7 @@ __device__ __forceinline__ double dp5_attempt_ds(const Coefs& cf, const Tabs& tb
     acc = dot_add2(acc, c_dp_e_ds[2], w.get2(3, p));
     acc = dot_add2(acc, c_dp_e_ds[3], w.get2(4, p));
     acc = dot_add2(acc, c_dp_e_ds[4], w.get2(5, p));
-    acc = dot_add2(acc, c_dp_e_ds[5], w.get2(7, p));
+    acc = dot_add2(acc, c_dp_e_ds[5], w.get2(1, p));
     w.put2(1, p, ds2_mul_l(hd2, dot_val2_l(acc)));
   }
   double sum = 0.0;

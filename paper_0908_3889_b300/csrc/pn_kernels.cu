@@ -458,12 +458,17 @@ __global__ void __launch_bounds__(kMaxBlock) k_integrate(const KArgs a, const do
 
 // The integration kernels with their rates in a per-thread shared-memory
 // workspace: PREC 0 FP64, PREC 1 FP32 right-hand side, PREC 2 double-single.
-// The FP32-RHS kernel is held to 168 registers, three warps per scheduler (it is
-// latency-bound, and measured faster so); the FP64 and double-single kernels
-// take up to 255 (two warps per scheduler), which measured faster for them.
+// The FP32-RHS kernels and the plain-schedule double-single kernel are held to
+// 168 registers, three warps per scheduler (they are latency-bound, and measured
+// faster so); the FP64 kernels and the persistent double-single kernel take up to
+// 255 (two warps per scheduler), which measured faster for them.
+constexpr int integrate_maxnreg(int prec, bool persist) {
+  return prec == 1 ? 168 : (prec == 2 && !persist ? 168 : 255);
+}
 template <int PREC, bool PERSIST, bool BOUNDED = false>
-__global__ void __maxnreg__(PREC == 1 ? 168 : 255) k_integrate_mx(const KArgs a, const double* __restrict__ ws,
-                                                                 int64_t stride) {
+__global__ void __maxnreg__(integrate_maxnreg(PREC, PERSIST)) k_integrate_mx(const KArgs a,
+                                                                            const double* __restrict__ ws,
+                                                                            int64_t stride) {
   integrate_body<PREC, PERSIST, false, BOUNDED, PREC == 0>(a, ws, stride, RecArgs{});
 }
 
