@@ -1,5 +1,5 @@
-"""Mixed precision (FP32 right-hand side, FP64 stages / state / error estimate / step control)
-against the FP64 oracle (needs a B300).
+"""Mixed precision (an FP32 or a double-single right-hand side; FP64 state accumulation and step
+control) against the FP64 oracle (needs a B300).
 
 FP32 rounding in the rates perturbs the embedded error estimate by ~1e-3 of
 its value, so a few step sizes (and, rarely, an accept/reject decision) differ
@@ -115,6 +115,22 @@ def test_ds_full_size_subsample_meets_dot_bar(pn, orc):
     for k in ("dot_s1s2", "dot_ls1", "dot_ls2"):
         assert report[k][0] <= DOT_TOL, (k, report[k])
     assert np.mean(decided_alike(g, o)) >= 0.999
+
+
+@pytest.mark.parametrize("precision", [1, 2])
+def test_mixed_schedules_and_blocks_bit_identical(pn, precision):
+    """Every launch shape gives the same bits in both mixed modes.  The double-single kernel's plain
+    and persistent instantiations are compiled under different register caps (168 and 255) and its
+    workspace layout depends on neither; the attempt's arithmetic must not change with them."""
+    import torch
+    ens = workloads.config("C2", n=3000)
+    inp = pn.to_device(ens)
+    ref = pn.to_numpy(pn.integrate(inp, precision=precision, schedule=1, block=128))
+    for sched, block, bpt in ((2, 64, 0), (2, 256, 0), (1, 64, 1), (2, 128, 0), (1, 128, 2), (1, 256, 1)):
+        g = pn.to_numpy(pn.integrate(inp, precision=precision, schedule=sched, block=block, bpt=bpt))
+        torch.cuda.synchronize()
+        for k in ref:
+            assert np.array_equal(ref[k], g[k], equal_nan=True), (precision, sched, block, bpt, k)
 
 
 @pytest.mark.parametrize("schedule", [1, 2])
