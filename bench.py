@@ -73,7 +73,9 @@ def executed_flops(prec: int, plain: bool = False):
     """(FP32, FP64) flops one attempt executes (an FMA is 2, a packed pair instruction 2 lanes) in the
     kernel of that precision at the persistent schedule (or at the plain one, where it was captured), or
     None when no capture of the current kernel sources is recorded."""
-    table = EXECUTED["per_attempt_plain"] if plain and prec in EXECUTED["per_attempt_plain"] else EXECUTED["per_attempt"]
+    table = EXECUTED["per_attempt"]
+    if plain and prec in EXECUTED["per_attempt_plain"]:
+        table = EXECUTED["per_attempt_plain"]
     if EXECUTED["kernel_sha"] != kernel_sha() or prec not in table:
         return None
     c = table[prec]
@@ -119,8 +121,9 @@ def parse_args():
     ap.add_argument("--profile-case", choices=("integrate", "stops", "adjoint", "adjoint_ds"), default=None,
                     help="no timing, the small cases the ncu section captures run: 'integrate' integrates the "
                          "first --n binaries of the workload once per precision (persistent schedule, 256 "
-                         "threads), then in double-single at the plain schedule (128 threads); 'stops' integrates them in FP64 once with the landing stop and once with "
-                         "the first-crossing stop; 'adjoint' runs one pn_batch_adjoint over the 65,536-binary "
+                         "threads), then in double-single at the plain schedule (128 threads); 'stops' "
+                         "integrates them in FP64 once with the landing stop and once with the "
+                         "first-crossing stop; 'adjoint' runs one pn_batch_adjoint over the 65,536-binary "
                          "adjoint ensemble, 'adjoint_ds' the same with the double-single reverse sweep")
     return ap.parse_args()
 
