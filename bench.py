@@ -625,20 +625,31 @@ def main():
         pp = workloads.config("PAPER_PERF", n=1_048_576, seed=workloads.SEED_BASE + 6 + 1000 * rank)
         inpp = pn.to_device(pp, device=dev)
         outp = pn.alloc_outputs(pp["m1"].shape[0], dev)
-        with pn.Batch(pp["m1"].shape[0], pn.params(precision=0)) as b:
-            b.integrate(inpp, outp)
-            torch.cuda.synchronize()
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            e0.record()
-            b.integrate(inpp, outp)
-            e1.record()
-            e1.synchronize()
-            msp = max_over_ranks(e0.elapsed_time(e1))
-        extras["paper_test_inspiral_fp64"] = {
-            "value": aggregate_rate(world, pp["m1"].shape[0], 1, msp), "unit": "inspirals/s", "ms": msp,
-            "workload": "one seeded inspiral, omega 0.004 -> 0.1, 1,048,576 copies (Sec. IV lock-step test)",
-            "paper_gpu_2009": {"value": 2700.0, "unit": "inspirals/s", "hardware": "1 GPU of a Tesla S1070, FP32"}}
-        del inpp, outp
+        pp_dots = {}
+        for prec, key in ((0, "paper_test_inspiral_fp64"), (1, "paper_test_inspiral_mixed_fp32"),
+                          (2, "paper_test_inspiral_mixed_ds")):
+            with pn.Batch(pp["m1"].shape[0], pn.params(precision=prec)) as b:
+                b.integrate(inpp, outp)
+                torch.cuda.synchronize()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record()
+                b.integrate(inpp, outp)
+                e1.record()
+                e1.synchronize()
+                msp = max_over_ranks(e0.elapsed_time(e1))
+            dots = {k: outp[k].clone() for k in ("dot_s1s2", "dot_ls1", "dot_ls2")}
+            if prec == 0:
+                pp_dots = dots
+            extras[key] = {
+                "value": aggregate_rate(world, pp["m1"].shape[0], 1, msp), "unit": "inspirals/s", "ms": msp,
+                "workload": "one seeded inspiral, omega 0.004 -> 0.1, 1,048,576 copies (Sec. IV lock-step test)",
+                "paper_gpu_2009": {"value": 2700.0, "unit": "inspirals/s",
+                                   "hardware": "1 GPU of a Tesla S1070, FP32"}}
+            if prec != 0:
+                extras[key]["speedup_vs_fp64"] = extras["paper_test_inspiral_fp64"]["ms"] / msp
+                extras[key]["max_dot_diff_vs_fp64"] = max(float((dots[k] - pp_dots[k]).abs().max())
+                                                          for k in dots)
+        del inpp, outp, pp_dots
         # Sec. V B-D's parameter sweeps: ten 100,000-binary ensembles (omega 0.00395 -> 0.05) in one
         # integrate launch, per-ensemble statistics from one segmented reduction.
         sw = workloads.paper_sweeps()
