@@ -32,7 +32,7 @@
 extern "C" {
 #endif
 
-#define PN_ABI_VERSION 2
+#define PN_ABI_VERSION 3
 
 /* ---- return codes ---- */
 #define PN_OK 0
@@ -67,6 +67,10 @@ extern "C" {
 
 #define PN_THETA_BCV2 0       /* 3PN: theta-hat multiplies eta once (default reading) */
 #define PN_THETA_AS_PRINTED 1 /* 3PN: theta-hat eta^2, as the paper's Eq. (1) prints it */
+
+#define PN_ORDER_INPUT 0  /* lanes take the binaries in input order */
+#define PN_ORDER_LENGTH 1 /* lanes take them sorted by predicted length, longest first (default);
+                             no result depends on the order */
 
 #define PN_SCHED_AUTO 0       /* use the autotuned choice if any, else persistent */
 #define PN_SCHED_PLAIN 1      /* one grid pass: BPT binaries per thread, fixed assignment */
@@ -107,10 +111,14 @@ typedef struct {
   int32_t fixed_step;    /* 1: accept every attempt with h = h0 (convergence studies), default 0 */
   int32_t precision;     /* PN_FP64, PN_MIXED or PN_MIXED_DS */
   int32_t schedule;      /* PN_SCHED_* */
-  int32_t block;         /* threads per block (multiple of 32, <= 512); 0 = autotuned / default */
+  int32_t block;         /* threads per block (multiple of 32, <= 256); 0 = autotuned / default */
   int32_t bpt;           /* plain schedule: binaries each thread integrates in turn, 1 or 2;
                             0 = autotuned / default 1 */
   int32_t ckpt_every;    /* adjoint: accepted steps between state checkpoints, default 64 */
+  int32_t order;         /* PN_ORDER_*: the order in which lanes take the binaries, default
+                            PN_ORDER_LENGTH.  The lanes of a warp run in lock-step, so binaries of
+                            similar length in one warp waste fewer lane-steps; the outputs are the
+                            same bits in either order.  pn_integrate_noalloc ignores it. */
 } pn_params;
 
 /* Inputs, one value per binary (device pointers).  Read-only for

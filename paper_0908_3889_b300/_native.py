@@ -17,6 +17,8 @@ PN_FP64, PN_MIXED, PN_MIXED_DS = 0, 1, 2
 PN_STOP_LAND, PN_STOP_FIRST_CROSS = 0, 1
 PN_THETA_BCV2, PN_THETA_AS_PRINTED = 0, 1
 PN_SCHED_AUTO, PN_SCHED_PLAIN, PN_SCHED_PERSISTENT = 0, 1, 2
+PN_ORDER_INPUT, PN_ORDER_LENGTH = 0, 1
+ABI_VERSION = 3  # PN_ABI_VERSION of the header these declarations follow
 (PN_TERM_1PN, PN_TERM_SO, PN_TERM_TAIL, PN_TERM_2PN, PN_TERM_SS, PN_TERM_25PN, PN_TERM_3PN, PN_TERM_35PN,
  PN_TERM_PREC) = (1 << i for i in range(9))
 PN_TERM_ALL = 0x1FF
@@ -31,7 +33,7 @@ class pn_params(C.Structure):
                 ("land_tol", C.c_double), ("max_steps", C.c_int64), ("land_max_iter", C.c_int32),
                 ("stop_mode", C.c_int32), ("term_mask", C.c_uint32), ("theta_mode", C.c_int32),
                 ("fixed_step", C.c_int32), ("precision", C.c_int32), ("schedule", C.c_int32),
-                ("block", C.c_int32), ("bpt", C.c_int32), ("ckpt_every", C.c_int32)]
+                ("block", C.c_int32), ("bpt", C.c_int32), ("ckpt_every", C.c_int32), ("order", C.c_int32)]
 
 
 INPUT_FIELDS = ("m1", "m2", "chi1", "chi2", "s1x", "s1y", "s1z", "s2x", "s2y", "s2z", "lx", "ly", "lz",
@@ -149,7 +151,7 @@ def load(path: str | None = None) -> C.CDLL:
         fn = getattr(lib, name)
         fn.restype = res
         fn.argtypes = args
-    if lib.pn_abi_version() != 2:
+    if lib.pn_abi_version() != ABI_VERSION:
         raise RuntimeError("libpn_b300.so ABI version mismatch")
     if path is None:
         _lib = lib

@@ -616,41 +616,6 @@ __global__ void k_order_count(const pn_outputs o, int64_t n, int32_t cap, unsign
   if ((int)(threadIdx.x & 31u) == __ffs(peers) - 1) atomicAdd(&bins[key], (unsigned long long)__popc(peers));
 }
 
-// In place: bins[k] <- number of binaries with a key above k (one block of 1024 threads).
-__global__ void __launch_bounds__(1024) k_order_scan(unsigned long long* bins, int32_t nb) {
-  __shared__ unsigned long long warp_tot[32];
-  __shared__ unsigned long long carry;
-  const unsigned lane = threadIdx.x & 31u, wid = threadIdx.x >> 5;
-  if (threadIdx.x == 0) carry = 0;
-  __syncthreads();
-  for (int32_t base = 0; base < nb; base += 1024) {
-    const int32_t r = base + (int32_t)threadIdx.x;  // rank from the top key down
-    const int32_t k = nb - 1 - r;
-    const unsigned long long v = (r < nb) ? bins[k] : 0ull;
-    unsigned long long x = v;  // inclusive scan within the warp
-    for (int d = 1; d < 32; d <<= 1) {
-      const unsigned long long t = __shfl_up_sync(0xffffffffu, x, d);
-      if ((int)lane >= d) x += t;
-    }
-    if (lane == 31u) warp_tot[wid] = x;
-    __syncthreads();
-    if (wid == 0) {
-      unsigned long long w = warp_tot[lane];
-      for (int d = 1; d < 32; d <<= 1) {
-        const unsigned long long t = __shfl_up_sync(0xffffffffu, w, d);
-        if ((int)lane >= d) w += t;
-      }
-      warp_tot[lane] = w;  // inclusive over warps
-    }
-    __syncthreads();
-    const unsigned long long before = carry + (wid ? warp_tot[wid - 1] : 0ull) + x - v;
-    if (r < nb) bins[k] = before;
-    __syncthreads();
-    if (threadIdx.x == 0) carry += warp_tot[31];
-    __syncthreads();
-  }
-}
-
 __global__ void k_order_scatter(const pn_outputs o, int64_t n, int32_t cap, unsigned long long* cursor,
                                 int64_t* order) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -880,7 +845,8 @@ cudaError_t launch_adjoint(const AdjArgs& a, int block, int grid, cudaStream_t s
   cudaError_t e = cudaMemsetAsync(a.bins, 0, (size_t)nb * sizeof(unsigned long long), s);
   if (e != cudaSuccess) return e;
   k_order_count<<<eg, 256, 0, s>>>(a.k.out, a.k.n, a.cap, a.bins);
-  k_order_scan<<<1, 1024, 0, s>>>(a.bins, nb);
+  e = launch_scan_above(a.bins, nb, s);
+  if (e != cudaSuccess) return e;
   k_order_scatter<<<eg, 256, 0, s>>>(a.k.out, a.k.n, a.cap, a.bins, a.order);
   e = cudaMemsetAsync(a.k.queue, 0, sizeof(unsigned long long), s);
   if (e != cudaSuccess) return e;

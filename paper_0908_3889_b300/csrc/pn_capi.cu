@@ -61,6 +61,9 @@ struct pn_batch {
   int32_t* d_adj_out_i = nullptr;
   int64_t* d_adj_order = nullptr;        // reverse sweep: binaries ordered by step count
   unsigned long long* d_adj_bins = nullptr;
+  int64_t* d_order = nullptr;           // PN_ORDER_LENGTH: the lanes' order of the binaries (n_max)
+  float* d_order_key = nullptr;         // its keys (n_max)
+  unsigned long long* d_order_bins = nullptr;  // its counting-sort bins (+ the key range)
   int64_t adj_bins_cap = 0;
   // saved integrator states between bounded calls (pn_batch_integrate_budget / pn_batch_resume)
   double* d_rs = nullptr;
@@ -135,6 +138,7 @@ extern "C" void pn_params_default(pn_params* p) {
   p->block = 0;
   p->bpt = 0;
   p->ckpt_every = 64;
+  p->order = PN_ORDER_LENGTH;
 }
 
 // Parameter domain.  Besides the integrator's own constraints, atol >= 1e-30
@@ -164,6 +168,7 @@ static bool params_valid(const pn_params* p, std::string* why) {
     return bad("block must be 0 or a multiple of 32 in [32, 256]");
   if (p->bpt < 0 || p->bpt > 2) return bad("bpt must be 0 (autotuned/default), 1 or 2");
   if (p->ckpt_every < 1) return bad("ckpt_every must be >= 1");
+  if (p->order != PN_ORDER_INPUT && p->order != PN_ORDER_LENGTH) return bad("bad order");
   return true;
 }
 
@@ -225,6 +230,9 @@ extern "C" void pn_batch_destroy(pn_batch* b) {
   cudaFree(b->d_adj_out_i);
   cudaFree(b->d_adj_order);
   cudaFree(b->d_adj_bins);
+  cudaFree(b->d_order);
+  cudaFree(b->d_order_key);
+  cudaFree(b->d_order_bins);
   if (b->s_in) cudaStreamSynchronize(b->s_in);
   if (b->s_out) cudaStreamSynchronize(b->s_out);
   for (int k = 0; k < 2; k++) {
@@ -368,6 +376,26 @@ int run_integrate(pn_batch* b, int64_t n, const pn_inputs* in, pn_outputs* out, 
     }
   }
   const int64_t stride = b->n_max;
+  const bool ordered = b->p.order == PN_ORDER_LENGTH;
+  if (ordered) {
+    if (!b->d_order) {
+      if (cudaMalloc(&b->d_order, (size_t)b->n_max * sizeof(int64_t)) != cudaSuccess ||
+          cudaMalloc(&b->d_order_key, (size_t)b->n_max * sizeof(float)) != cudaSuccess ||
+          cudaMalloc(&b->d_order_bins, ((size_t)pn::kOrderBins + 1) * sizeof(unsigned long long)) != cudaSuccess) {
+        cudaGetLastError();
+        cudaFree(b->d_order);
+        cudaFree(b->d_order_key);
+        b->d_order = nullptr;
+        b->d_order_key = nullptr;
+        b->d_order_bins = nullptr;
+        return fail(b, PN_E_NOMEM, "order workspace allocation failed");
+      }
+    }
+    a.order = b->d_order;
+  }
+  auto order_on = [&](cudaStream_t s) -> cudaError_t {
+    return ordered ? pn::launch_order(a.in, n, b->d_order, b->d_order_key, b->d_order_bins, s) : cudaSuccess;
+  };
   if (budget > 0 || resume) {
     if (!b->d_rs) {
       if (resume) return fail(b, PN_E_ARG, "resume without a bounded run to continue");
@@ -384,6 +412,10 @@ int run_integrate(pn_batch* b, int64_t n, const pn_inputs* in, pn_outputs* out, 
     a.ri = b->d_ri;
     a.rs_stride = b->n_max;
     if (sh.persistent) PN_CUDA(b, cudaMemsetAsync(b->d_queue, 0, sizeof(unsigned long long), b->stream));
+    {
+      cudaError_t e = order_on(b->stream);
+      if (e != cudaSuccess) return cuda_fail(b, e, "order kernels launch");
+    }
     if (!resume) {
       cudaError_t e = pn::launch_setup(prec, a, b->d_setup, stride, b->stream);
       if (e != cudaSuccess) return cuda_fail(b, e, "set-up kernel launch");
@@ -391,7 +423,9 @@ int run_integrate(pn_batch* b, int64_t n, const pn_inputs* in, pn_outputs* out, 
     return launch_timed_kernel(b, prec, sh, a, stride, b->stream);
   }
   if (!sh.persistent) {
-    cudaError_t e = pn::launch_setup(prec, a, b->d_setup, stride, b->stream);
+    cudaError_t e = order_on(b->stream);
+    if (e != cudaSuccess) return cuda_fail(b, e, "order kernels launch");
+    e = pn::launch_setup(prec, a, b->d_setup, stride, b->stream);
     if (e != cudaSuccess) return cuda_fail(b, e, "set-up kernel launch");
     return launch_timed_kernel(b, prec, sh, a, stride, b->stream);
   }
@@ -401,7 +435,8 @@ int run_integrate(pn_batch* b, int64_t n, const pn_inputs* in, pn_outputs* out, 
     cudaGraph_t g = nullptr;
     PN_CUDA(b, cudaStreamBeginCapture(b->cap_stream, cudaStreamCaptureModeThreadLocal));
     cudaError_t e1 = cudaMemsetAsync(b->d_queue, 0, sizeof(unsigned long long), b->cap_stream);
-    cudaError_t e2 = pn::launch_setup(prec, a, b->d_setup, stride, b->cap_stream);
+    cudaError_t e2 = order_on(b->cap_stream);
+    if (e2 == cudaSuccess) e2 = pn::launch_setup(prec, a, b->d_setup, stride, b->cap_stream);
     // External event record nodes: the events are recorded (and timed) each time the graph runs.
     if (e2 == cudaSuccess) e2 = cudaEventRecordWithFlags(b->kev[0], b->cap_stream, cudaEventRecordExternal);
     if (e2 == cudaSuccess) e2 = pn::launch_integrate_only(prec, true, sh.block, sh.grid, a, b->d_setup, stride, b->cap_stream);

@@ -27,6 +27,7 @@ struct KArgs {
   int32_t* ri;                // saved integrator state, kResumeI int32 per binary (field-major, rs_stride)
   int64_t rs_stride;
   double* land;               // deferred landing moves (set by the launchers: the table's last kLandFields fields)
+  const int64_t* order;       // lanes take binary order[k] as their k-th (nullptr: binary k)
 };
 
 // Saved state of a binary between bounded calls: y[10], f(y)[10], t, h, h_lo,
@@ -36,6 +37,18 @@ constexpr int kResumeD = 24;
 constexpr int kResumeI = 6;
 
 constexpr int kMaxBlock = 256;
+
+// Counting sort into descending key order: in place, bins[k] <- the number of
+// entries with a key above k (nb bins).
+cudaError_t launch_scan_above(unsigned long long* bins, int32_t nb, cudaStream_t s);
+
+// The order in which lanes take the binaries (PN_ORDER_LENGTH): order[0..n) is
+// the permutation of the binaries by their predicted length, longest first.
+// Scratch: key (n floats), bins (kOrderBins + 1 words; the last holds the key
+// range).
+constexpr int kOrderBins = 4096;
+cudaError_t launch_order(const pn_inputs& in, int64_t n, int64_t* order, float* key, unsigned long long* bins,
+                         cudaStream_t s);
 
 // Recording of accepted steps and checkpoints by the forward pass of the adjoint.
 struct RecArgs {

@@ -414,10 +414,11 @@ __device__ __forceinline__ void integrate_body(const KArgs& a, const double* __r
     }
     if (need) {
       if (idx >= 0 && idx < a.n) {
-        have = lane_load<PREC, BOUNDED>(L, a, ws, stride, idx);
+        const int64_t bi = a.order ? a.order[idx] : idx;  // the binary this lane takes
+        have = lane_load<PREC, BOUNDED>(L, a, ws, stride, bi);
         if (RECORD && have)
 #pragma unroll
-          for (int c = 0; c < 10; c++) rec.ck[(size_t)c * rec.stride + idx] = L.y[c];
+          for (int c = 0; c < 10; c++) rec.ck[(size_t)c * rec.stride + bi] = L.y[c];
       }
       if ((!PERSIST && taken >= bpt) || idx >= a.n) exhausted = true;
     }
@@ -861,6 +862,143 @@ cudaError_t launch_stats_segments(int32_t n_seg, const int64_t* off, const pn_in
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   k_stats_total<<<(unsigned)n_seg, 256, 0, s>>>(part, bps, total);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// The order in which lanes take the binaries.  The lanes of a warp run in
+// lock-step, so a warp lasts as long as its longest binary and its lanes take
+// a step decision's branches together only while their binaries behave alike.
+// Binaries sorted by a predicted length, longest first, give a warp binaries of
+// similar length and similar step sequences (and the persistent queue the
+// longest ones first).  The order changes no result: each binary's arithmetic
+// does not depend on its lane.
+// ---------------------------------------------------------------------------
+
+// In place: bins[k] <- the number of entries with a key above k (one block of
+// 1024 threads; nb bins).
+__global__ void __launch_bounds__(1024) k_scan_above(unsigned long long* bins, int32_t nb) {
+  __shared__ unsigned long long warp_tot[32];
+  __shared__ unsigned long long carry;
+  const unsigned lane = threadIdx.x & 31u, wid = threadIdx.x >> 5;
+  if (threadIdx.x == 0) carry = 0;
+  __syncthreads();
+  for (int32_t base = 0; base < nb; base += 1024) {
+    const int32_t r = base + (int32_t)threadIdx.x;  // rank from the top key down
+    const int32_t k = nb - 1 - r;
+    const unsigned long long v = (r < nb) ? bins[k] : 0ull;
+    unsigned long long x = v;  // inclusive scan within the warp
+    for (int d = 1; d < 32; d <<= 1) {
+      const unsigned long long t = __shfl_up_sync(0xffffffffu, x, d);
+      if ((int)lane >= d) x += t;
+    }
+    if (lane == 31u) warp_tot[wid] = x;
+    __syncthreads();
+    if (wid == 0) {
+      unsigned long long w = warp_tot[lane];
+      for (int d = 1; d < 32; d <<= 1) {
+        const unsigned long long t = __shfl_up_sync(0xffffffffu, w, d);
+        if ((int)lane >= d) w += t;
+      }
+      warp_tot[lane] = w;  // inclusive over warps
+    }
+    __syncthreads();
+    const unsigned long long before = carry + (wid ? warp_tot[wid - 1] : 0ull) + x - v;
+    if (r < nb) bins[k] = before;
+    __syncthreads();
+    if (threadIdx.x == 0) carry += warp_tot[31];
+    __syncthreads();
+  }
+}
+
+cudaError_t launch_scan_above(unsigned long long* bins, int32_t nb, cudaStream_t s) {
+  k_scan_above<<<1, 1024, 0, s>>>(bins, nb);
+  return cudaGetLastError();
+}
+
+// Predicted length of binary i: the Newtonian count
+// (omega_0^(-5/3) - omega_f^(-5/3)) / eta, which grows with the number of
+// orbits between the two frequencies, times 1 + 0.1 (S + S.L) + 0.2 S1.S2, with
+// S = |S1| + |S2| and S.L = (S1 + S2).L-hat at the start: spins lengthen the
+// run (along L-hat they slow the chirp) and shorten its steps.  The spin
+// weights are empirical (they sorted sample ensembles' attempt counts best);
+// only the order depends on them.  In FP32; invalid inputs get 0 (they are
+// taken last and finish at once).
+__device__ __forceinline__ float len_key(const pn_inputs& in, int64_t i) {
+  const float m1 = (float)in.m1[i], m2 = (float)in.m2[i];
+  const float S1 = (float)in.chi1[i] * m1 * m1, S2 = (float)in.chi2[i] * m2 * m2;
+  const float lx = (float)in.lx[i], ly = (float)in.ly[i], lz = (float)in.lz[i];
+  const float s1x = (float)in.s1x[i], s1y = (float)in.s1y[i], s1z = (float)in.s1z[i];
+  const float s2x = (float)in.s2x[i], s2y = (float)in.s2y[i], s2z = (float)in.s2z[i];
+  const float sl = S1 * (s1x * lx + s1y * ly + s1z * lz) + S2 * (s2x * lx + s2y * ly + s2z * lz);
+  const float ss = S1 * S2 * (s1x * s2x + s1y * s2y + s1z * s2z);
+  const float nN = (exp2f(-5.0f / 3.0f * log2f((float)in.omega0[i])) -
+                    exp2f(-5.0f / 3.0f * log2f((float)in.omega_f[i]))) / (m1 * m2);
+  const float k = nN * (1.0f + 0.1f * (S1 + S2 + sl) + 0.2f * ss);
+  return (k > 0.0f && k <= 3.4e38f) ? k : 0.0f;
+}
+
+// Keys, and the range of the positive ones: range[0] (set to all ones before)
+// takes the smallest key's bits, range[1] (zero before) the largest's; positive
+// floats order like their bit patterns.
+__global__ void k_len_key(const pn_inputs in, int64_t n, float* key, unsigned int* range) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const float k = len_key(in, i);
+  key[i] = k;
+  const unsigned act = __activemask();
+  const unsigned bits = __float_as_uint(k);
+  const unsigned lo = __reduce_min_sync(act, k > 0.0f ? bits : 0xffffffffu);
+  const unsigned hi = __reduce_max_sync(act, bits);
+  if ((int)(threadIdx.x & 31u) == __ffs(act) - 1) {
+    if (lo != 0xffffffffu) atomicMin(&range[0], lo);
+    atomicMax(&range[1], hi);
+  }
+}
+
+__device__ __forceinline__ int32_t len_bin(float k, const unsigned int* range) {
+  const float lo = __uint_as_float(range[0]), hi = __uint_as_float(range[1]);
+  if (!(k > 0.0f) || !(hi > lo)) return 0;
+  const int32_t b = (int32_t)((k - lo) / (hi - lo) * (float)kOrderBins);
+  return b < 0 ? 0 : (b >= kOrderBins ? kOrderBins - 1 : b);
+}
+
+__global__ void k_len_count(const float* key, int64_t n, const unsigned int* range, unsigned long long* bins) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int32_t b = len_bin(key[i], range);
+  const unsigned peers = __match_any_sync(__activemask(), b);
+  if ((int)(threadIdx.x & 31u) == __ffs(peers) - 1) atomicAdd(&bins[b], (unsigned long long)__popc(peers));
+}
+
+__global__ void k_len_scatter(const float* key, int64_t n, const unsigned int* range, unsigned long long* cursor,
+                              int64_t* order) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int32_t b = len_bin(key[i], range);
+  const unsigned lane = threadIdx.x & 31u;
+  const unsigned peers = __match_any_sync(__activemask(), b);
+  const int leader = __ffs(peers) - 1;
+  unsigned long long base = 0;
+  if ((int)lane == leader) base = atomicAdd(&cursor[b], (unsigned long long)__popc(peers));
+  base = __shfl_sync(peers, base, leader);
+  order[base + __popc(peers & ((1u << lane) - 1u))] = i;
+}
+
+cudaError_t launch_order(const pn_inputs& in, int64_t n, int64_t* order, float* key, unsigned long long* bins,
+                         cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  unsigned int* range = reinterpret_cast<unsigned int*>(bins + kOrderBins);
+  cudaError_t e = cudaMemsetAsync(bins, 0, (size_t)kOrderBins * sizeof(unsigned long long), s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(range, 0xff, sizeof(unsigned int), s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(range + 1, 0, sizeof(unsigned int), s);
+  if (e != cudaSuccess) return e;
+  const unsigned g = (unsigned)((n + 255) / 256);
+  k_len_key<<<g, 256, 0, s>>>(in, n, key, range);
+  k_len_count<<<g, 256, 0, s>>>(key, n, range, bins);
+  e = launch_scan_above(bins, kOrderBins, s);
+  if (e != cudaSuccess) return e;
+  k_len_scatter<<<g, 256, 0, s>>>(key, n, range, bins, order);
   return cudaGetLastError();
 }
 

@@ -72,6 +72,7 @@ def test_defaults_follow_the_paper(native):
     assert p.rtol == 5e-7 and p.atol == 5e-7 and p.h0 == 10.0  # Sec. II
     assert p.term_mask == native.PN_TERM_ALL and p.precision == native.PN_FP64 and p.stop_mode == 0
     assert p.ckpt_every == 64
+    assert p.order == native.PN_ORDER_LENGTH  # lanes take the binaries sorted by predicted length
 
 
 def test_argument_errors_before_any_cuda_call(native):
@@ -83,7 +84,7 @@ def test_argument_errors_before_any_cuda_call(native):
     assert lib.pn_batch_init(C.byref(h), 0, C.byref(p), None) == native.PN_E_ARG
     assert b"n_max" in lib.pn_last_error(None)
     for field, bad in (("atol", 0.0), ("h0", -1.0), ("fac_min", 2.0), ("land_max_iter", 0), ("block", 48),
-                       ("precision", 7), ("term_mask", 0x400), ("bpt", 3)):
+                       ("precision", 7), ("term_mask", 0x400), ("bpt", 3), ("order", 2), ("order", -1)):
         q = native.pn_params()
         lib.pn_params_default(C.byref(q))
         setattr(q, field, bad)
