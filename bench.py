@@ -48,7 +48,7 @@ FP64_DATASHEET_TFLOPS = 1.25  # nominal dense FP64 of one B300
 # DRAM traffic of the integration kernel per binary from an ncu capture
 # (dram__bytes_read.sum + dram__bytes_write.sum, profiles/); valid only while
 # the kernel sources hash (kernel_sha) to the recorded value.
-PROFILED = {"kernel_sha": "9d898a1d093bdc42", "dram_bytes_per_binary": (39.510016e6 + 0.897024e6) / 131072}
+PROFILED = {"kernel_sha": "7389c9c2d71b3a47", "dram_bytes_per_binary": (55.832576e6 + 16.384512e6) / 131072}
 
 
 # Executed floating-point thread instructions per attempt of each integration kernel
@@ -57,7 +57,7 @@ PROFILED = {"kernel_sha": "9d898a1d093bdc42", "dram_bytes_per_binary": (39.51001
 # ncu capture of the 131,072-binary case (profiles/k_integrate_pipes_C1_131072.md): sums of
 # smsp__sass_thread_inst_executed_op_{ffma,fadd,fmul,ffma2,fadd2,fmul2,dfma,dadd,dmul}_pred_on over
 # the launch divided by its attempts.  Valid only while the kernel sources hash to kernel_sha.
-EXECUTED = {"kernel_sha": "9d898a1d093bdc42", "per_attempt": {
+EXECUTED = {"kernel_sha": "7389c9c2d71b3a47", "per_attempt": {
     0: {"ffma": 130.84, "fadd": 397.54, "fmul": 93.55, "ffma2": 0.0, "fadd2": 0.0, "fmul2": 0.0,
         "dfma": 505.94, "dadd": 44.96, "dmul": 242.83},
     1: {"ffma": 318.97, "fadd": 51.53, "fmul": 263.58, "ffma2": 190.0, "fadd2": 395.0, "fmul2": 55.0,
@@ -711,8 +711,9 @@ def main():
                            "parallelism": f"replicas x{world}", "attempts_per_binary": attempts / n,
                            "kernel_sha": sha},
                 "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
-                # per step: k_setup + k_integrate + k_dots (the queue reset is a memset node)
-                "gpu_launches": 3 * args.steps,
+                # per step: the lanes' order (k_len_key, k_len_count, k_scan_above, k_len_scatter) when
+                # on, k_setup, k_integrate_mx, k_dots (the queue reset and the sort's bins are memset nodes)
+                "gpu_launches": (7 if pn.params().order == pn.native.PN_ORDER_LENGTH else 3) * args.steps,
                 "clocks": clocks, "mixed": mixed, "mixed_ds": mixed_ds, "extras": extras,
                 "fp32_fma_peak_tflops": (f32_peak or 0) / 1e12, "fp64_fma_peak_tflops": (f64_peak or 0) / 1e12,
                 "peak_probe_clocks": probe_clocks}

@@ -918,23 +918,26 @@ cudaError_t launch_scan_above(unsigned long long* bins, int32_t nb, cudaStream_t
 
 // Predicted length of binary i: the Newtonian count
 // (omega_0^(-5/3) - omega_f^(-5/3)) / eta, which grows with the number of
-// orbits between the two frequencies, times 1 + 0.1 (S + S.L) + 0.2 S1.S2, with
-// S = |S1| + |S2| and S.L = (S1 + S2).L-hat at the start: spins lengthen the
-// run (along L-hat they slow the chirp) and shorten its steps.  The spin
-// weights are empirical (they sorted sample ensembles' attempt counts best);
-// only the order depends on them.  In FP32; invalid inputs get 0 (they are
-// taken last and finish at once).
+// orbits between the two frequencies, times 1 + 0.2 (S + S.L + |S_perp|), with
+// S = |S1| + |S2| and, for the total spin S1 + S2 at the start, S.L its
+// projection on L-hat and S_perp its part across L-hat: spins lengthen the run
+// (along L-hat they slow the chirp) and shorten its steps (the part across
+// L-hat precesses, and the error control follows it).  The weights are
+// empirical (they sorted sample ensembles' attempt counts best); only the order
+// depends on them.  In FP32; invalid inputs get 0 (they are taken last and
+// finish at once).
 __device__ __forceinline__ float len_key(const pn_inputs& in, int64_t i) {
   const float m1 = (float)in.m1[i], m2 = (float)in.m2[i];
   const float S1 = (float)in.chi1[i] * m1 * m1, S2 = (float)in.chi2[i] * m2 * m2;
   const float lx = (float)in.lx[i], ly = (float)in.ly[i], lz = (float)in.lz[i];
-  const float s1x = (float)in.s1x[i], s1y = (float)in.s1y[i], s1z = (float)in.s1z[i];
-  const float s2x = (float)in.s2x[i], s2y = (float)in.s2y[i], s2z = (float)in.s2z[i];
-  const float sl = S1 * (s1x * lx + s1y * ly + s1z * lz) + S2 * (s2x * lx + s2y * ly + s2z * lz);
-  const float ss = S1 * S2 * (s1x * s2x + s1y * s2y + s1z * s2z);
+  const float tx = S1 * (float)in.s1x[i] + S2 * (float)in.s2x[i];
+  const float ty = S1 * (float)in.s1y[i] + S2 * (float)in.s2y[i];
+  const float tz = S1 * (float)in.s1z[i] + S2 * (float)in.s2z[i];
+  const float tl = tx * lx + ty * ly + tz * lz;
+  const float px = tx - tl * lx, py = ty - tl * ly, pz = tz - tl * lz;
   const float nN = (exp2f(-5.0f / 3.0f * log2f((float)in.omega0[i])) -
                     exp2f(-5.0f / 3.0f * log2f((float)in.omega_f[i]))) / (m1 * m2);
-  const float k = nN * (1.0f + 0.1f * (S1 + S2 + sl) + 0.2f * ss);
+  const float k = nN * (1.0f + 0.2f * (S1 + S2 + tl + sqrtf(px * px + py * py + pz * pz)));
   return (k > 0.0f && k <= 3.4e38f) ? k : 0.0f;
 }
 

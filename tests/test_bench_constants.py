@@ -28,7 +28,10 @@ def test_executed_counts_are_consistent(monkeypatch):
     assert 0.9 * bench.FLOPS_ATTEMPT < f64_0 < 1.0 * bench.FLOPS_ATTEMPT
     f32_2, f64_2 = bench.executed_flops(2)
     assert f64_2 < 0.2 * f64_0 and f32_2 > 5 * bench.FLOPS_ATTEMPT  # double-single: the FP32 pipe does the work
-    assert 250 < bench.PROFILED["dram_bytes_per_binary"] < 400
+    # The 37-double set-up table read once (296 B) and the 128-byte results written once, plus part
+    # of the deferred landing moves; with the lanes' length order the table rows and the results are
+    # touched in scattered order, so whole 32-byte sectors move for 8-byte values.
+    assert 250 < bench.PROFILED["dram_bytes_per_binary"] < 700
 
 
 def test_paper_sweep_ensembles():
