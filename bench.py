@@ -681,7 +681,7 @@ def main():
                                 "workload": "65,536 binaries, q ~ U[1,4], chi = 1, omega 0.01 -> 0.05; "
                                             "d(S1-hat.S2-hat final)/d(S1-hat, S2-hat, q), checkpoint every 64"}
         extras["adjoint_C4_ds_sweep"] = {"value": aggregate_rate(world, n4, 1, ms4ds), "unit": "gradients/s",
-                                         "ms": ms4ds, "sweep": "double-single reverse sweep (FP64 forward record)"}
+                                         "ms": ms4ds, "sweep": "double-single recording pass and reverse sweep"}
 
     nvtx.range_pop()
     cpu = None

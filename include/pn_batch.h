@@ -354,12 +354,14 @@ int pn_batch_autotune(pn_batch *b, int64_t n, const pn_inputs *in, pn_outputs *s
  * step sizes and a checkpoint every params.ckpt_every accepted steps in
  * library-owned device memory (grown on demand), then sweeps backwards one
  * checkpoint segment at a time, recomputing the segment's states.  Requires
- * PN_STOP_LAND and adaptive steps.  The forward pass is always FP64; with
- * precision PN_FP64 the backward sweep is FP64, with PN_MIXED_DS it runs in
- * double-single arithmetic on the FP32 pipe (faster; gradients within ~1e-8
- * relative of the FP64 sweep's); PN_MIXED is refused.  Binaries whose status
- * is not PN_ST_OK get NaN gradients.  If out is not NULL the forward outputs
- * are written there too.  Errors: PN_E_ARG, PN_E_NOMEM, PN_E_CUDA,
+ * PN_STOP_LAND and adaptive steps.  With precision PN_FP64 the forward pass
+ * and the backward sweep are FP64; with PN_MIXED_DS both run in double-single
+ * arithmetic on the FP32 pipe, the forward pass being pn_batch_integrate's
+ * PN_MIXED_DS attempt (faster; gradients within ~1e-8 relative of the FP64
+ * ones, the same steps taken); PN_MIXED is refused.  The forward pass takes
+ * the binaries in params.order, as pn_batch_integrate does.  Binaries whose
+ * status is not PN_ST_OK get NaN gradients.  If out is not NULL the forward
+ * outputs are written there too (in PN_MIXED_DS, the double-single run's).  Errors: PN_E_ARG, PN_E_NOMEM, PN_E_CUDA,
  * PN_E_UNIMPLEMENTED (other modes). */
 int pn_batch_adjoint(pn_batch *b, int64_t n, const pn_inputs *in, const pn_cotangents *gbar,
                      pn_grads *grad, pn_outputs *out);

@@ -1,4 +1,5 @@
-// pn_adjoint.cu -- reverse mode (discrete adjoint) of the FP64 integration.
+// pn_adjoint.cu -- reverse mode (discrete adjoint) of the integration (FP64,
+// or double-single for pn_batch_adjoint with PN_MIXED_DS).
 //
 // Gradients of the loss sum_i gbar_i . out_i (final dot products, S1, S2,
 // L-hat, t of each binary) with respect to the initial spin directions and the
@@ -9,7 +10,8 @@
 // nu = d omega5/dh the cotangent passed back through the landing step is
 // ybar_f - (mu/nu) e_omega (two reverse sweeps of that step).
 //
-// The forward pass (k_integrate with recording) keeps the accepted step sizes
+// The forward pass (k_integrate with recording, in the sweep's precision, the
+// lanes taking the binaries in the batch's order) keeps the accepted step sizes
 // and the state every `every` accepted steps.  The reverse sweep takes one
 // such segment at a time: it recomputes the segment's steps from its
 // checkpoint with the forward kernel's stage arithmetic, keeping each step's
@@ -302,9 +304,9 @@ __device__ double dp5_step_vjp(const Coef<double>& c, const float* __restrict__ 
 // pairs of FP32 (~48-bit significands) on the FP32 pipe, each line undoing the
 // matching line of the forward pass as in rhs64_vjp.  Constants that are not
 // exact in FP32 enter as double-single pairs.  The recorded step sizes and
-// checkpoints are the FP64 forward run's; the states between checkpoints are
-// recomputed with double-single stage sums and FP64 state accumulation, so the
-// gradient is evaluated within ~1e-13 of the FP64 trajectory.  Products are the
+// checkpoints are the double-single forward run's (the FP64 run's steps, its
+// states within ~1e-13); the states between checkpoints are recomputed with
+// double-single stage sums and FP64 state accumulation.  Products are the
 // lazy (unnormalized) ones of the forward kernel; sums keep their
 // renormalization.
 // ---------------------------------------------------------------------------

@@ -346,6 +346,24 @@ static int launch_timed_kernel(pn_batch* b, int prec, const Shape& sh, const KAr
   return PN_OK;
 }
 
+// The lanes' order of the binaries (PN_ORDER_LENGTH) and its sort workspace,
+// allocated on first use (n_max entries).
+static int ensure_order(pn_batch* b) {
+  if (b->d_order) return PN_OK;
+  if (cudaMalloc(&b->d_order, (size_t)b->n_max * sizeof(int64_t)) != cudaSuccess ||
+      cudaMalloc(&b->d_order_key, (size_t)b->n_max * sizeof(float)) != cudaSuccess ||
+      cudaMalloc(&b->d_order_bins, ((size_t)pn::kOrderBins + 1) * sizeof(unsigned long long)) != cudaSuccess) {
+    cudaGetLastError();
+    cudaFree(b->d_order);
+    cudaFree(b->d_order_key);
+    b->d_order = nullptr;
+    b->d_order_key = nullptr;
+    b->d_order_bins = nullptr;
+    return fail(b, PN_E_NOMEM, "order workspace allocation failed");
+  }
+  return PN_OK;
+}
+
 // Launch one integration of n binaries with the given shape on b->stream.
 // The persistent shape goes through a CUDA graph (queue reset + kernel),
 // captured on a private stream and re-used while the arguments repeat.
@@ -378,19 +396,8 @@ int run_integrate(pn_batch* b, int64_t n, const pn_inputs* in, pn_outputs* out, 
   const int64_t stride = b->n_max;
   const bool ordered = b->p.order == PN_ORDER_LENGTH;
   if (ordered) {
-    if (!b->d_order) {
-      if (cudaMalloc(&b->d_order, (size_t)b->n_max * sizeof(int64_t)) != cudaSuccess ||
-          cudaMalloc(&b->d_order_key, (size_t)b->n_max * sizeof(float)) != cudaSuccess ||
-          cudaMalloc(&b->d_order_bins, ((size_t)pn::kOrderBins + 1) * sizeof(unsigned long long)) != cudaSuccess) {
-        cudaGetLastError();
-        cudaFree(b->d_order);
-        cudaFree(b->d_order_key);
-        b->d_order = nullptr;
-        b->d_order_key = nullptr;
-        b->d_order_bins = nullptr;
-        return fail(b, PN_E_NOMEM, "order workspace allocation failed");
-      }
-    }
+    const int rc = ensure_order(b);
+    if (rc != PN_OK) return rc;
     a.order = b->d_order;
   }
   auto order_on = [&](cudaStream_t s) -> cudaError_t {
@@ -740,6 +747,8 @@ extern "C" int pn_batch_adjoint(pn_batch* b, int64_t n, const pn_inputs* in, con
     }
   }
   const int every = b->p.ckpt_every;
+  // The recording pass runs in the sweep's precision: FP64, or double-single for the double-single sweep.
+  const int fprec = ds_sweep ? PN_MIXED_DS : PN_FP64;
   KArgs a;
   std::memset(&a, 0, sizeof(a));
   a.in = *in;
@@ -748,7 +757,13 @@ extern "C" int pn_batch_adjoint(pn_batch* b, int64_t n, const pn_inputs* in, con
   a.queue = b->d_queue;
   a.tabf = b->d_tab;
   a.ctl = make_ctl(b->p);
+  if (b->p.order == PN_ORDER_LENGTH) {  // lanes take the binaries longest first, as in pn_batch_integrate
+    const int rc = ensure_order(b);
+    if (rc != PN_OK) return rc;
+    a.order = b->d_order;
+  }
   PN_CUDA(b, cudaEventRecord(b->ev[4], b->stream));
+  if (a.order) PN_CUDA(b, pn::launch_order(a.in, n, b->d_order, b->d_order_key, b->d_order_bins, b->stream));
 
   // Forward pass recording the accepted steps; grow the record and rerun if a
   // binary needed more steps than it holds.
@@ -780,13 +795,13 @@ extern "C" int pn_batch_adjoint(pn_batch* b, int64_t n, const pn_inputs* in, con
     rec.every = every;
     const int block = 128;
     int per_sm = 0;
-    PN_CUDA(b, pn::record_occupancy(block, &per_sm));
+    PN_CUDA(b, pn::record_occupancy(fprec, block, &per_sm));
     const int64_t full = (n + block - 1) / block, capg = (int64_t)b->num_sms * (per_sm > 0 ? per_sm : 1);
     const int grid = (int)(full < capg ? full : capg);
     PN_CUDA(b, cudaMemsetAsync(b->d_overflow, 0, sizeof(int), b->stream));
     PN_CUDA(b, cudaMemsetAsync(b->d_queue, 0, sizeof(unsigned long long), b->stream));
-    PN_CUDA(b, pn::launch_setup(PN_FP64, a, b->d_setup, b->n_max, b->stream));
-    PN_CUDA(b, pn::launch_integrate_record(a, b->d_setup, b->n_max, rec, block, grid, b->stream));
+    PN_CUDA(b, pn::launch_setup(fprec, a, b->d_setup, b->n_max, b->stream));
+    PN_CUDA(b, pn::launch_integrate_record(fprec, a, b->d_setup, b->n_max, rec, block, grid, b->stream));
     int overflow = 0;
     PN_CUDA(b, cudaMemcpyAsync(&overflow, b->d_overflow, sizeof(int), cudaMemcpyDeviceToHost, b->stream));
     PN_CUDA(b, cudaStreamSynchronize(b->stream));

@@ -59,10 +59,11 @@ struct RecArgs {
   int32_t cap, every;
 };
 
-// The recording forward pass of the adjoint (k_integrate<FP64, persistent, RECORD>).
-cudaError_t launch_integrate_record(const KArgs& a, const double* ws, int64_t stride, const RecArgs& rec, int block,
-                                    int grid, cudaStream_t s);
-cudaError_t record_occupancy(int block, int* blocks_per_sm);
+// The recording forward pass of the adjoint (k_integrate<prec, persistent, RECORD>),
+// prec PN_FP64 or PN_MIXED_DS.
+cudaError_t launch_integrate_record(int prec, const KArgs& a, const double* ws, int64_t stride, const RecArgs& rec,
+                                    int block, int grid, cudaStream_t s);
+cudaError_t record_occupancy(int prec, int block, int* blocks_per_sm);
 
 // Set-up table: setup_fields() doubles per binary, field-major with the given stride (>= n): the
 // kSetupFields set-up fields (16 coefficients, y0, k1 = f(y0), omega_f), then kLandFields fields for

@@ -15,8 +15,9 @@
 // Inputs and outputs are structure-of-arrays: lane i touches element i of
 // each array, so every load and store of a warp is one coalesced 256-byte
 // transaction.  All three precisions keep their stage rates in a per-thread
-// shared-memory workspace (k_integrate_mx; k_integrate is the adjoint's FP64
-// recording pass), so their stage loops stay small: one right-hand-side copy.
+// shared-memory workspace (k_integrate_mx; k_integrate is the adjoint's recording
+// pass, FP64 or double-single), so their stage loops stay small: one
+// right-hand-side copy.
 
 #include <cmath>
 
@@ -448,9 +449,9 @@ __device__ __forceinline__ void integrate_body(const KArgs& a, const double* __r
   }
 }
 
-// The recording pass of the adjoint (FP64, persistent, RECORD): the FP64
-// attempt with its rates in the dynamic shared-memory workspace, as in
-// k_integrate_mx<0>.
+// The recording pass of the adjoint (persistent, RECORD): PREC 0 the FP64
+// attempt, PREC 2 the double-single one, each with its rates in the dynamic
+// shared-memory workspace as in k_integrate_mx<PREC>.
 template <int PREC, bool PERSIST, bool RECORD = false, bool BOUNDED = false>
 __global__ void __launch_bounds__(kMaxBlock) k_integrate(const KArgs a, const double* __restrict__ ws, int64_t stride,
                                                          const RecArgs rec = RecArgs{}) {
@@ -541,8 +542,9 @@ static size_t integrate_smem(int prec, int block) {
 }
 
 cudaError_t prepare_integrate_kernels() {
-  const void* ds[4] = {(const void*)k_integrate_mx<2, true>, (const void*)k_integrate_mx<2, false>,
-                       (const void*)k_integrate_mx<2, true, true>, (const void*)k_integrate_mx<2, false, true>};
+  const void* ds[5] = {(const void*)k_integrate_mx<2, true>, (const void*)k_integrate_mx<2, false>,
+                       (const void*)k_integrate_mx<2, true, true>, (const void*)k_integrate_mx<2, false, true>,
+                       (const void*)k_integrate<2, true, true>};
   const void* f32[4] = {(const void*)k_integrate_mx<1, true>, (const void*)k_integrate_mx<1, false>,
                         (const void*)k_integrate_mx<1, true, true>, (const void*)k_integrate_mx<1, false, true>};
   for (const void* f : ds) {
@@ -610,17 +612,21 @@ cudaError_t integrate_occupancy(int prec, bool persistent, int block, int* block
                                                        integrate_smem(prec, block));
 }
 
-cudaError_t launch_integrate_record(const KArgs& a, const double* ws, int64_t stride, const RecArgs& rec, int block,
-                                    int grid, cudaStream_t s) {
+cudaError_t launch_integrate_record(int prec, const KArgs& a, const double* ws, int64_t stride, const RecArgs& rec,
+                                    int block, int grid, cudaStream_t s) {
   if (grid <= 0) return cudaSuccess;
-  k_integrate<0, true, true><<<grid, block, integrate_smem(PN_FP64, block), s>>>(with_land(a, ws, stride), ws, stride,
-                                                                                 rec);
+  const KArgs al = with_land(a, ws, stride);
+  if (prec == PN_MIXED_DS) k_integrate<2, true, true><<<grid, block, integrate_smem(prec, block), s>>>(al, ws, stride, rec);
+  else k_integrate<0, true, true><<<grid, block, integrate_smem(PN_FP64, block), s>>>(al, ws, stride, rec);
   const cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   return launch_dots(a.out, a.n, ws, stride, s);
 }
 
-cudaError_t record_occupancy(int block, int* blocks_per_sm) {
+cudaError_t record_occupancy(int prec, int block, int* blocks_per_sm) {
+  if (prec == PN_MIXED_DS)
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, (const void*)k_integrate<2, true, true>, block,
+                                                         integrate_smem(prec, block));
   return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, (const void*)k_integrate<0, true, true>, block,
                                                        integrate_smem(PN_FP64, block));
 }
