@@ -580,6 +580,19 @@ def main():
     extras = None
     if not args.no_extras:
         extras = {}
+        # The headline ensemble at fixed schedules: the plain FP64 kernel against the persistent
+        # double-single one (the mixed form at the 1e-6 dot bar, in the persistent schedule).
+        c1_shapes = {}
+        for key, prec, sched, block in (("fp64_plain", 0, 1, 256), ("mixed_ds_persistent", 2, 2, 128)):
+            with pn.Batch(n, pn.params(precision=prec, schedule=sched, block=block)) as b:
+                rate_ms, _, _ = timed_run(b, args.steps, 1)
+            rate_ms = max_over_ranks(rate_ms)
+            c1_shapes[key] = {"value": aggregate_rate(world, n, args.steps, rate_ms), "unit": "inspirals/s",
+                              "ms_per_step": rate_ms / args.steps, "block": block,
+                              "schedule": {1: "plain", 2: "persistent"}[sched]}
+        c1_shapes["mixed_ds_persistent"]["speedup_vs_fp64_plain"] = (
+            c1_shapes["mixed_ds_persistent"]["value"] / c1_shapes["fp64_plain"]["value"])
+        extras["C1_fixed_schedules"] = c1_shapes
         c2 = workloads.config("C2", seed=workloads.SEED_BASE + 2 + 1000 * rank)
         n2 = c2["m1"].shape[0]
         inp2 = pn.to_device(c2, device=dev)
