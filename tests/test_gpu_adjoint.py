@@ -79,17 +79,19 @@ def test_adjoint_full_size_subsample(pn, orc):
     assert rel_err(got[:, idx], ref) < GRAD_TOL
 
 
-def test_recording_pass_outputs_equal_plain_integration(pn):
-    """The adjoint's recording forward pass (its own kernel) integrates exactly as pn_batch_integrate:
-    its outputs are bit-identical, landing moves and output dot products included."""
+@pytest.mark.parametrize("precision", [0, 2])
+def test_recording_pass_outputs_equal_plain_integration(pn, precision):
+    """The adjoint's recording forward pass (its own kernel, in the sweep's precision) integrates exactly
+    as pn_batch_integrate in that precision: its outputs are bit-identical, landing moves and output dot
+    products included."""
     import torch
     ens = workloads.config("C4", n=3000, seed=905)
     inp = pn.to_device(ens)
-    plain = pn.to_numpy(pn.integrate(inp))
+    plain = pn.to_numpy(pn.integrate(inp, precision=precision))
     cot = {"dot_s1s2": torch.ones(3000, dtype=torch.float64, device="cuda")}
     grads = {f: torch.empty(3000, dtype=torch.float64, device="cuda") for f in pn.native.GRAD_FIELDS}
     out = pn.alloc_outputs(3000)
-    with pn.Batch(3000) as b:
+    with pn.Batch(3000, pn.params(precision=precision)) as b:
         pn.pn_batch_adjoint(b.handle, 3000, inp, cot, grads, outputs=out)
         torch.cuda.synchronize()
     rec = pn.to_numpy(out)
