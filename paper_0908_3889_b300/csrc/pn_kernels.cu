@@ -429,13 +429,13 @@ __device__ __forceinline__ void integrate_body(const KArgs& a, const double* __r
       double s;
       if constexpr (PREC == 2)
         s = dp5_attempt_ds(L.cf, tb, a.ctl, L.y, L.k1, L.h, y5, k7,
-                           DsWork{reinterpret_cast<ulonglong2*>(s_dsw), (int)blockDim.x, (int)threadIdx.x});
+                           DsWork{warp_tile_base<ulonglong2, kDsVectors * 5>(s_dsw)});
       else if constexpr (PREC == 1)
         s = dp5_attempt_f32(L.cf.c32, a.ctl, L.y, L.k1, L.h, y5, k7,
-                            F32Work{reinterpret_cast<f2*>(s_dsw), (int)blockDim.x, (int)threadIdx.x});
+                            F32Work{warp_tile_base<f2, kF32WorkBytes / 8>(s_dsw)});
       else
         s = dp5_attempt_ws(L.cf, tb, a.ctl, L.y, L.k1, L.h, y5, k7,
-                           F64Work{reinterpret_cast<double*>(s_dsw), (int)blockDim.x, (int)threadIdx.x});
+                           F64Work{warp_tile_base<double, kF64WorkBytes / 8>(s_dsw)});
       L.attempts++;
       int32_t st;
       if (lane_decide<RECORD>(L, a.ctl, y5, k7, s, &st, rec, a.land, stride)) {
