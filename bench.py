@@ -48,7 +48,7 @@ FP64_DATASHEET_TFLOPS = 1.25  # nominal dense FP64 of one B300
 # DRAM traffic of the integration kernel per binary from an ncu capture
 # (dram__bytes_read.sum + dram__bytes_write.sum, profiles/); valid only while
 # the kernel sources hash (kernel_sha) to the recorded value.
-PROFILED = {"kernel_sha": "ea539e7889fd9474", "dram_bytes_per_binary": (55.890e6 + 16.371e6) / 131072}
+PROFILED = {"kernel_sha": "e314df376c8c2352", "dram_bytes_per_binary": (55.632e6 + 16.416e6) / 131072}
 
 
 # Executed floating-point thread instructions per attempt of each integration kernel
@@ -57,10 +57,10 @@ PROFILED = {"kernel_sha": "ea539e7889fd9474", "dram_bytes_per_binary": (55.890e6
 # ncu capture of the 131,072-binary case (profiles/k_integrate_pipes_C1_131072.md): sums of
 # smsp__sass_thread_inst_executed_op_{ffma,fadd,fmul,ffma2,fadd2,fmul2,dfma,dadd,dmul}_pred_on over
 # the launch divided by its attempts.  Valid only while the kernel sources hash to kernel_sha.
-EXECUTED = {"kernel_sha": "ea539e7889fd9474", "per_attempt": {
-    0: {"ffma": 130.84, "fadd": 397.54, "fmul": 93.55, "ffma2": 0.0, "fadd2": 0.0, "fmul2": 0.0,
+EXECUTED = {"kernel_sha": "e314df376c8c2352", "per_attempt": {
+    0: {"ffma": 130.84, "fadd": 397.46, "fmul": 93.55, "ffma2": 0.0, "fadd2": 0.0, "fmul2": 0.0,
         "dfma": 505.94, "dadd": 44.96, "dmul": 242.83},
-    1: {"ffma": 318.97, "fadd": 51.53, "fmul": 263.58, "ffma2": 190.0, "fadd2": 395.0, "fmul2": 55.0,
+    1: {"ffma": 318.97, "fadd": 51.45, "fmul": 263.58, "ffma2": 190.0, "fadd2": 395.0, "fmul2": 55.0,
         "dfma": 15.97, "dadd": 10.96, "dmul": 10.91},
     2: {"ffma": 1252.84, "fadd": 2745.46, "fmul": 516.83, "ffma2": 495.0, "fadd2": 1090.0, "fmul2": 165.0,
         "dfma": 45.94, "dadd": 60.96, "dmul": 18.83}},
@@ -599,7 +599,8 @@ def main():
         out2 = pn.alloc_outputs(n2, dev)
         for name, sched in (("plain", 1), ("persistent", 2)):
             for prec, pname in ((0, "fp64"), (2, "mixed_ds")):
-                with pn.Batch(n2, pn.params(precision=prec, schedule=sched, block=256)) as b:
+                blk2 = 256 if prec == 0 else 128  # each precision's best block (double-single: 3 blocks per SM)
+                with pn.Batch(n2, pn.params(precision=prec, schedule=sched, block=blk2)) as b:
                     b.integrate(inp2, out2)
                     torch.cuda.synchronize()
                     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -610,7 +611,7 @@ def main():
                     ms2 = max_over_ranks(e0.elapsed_time(e1))
                     st2 = b.stats(inp2, out2)
                 extras[f"uneven_C2_{pname}_{name}"] = {"value": aggregate_rate(world, n2, 1, ms2),
-                                                      "unit": "inspirals/s", "ms": ms2,
+                                                      "unit": "inspirals/s", "ms": ms2, "block": blk2,
                                                       "accepted_steps_min_max": [st2["acc_min"], st2["acc_max"]],
                                                       "attempts_min_max": [st2["attempts_min"], st2["attempts_max"]]}
         del inp2, out2
