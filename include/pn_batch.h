@@ -353,7 +353,11 @@ int pn_batch_autotune(pn_batch *b, int64_t n, const pn_inputs *in, pn_outputs *s
  * solves omega(h*) = omega_f).  Runs the forward pass, records the accepted
  * step sizes and a checkpoint every params.ckpt_every accepted steps in
  * library-owned device memory (grown on demand), then sweeps backwards one
- * checkpoint segment at a time, recomputing the segment's states.  Requires
+ * checkpoint segment at a time, recomputing the segment's states.  Each lane
+ * of the sweep (at most a few tens of thousands on one GPU) keeps the
+ * recomputed segment: ckpt_every x 306 doubles in the FP64 sweep (the stage
+ * states with the right-hand side's intermediate values, ~6 GB for a full
+ * B300 grid at the default stride), ckpt_every x 60 in the double-single one.  Requires
  * PN_STOP_LAND and adaptive steps.  With precision PN_FP64 the forward pass
  * and the backward sweep are FP64; with PN_MIXED_DS both run in double-single
  * arithmetic on the FP32 pipe, the forward pass being pn_batch_integrate's

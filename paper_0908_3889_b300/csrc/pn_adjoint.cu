@@ -23,10 +23,11 @@
 //    the binaries are first ordered by N (counting sort, longest first), and
 //    each warp claims 32 consecutive entries of that order: its lanes walk the
 //    same segments and steps in lock-step, and the longest binaries start first.
-//  - The stage states go to a lane-private segment buffer (every x 60 doubles
-//    per lane, lane-contiguous so the warp's accesses coalesce).  The reverse
-//    step then runs no forward stage: each stage costs one rhs64_vjp, which
-//    hands back the stage rate for the step-size cotangent as well.
+//  - The stage states go to a lane-private segment buffer (lane-contiguous so
+//    the warp's accesses coalesce), in the FP64 sweep with the right-hand
+//    side's intermediates at each of them.  The reverse step then runs no
+//    forward stage: each stage costs the reverse half of one rhs64_vjp, which
+//    hands back the kept stage rate for the step-size cotangent as well.
 
 #include "pn_device.cuh"
 #include "pn_adjoint.h"
@@ -36,10 +37,14 @@ namespace {
 
 // ---------------------------------------------------------------------------
 // Reverse mode (adjoint) of the FP64 right-hand side.
-// rhs64_vjp recomputes rhs64's intermediates at y and returns
-//   yb = (df/dy)^T fb   and adds (df/dc)^T fb to cb (the 16 coefficients),
-// each line of the reverse sweep undoing one line of rhs64, in reverse order;
-// it also returns f = f(y) itself (the stage rate k_s the step-size cotangent needs).
+// The segment recompute evaluates rhs64 at every stage state and keeps its
+// intermediate values (rhs64's keep sink, KeepIdx order) beside the state, so
+// the reverse sweep of one stage runs only the reverse half: rhs64_vjp returns
+//   yb = (df/dy)^T fb   and adds (df/dc)^T fb to cb,
+// each line undoing one line of rhs64 in reverse order, and also returns the
+// kept rate f = f(y) (the stage rate the step-size cotangent needs).  c and cb
+// are in rhs64's folded form (fold_K: the eleven coefficients of P times K);
+// unfold_cotangents maps cb to the coefficients of make_coef at the end.
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ void cross_vjp(const double* a, const double* b, const double* cb_, double* ab, double* bb) {
   // c = a x b:  ab += b x cb,  bb += cb x a
@@ -51,52 +56,36 @@ __device__ __forceinline__ void cross_vjp(const double* a, const double* b, cons
   bb[2] += cb_[0] * a[1] - cb_[1] * a[0];
 }
 
-__device__ __noinline__ void rhs64_vjp(const Coef<double>& c,
-                                       const float* __restrict__ tabf, const double* y, const double* fb, double* yb,
-                                       Coef<double>& cb, double* f) {
-  // ---- forward (as rhs64) ----
+static_assert(kF64StageWords == 10 + KP_COUNT, "an FP64 stage block is the state and rhs64's kept values");
+
+// Stores rhs64's intermediates to kp[k * ss] (the lane's segment buffer).
+struct SegKeep {
+  double* kp;
+  size_t ss;
+  __device__ __forceinline__ void operator()(int k, double x) const { kp[(size_t)k * ss] = x; }
+};
+
+__device__ __noinline__ void rhs64_vjp(const Coef<double>& c, const double* kp, size_t ss, const double* y,
+                                       const double* fb, double* yb, Coef<double>& cb, double* f) {
+  // ---- the kept forward values ----
   const double w = y[0];
   const double S1[3] = {y[1], y[2], y[3]}, S2[3] = {y[4], y[5], y[6]}, L[3] = {y[7], y[8], y[9]};
-  double r = inv_cbrt(w);
-  if ((hi32(w) & 0x7fffffffu) - (897u << 20) >= ((1151u - 897u) << 20)) r = dnan();
-  const double r2 = r * r;
-  const double v = w * r2;
-  const double v2 = v * v;
-  const double lw = log_w(w, tabf);
-  const double LS1 = L[0] * S1[0] + L[1] * S1[1] + L[2] * S1[2];
-  const double LS2 = L[0] * S2[0] + L[1] * S2[1] + L[2] * S2[2];
-  const double S12 = S1[0] * S2[0] + S1[1] * S2[1] + S1[2] * S2[2];
-  const double so = fma(c.w1, LS1, fma(c.w2, LS2, -c.tail));
-  const double c2p = fma(c.ss721, LS1 * LS2, fma(-c.ss247, S12, c.c2));
-  const double c3p = fma(c.clog, lw, c.c3l);
-  const double P6 = fma(v, c.c35, c3p);
-  const double P5 = fma(v, P6, c.c25);
-  const double P4 = fma(v, P5, c2p);
-  const double P3 = fma(v, P4, -so);
-  const double P2 = fma(v, P3, c.c1);
-  const double P = fma(v2, P2, 1.0);
-  const double w2 = w * w;
-  const double Q = (w2 * w) * v2;
-  // Eq. (4): Omega_i = pre U_i, U_1 = q1 L + S2, q1 = a1 r - 3 LS2 (1 <-> 2); dS_i/dt = pre (U_i x S_i).
-  const double pre = c.prec * w2;
-  const double q1 = fma(c.a1, r, -3.0 * LS2), q2 = fma(c.a2, r, -3.0 * LS1);
+  const double r = kp[KP_R * ss], v = kp[KP_V * ss], v2 = kp[KP_V2 * ss], lw = kp[KP_LW * ss];
+  const double LS1 = kp[KP_LS1 * ss], LS2 = kp[KP_LS2 * ss], S12 = kp[KP_S12 * ss];
+  const double P6 = kp[KP_P6 * ss], P5 = kp[KP_P5 * ss], P4 = kp[KP_P4 * ss], P3 = kp[KP_P3 * ss];
+  const double P2 = kp[KP_P2 * ss], P = kp[KP_P * ss], w2 = kp[KP_W2 * ss], Q = kp[KP_Q * ss];
+  const double q1 = kp[KP_Q1 * ss], q2 = kp[KP_Q2 * ss], pre = kp[KP_PRE * ss], lf = kp[KP_LF * ss];
   double U1[3], U2[3], X1[3], X2[3], d1[3], d2[3];
   for (int k = 0; k < 3; k++) {
-    U1[k] = fma(q1, L[k], S2[k]);
-    U2[k] = fma(q2, L[k], S1[k]);
+    U1[k] = kp[(KP_U1 + k) * ss];
+    U2[k] = kp[(KP_U2 + k) * ss];
+    X1[k] = kp[(KP_X1 + k) * ss];
+    X2[k] = kp[(KP_X2 + k) * ss];
   }
-  X1[0] = U1[1] * S1[2] - U1[2] * S1[1]; X1[1] = U1[2] * S1[0] - U1[0] * S1[2]; X1[2] = U1[0] * S1[1] - U1[1] * S1[0];
-  X2[0] = U2[1] * S2[2] - U2[2] * S2[1]; X2[1] = U2[2] * S2[0] - U2[0] * S2[2]; X2[2] = U2[0] * S2[1] - U2[1] * S2[0];
+  for (int k = 0; k < 10; k++) f[k] = kp[(KP_F + k) * ss];
   for (int k = 0; k < 3; k++) {
-    d1[k] = pre * X1[k];
-    d2[k] = pre * X2[k];
-  }
-  const double lf = v * c.nie;
-  f[0] = (Q * c.K) * P;
-  for (int k = 0; k < 3; k++) {
-    f[1 + k] = d1[k];
-    f[4 + k] = d2[k];
-    f[7 + k] = lf * (d1[k] + d2[k]);
+    d1[k] = f[1 + k];
+    d2[k] = f[4 + k];
   }
   // ---- reverse ----
   double S1b[3] = {0, 0, 0}, S2b[3] = {0, 0, 0}, Lb[3] = {0, 0, 0};
@@ -131,16 +120,16 @@ __device__ __noinline__ void rhs64_vjp(const Coef<double>& c,
   double LS2b = -3.0 * q1b, LS1b = -3.0 * q2b;
   double w2b = preb * c.prec;  // pre = prec w2
   cb.prec += preb * w2;
-  const double f0b = fb[0];  // f0 = Q K P
-  const double Qb = f0b * c.K * P;
-  cb.K += f0b * Q * P;
-  const double Pb = f0b * Q * c.K;
+  const double f0b = fb[0];  // f0 = Q P (P carries K)
+  const double Qb = f0b * P;
+  const double Pb = f0b * Q;
   w2b += Qb * w * v2;  // Q = w2 w v2
   double wb = Qb * w2 * v2;
   double v2b = Qb * w2 * w;
   wb += 2.0 * w * w2b;  // w2 = w^2
-  v2b += Pb * P2;       // P = v2 P2 + 1
+  v2b += Pb * P2;       // P = v2 P2 + K
   const double P2b = Pb * v2;
+  cb.K += Pb;
   vb += P2b * P3;       // P2 = v P3 + c1
   const double P3b = P2b * v;
   cb.c1 += P2b;
@@ -175,6 +164,7 @@ __device__ __noinline__ void rhs64_vjp(const Coef<double>& c,
     S1b[k] += LS1b * L[k] + S12b * S2[k];
     S2b[k] += LS2b * L[k] + S12b * S1[k];
   }
+  const double r2 = r * r;
   const double r3 = r2 * r;  // = 1/w
   wb += lwb * r3;            // lw = ln|w|
   vb += 2.0 * v * v2b;       // v2 = v^2
@@ -187,6 +177,20 @@ __device__ __noinline__ void rhs64_vjp(const Coef<double>& c,
     yb[4 + k] = S2b[k];
     yb[7 + k] = Lb[k];
   }
+}
+
+// Cotangents of rhs64's folded coefficients (fold_K: c'_i = K c_i for the eleven
+// coefficients of P) mapped, in place, to those of make_coef's c: c_i-bar =
+// K c'_i-bar and K-bar += sum_i c_i c'_i-bar.
+__device__ __forceinline__ void unfold_cotangents(const Coef<double>& c, Coef<double>& b) {
+  double* const bf[11] = {&b.w1, &b.w2, &b.tail, &b.ss247, &b.ss721, &b.c1, &b.c2, &b.c25, &b.c35, &b.c3l, &b.clog};
+  const double cv[11] = {c.w1, c.w2, c.tail, c.ss247, c.ss721, c.c1, c.c2, c.c25, c.c35, c.c3l, c.clog};
+  double kb = b.K;
+  for (int i = 0; i < 11; i++) {
+    kb += cv[i] * *bf[i];
+    *bf[i] *= c.K;
+  }
+  b.K = kb;
 }
 
 // Reverse mode of make_coef: (m1b, m2b) += (dc/dm)^T cb, from the closed forms
@@ -234,15 +238,17 @@ __constant__ double c_dp_B[6] = {DP_B1, 0.0, DP_B3, DP_B4, DP_B5, DP_B6};
 
 // One Dormand-Prince step y -> y5 with a fixed h (the map the accepted steps
 // apply; same FP64 arithmetic as the forward kernel's stages, so c holds the
-// coefficients with K folded in, as there), writing the six
-// stage states Y_0 = y, ..., Y_5 to sp[(10 s + k) * ss].  With y5 == nullptr
-// only the stage states are made (the last rate k_6 is then not needed).
+// coefficients with K folded in, as there).  Stage s's block of the step's
+// segment words (kF64StageWords words at sp[kF64StageWords s * ss]) holds the
+// stage state Y_s (words 0..9) and the intermediates of rhs64 at Y_s that the
+// reverse sweep needs (words 10.., KeepIdx order), the rate f(Y_s) among them.
+// With y5 == nullptr the step's result is not formed.
 __device__ __forceinline__ void dp5_stages(const Coef<double>& c,
                                            const float* __restrict__ tabf, const double* y, double h, double* sp,
                                            size_t ss, double* y5) {
   double K[6][10], ys[10];
   for (int i = 0; i < 10; i++) sp[(size_t)i * ss] = y[i];
-  rhs64(c, tabf, y, K[0]);
+  rhs64(c, tabf, y, K[0], SegKeep{sp + (size_t)10 * ss, ss});
 #pragma unroll 1
   for (int s = 1; s < 6; s++) {
     for (int i = 0; i < 10; i++) ys[i] = y[i];
@@ -251,8 +257,9 @@ __device__ __forceinline__ void dp5_stages(const Coef<double>& c,
       if (a != 0.0)
         for (int i = 0; i < 10; i++) ys[i] = fma(a, K[j][i], ys[i]);
     }
-    for (int i = 0; i < 10; i++) sp[(size_t)(10 * s + i) * ss] = ys[i];
-    if (s < 5 || y5) rhs64(c, tabf, ys, K[s]);
+    double* const blk = sp + (size_t)(kF64StageWords * s) * ss;
+    for (int i = 0; i < 10; i++) blk[(size_t)i * ss] = ys[i];
+    rhs64(c, tabf, ys, K[s], SegKeep{blk + (size_t)10 * ss, ss});
   }
   if (!y5) return;
   for (int i = 0; i < 10; i++) y5[i] = y[i];
@@ -263,14 +270,24 @@ __device__ __forceinline__ void dp5_stages(const Coef<double>& c,
   }
 }
 
-// Reverse mode of one step from its stored stage states: on entry lam is the
-// cotangent of y5, on exit the cotangent of y; the coefficient cotangents are
-// added to cb; returns the cotangent of h.  With
+// Reverse mode of one step from its kept stage blocks: on entry lam is the
+// cotangent of y5, on exit the cotangent of y; the (folded) coefficient
+// cotangents are added to cb; returns the cotangent of h.  With
 //   y5 = y + h sum_j b_j k_j,  Y_s = y + h sum_{j<s} a_sj k_j,  k_s = f(Y_s)
 // and kp_j = b_j lam + sum_{s>j} a_sj Yb_s (the cotangent of k_j is h kp_j):
 //   Yb_s = J(Y_s)^T (h kp_s),  yb = lam + sum_s Yb_s,  hb = sum_j k_j . kp_j.
-__device__ double dp5_step_vjp(const Coef<double>& c, const float* __restrict__ tabf,
-                               const double* sp, size_t ss, double h, double* lam, Coef<double>& cb) {
+// While stage s is reversed, the block of the stage reversed next (s - 1, or
+// for s = 0 the block pf, stage 5 of the step reversed after this one, if any)
+// is prefetched: the blocks come from DRAM (the whole segment was recomputed
+// first), and at two warps per scheduler their latency would otherwise stall
+// the FP64 pipe.
+__device__ __forceinline__ void prefetch_block(const double* blk, size_t ss) {
+#pragma unroll 1
+  for (int k = 0; k < kF64StageWords; k++) asm volatile("prefetch.global.L2 [%0];" ::"l"(blk + (size_t)k * ss));
+}
+
+__device__ double dp5_step_vjp(const Coef<double>& c, const double* sp, size_t ss, double h, double* lam,
+                               Coef<double>& cb, const double* pf) {
   double kp[6][10], yb[10];
   for (int j = 0; j < 6; j++)
     for (int i = 0; i < 10; i++) kp[j][i] = c_dp_B[j] * lam[i];
@@ -279,11 +296,14 @@ __device__ double dp5_step_vjp(const Coef<double>& c, const float* __restrict__ 
 #pragma unroll 1
   for (int s = 5; s >= 0; s--) {
     double Ys[10], fb[10], Yb[10], ks[10];
+    const double* const blk = sp + (size_t)(kF64StageWords * s) * ss;
+    const double* const next = s > 0 ? blk - (size_t)kF64StageWords * ss : pf;
+    if (next) prefetch_block(next, ss);
     for (int i = 0; i < 10; i++) {
-      Ys[i] = sp[(size_t)(10 * s + i) * ss];
+      Ys[i] = blk[(size_t)i * ss];
       fb[i] = h * kp[s][i];
     }
-    rhs64_vjp(c, tabf, Ys, fb, Yb, cb, ks);
+    rhs64_vjp(c, blk + (size_t)10 * ss, ss, Ys, fb, Yb, cb, ks);
     for (int i = 0; i < 10; i++) {
       hb = fma(ks[i], kp[s][i], hb);
       yb[i] += Yb[i];
@@ -706,7 +726,7 @@ __device__ void adjoint_one(const AdjArgs& a, const float* __restrict__ tabf,
 
   const int32_t every = a.every;
   const int32_t nseg = (N + every - 1) / every;
-  const size_t step_words = (size_t)kAdjStageWords * ss;
+  const size_t step_words = (size_t)(DS ? kAdjStepWordsDS : kAdjStepWordsF64) * ss;
   if constexpr (DS) {
     const Coef<ds> cd = to_ds(c);
     Coef<ds> cbd;
@@ -772,6 +792,8 @@ __device__ void adjoint_one(const AdjArgs& a, const float* __restrict__ tabf,
 #pragma unroll 1
     for (int32_t n = n1s - 1; n >= n0; n--) {
       const double* sp = sp0 + (size_t)(n - n0) * step_words;
+      // stage 5 of the step reversed next (in this segment), prefetched during this one
+      const double* pf = n > n0 ? sp - step_words + (size_t)(5 * kF64StageWords) * ss : nullptr;
       const double hn = a.h[(size_t)n * a.stride + i];
       if (n == N - 1) {  // landing step: implicit h*
         Coef<double> cA, cB;
@@ -781,16 +803,17 @@ __device__ void adjoint_one(const AdjArgs& a, const float* __restrict__ tabf,
         double lA[10];
         for (int k = 0; k < 10; k++) lA[k] = 0.0;
         lA[0] = 1.0;
-        const double nu = dp5_step_vjp(c, tabf, sp, ss, hn, lA, cA);
-        const double mu = dp5_step_vjp(c, tabf, sp, ss, hn, lam, cB) + tbar;
+        const double nu = dp5_step_vjp(cf, sp, ss, hn, lA, cA, sp + (size_t)(5 * kF64StageWords) * ss);
+        const double mu = dp5_step_vjp(cf, sp, ss, hn, lam, cB, pf) + tbar;
         const double ratio = mu / nu;
         for (int k = 0; k < 10; k++) lam[k] -= ratio * lA[k];
         for (int f = 0; f < 16; f++) cbv[f] += bv[f] - ratio * av[f];
       } else {
-        (void)dp5_step_vjp(c, tabf, sp, ss, hn, lam, cb);
+        (void)dp5_step_vjp(cf, sp, ss, hn, lam, cb, pf);
       }
     }
   }
+  unfold_cotangents(c, cb);  // the FP64 sweep's cotangents are the folded coefficients'
   }
   // Initial state S_i = chi_i m_i^2 S_i-hat, and the mass ratio q = m1/m2 (M = 1).
   const double s1[3] = {in.s1x[i], in.s1y[i], in.s1z[i]}, s2[3] = {in.s2x[i], in.s2y[i], in.s2z[i]};

@@ -6,15 +6,19 @@
 
 namespace pn {
 
-// 8-byte words the reverse sweep keeps per recomputed step: the six stage
-// states (doubles, or pairs of floats in the double-single sweep).
-constexpr int kAdjStageWords = 60;
+// 8-byte words the reverse sweep keeps per recomputed step.  FP64 sweep: per
+// stage, the stage state (10 doubles) and the right-hand side's intermediate
+// values there (41: rhs64's keep indices, the rate among them).  Double-single
+// sweep: the six stage states as pairs of floats.
+constexpr int kF64StageWords = 51;
+constexpr int kAdjStepWordsF64 = 6 * kF64StageWords;
+constexpr int kAdjStepWordsDS = 60;
 
 struct AdjArgs {
   KArgs k;           // inputs, forward outputs, n, queue, log table, controls
   const double* h;   // recorded step sizes (RecArgs layout)
   const double* ck;  // recorded checkpoints
-  double* seg;       // per-lane stage states: every x kAdjStageWords x seg_stride
+  double* seg;       // per-lane stage blocks: every x kAdjStepWords* x seg_stride
   unsigned long long* bins;  // cap + 1 counters for the ordering by step count
   int64_t* order;    // n binary indices, longest record first
   int64_t stride, seg_stride;

@@ -53,6 +53,7 @@ struct pn_batch {
   double* d_seg = nullptr;
   int64_t seg_lanes = 0;
   int32_t seg_every = 0;
+  int32_t seg_words = 0;  // words per step the segment buffer was sized for (FP64 and double-single sweeps differ)
   double* d_adj_out = nullptr;   // forward outputs when the caller passes none
   unsigned long long* d_hist = nullptr;  // analysis scratch: histogram counts (hist_cap bins)
   int64_t hist_cap = 0;
@@ -823,17 +824,20 @@ extern "C" int pn_batch_adjoint(pn_batch* b, int64_t n, const pn_inputs* in, con
   const int64_t full = (n + block - 1) / block, capg = (int64_t)b->num_sms * (per_sm > 0 ? per_sm : 1);
   const int grid = (int)(full < capg ? full : capg);
   const int64_t lanes = (int64_t)grid * block;
-  if (!b->d_seg || b->seg_lanes < lanes || b->seg_every != every) {
+  const int32_t step_words = ds_sweep ? pn::kAdjStepWordsDS : pn::kAdjStepWordsF64;
+  if (!b->d_seg || b->seg_lanes < lanes || b->seg_every != every || b->seg_words < step_words) {
     cudaFree(b->d_seg);
     b->d_seg = nullptr;
     b->seg_lanes = 0;
-    if (cudaMalloc(&b->d_seg, (size_t)lanes * every * pn::kAdjStageWords * sizeof(double)) != cudaSuccess) {
+    b->seg_words = 0;
+    if (cudaMalloc(&b->d_seg, (size_t)lanes * every * step_words * sizeof(double)) != cudaSuccess) {
       cudaGetLastError();
       b->d_seg = nullptr;
       return fail(b, PN_E_NOMEM, "adjoint segment allocation failed");
     }
     b->seg_lanes = lanes;
     b->seg_every = every;
+    b->seg_words = step_words;
   }
   if (!b->d_adj_order || b->adj_bins_cap < (int64_t)b->rec_cap + 1) {
     cudaFree(b->d_adj_order);

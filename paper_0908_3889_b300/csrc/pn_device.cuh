@@ -241,8 +241,22 @@ __device__ __forceinline__ double log_w(double x, const float* __restrict__ tabf
 // ---------------------------------------------------------------------------
 // c holds the coefficients of P with the prefactor K folded in (fold_K), so that
 // omega-dot = omega^2 v^5 P_K with P_K = K P.
+//
+// keep(k, x) receives the intermediate values the adjoint's reverse sweep
+// needs (indices below), in the order they are formed; the integration kernels
+// pass NoKeep, which compiles to nothing.
+enum KeepIdx {
+  KP_R, KP_V, KP_V2, KP_LW, KP_LS1, KP_LS2, KP_S12, KP_P6, KP_P5, KP_P4, KP_P3, KP_P2, KP_P, KP_W2, KP_Q,
+  KP_Q1, KP_Q2, KP_U1, KP_U2 = KP_U1 + 3, KP_PRE = KP_U2 + 3, KP_X1, KP_X2 = KP_X1 + 3, KP_LF = KP_X2 + 3,
+  KP_F, KP_COUNT = KP_F + 10  // KP_F..: the rates f themselves
+};
+struct NoKeep {
+  __device__ __forceinline__ void operator()(int, double) const {}
+};
+template <class Keep = NoKeep>
 __device__ __forceinline__ void rhs64(const Coef<double>& c,
-                                      const float* __restrict__ tabf, const double* y, double* f) {
+                                      const float* __restrict__ tabf, const double* y, double* f,
+                                      Keep keep = Keep()) {
   const double w = y[0];
   const double S1x = y[1], S1y = y[2], S1z = y[3];
   const double S2x = y[4], S2y = y[5], S2z = y[6];
@@ -262,14 +276,15 @@ __device__ __forceinline__ void rhs64(const Coef<double>& c,
   const double so = fma(c.w1, LS1, fma(c.w2, LS2, -c.tail));
   const double c2p = fma(c.ss721, LS1 * LS2, fma(-c.ss247, S12, c.c2));
   const double c3p = fma(c.clog, lw, c.c3l);
-  double P = fma(v, c.c35, c3p);
-  P = fma(v, P, c.c25);
-  P = fma(v, P, c2p);
-  P = fma(v, P, -so);
-  P = fma(v, P, c.c1);
+  const double P6 = fma(v, c.c35, c3p);
+  const double P5 = fma(v, P6, c.c25);
+  const double P4 = fma(v, P5, c2p);
+  const double P3 = fma(v, P4, -so);
+  const double P2 = fma(v, P3, c.c1);
   const double w2 = w * w;
-  P = fma(v2, P, c.K);
-  f[0] = ((w2 * w) * v2) * P;
+  const double P = fma(v2, P2, c.K);
+  const double Q = (w2 * w) * v2;
+  f[0] = Q * P;
 
   // Eq. (4) as Omega_i = pre U_i with U_1 = q1 L + S2, q1 = a1/v - 3 L.S2 (1 <-> 2),
   // and dS_i/dt = pre (U_i x S_i): 29 FP64 operations for both spins.
@@ -278,16 +293,29 @@ __device__ __forceinline__ void rhs64(const Coef<double>& c,
   const double U1x = fma(q1, Lx, S2x), U1y = fma(q1, Ly, S2y), U1z = fma(q1, Lz, S2z);
   const double U2x = fma(q2, Lx, S1x), U2y = fma(q2, Ly, S1y), U2z = fma(q2, Lz, S1z);
   const double pre = half_or_zero(c.prec, w2);
-  const double d1x = pre * fma(U1y, S1z, -U1z * S1y), d1y = pre * fma(U1z, S1x, -U1x * S1z),
-               d1z = pre * fma(U1x, S1y, -U1y * S1x);
-  const double d2x = pre * fma(U2y, S2z, -U2z * S2y), d2y = pre * fma(U2z, S2x, -U2x * S2z),
-               d2z = pre * fma(U2x, S2y, -U2y * S2x);
+  const double X1x = fma(U1y, S1z, -U1z * S1y), X1y = fma(U1z, S1x, -U1x * S1z), X1z = fma(U1x, S1y, -U1y * S1x);
+  const double X2x = fma(U2y, S2z, -U2z * S2y), X2y = fma(U2z, S2x, -U2x * S2z), X2z = fma(U2x, S2y, -U2y * S2x);
+  const double d1x = pre * X1x, d1y = pre * X1y, d1z = pre * X1z;
+  const double d2x = pre * X2x, d2y = pre * X2y, d2z = pre * X2z;
   f[1] = d1x; f[2] = d1y; f[3] = d1z;
   f[4] = d2x; f[5] = d2y; f[6] = d2z;
   const double lf = v * c.nie;
   f[7] = lf * (d1x + d2x);
   f[8] = lf * (d1y + d2y);
   f[9] = lf * (d1z + d2z);
+
+  keep(KP_R, r); keep(KP_V, v); keep(KP_V2, v2); keep(KP_LW, lw);
+  keep(KP_LS1, LS1); keep(KP_LS2, LS2); keep(KP_S12, S12);
+  keep(KP_P6, P6); keep(KP_P5, P5); keep(KP_P4, P4); keep(KP_P3, P3); keep(KP_P2, P2); keep(KP_P, P);
+  keep(KP_W2, w2); keep(KP_Q, Q); keep(KP_Q1, q1); keep(KP_Q2, q2);
+  keep(KP_U1, U1x); keep(KP_U1 + 1, U1y); keep(KP_U1 + 2, U1z);
+  keep(KP_U2, U2x); keep(KP_U2 + 1, U2y); keep(KP_U2 + 2, U2z);
+  keep(KP_PRE, pre);
+  keep(KP_X1, X1x); keep(KP_X1 + 1, X1y); keep(KP_X1 + 2, X1z);
+  keep(KP_X2, X2x); keep(KP_X2 + 1, X2y); keep(KP_X2 + 2, X2z);
+  keep(KP_LF, lf);
+#pragma unroll
+  for (int k = 0; k < 10; k++) keep(KP_F + k, f[k]);
 }
 
 // x^(-1/3) to ~5e-7 relative from the special function unit's approximate
