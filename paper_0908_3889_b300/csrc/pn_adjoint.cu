@@ -270,6 +270,12 @@ __device__ __forceinline__ void dp5_stages(const Coef<double>& c,
   }
 }
 
+// Prefetch of one kept stage block into L2.
+__device__ __forceinline__ void prefetch_block(const double* blk, size_t ss) {
+#pragma unroll 1
+  for (int k = 0; k < kF64StageWords; k++) asm volatile("prefetch.global.L2 [%0];" ::"l"(blk + (size_t)k * ss));
+}
+
 // Reverse mode of one step from its kept stage blocks: on entry lam is the
 // cotangent of y5, on exit the cotangent of y; the (folded) coefficient
 // cotangents are added to cb; returns the cotangent of h.  With
@@ -280,14 +286,13 @@ __device__ __forceinline__ void dp5_stages(const Coef<double>& c,
 // for s = 0 the block pf, stage 5 of the step reversed after this one, if any)
 // is prefetched: the blocks come from DRAM (the whole segment was recomputed
 // first), and at two warps per scheduler their latency would otherwise stall
-// the FP64 pipe.
-__device__ __forceinline__ void prefetch_block(const double* blk, size_t ss) {
-#pragma unroll 1
-  for (int k = 0; k < kF64StageWords; k++) asm volatile("prefetch.global.L2 [%0];" ::"l"(blk + (size_t)k * ss));
-}
+// the FP64 pipe.  One out-of-line copy serves the landing step's two calls and
+// the other steps' one (24.8 against 25.6 ms for the C4 call inlined; the
+// double-single step VJP, whose sweep is bound by instruction fetch, measured
+// the other way).
 
-__device__ double dp5_step_vjp(const Coef<double>& c, const double* sp, size_t ss, double h, double* lam,
-                               Coef<double>& cb, const double* pf) {
+__device__ __noinline__ double dp5_step_vjp(const Coef<double>& c, const double* sp, size_t ss, double h,
+                                            double* lam, Coef<double>& cb, const double* pf) {
   double kp[6][10], yb[10];
   for (int j = 0; j < 6; j++)
     for (int i = 0; i < 10; i++) kp[j][i] = c_dp_B[j] * lam[i];
