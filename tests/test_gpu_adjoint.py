@@ -99,6 +99,37 @@ def test_recording_pass_outputs_equal_plain_integration(pn, precision):
         assert np.array_equal(plain[k], rec[k], equal_nan=True), k
 
 
+def test_precision_switch_on_one_batch(pn):
+    """One batch running the double-single adjoint, then FP64, then double-single again (its per-lane
+    segment buffer holds 60 words per step for the double-single sweep and 306 for the FP64 one, and
+    grows between them): each call's gradients bit-identical to a fresh batch's in that precision."""
+    import torch
+    n = 2000
+    ens = workloads.config("C4", n=n, seed=907)
+    inp = pn.to_device(ens)
+    cot = {"dot_s1s2": torch.ones(n, dtype=torch.float64, device="cuda"),
+           "Lz": torch.full((n,), 0.25, dtype=torch.float64, device="cuda")}
+
+    def grads_of(b):
+        g = {f: torch.empty(n, dtype=torch.float64, device="cuda") for f in pn.native.GRAD_FIELDS}
+        pn.pn_batch_adjoint(b.handle, n, inp, cot, g)
+        torch.cuda.synchronize()
+        return {k: v.cpu().numpy() for k, v in g.items()}
+
+    fresh = {}
+    for prec in (0, 2):
+        with pn.Batch(n, pn.params(precision=prec)) as b:
+            fresh[prec] = grads_of(b)
+    with pn.Batch(n, pn.params(precision=2)) as b:
+        seq = []
+        for prec in (2, 0, 2):
+            b.set_params(pn.params(precision=prec))
+            seq.append((prec, grads_of(b)))
+    for prec, g in seq:
+        for k in g:
+            assert np.array_equal(g[k], fresh[prec][k], equal_nan=True), (prec, k)
+
+
 def test_checkpoint_stride_does_not_change_gradients(pn):
     ens = workloads.config("C2", n=500, seed=77)
     g = cotangents(500, 3)
