@@ -58,6 +58,25 @@ __device__ __forceinline__ void cross_vjp(const double* a, const double* b, cons
 
 static_assert(kF64StageWords == 10 + KP_COUNT, "an FP64 stage block is the state and rhs64's kept values");
 
+// Per-thread workspace of the double-single sweep in shared memory, in per-warp
+// tiles (constant lane stride 32): the six stage rates of a step's recompute,
+// then the six rate cotangents of its reverse step ([6][5] double-single
+// component pairs, 480 bytes).  Indexed by the stage at run time, they would
+// otherwise live in local memory, which the sweep's spills already crowd: the
+// C4 double-single call ran 11.8 -> 10.1 ms with them here.  (The FP64 sweep,
+// bound by its FP64 pipe, keeps its [6][10] arrays local: in shared memory it
+// measured 25.0 against 24.7 ms.)
+constexpr int kAdjWorkBytes = 480;
+
+struct RateWorkDs {
+  ulonglong2* b;  // warp_tile_base<ulonglong2, 30>
+  __device__ __forceinline__ ds2 get(int j, int p) const {
+    const ulonglong2 x = b[(j * 5 + p) * 32];
+    return ds2{x.x, x.y};
+  }
+  __device__ __forceinline__ void put(int j, int p, ds2 v) const { b[(j * 5 + p) * 32] = make_ulonglong2(v.hi, v.lo); }
+};
+
 // Stores rhs64's intermediates to kp[k * ss] (the lane's segment buffer).
 struct SegKeep {
   double* kp;
@@ -539,8 +558,7 @@ __device__ __noinline__ void rhs_ds_vjp(const Coef<ds>& c, const float* __restri
 // FP64 from the double-single increment.  The stage sums run on packed pairs of
 // components (2p, 2p + 1), operation for operation as the scalar sums.
 __device__ __forceinline__ void dp5_stages_ds(const Coef<ds>& c, const float* __restrict__ tabf, const double* y,
-                                              double h, float2* sp, size_t ss, double* y5) {
-  ds2 K[6][5];
+                                              double h, float2* sp, size_t ss, double* y5, RateWorkDs K) {
   ds yd[10], kn[10];
   const ds hd = split64(h);
   const ds2 hd2 = ds2_dup(hd);
@@ -549,13 +567,13 @@ __device__ __forceinline__ void dp5_stages_ds(const Coef<ds>& c, const float* __
     sp[(size_t)i * ss] = make_float2(yd[i].hi, yd[i].lo);
   }
   rhs_ds(c, tabf, yd, kn);
-  for (int p = 0; p < 5; p++) K[0][p] = ds2_of(kn[2 * p], kn[2 * p + 1]);
+  for (int p = 0; p < 5; p++) K.put(0, p, ds2_of(kn[2 * p], kn[2 * p + 1]));
 #pragma unroll 1
   for (int s = 1; s < 6; s++) {
     ds ys[10];
     for (int p = 0; p < 5; p++) {
-      dacc2 acc = dot_first2(c_dp_a_ds[s - 1][0], K[0][p]);
-      for (int j = 1; j < s; j++) acc = dot_add2(acc, c_dp_a_ds[s - 1][j], K[j][p]);
+      dacc2 acc = dot_first2(c_dp_a_ds[s - 1][0], K.get(0, p));
+      for (int j = 1; j < s; j++) acc = dot_add2(acc, c_dp_a_ds[s - 1][j], K.get(j, p));
       const ds2 yy = ds2_add(ds2_of(yd[2 * p], yd[2 * p + 1]), ds2_mul_l(hd2, dot_val2_l(acc)));
       ys[2 * p] = ds2_x(yy);
       ys[2 * p + 1] = ds2_y(yy);
@@ -564,13 +582,13 @@ __device__ __forceinline__ void dp5_stages_ds(const Coef<ds>& c, const float* __
     }
     if (s < 5 || y5) {
       rhs_ds(c, tabf, ys, kn);
-      for (int p = 0; p < 5; p++) K[s][p] = ds2_of(kn[2 * p], kn[2 * p + 1]);
+      for (int p = 0; p < 5; p++) K.put(s, p, ds2_of(kn[2 * p], kn[2 * p + 1]));
     }
   }
   if (!y5) return;
   for (int p = 0; p < 5; p++) {
-    dacc2 acc = dot_first2(c_dp_a_ds[5][0], K[0][p]);
-    for (int j = 2; j < 6; j++) acc = dot_add2(acc, c_dp_a_ds[5][j], K[j][p]);
+    dacc2 acc = dot_first2(c_dp_a_ds[5][0], K.get(0, p));
+    for (int j = 2; j < 6; j++) acc = dot_add2(acc, c_dp_a_ds[5][j], K.get(j, p));
     const ds2 inc = ds2_mul_l(hd2, dot_val2_l(acc));
     const ds i0 = ds2_x(inc), i1 = ds2_y(inc);
     y5[2 * p] = y[2 * p] + (f32_to_f64(i0.hi) + f32_to_f64(i0.lo));
@@ -582,12 +600,12 @@ __device__ __forceinline__ void dp5_stages_ds(const Coef<ds>& c, const float* __
 // recurrences as dp5_step_vjp): lam in/out, cb accumulated, returns h's cotangent.
 // The component sums run on packed pairs of components; hb keeps its scalar order.
 __device__ double dp5_step_vjp_ds(const Coef<ds>& c, const float* __restrict__ tabf, const float2* sp, size_t ss,
-                                  double h, ds* lam, Coef<ds>& cb) {
-  ds2 kp[6][5], yb[5];
+                                  double h, ds* lam, Coef<ds>& cb, RateWorkDs kp) {
+  ds2 yb[5];
   const ds hd = split64(h);
   const ds2 hd2 = ds2_dup(hd);
   for (int j = 0; j < 6; j++)
-    for (int p = 0; p < 5; p++) kp[j][p] = ds2_mul_l(ds2_dup(dconst(c_dp_a_ds[5][j])), ds2_of(lam[2 * p], lam[2 * p + 1]));
+    for (int p = 0; p < 5; p++) kp.put(j, p, ds2_mul_l(ds2_dup(dconst(c_dp_a_ds[5][j])), ds2_of(lam[2 * p], lam[2 * p + 1])));
   for (int p = 0; p < 5; p++) yb[p] = ds2_of(lam[2 * p], lam[2 * p + 1]);
   ds hb = dzero();
 #pragma unroll 1
@@ -598,15 +616,15 @@ __device__ double dp5_step_vjp_ds(const Coef<ds>& c, const float* __restrict__ t
       Ys[i] = ds{t.x, t.y};
     }
     for (int p = 0; p < 5; p++) {
-      const ds2 f = ds2_mul_l(hd2, kp[s][p]);
+      const ds2 f = ds2_mul_l(hd2, kp.get(s, p));
       fb[2 * p] = ds2_x(f);
       fb[2 * p + 1] = ds2_y(f);
     }
     rhs_ds_vjp(c, tabf, Ys, fb, Yb, cb, ks);
     ds2 Yb2[5];
     for (int p = 0; p < 5; p++) {
-      hb = dfma(ks[2 * p], ds2_x(kp[s][p]), hb);
-      hb = dfma(ks[2 * p + 1], ds2_y(kp[s][p]), hb);
+      hb = dfma(ks[2 * p], ds2_x(kp.get(s, p)), hb);
+      hb = dfma(ks[2 * p + 1], ds2_y(kp.get(s, p)), hb);
       Yb2[p] = ds2_of(Yb[2 * p], Yb[2 * p + 1]);
       yb[p] = ds2_add(yb[p], Yb2[p]);
     }
@@ -614,7 +632,7 @@ __device__ double dp5_step_vjp_ds(const Coef<ds>& c, const float* __restrict__ t
       const ds a = dconst(c_dp_a_ds[s - 1][j]);
       if (a.hi != 0.0f) {
         const ds2 a2 = ds2_dup(a);
-        for (int p = 0; p < 5; p++) kp[j][p] = ds2_fma(a2, Yb2[p], kp[j][p]);
+        for (int p = 0; p < 5; p++) kp.put(j, p, ds2_fma(a2, Yb2[p], kp.get(j, p)));
       }
     }
   }
@@ -672,7 +690,7 @@ __device__ __forceinline__ void angle_grads(const double* gv, const double* s, d
 // Gradients of binary i; sp0 is the lane's segment buffer (stride ss).
 template <bool DS>
 __device__ void adjoint_one(const AdjArgs& a, const float* __restrict__ tabf,
-                            int64_t i, double* sp0, size_t ss) {
+                            int64_t i, double* sp0, size_t ss, void* rw) {
   const pn_outputs& o = a.k.out;
   const pn_grads& g = a.grad;
   const int32_t N = o.n_acc[i];
@@ -751,7 +769,7 @@ __device__ void adjoint_one(const AdjArgs& a, const float* __restrict__ tabf,
         double y5[10];
         const bool more = n + 1 < n1s;
         dp5_stages_ds(cd, tabf, y, a.h[(size_t)n * a.stride + i], sf0 + (size_t)(n - n0) * step_words, ss,
-                      more ? y5 : nullptr);
+                      more ? y5 : nullptr, RateWorkDs{static_cast<ulonglong2*>(rw)});
         if (more)
           for (int k = 0; k < 10; k++) y[k] = y5[k];
       }
@@ -767,13 +785,13 @@ __device__ void adjoint_one(const AdjArgs& a, const float* __restrict__ tabf,
           ds lA[10];
           for (int k = 0; k < 10; k++) lA[k] = dzero();
           lA[0] = ds_of(1.0f);
-          const double nu = dp5_step_vjp_ds(cd, tabf, sp, ss, hn, lA, cA);
-          const double mu = dp5_step_vjp_ds(cd, tabf, sp, ss, hn, lamd, cB) + tbar;
+          const double nu = dp5_step_vjp_ds(cd, tabf, sp, ss, hn, lA, cA, RateWorkDs{static_cast<ulonglong2*>(rw)});
+          const double mu = dp5_step_vjp_ds(cd, tabf, sp, ss, hn, lamd, cB, RateWorkDs{static_cast<ulonglong2*>(rw)}) + tbar;
           const ds ratio = split64(mu / nu);
           for (int k = 0; k < 10; k++) lamd[k] = ds_sub(lamd[k], ds_mul(ratio, lA[k]));
           for (int f = 0; f < 16; f++) cbdv[f] = ds_add(cbdv[f], ds_sub(bv[f], ds_mul(ratio, av[f])));
         } else {
-          (void)dp5_step_vjp_ds(cd, tabf, sp, ss, hn, lamd, cbd);
+          (void)dp5_step_vjp_ds(cd, tabf, sp, ss, hn, lamd, cbd, RateWorkDs{static_cast<ulonglong2*>(rw)});
         }
       }
     }
@@ -851,18 +869,20 @@ __device__ void adjoint_one(const AdjArgs& a, const float* __restrict__ tabf,
 template <bool DS>
 __global__ void __launch_bounds__(128) k_adjoint(const AdjArgs a) {
   __shared__ float s_tabf[512];
+  extern __shared__ __align__(16) ulonglong2 s_rate[];  // double-single sweep: kAdjWorkBytes per thread
   for (int q = threadIdx.x; q < 512; q += blockDim.x) s_tabf[q] = a.k.tabf[q];
   __syncthreads();
   const int64_t slot = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const unsigned lane = threadIdx.x & 31u;
   double* sp0 = a.seg + slot;
+  void* const rw = DS ? static_cast<void*>(warp_tile_base<ulonglong2, kAdjWorkBytes / 16>(s_rate)) : nullptr;
   for (;;) {
     unsigned long long base = 0;
     if (lane == 0) base = atomicAdd(a.k.queue, 32ull);
     base = __shfl_sync(0xffffffffu, base, 0);
     if (base >= (unsigned long long)a.k.n) break;
     const int64_t p = (int64_t)base + lane;
-    if (p < a.k.n) adjoint_one<DS>(a, s_tabf, a.order[p], sp0, (size_t)a.seg_stride);
+    if (p < a.k.n) adjoint_one<DS>(a, s_tabf, a.order[p], sp0, (size_t)a.seg_stride, rw);
   }
 }
 
@@ -880,14 +900,21 @@ cudaError_t launch_adjoint(const AdjArgs& a, int block, int grid, cudaStream_t s
   k_order_scatter<<<eg, 256, 0, s>>>(a.k.out, a.k.n, a.cap, a.bins, a.order);
   e = cudaMemsetAsync(a.k.queue, 0, sizeof(unsigned long long), s);
   if (e != cudaSuccess) return e;
-  if (a.ds) k_adjoint<true><<<grid, block, 0, s>>>(a);
-  else k_adjoint<false><<<grid, block, 0, s>>>(a);
+  const size_t smem = a.ds ? (size_t)kAdjWorkBytes * block : 0;
+  e = cudaFuncSetAttribute(a.ds ? (const void*)k_adjoint<true> : (const void*)k_adjoint<false>,
+                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  if (a.ds) k_adjoint<true><<<grid, block, smem, s>>>(a);
+  else k_adjoint<false><<<grid, block, smem, s>>>(a);
   return cudaGetLastError();
 }
 
 cudaError_t adjoint_occupancy(bool ds, int block, int* blocks_per_sm) {
-  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-      blocks_per_sm, ds ? (const void*)k_adjoint<true> : (const void*)k_adjoint<false>, block, 0);
+  const void* f = ds ? (const void*)k_adjoint<true> : (const void*)k_adjoint<false>;
+  const size_t smem = ds ? (size_t)kAdjWorkBytes * block : 0;
+  const cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, f, block, smem);
 }
 
 }  // namespace pn
