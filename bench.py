@@ -301,6 +301,12 @@ def workloads_seed(chunk: int) -> int:
     return 0x0908_3889_5B00 + chunk
 
 
+def bench_config(n: int, world: int) -> dict:
+    """The workload both arms measure (the same dict in the GPU line and the oracle's line)."""
+    return {"workload": WORKLOAD, "n_binaries_per_gpu": n, "precision": "fp64",
+            "l2": "GPU arm: L2 flushed before each step (256 MB write)", "parallelism": f"replicas x{world}"}
+
+
 def reference_arm(args, rank, world):
     """The oracle, as it stands, on the host cores: the base contract's reference arm for this path."""
     if rank != 0:
@@ -324,7 +330,7 @@ def reference_arm(args, rank, world):
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "inspirals/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "sample_per_step": per_step, "device": "host CPU"},
+            "config": bench_config(ens["m1"].shape[0], world),
             "cpu_baseline": {"value": value, "unit": "inspirals/s", "cores": threads, "kind": "oracle",
                              "sample": f"{per_step} binaries of the 1,048,576-binary ensemble per step"},
             "e2e": {"value": value, "unit": "inspirals/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -718,12 +724,10 @@ def main():
         line = {"metric": METRIC, "value": value, "unit": "inspirals/s", "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-                "config": {"workload": WORKLOAD, "n_binaries_per_gpu": n, "precision": "fp64",
-                           "schedule": {1: "plain", 2: "persistent"}.get(tune["schedule"], tune["schedule"]),
+                "config": bench_config(n, world),
+                "launch": {"schedule": {1: "plain", 2: "persistent"}.get(tune["schedule"], tune["schedule"]),
                            "block": tune["block"], "binaries_per_thread": tune["bpt"],
-                           "l2": "flushed before each step (256 MB write)",
-                           "parallelism": f"replicas x{world}", "attempts_per_binary": attempts / n,
-                           "kernel_sha": sha},
+                           "attempts_per_binary": attempts / n, "kernel_sha": sha},
                 "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
                 # per step: the lanes' order (k_len_key, k_len_count, k_scan_above, k_len_scatter) when
                 # on, k_setup, k_integrate_mx, k_dots (the queue reset and the sort's bins are memset nodes)
