@@ -39,7 +39,7 @@ extern "C" {
 #define PN_E_ARG (-1)           /* invalid argument (NULL, n out of range, bad parameter) */
 #define PN_E_CUDA (-2)          /* a CUDA runtime call or kernel launch failed */
 #define PN_E_NOMEM (-3)         /* device or host allocation failed */
-#define PN_E_UNIMPLEMENTED (-4) /* option not supported by this build */
+#define PN_E_UNIMPLEMENTED (-4) /* option the library does not support */
 
 /* ---- per-binary status (outputs.status) ---- */
 #define PN_ST_OK 0
