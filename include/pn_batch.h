@@ -40,6 +40,7 @@ extern "C" {
 #define PN_E_CUDA (-2)          /* a CUDA runtime call or kernel launch failed */
 #define PN_E_NOMEM (-3)         /* device or host allocation failed */
 #define PN_E_UNIMPLEMENTED (-4) /* option the library does not support */
+#define PN_E_CHECK (-5)         /* debug build only: a device bounds check failed (pn_last_error names the site) */
 
 /* ---- per-binary status (outputs.status) ---- */
 #define PN_ST_OK 0
@@ -440,6 +441,20 @@ void pn_batch_destroy(pn_batch *b);
  * logarithm table and waits for the device; make that first call before any
  * stream capture.  Errors: PN_E_ARG, PN_E_CUDA; message via pn_last_error(NULL). */
 int pn_integrate_noalloc(int64_t n, const pn_params *p, const pn_inputs *in, pn_outputs *out, void *cuda_stream);
+
+/* Self-test of the debug build's device bounds checks; the paper has no
+ * counterpart.  The debug build (libpn_b300_debug.so, compiled with -DPN_DEBUG)
+ * stands in for a memory checker: its kernels check the indices that come from
+ * data (the lanes' permutation of the binaries, scatter positions, histogram
+ * bins) and the per-thread shared-memory workspaces against the launch, skip
+ * an access that fails its check and record the site, and each entry point
+ * that launches device work then waits for it and returns PN_E_CHECK if a
+ * check failed (debug builds therefore synchronise and cannot be captured in a
+ * CUDA graph).  This call launches one kernel whose single check fails on
+ * purpose (it guards no memory access) and returns PN_OK when that failure is
+ * reported and cleared, PN_E_CHECK otherwise, PN_E_CUDA on a CUDA error, and
+ * PN_E_UNIMPLEMENTED in the release build.  Message via pn_last_error(NULL). */
+int pn_debug_selftest(void);
 
 /* Message of the last error on b (or, when b is NULL, of the last failed
  * pn_batch_init or pn_integrate_noalloc on this thread); empty string if none.

@@ -9,9 +9,13 @@ import ctypes as C
 import os
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(HERE, "libpn_b300.so")
+RELEASE_LIB_PATH = os.path.join(HERE, "libpn_b300.so")
+# The debug build (device bounds checks that report PN_E_CHECK; every call waits for its work).
+DEBUG_LIB_PATH = os.path.join(HERE, "libpn_b300_debug.so")
+# PN_B300_DEBUG=1 in the environment selects the debug build for the whole process.
+LIB_PATH = DEBUG_LIB_PATH if os.environ.get("PN_B300_DEBUG") == "1" else RELEASE_LIB_PATH
 
-PN_OK, PN_E_ARG, PN_E_CUDA, PN_E_NOMEM, PN_E_UNIMPLEMENTED = 0, -1, -2, -3, -4
+PN_OK, PN_E_ARG, PN_E_CUDA, PN_E_NOMEM, PN_E_UNIMPLEMENTED, PN_E_CHECK = 0, -1, -2, -3, -4, -5
 PN_ST_OK, PN_ST_MAX_STEPS, PN_ST_H_UNDERFLOW, PN_ST_NONFINITE, PN_ST_BAD_INPUT, PN_ST_LAND_MAXIT, PN_ST_RUNNING = range(7)
 PN_FP64, PN_MIXED, PN_MIXED_DS = 0, 1, 2
 PN_STOP_LAND, PN_STOP_FIRST_CROSS = 0, 1
@@ -132,6 +136,7 @@ SIGNATURES = {
     "pn_batch_destroy": (None, [C.c_void_p]),
     "pn_integrate_noalloc": (C.c_int, [C.c_int64, C.POINTER(pn_params), C.POINTER(pn_inputs), C.POINTER(pn_outputs),
                                        C.c_void_p]),
+    "pn_debug_selftest": (C.c_int, []),
     "pn_last_error": (C.c_char_p, [C.c_void_p]),
 }
 

@@ -31,6 +31,7 @@
 
 #include "pn_device.cuh"
 #include "pn_adjoint.h"
+#include "pn_debug.h"
 
 namespace pn {
 namespace {
@@ -672,7 +673,8 @@ __global__ void k_order_scatter(const pn_outputs o, int64_t n, int32_t cap, unsi
   unsigned long long base = 0;
   if ((int)lane == leader) base = atomicAdd(&cursor[key], (unsigned long long)__popc(peers));
   base = __shfl_sync(peers, base, leader);
-  order[base + __popc(peers & ((1u << lane) - 1u))] = i;
+  const unsigned long long pos = base + __popc(peers & ((1u << lane) - 1u));
+  if (PN_DCHECK(pos < (unsigned long long)n, 20)) order[pos] = i;
 }
 
 // Derivatives of a loss with gradient gv (with respect to the components of s)
@@ -864,6 +866,15 @@ __device__ void adjoint_one(const AdjArgs& a, const float* __restrict__ tabf,
   g.q[i] = (m1b - m2b) * (m2 * m2);  // dm1/dq = m2^2 = -dm2/dq
 }
 
+#ifdef PN_DEBUG
+// The launch's dynamic shared memory in bytes (the debug build's checks).
+__device__ __forceinline__ size_t adj_dynamic_smem_bytes() {
+  unsigned int b;
+  asm("mov.u32 %0, %%dynamic_smem_size;" : "=r"(b));
+  return b;
+}
+#endif
+
 // Persistent sweep: each warp claims 32 consecutive entries of the order.
 // blockDim.x must be a multiple of 32.  DS: the double-single sweep.
 template <bool DS>
@@ -874,6 +885,11 @@ __global__ void __launch_bounds__(128) k_adjoint(const AdjArgs a) {
   __syncthreads();
   const int64_t slot = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const unsigned lane = threadIdx.x & 31u;
+  // Debug builds: the segment buffer has a column for every lane of the warp,
+  // and the launch's dynamic shared memory every lane's rate workspace; a
+  // failure returns whole warps (the loop below shuffles across the warp).
+  if (!PN_DCHECK(__all_sync(0xffffffffu, slot < a.seg_stride), 22)) return;
+  if (DS && !PN_DCHECK((size_t)blockDim.x * kAdjWorkBytes <= adj_dynamic_smem_bytes(), 23)) return;
   double* sp0 = a.seg + slot;
   void* const rw = DS ? static_cast<void*>(warp_tile_base<ulonglong2, kAdjWorkBytes / 16>(s_rate)) : nullptr;
   for (;;) {
@@ -882,7 +898,10 @@ __global__ void __launch_bounds__(128) k_adjoint(const AdjArgs a) {
     base = __shfl_sync(0xffffffffu, base, 0);
     if (base >= (unsigned long long)a.k.n) break;
     const int64_t p = (int64_t)base + lane;
-    if (p < a.k.n) adjoint_one<DS>(a, s_tabf, a.order[p], sp0, (size_t)a.seg_stride, rw);
+    if (p < a.k.n) {
+      const int64_t i = a.order[p];
+      if (PN_DCHECK(i >= 0 && i < a.k.n, 21)) adjoint_one<DS>(a, s_tabf, i, sp0, (size_t)a.seg_stride, rw);
+    }
   }
 }
 
@@ -916,5 +935,14 @@ cudaError_t adjoint_occupancy(bool ds, int block, int* blocks_per_sm) {
   if (e != cudaSuccess) return e;
   return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, f, block, smem);
 }
+
+#ifdef PN_DEBUG
+cudaError_t debug_take_adjoint(unsigned int* site) { return debug_take_local(site); }
+#else
+cudaError_t debug_take_adjoint(unsigned int* site) {
+  *site = 0u;
+  return cudaSuccess;
+}
+#endif
 
 }  // namespace pn

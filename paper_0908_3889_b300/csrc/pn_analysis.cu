@@ -11,6 +11,7 @@
 #include <cmath>
 
 #include "pn_analysis.h"
+#include "pn_debug.h"
 
 namespace pn {
 
@@ -61,7 +62,7 @@ __global__ void __launch_bounds__(256) k_histogram(pn_inputs in, pn_outputs out,
       if (ky < 0) continue;
       k = kx * sp.ny + ky;
     }
-    atomicAdd(&h[k], 1u);
+    if (PN_DCHECK(k < nbins, 30)) atomicAdd(&h[k], 1u);
   }
   __syncthreads();
   for (int k = threadIdx.x; k < nbins; k += blockDim.x)
@@ -89,7 +90,8 @@ __global__ void __launch_bounds__(256) k_histogram_global(pn_inputs in, pn_outpu
       }
     }
     const unsigned peers = __match_any_sync(0xffffffffu, k);
-    if (k >= 0 && (int)lane == __ffs(peers) - 1) atomicAdd(&counts[k], (unsigned long long)__popc(peers));
+    if (k >= 0 && (int)lane == __ffs(peers) - 1 && PN_DCHECK(k < sp.nx * sp.ny, 31))
+      atomicAdd(&counts[k], (unsigned long long)__popc(peers));
   }
 }
 
@@ -168,6 +170,15 @@ cudaError_t launch_kde(const pn_inputs& in, const pn_outputs& out, int64_t n, in
   k_kde<<<(unsigned)m, 256, 0, s>>>(in, out, n, q, grid, h, count, density);
   return cudaGetLastError();
 }
+
+#ifdef PN_DEBUG
+cudaError_t debug_take_analysis(unsigned int* site) { return debug_take_local(site); }
+#else
+cudaError_t debug_take_analysis(unsigned int* site) {
+  *site = 0u;
+  return cudaSuccess;
+}
+#endif
 
 }  // namespace pn
 

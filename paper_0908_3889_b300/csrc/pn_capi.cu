@@ -13,6 +13,7 @@
 
 #include "pn_adjoint.h"
 #include "pn_analysis.h"
+#include "pn_debug.h"
 #include "pn_internal.h"
 
 using pn::KArgs;
@@ -95,6 +96,16 @@ static int cuda_fail(pn_batch* b, cudaError_t e, const char* what) {
   snprintf(buf, sizeof(buf), "%s: %s", what, cudaGetErrorString(e));
   return fail(b, PN_E_CUDA, buf);
 }
+
+// Entry points that launch device work.  A debug build (-DPN_DEBUG) compiles
+// their bodies as static functions and exports a wrapper (end of this file)
+// that synchronises the device and reports the debug bounds checks' flags;
+// a release build exports the bodies themselves.
+#ifdef PN_DEBUG
+#define PN_ENTRY(name) static int name##_body
+#else
+#define PN_ENTRY(name) extern "C" int name
+#endif
 
 #define PN_CUDA(b, call)                               \
   do {                                                 \
@@ -482,7 +493,7 @@ int run_integrate(pn_batch* b, int64_t n, const pn_inputs* in, pn_outputs* out, 
 
 }  // namespace
 
-extern "C" int pn_batch_integrate(pn_batch* b, int64_t n, const pn_inputs* in, pn_outputs* out) {
+PN_ENTRY(pn_batch_integrate)(pn_batch* b, int64_t n, const pn_inputs* in, pn_outputs* out) {
   if (!b) return fail(nullptr, PN_E_ARG, "batch is NULL");
   if (n < 0 || n > b->n_max) return fail(b, PN_E_ARG, "n must be in [0, n_max]");
   if (!inputs_ok(in)) return fail(b, PN_E_ARG, "NULL input pointer");
@@ -530,16 +541,16 @@ static int integrate_bounded(pn_batch* b, int64_t n, const pn_inputs* in, pn_out
   return PN_OK;
 }
 
-extern "C" int pn_batch_integrate_budget(pn_batch* b, int64_t n, const pn_inputs* in, pn_outputs* out,
+PN_ENTRY(pn_batch_integrate_budget)(pn_batch* b, int64_t n, const pn_inputs* in, pn_outputs* out,
                                          int32_t budget) {
   return integrate_bounded(b, n, in, out, budget, 0);
 }
 
-extern "C" int pn_batch_resume(pn_batch* b, int64_t n, const pn_inputs* in, pn_outputs* out, int32_t budget) {
+PN_ENTRY(pn_batch_resume)(pn_batch* b, int64_t n, const pn_inputs* in, pn_outputs* out, int32_t budget) {
   return integrate_bounded(b, n, in, out, budget, 1);
 }
 
-extern "C" int pn_batch_integrate_host_async(pn_batch* b, int64_t n, const pn_inputs* hin, pn_outputs* hout) {
+PN_ENTRY(pn_batch_integrate_host_async)(pn_batch* b, int64_t n, const pn_inputs* hin, pn_outputs* hout) {
   if (!b) return fail(nullptr, PN_E_ARG, "batch is NULL");
   if (n < 0 || n > b->n_max) return fail(b, PN_E_ARG, "n must be in [0, n_max]");
   if (!inputs_ok(hin)) return fail(b, PN_E_ARG, "NULL input pointer");
@@ -607,7 +618,7 @@ extern "C" int pn_batch_integrate_host_async(pn_batch* b, int64_t n, const pn_in
   return PN_OK;
 }
 
-extern "C" int pn_batch_host_wait(pn_batch* b) {
+PN_ENTRY(pn_batch_host_wait)(pn_batch* b) {
   if (!b) return fail(nullptr, PN_E_ARG, "batch is NULL");
   if (b->s_in) PN_CUDA(b, cudaStreamSynchronize(b->s_in));
   if (b->s_out) PN_CUDA(b, cudaStreamSynchronize(b->s_out));
@@ -615,13 +626,13 @@ extern "C" int pn_batch_host_wait(pn_batch* b) {
   return PN_OK;
 }
 
-extern "C" int pn_batch_integrate_host(pn_batch* b, int64_t n, const pn_inputs* hin, pn_outputs* hout) {
+PN_ENTRY(pn_batch_integrate_host)(pn_batch* b, int64_t n, const pn_inputs* hin, pn_outputs* hout) {
   const int rc = pn_batch_integrate_host_async(b, n, hin, hout);
   if (rc != PN_OK) return rc;
   return pn_batch_host_wait(b);
 }
 
-extern "C" int pn_batch_eval_rhs(pn_batch* b, int64_t n, const double* m1, const double* m2, const double* y,
+PN_ENTRY(pn_batch_eval_rhs)(pn_batch* b, int64_t n, const double* m1, const double* m2, const double* y,
                                  double* f) {
   if (!b) return fail(nullptr, PN_E_ARG, "batch is NULL");
   if (n < 0) return fail(b, PN_E_ARG, "n must be >= 0");
@@ -632,7 +643,7 @@ extern "C" int pn_batch_eval_rhs(pn_batch* b, int64_t n, const double* m1, const
   return PN_OK;
 }
 
-extern "C" int pn_batch_autotune(pn_batch* b, int64_t n, const pn_inputs* in, pn_outputs* scratch,
+PN_ENTRY(pn_batch_autotune)(pn_batch* b, int64_t n, const pn_inputs* in, pn_outputs* scratch,
                                  pn_tune_result* res) {
   if (!b) return fail(nullptr, PN_E_ARG, "batch is NULL");
   if (n < 1 || n > b->n_max) return fail(b, PN_E_ARG, "n must be in [1, n_max]");
@@ -687,7 +698,7 @@ extern "C" int pn_batch_autotune(pn_batch* b, int64_t n, const pn_inputs* in, pn
   return PN_OK;
 }
 
-extern "C" int pn_batch_adjoint(pn_batch* b, int64_t n, const pn_inputs* in, const pn_cotangents* gbar,
+PN_ENTRY(pn_batch_adjoint)(pn_batch* b, int64_t n, const pn_inputs* in, const pn_cotangents* gbar,
                                 pn_grads* grad, pn_outputs* out) {
   if (!b) return fail(nullptr, PN_E_ARG, "batch is NULL");
   if (n < 0 || n > b->n_max) return fail(b, PN_E_ARG, "n must be in [0, n_max]");
@@ -876,7 +887,7 @@ extern "C" int pn_batch_adjoint(pn_batch* b, int64_t n, const pn_inputs* in, con
   return PN_OK;
 }
 
-extern "C" int pn_batch_sample(pn_batch* b, uint64_t seed, const pn_dist* d, int64_t n, const pn_inputs* in) {
+PN_ENTRY(pn_batch_sample)(pn_batch* b, uint64_t seed, const pn_dist* d, int64_t n, const pn_inputs* in) {
   if (!b) return fail(nullptr, PN_E_ARG, "batch is NULL");
   if (!d) return fail(b, PN_E_ARG, "dist is NULL");
   if (n < 0 || n > b->n_max) return fail(b, PN_E_ARG, "n must be in [0, n_max]");
@@ -891,7 +902,7 @@ extern "C" int pn_batch_sample(pn_batch* b, uint64_t seed, const pn_dist* d, int
   return PN_OK;
 }
 
-extern "C" int pn_batch_masses(pn_batch* b, int64_t n, const double* q, double* m1, double* m2) {
+PN_ENTRY(pn_batch_masses)(pn_batch* b, int64_t n, const double* q, double* m1, double* m2) {
   if (!b) return fail(nullptr, PN_E_ARG, "batch is NULL");
   if (n < 0 || n > b->n_max) return fail(b, PN_E_ARG, "n must be in [0, n_max]");
   if (n > 0 && (!q || !m1 || !m2)) return fail(b, PN_E_ARG, "NULL q, m1 or m2");
@@ -902,7 +913,7 @@ extern "C" int pn_batch_masses(pn_batch* b, int64_t n, const double* q, double* 
 
 static void stats_from_record(pn_batch* b, int64_t n, const double* t, pn_stats* host);
 
-extern "C" int pn_batch_stats(pn_batch* b, int64_t n, const pn_inputs* in, const pn_outputs* out, pn_stats* host) {
+PN_ENTRY(pn_batch_stats)(pn_batch* b, int64_t n, const pn_inputs* in, const pn_outputs* out, pn_stats* host) {
   if (!b) return fail(nullptr, PN_E_ARG, "batch is NULL");
   if (n < 0 || n > b->n_max) return fail(b, PN_E_ARG, "n must be in [0, n_max]");
   if (!inputs_ok(in)) return fail(b, PN_E_ARG, "NULL input pointer");
@@ -917,7 +928,7 @@ extern "C" int pn_batch_stats(pn_batch* b, int64_t n, const pn_inputs* in, const
   return PN_OK;
 }
 
-extern "C" int pn_batch_stats_segments(pn_batch* b, int32_t n_seg, const int64_t* host_offsets, const pn_inputs* in,
+PN_ENTRY(pn_batch_stats_segments)(pn_batch* b, int32_t n_seg, const int64_t* host_offsets, const pn_inputs* in,
                                        const pn_outputs* out, pn_stats* host) {
   if (!b) return fail(nullptr, PN_E_ARG, "batch is NULL");
   if (n_seg < 0 || n_seg > pn::kMaxSegments) return fail(b, PN_E_ARG, "n_seg must be in [0, 65535]");
@@ -990,7 +1001,7 @@ static void stats_from_record(pn_batch* b, int64_t n, const double* t, pn_stats*
   cudaGetLastError();
 }
 
-extern "C" int pn_batch_histogram(pn_batch* b, int64_t n, const pn_inputs* in, const pn_outputs* out,
+PN_ENTRY(pn_batch_histogram)(pn_batch* b, int64_t n, const pn_inputs* in, const pn_outputs* out,
                                   const pn_hist_spec* sp, int64_t* host_counts) {
   if (!b) return fail(nullptr, PN_E_ARG, "batch is NULL");
   if (n < 0 || n > b->n_max) return fail(b, PN_E_ARG, "n must be in [0, n_max]");
@@ -1021,7 +1032,7 @@ extern "C" int pn_batch_histogram(pn_batch* b, int64_t n, const pn_inputs* in, c
   return PN_OK;
 }
 
-extern "C" int pn_batch_kde(pn_batch* b, int64_t n, const pn_inputs* in, const pn_outputs* out, int32_t q,
+PN_ENTRY(pn_batch_kde)(pn_batch* b, int64_t n, const pn_inputs* in, const pn_outputs* out, int32_t q,
                             const double* host_grid, int64_t m, double* host_density, double* host_h) {
   if (!b) return fail(nullptr, PN_E_ARG, "batch is NULL");
   if (n < 0 || n > b->n_max) return fail(b, PN_E_ARG, "n must be in [0, n_max]");
@@ -1063,3 +1074,100 @@ extern "C" int pn_batch_kde(pn_batch* b, int64_t n, const pn_inputs* in, const p
   if (host_h) *host_h = h;
   return PN_OK;
 }
+
+// ---------------------------------------------------------------------------
+// Debug build: every entry point that launches device work waits for it, then
+// reads and clears the device bounds checks' flags (pn_debug.h).  A failed
+// check becomes PN_E_CHECK, with the entry point and the site in the message.
+// ---------------------------------------------------------------------------
+static int debug_after(pn_batch* b, int rc, const char* what) {
+#ifdef PN_DEBUG
+  if (rc != PN_OK) return rc;  // an argument or CUDA error stands as it is
+  cudaError_t e = cudaDeviceSynchronize();
+  unsigned int site[3] = {0u, 0u, 0u};
+  if (e == cudaSuccess) e = pn::debug_take_kernels(&site[0]);
+  if (e == cudaSuccess) e = pn::debug_take_adjoint(&site[1]);
+  if (e == cudaSuccess) e = pn::debug_take_analysis(&site[2]);
+  if (e != cudaSuccess) return cuda_fail(b, e, what);
+  for (unsigned int v : site)
+    if (v) return fail(b, PN_E_CHECK, std::string(what) + ": debug bounds check at site " + std::to_string(v) + " failed");
+#else
+  (void)b;
+  (void)what;
+#endif
+  return rc;
+}
+
+extern "C" int pn_debug_selftest(void) {
+#ifdef PN_DEBUG
+  unsigned int site = 0u;
+  cudaError_t e = pn::launch_debug_selftest(0);
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  if (e == cudaSuccess) e = pn::debug_take_kernels(&site);
+  if (e != cudaSuccess) return cuda_fail(nullptr, e, "pn_debug_selftest");
+  if (site != 99u) return fail(nullptr, PN_E_CHECK, "pn_debug_selftest: the deliberate check failure was not reported");
+  e = pn::debug_take_kernels(&site);
+  if (e != cudaSuccess) return cuda_fail(nullptr, e, "pn_debug_selftest");
+  if (site != 0u) return fail(nullptr, PN_E_CHECK, "pn_debug_selftest: the flag was not cleared");
+  return PN_OK;
+#else
+  (void)debug_after;
+  return fail(nullptr, PN_E_UNIMPLEMENTED, "pn_debug_selftest: release build (no bounds checks)");
+#endif
+}
+
+#ifdef PN_DEBUG
+extern "C" int pn_batch_integrate(pn_batch* b, int64_t n, const pn_inputs* in, pn_outputs* out) {
+  return debug_after(b, pn_batch_integrate_body(b, n, in, out), "pn_batch_integrate");
+}
+extern "C" int pn_batch_integrate_budget(pn_batch* b, int64_t n, const pn_inputs* in, pn_outputs* out,
+                                         int32_t budget) {
+  return debug_after(b, pn_batch_integrate_budget_body(b, n, in, out, budget), "pn_batch_integrate_budget");
+}
+extern "C" int pn_batch_resume(pn_batch* b, int64_t n, const pn_inputs* in, pn_outputs* out, int32_t budget) {
+  return debug_after(b, pn_batch_resume_body(b, n, in, out, budget), "pn_batch_resume");
+}
+extern "C" int pn_batch_integrate_host_async(pn_batch* b, int64_t n, const pn_inputs* hin, pn_outputs* hout) {
+  return debug_after(b, pn_batch_integrate_host_async_body(b, n, hin, hout), "pn_batch_integrate_host_async");
+}
+extern "C" int pn_batch_host_wait(pn_batch* b) {
+  return debug_after(b, pn_batch_host_wait_body(b), "pn_batch_host_wait");
+}
+extern "C" int pn_batch_integrate_host(pn_batch* b, int64_t n, const pn_inputs* hin, pn_outputs* hout) {
+  return debug_after(b, pn_batch_integrate_host_body(b, n, hin, hout), "pn_batch_integrate_host");
+}
+extern "C" int pn_batch_eval_rhs(pn_batch* b, int64_t n, const double* m1, const double* m2, const double* y,
+                                 double* f) {
+  return debug_after(b, pn_batch_eval_rhs_body(b, n, m1, m2, y, f), "pn_batch_eval_rhs");
+}
+extern "C" int pn_batch_autotune(pn_batch* b, int64_t n, const pn_inputs* in, pn_outputs* scratch,
+                                 pn_tune_result* res) {
+  return debug_after(b, pn_batch_autotune_body(b, n, in, scratch, res), "pn_batch_autotune");
+}
+extern "C" int pn_batch_adjoint(pn_batch* b, int64_t n, const pn_inputs* in, const pn_cotangents* gbar,
+                                pn_grads* grad, pn_outputs* out) {
+  return debug_after(b, pn_batch_adjoint_body(b, n, in, gbar, grad, out), "pn_batch_adjoint");
+}
+extern "C" int pn_batch_sample(pn_batch* b, uint64_t seed, const pn_dist* d, int64_t n, const pn_inputs* in) {
+  return debug_after(b, pn_batch_sample_body(b, seed, d, n, in), "pn_batch_sample");
+}
+extern "C" int pn_batch_masses(pn_batch* b, int64_t n, const double* q, double* m1, double* m2) {
+  return debug_after(b, pn_batch_masses_body(b, n, q, m1, m2), "pn_batch_masses");
+}
+extern "C" int pn_batch_stats(pn_batch* b, int64_t n, const pn_inputs* in, const pn_outputs* out, pn_stats* host) {
+  return debug_after(b, pn_batch_stats_body(b, n, in, out, host), "pn_batch_stats");
+}
+extern "C" int pn_batch_stats_segments(pn_batch* b, int32_t n_seg, const int64_t* host_offsets, const pn_inputs* in,
+                                       const pn_outputs* out, pn_stats* host) {
+  return debug_after(b, pn_batch_stats_segments_body(b, n_seg, host_offsets, in, out, host),
+                     "pn_batch_stats_segments");
+}
+extern "C" int pn_batch_histogram(pn_batch* b, int64_t n, const pn_inputs* in, const pn_outputs* out,
+                                  const pn_hist_spec* sp, int64_t* host_counts) {
+  return debug_after(b, pn_batch_histogram_body(b, n, in, out, sp, host_counts), "pn_batch_histogram");
+}
+extern "C" int pn_batch_kde(pn_batch* b, int64_t n, const pn_inputs* in, const pn_outputs* out, int32_t q,
+                            const double* host_grid, int64_t m, double* host_density, double* host_h) {
+  return debug_after(b, pn_batch_kde_body(b, n, in, out, q, host_grid, m, host_density, host_h), "pn_batch_kde");
+}
+#endif

@@ -21,6 +21,7 @@
 
 #include <cmath>
 
+#include "pn_debug.h"
 #include "pn_internal.h"
 
 namespace pn {
@@ -381,12 +382,29 @@ __device__ __forceinline__ bool lane_decide(Lane& L, const Ctl& ctl, double* y5,
 // BOUNDED: the launch may stop binaries at a per-launch attempt budget and may
 // resume saved ones (pn_batch_integrate_budget / pn_batch_resume); the default
 // launches are compiled without that bookkeeping.
+// Per-thread bytes of the stage workspace of the integration kernels.
+template <int PREC>
+__device__ __forceinline__ constexpr size_t work_bytes() {
+  return PREC == 2 ? (size_t)kDsWorkBytes : (PREC == 1 ? (size_t)kF32WorkBytes : (size_t)kF64WorkBytes);
+}
+#ifdef PN_DEBUG
+// The launch's dynamic shared memory in bytes (the debug build's checks).
+__device__ __forceinline__ size_t dynamic_smem_bytes() {
+  unsigned int b;
+  asm("mov.u32 %0, %%dynamic_smem_size;" : "=r"(b));
+  return b;
+}
+#endif
+
 template <int PREC, bool PERSIST, bool RECORD, bool BOUNDED, bool WS>
 __device__ __forceinline__ void integrate_body(const KArgs& a, const double* __restrict__ ws, int64_t stride,
                                                const RecArgs& rec) {
   __shared__ float s_tabf[512];
   extern __shared__ __align__(16) float2 s_dsw[];  // per-thread stage workspace (PREC 0: kF64WorkBytes, 1: kF32WorkBytes, 2: kDsWorkBytes)
   const Tabs tb = load_tabs<PREC>(a.tabf, s_tabf);
+  // Debug builds: the launch's dynamic shared memory holds every lane's stage
+  // workspace (the same outcome for the whole block, after its one barrier).
+  if (!PN_DCHECK((size_t)blockDim.x * work_bytes<PREC>() <= dynamic_smem_bytes(), 1)) return;
 
   const unsigned lane = threadIdx.x & 31u;
   Lane L;
@@ -416,7 +434,7 @@ __device__ __forceinline__ void integrate_body(const KArgs& a, const double* __r
     if (need) {
       if (idx >= 0 && idx < a.n) {
         const int64_t bi = a.order ? a.order[idx] : idx;  // the binary this lane takes
-        have = lane_load<PREC, BOUNDED>(L, a, ws, stride, bi);
+        if (PN_DCHECK(bi >= 0 && bi < a.n, 2)) have = lane_load<PREC, BOUNDED>(L, a, ws, stride, bi);
         if (RECORD && have)
 #pragma unroll
           for (int c = 0; c < 10; c++) rec.ck[(size_t)c * rec.stride + bi] = L.y[c];
@@ -991,7 +1009,8 @@ __global__ void k_len_scatter(const float* key, int64_t n, const unsigned int* r
   unsigned long long base = 0;
   if ((int)lane == leader) base = atomicAdd(&cursor[b], (unsigned long long)__popc(peers));
   base = __shfl_sync(peers, base, leader);
-  order[base + __popc(peers & ((1u << lane) - 1u))] = i;
+  const unsigned long long pos = base + __popc(peers & ((1u << lane) - 1u));
+  if (PN_DCHECK(pos < (unsigned long long)n, 3)) order[pos] = i;
 }
 
 cudaError_t launch_order(const pn_inputs& in, int64_t n, int64_t* order, float* key, unsigned long long* bins,
@@ -1022,5 +1041,26 @@ void fill_log_table(float* tabf) {
     tabf[4 * j + 3] = (float)(ln - (long double)lh);
   }
 }
+
+#ifdef PN_DEBUG
+// The self-test's one check fails on purpose; it guards no memory access.
+__global__ void k_debug_selftest(int v) {
+  if (!PN_DCHECK(v == 0, 99)) return;
+}
+
+cudaError_t debug_take_kernels(unsigned int* site) { return debug_take_local(site); }
+
+cudaError_t launch_debug_selftest(cudaStream_t s) {
+  k_debug_selftest<<<1, 32, 0, s>>>(1);
+  return cudaGetLastError();
+}
+#else
+cudaError_t debug_take_kernels(unsigned int* site) {
+  *site = 0u;
+  return cudaSuccess;
+}
+
+cudaError_t launch_debug_selftest(cudaStream_t) { return cudaErrorNotSupported; }
+#endif
 
 }  // namespace pn

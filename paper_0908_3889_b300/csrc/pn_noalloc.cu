@@ -23,6 +23,7 @@
 #include <mutex>
 #include <string>
 
+#include "pn_debug.h"
 #include "pn_internal.h"
 
 namespace {
@@ -66,8 +67,15 @@ int scratch_for_current_device(unsigned char** out, std::string* why) {
 
 }  // namespace
 
+// A debug build (-DPN_DEBUG) exports a wrapper (below) that waits for the work
+// and reports the device bounds checks' flags (pn_debug.h).
+#ifdef PN_DEBUG
+static int pn_integrate_noalloc_body(int64_t n, const pn_params* p, const pn_inputs* in, pn_outputs* out,
+                                     void* cuda_stream) {
+#else
 extern "C" int pn_integrate_noalloc(int64_t n, const pn_params* p, const pn_inputs* in, pn_outputs* out,
                                     void* cuda_stream) {
+#endif
   std::string why;
   if (!p || !in || !out) return pn::set_thread_error(PN_E_ARG, "NULL params, inputs or outputs");
   if (n < 0) return pn::set_thread_error(PN_E_ARG, "n must be >= 0");
@@ -108,3 +116,19 @@ extern "C" int pn_integrate_noalloc(int64_t n, const pn_params* p, const pn_inpu
   if (e != cudaSuccess) return pn::set_thread_error(PN_E_CUDA, std::string("launch: ") + cudaGetErrorString(e));
   return PN_OK;
 }
+
+#ifdef PN_DEBUG
+extern "C" int pn_integrate_noalloc(int64_t n, const pn_params* p, const pn_inputs* in, pn_outputs* out,
+                                    void* cuda_stream) {
+  const int rc = pn_integrate_noalloc_body(n, p, in, out, cuda_stream);
+  if (rc != PN_OK) return rc;
+  unsigned int site = 0u;
+  cudaError_t e = cudaDeviceSynchronize();
+  if (e == cudaSuccess) e = pn::debug_take_kernels(&site);
+  if (e != cudaSuccess) return pn::set_thread_error(PN_E_CUDA, std::string("pn_integrate_noalloc: ") + cudaGetErrorString(e));
+  if (site)
+    return pn::set_thread_error(PN_E_CHECK, "pn_integrate_noalloc: debug bounds check at site " + std::to_string(site) +
+                                                " failed");
+  return PN_OK;
+}
+#endif

@@ -25,16 +25,20 @@ def declared_functions():
     return sorted(set(re.findall(r"^\s*(?:const\s+)?\w+\s*\*?\s*(pn_\w+)\s*\(", src, flags=re.M)))
 
 
-def test_every_declared_function_is_exported_and_bound(native):
+@pytest.mark.parametrize("build_kind", ["release", "debug"])
+def test_every_declared_function_is_exported_and_bound(native, build_kind):
+    """Both builds (the release library and its bounds-checked debug build) export the whole ABI."""
+    path = native.RELEASE_LIB_PATH if build_kind == "release" else native.DEBUG_LIB_PATH
     names = declared_functions()
     assert len(names) >= 12
-    lib = C.CDLL(native.LIB_PATH)
+    lib = C.CDLL(path)
     for n in names:
         assert hasattr(lib, n), n
         assert n in native.SIGNATURES, n
-    out = subprocess.run(["nm", "-D", "--defined-only", native.LIB_PATH], capture_output=True, text=True).stdout
+    out = subprocess.run(["nm", "-D", "--defined-only", path], capture_output=True, text=True).stdout
     exported = set(re.findall(r" T (pn_\w+)", out))
     assert set(names) <= exported
+    assert lib.pn_abi_version() == native.ABI_VERSION
 
 
 def test_struct_layouts_match_header(native, tmp_path):
@@ -75,8 +79,9 @@ def test_defaults_follow_the_paper(native):
     assert p.order == native.PN_ORDER_LENGTH  # lanes take the binaries sorted by predicted length
 
 
-def test_argument_errors_before_any_cuda_call(native):
-    lib = native.load()
+@pytest.mark.parametrize("build_kind", ["release", "debug"])
+def test_argument_errors_before_any_cuda_call(native, build_kind):
+    lib = native.load(native.RELEASE_LIB_PATH if build_kind == "release" else native.DEBUG_LIB_PATH)
     p = native.pn_params()
     lib.pn_params_default(C.byref(p))
     h = C.c_void_p()
@@ -102,6 +107,13 @@ def test_argument_errors_before_any_cuda_call(native):
     assert lib.pn_batch_timing(None, None, None) == native.PN_E_ARG
     assert lib.pn_batch_stats_segments(None, 1, None, None, None, None) == native.PN_E_ARG
     lib.pn_batch_destroy(None)
+
+
+def test_release_build_has_no_debug_checks(native):
+    """The bounds-check self-test belongs to the debug build; the release library says so without a GPU."""
+    lib = native.load(native.RELEASE_LIB_PATH)
+    assert lib.pn_debug_selftest() == native.PN_E_UNIMPLEMENTED
+    assert b"release build" in lib.pn_last_error(None)
 
 
 def test_product_path_refuses_to_run_without_the_library(tmp_path):
