@@ -48,7 +48,7 @@ FP64_DATASHEET_TFLOPS = 1.25  # nominal dense FP64 of one B300
 # DRAM traffic of the integration kernel per binary from an ncu capture
 # (dram__bytes_read.sum + dram__bytes_write.sum, profiles/); valid only while
 # the kernel sources hash (kernel_sha) to the recorded value.
-PROFILED = {"kernel_sha": "177381136086b4fe", "dram_bytes_per_binary": (55.596e6 + 16.413e6) / 131072}
+PROFILED = {"kernel_sha": "c18364a7dbdf2184", "dram_bytes_per_binary": (55.538e6 + 16.341e6) / 131072}
 
 
 # Executed floating-point thread instructions per attempt of each integration kernel
@@ -57,7 +57,7 @@ PROFILED = {"kernel_sha": "177381136086b4fe", "dram_bytes_per_binary": (55.596e6
 # ncu capture of the 131,072-binary case (profiles/k_integrate_pipes_C1_131072.md): sums of
 # smsp__sass_thread_inst_executed_op_{ffma,fadd,fmul,ffma2,fadd2,fmul2,dfma,dadd,dmul}_pred_on over
 # the launch divided by its attempts.  Valid only while the kernel sources hash to kernel_sha.
-EXECUTED = {"kernel_sha": "177381136086b4fe", "per_attempt": {
+EXECUTED = {"kernel_sha": "c18364a7dbdf2184", "per_attempt": {
     0: {"ffma": 130.84, "fadd": 397.46, "fmul": 93.55, "ffma2": 0.0, "fadd2": 0.0, "fmul2": 0.0,
         "dfma": 505.94, "dadd": 44.96, "dmul": 242.83},
     1: {"ffma": 232.97, "fadd": 29.45, "fmul": 267.58, "ffma2": 190.0, "fadd2": 395.0, "fmul2": 55.0,
