@@ -203,7 +203,7 @@ typedef struct {
 /* Result of pn_batch_autotune. */
 typedef struct {
   int32_t schedule, block, bpt;
-  int32_t n_candidates;
+  int32_t n_candidates; /* shapes timed by this call (0: the shape came from the process's cache) */
   double best_ms;     /* time of the chosen configuration on the tuning prefix */
   int64_t n_tuned;    /* binaries in the tuning prefix */
 } pn_tune_result;
@@ -343,7 +343,13 @@ int pn_batch_eval_rhs(pn_batch *b, int64_t n, const double *m1, const double *m2
  * {64, 128, 256} threads x {1, 2} binaries per thread, persistent schedule x
  * {64, 128, 256} threads -- on the first min(n, 262144) binaries of *in (writing
  * *scratch_out), keep the fastest for later calls with schedule/block/bpt = 0,
- * and report it in *res (may be NULL).  Synchronises.  Errors: PN_E_ARG, PN_E_CUDA. */
+ * and report it in *res (may be NULL).  The process keeps each result in a cache
+ * keyed by the device, the precision, the tuning prefix's size, the parameters
+ * that change the work (tolerances, step control, stop, PN terms, lanes' order)
+ * and a 64-bit fingerprint of the prefix's inputs; a call that finds its key
+ * there times nothing, takes the cached shape and reports n_candidates = 0 with
+ * the cached best_ms (the scratch outputs are then not written).  Synchronises.
+ * Errors: PN_E_ARG, PN_E_CUDA. */
 int pn_batch_autotune(pn_batch *b, int64_t n, const pn_inputs *in, pn_outputs *scratch_out,
                       pn_tune_result *res);
 

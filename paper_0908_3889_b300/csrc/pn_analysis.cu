@@ -171,6 +171,38 @@ cudaError_t launch_kde(const pn_inputs& in, const pn_outputs& out, int64_t n, in
   return cudaGetLastError();
 }
 
+// SplitMix64's finaliser (Steele, Lea & Flood 2014) as a mixing function.
+__device__ __forceinline__ unsigned long long fp_mix(unsigned long long z) {
+  z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ull;
+  z = (z ^ (z >> 27)) * 0x94d049bb133111ebull;
+  return z ^ (z >> 31);
+}
+
+// Sum over binaries i and fields f of mix(bits(f, i) ^ mix(f * n + i)) (mod 2^64): the sum makes the
+// result independent of the reduction's order, the position inside the mix makes it depend on the
+// inputs' order.  One 64-bit atomic add per warp.
+__global__ void __launch_bounds__(256) k_input_fingerprint(pn_inputs in, int64_t n, unsigned long long* acc) {
+  const double* const f[15] = {in.m1, in.m2, in.chi1, in.chi2, in.s1x, in.s1y, in.s1z, in.s2x, in.s2y,
+                               in.s2z, in.lx, in.ly, in.lz, in.omega0, in.omega_f};
+  unsigned long long h = 0ull;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+#pragma unroll
+    for (int k = 0; k < 15; k++) {
+      const unsigned long long bits = (unsigned long long)__double_as_longlong(f[k][i]);
+      h += fp_mix(bits ^ fp_mix((unsigned long long)k * (unsigned long long)n + (unsigned long long)i));
+    }
+  }
+  for (int o = 16; o > 0; o >>= 1) h += __shfl_xor_sync(0xffffffffu, h, o);
+  if ((threadIdx.x & 31u) == 0u) atomicAdd(acc, h);
+}
+
+cudaError_t launch_input_fingerprint(const pn_inputs& in, int64_t n, unsigned long long* acc, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  const int64_t blocks = (n + 255) / 256;
+  k_input_fingerprint<<<(unsigned)(blocks < 1184 ? blocks : 1184), 256, 0, s>>>(in, n, acc);
+  return cudaGetLastError();
+}
+
 #ifdef PN_DEBUG
 cudaError_t debug_take_analysis(unsigned int* site) { return debug_take_local(site); }
 #else

@@ -12,6 +12,10 @@ cudaError_t launch_histogram(const pn_inputs& in, const pn_outputs& out, int64_t
                              unsigned long long* counts, cudaStream_t s);
 cudaError_t launch_moments(const pn_inputs& in, const pn_outputs& out, int64_t n, int q, double* part, int blocks,
                            cudaStream_t s);
+// A 64-bit fingerprint of binaries 0..n-1 of the inputs (all 15 fields, bit patterns and positions),
+// added into *acc (zeroed by the caller): the autotuner's workload key.  Equal inputs give equal
+// fingerprints; a change to any value or to the order changes it except with probability ~2^-64.
+cudaError_t launch_input_fingerprint(const pn_inputs& in, int64_t n, unsigned long long* acc, cudaStream_t s);
 cudaError_t launch_kde(const pn_inputs& in, const pn_outputs& out, int64_t n, int q, const double* grid, int64_t m,
                        double h, double count, double* density, cudaStream_t s);
 

@@ -7,7 +7,10 @@
 
 #include <cmath>
 #include <cstdio>
+#include <array>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <vector>
 #include <string>
 
@@ -643,6 +646,36 @@ PN_ENTRY(pn_batch_eval_rhs)(pn_batch* b, int64_t n, const double* m1, const doub
   return PN_OK;
 }
 
+// The autotuner's process-wide cache: device and precision, tuning prefix, parameters that change
+// the work, and the prefix inputs' fingerprint -> the chosen shape and its time.
+namespace {
+using TuneKey = std::array<uint64_t, 4>;
+struct TuneEntry {
+  int schedule, block, bpt;
+  double best_ms;
+};
+std::mutex g_tune_mu;
+std::map<TuneKey, TuneEntry> g_tune_cache;
+constexpr size_t kTuneCacheMax = 1024;  // entries kept before the cache starts over
+
+uint64_t fnv1a(uint64_t h, const void* p, size_t n) {
+  const unsigned char* c = static_cast<const unsigned char*>(p);
+  for (size_t k = 0; k < n; k++) h = (h ^ c[k]) * 0x100000001b3ull;
+  return h;
+}
+
+// FNV-1a over the parameters that change the integration's work (not the launch shape or the
+// adjoint's checkpoint stride; the precision is a key field of its own).
+uint64_t params_fingerprint(const pn_params& p) {
+  uint64_t h = 0xcbf29ce484222325ull;
+  const double d[8] = {p.rtol, p.atol, p.h0, p.safety, p.fac_min, p.fac_max, p.h_min, p.land_tol};
+  h = fnv1a(h, d, sizeof(d));
+  const int64_t i[7] = {p.max_steps, p.land_max_iter, p.stop_mode, (int64_t)p.term_mask, p.theta_mode,
+                        p.fixed_step, p.order};
+  return fnv1a(h, i, sizeof(i));
+}
+}  // namespace
+
 PN_ENTRY(pn_batch_autotune)(pn_batch* b, int64_t n, const pn_inputs* in, pn_outputs* scratch,
                                  pn_tune_result* res) {
   if (!b) return fail(nullptr, PN_E_ARG, "batch is NULL");
@@ -658,6 +691,38 @@ PN_ENTRY(pn_batch_autotune)(pn_batch* b, int64_t n, const pn_inputs* in, pn_outp
                          {PN_SCHED_PLAIN, 64, 2},  {PN_SCHED_PLAIN, 128, 2}, {PN_SCHED_PLAIN, 256, 2},
                          {PN_SCHED_PERSISTENT, 64, 1}, {PN_SCHED_PERSISTENT, 128, 1},
                          {PN_SCHED_PERSISTENT, 256, 1}};
+  int dev = 0;
+  PN_CUDA(b, cudaGetDevice(&dev));
+  unsigned long long fp = 0ull;
+  unsigned long long* d_fp = reinterpret_cast<unsigned long long*>(b->d_stat_total);  // synchronous scratch
+  PN_CUDA(b, cudaMemsetAsync(d_fp, 0, sizeof(fp), b->stream));
+  {
+    const cudaError_t e = pn::launch_input_fingerprint(*in, nt, d_fp, b->stream);
+    if (e != cudaSuccess) return cuda_fail(b, e, "input fingerprint kernel launch");
+  }
+  PN_CUDA(b, cudaMemcpyAsync(&fp, d_fp, sizeof(fp), cudaMemcpyDeviceToHost, b->stream));
+  PN_CUDA(b, cudaStreamSynchronize(b->stream));
+  const TuneKey key = {((uint64_t)(uint32_t)dev << 32) | (uint32_t)prec, (uint64_t)nt, params_fingerprint(b->p),
+                       (uint64_t)fp};
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    const auto it = g_tune_cache.find(key);
+    if (it != g_tune_cache.end()) {
+      b->tuned[prec].valid = true;
+      b->tuned[prec].schedule = it->second.schedule;
+      b->tuned[prec].block = it->second.block;
+      b->tuned[prec].bpt = it->second.bpt;
+      if (res) {
+        res->schedule = it->second.schedule;
+        res->block = it->second.block;
+        res->bpt = it->second.bpt;
+        res->n_candidates = 0;
+        res->best_ms = it->second.best_ms;
+        res->n_tuned = nt;
+      }
+      return PN_OK;
+    }
+  }
   double best = 1e300;
   int bs = PN_SCHED_PERSISTENT, bb = 128, bp = 1, nc = 0;
   for (const Cand& cd : cands) {
@@ -687,6 +752,11 @@ PN_ENTRY(pn_batch_autotune)(pn_batch* b, int64_t n, const pn_inputs* in, pn_outp
   b->tuned[prec].schedule = bs;
   b->tuned[prec].block = bb;
   b->tuned[prec].bpt = bp;
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    if (g_tune_cache.size() >= kTuneCacheMax) g_tune_cache.clear();
+    g_tune_cache[key] = TuneEntry{bs, bb, bp, best};
+  }
   if (res) {
     res->schedule = bs;
     res->block = bb;

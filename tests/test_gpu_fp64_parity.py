@@ -273,6 +273,31 @@ def test_autotune_choice_gives_same_results(pn):
         assert np.array_equal(ref[k], g[k], equal_nan=True)
 
 
+def test_autotune_cache_keys_on_workload_and_parameters(pn):
+    """The process's tuning cache: the same inputs and parameters on a new batch reuse the shape
+    without timing anything; other inputs (one value changed) or another tolerance tune afresh."""
+    ens = workloads.config("C2", n=30000, seed=77)
+    inp = pn.to_device(ens)
+    with pn.Batch(30000) as b:
+        r1 = b.autotune(inp)
+    assert r1["n_candidates"] == 9
+    with pn.Batch(30000) as b:
+        r2 = b.autotune(inp)
+        assert b.integrate(inp)["status"].eq(0).all()
+    assert r2["n_candidates"] == 0
+    assert (r2["schedule"], r2["block"], r2["bpt"], r2["best_ms"]) == (r1["schedule"], r1["block"], r1["bpt"],
+                                                                        r1["best_ms"])
+    changed = pn.to_device(ens)
+    changed["omega0"][12345] = 0.0101
+    with pn.Batch(30000) as b:
+        assert b.autotune(changed)["n_candidates"] == 9
+    with pn.Batch(30000, pn.params(rtol=4e-7)) as b:
+        assert b.autotune(inp)["n_candidates"] == 9
+    with pn.Batch(30000, pn.params(precision=2)) as b:
+        assert b.autotune(inp)["n_candidates"] == 9
+
+
+
 def test_sampler_bit_exact_against_oracle(pn, orc):
     import torch
     for d, od in (
