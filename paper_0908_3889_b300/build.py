@@ -54,6 +54,9 @@ def build(force: bool = False, verbose: bool = False) -> str:
         jobs.append((PEAK_LIB, _nvcc(PEAK_LIB, [PEAK_SRC], verbose)))
     failed = [out for out, p in jobs if p.wait() != 0]
     if failed:
+        for out, _ in jobs:  # no partial output is left beside the sources
+            if os.path.exists(out + ".tmp"):
+                os.remove(out + ".tmp")
         raise RuntimeError("nvcc failed for " + ", ".join(os.path.basename(f) for f in failed))
     for out, _ in jobs:
         os.replace(out + ".tmp", out)
